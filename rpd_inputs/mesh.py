@@ -1,0 +1,251 @@
+"""Seeded tetrahedral meshes from a jittered lattice (input generator only).
+
+A shape is given by a signed distance function (negative inside).  The
+generator lays a lattice of spacing ``h`` over the shape's bounding box,
+jitters the lattice points, snaps them to the integer grid of spacing
+``2**-grid_bits``, splits every lattice cube into the six Freudenthal (Kuhn)
+tetrahedra that share the cube's main diagonal, keeps the tetrahedra whose
+centroid lies inside the shape, and then removes tetrahedra until the kept
+set is a manifold solid with one face-connected component.
+
+The paper assumes its input is a manifold tetrahedral mesh with one connected
+component and no cavity (Sec. 3.3, Assumption); ``validate`` reports those
+properties so that callers can reject a seed that violates them.
+
+This module computes mesh topology and geometry for building inputs; it holds
+none of the restricted-power-diagram arithmetic.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.sparse import coo_matrix
+from scipy.sparse.csgraph import connected_components
+
+# Cube corner c = x + 2y + 4z; each tet walks 0 -> e_a -> e_a+e_b -> 7.
+KUHN = np.array([(0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7),
+                 (0, 2, 6, 7), (0, 4, 5, 7), (0, 4, 6, 7)], dtype=np.int64)
+# Face f of a tet is the triangle opposite local vertex f.
+FACE_LOCAL = np.array([(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)], dtype=np.int64)
+EDGE_LOCAL = np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)], dtype=np.int64)
+
+MAX_COORD = (1 << 21) - 1   # |integer coordinate| bound assumed by the library
+
+
+def snap(x: np.ndarray, grid_bits: int) -> np.ndarray:
+    """Round to the grid 2**-grid_bits (round half to even, like rint)."""
+    return np.rint(np.asarray(x, dtype=np.float64) * float(1 << grid_bits)).astype(np.int64)
+
+
+def orient_int(q: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    """Exact sign of det[p1-p0, p2-p0, p3-p0] for integer points (local coords)."""
+    p0 = q[tets[:, 0]]
+    a = q[tets[:, 1]] - p0
+    b = q[tets[:, 2]] - p0
+    c = q[tets[:, 3]] - p0
+    if max(np.abs(a).max(initial=0), np.abs(b).max(initial=0), np.abs(c).max(initial=0)) >= (1 << 20):
+        # fall back to Python integers for long edges
+        out = np.empty(len(tets), dtype=np.int64)
+        for n in range(len(tets)):
+            ax, ay, az = (int(v) for v in a[n])
+            bx, by, bz = (int(v) for v in b[n])
+            cx, cy, cz = (int(v) for v in c[n])
+            d = ax * (by * cz - bz * cy) - ay * (bx * cz - bz * cx) + az * (bx * cy - by * cx)
+            out[n] = (d > 0) - (d < 0)
+        return out
+    cr = np.cross(b, c)              # |.| < 2^41
+    d = np.einsum('ij,ij->i', a, cr)  # |.| < 3 * 2^61
+    return np.sign(d)
+
+
+def _face_keys(tets: np.ndarray, nv: int) -> np.ndarray:
+    f = np.sort(tets[:, FACE_LOCAL], axis=2)          # (T,4,3)
+    return (f[..., 0] * nv + f[..., 1]) * nv + f[..., 2]
+
+
+def _edge_keys(tets: np.ndarray, nv: int) -> np.ndarray:
+    e = np.sort(tets[:, EDGE_LOCAL], axis=2)          # (T,6,2)
+    return e[..., 0] * nv + e[..., 1]
+
+
+def face_adjacency(tets: np.ndarray, nv: int):
+    """adj[t,f] = tet across face f (-1 on the boundary); also the face counts."""
+    T = len(tets)
+    keys = _face_keys(tets, nv).ravel()
+    order = np.argsort(keys, kind='stable')
+    sk = keys[order]
+    uniq, start, counts = np.unique(sk, return_index=True, return_counts=True)
+    if counts.size and counts.max() > 2:
+        raise ValueError("a face is shared by more than two tets")
+    adj = -np.ones(4 * T, dtype=np.int64)
+    pairs = start[counts == 2]
+    a = order[pairs]
+    b = order[pairs + 1]
+    adj[a] = b // 4
+    adj[b] = a // 4
+    return adj.reshape(T, 4), counts
+
+
+def _vertex_badness(tets: np.ndarray, nv: int):
+    """Per vertex: number of face-connected tet clusters around it and the Euler
+    characteristic of its link (a disk has 1, a sphere 2)."""
+    T = len(tets)
+    adj, fcounts = face_adjacency(tets, nv)
+    # graph on (tet, local vertex) corners, joined through interior faces
+    t_idx, f_idx = np.nonzero(adj > np.arange(T)[:, None])
+    t2 = adj[t_idx, f_idx]
+    rows, cols = [], []
+    for k in range(3):
+        lv = FACE_LOCAL[f_idx, k]
+        gv = tets[t_idx, lv]
+        # local index of gv inside t2
+        l2 = np.argmax(tets[t2] == gv[:, None], axis=1)
+        rows.append(4 * t_idx + lv)
+        cols.append(4 * t2 + l2)
+    rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    g = coo_matrix((np.ones(len(rows), dtype=np.int8), (rows, cols)), shape=(4 * T, 4 * T))
+    _, lab = connected_components(g, directed=False)
+    corner_v = tets.ravel()
+    pair = np.unique(corner_v.astype(np.int64) * (4 * T) + lab)
+    clusters = np.bincount(pair // (4 * T), minlength=nv)
+    # link Euler characteristic: (#edges at v) - (#faces at v) + (#tets at v)
+    ek = np.unique(_edge_keys(tets, nv).ravel())
+    nedge = np.bincount(ek // nv, minlength=nv) + np.bincount(ek % nv, minlength=nv)
+    fk = np.unique(_face_keys(tets, nv).ravel())
+    fa, fb, fc = fk // (nv * nv), (fk // nv) % nv, fk % nv
+    nface = np.bincount(fa, minlength=nv) + np.bincount(fb, minlength=nv) + np.bincount(fc, minlength=nv)
+    ntet = np.bincount(corner_v, minlength=nv)
+    chi_link = nedge - nface + ntet
+    return clusters, chi_link, lab
+
+
+def _largest_component(tets: np.ndarray, nv: int) -> np.ndarray:
+    T = len(tets)
+    adj, _ = face_adjacency(tets, nv)
+    t_idx, f_idx = np.nonzero(adj >= 0)
+    g = coo_matrix((np.ones(len(t_idx), dtype=np.int8), (t_idx, adj[t_idx, f_idx])), shape=(T, T))
+    n, lab = connected_components(g, directed=False)
+    if n <= 1:
+        return tets
+    big = np.argmax(np.bincount(lab))
+    return tets[lab == big]
+
+
+def make_manifold(tets: np.ndarray, nv: int, max_iter: int = 64) -> np.ndarray:
+    """Remove tets until every vertex star is a single face-connected cluster
+    whose link is a disk or a sphere (which also makes every edge manifold)."""
+    for _ in range(max_iter):
+        tets = _largest_component(tets, nv)
+        clusters, chi_link, lab = _vertex_badness(tets, nv)
+        used = np.bincount(tets.ravel(), minlength=nv) > 0
+        bad = used & ((clusters != 1) | ((chi_link != 1) & (chi_link != 2)))
+        if not bad.any():
+            return tets
+        T = len(tets)
+        drop = np.zeros(T, dtype=bool)
+        corner_v = tets.ravel()
+        corner_bad = bad[corner_v]
+        # keep only the biggest cluster around a multi-cluster vertex
+        cb = np.nonzero(corner_bad)[0]
+        v_of = corner_v[cb]
+        l_of = lab[cb]
+        key = v_of.astype(np.int64) * (4 * T) + l_of
+        uk, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+        best = {}
+        for k_, c_ in zip(uk, cnt):
+            v_ = int(k_ // (4 * T))
+            if v_ not in best or c_ > best[v_][1]:
+                best[v_] = (int(k_), int(c_))
+        for n_, c in enumerate(cb):
+            v_ = int(v_of[n_])
+            single = clusters[v_] == 1
+            if single or key[n_] != best[v_][0]:
+                drop[c // 4] = True
+        tets = tets[~drop]
+    raise RuntimeError("mesh cleaning did not converge")
+
+
+def compact(q: np.ndarray, tets: np.ndarray):
+    used = np.unique(tets.ravel())
+    remap = -np.ones(len(q), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    return q[used], remap[tets]
+
+
+def validate(q: np.ndarray, tets: np.ndarray) -> dict:
+    """Orientation, manifoldness, components, boundary shells and chi of a mesh."""
+    nv, T = len(q), len(tets)
+    info = {}
+    info['orient_min'] = int(orient_int(q, tets).min()) if T else 0
+    adj, fcounts = face_adjacency(tets, nv)
+    clusters, chi_link, _ = _vertex_badness(tets, nv)
+    used = np.bincount(tets.ravel(), minlength=nv) > 0
+    info['manifold'] = bool(np.all(~used | ((clusters == 1) & ((chi_link == 1) | (chi_link == 2)))))
+    t_idx, f_idx = np.nonzero(adj >= 0)
+    g = coo_matrix((np.ones(len(t_idx), dtype=np.int8), (t_idx, adj[t_idx, f_idx])), shape=(T, T))
+    info['components'] = int(connected_components(g, directed=False)[0])
+    # boundary shells: boundary faces joined through shared edges
+    bt, bf = np.nonzero(adj < 0)
+    nb = len(bt)
+    if nb:
+        tri = np.sort(tets[bt[:, None], FACE_LOCAL[bf]], axis=1)
+        ek = np.concatenate([tri[:, 0] * nv + tri[:, 1], tri[:, 0] * nv + tri[:, 2], tri[:, 1] * nv + tri[:, 2]])
+        fid = np.concatenate([np.arange(nb)] * 3)
+        o = np.argsort(ek, kind='stable')
+        ek, fid = ek[o], fid[o]
+        same = ek[1:] == ek[:-1]
+        gb = coo_matrix((np.ones(int(same.sum()), np.int8), (fid[:-1][same], fid[1:][same])), shape=(nb, nb))
+        info['shells'] = int(connected_components(gb, directed=False)[0])
+    else:
+        info['shells'] = 0
+    nE = len(np.unique(_edge_keys(tets, nv)))
+    nF = len(np.unique(_face_keys(tets, nv)))
+    info['V'], info['E'], info['F'], info['T'] = int(used.sum()), int(nE), int(nF), int(T)
+    info['chi'] = int(used.sum()) - nE + nF - T
+    return info
+
+
+def lattice_mesh(sdf, lo, hi, h: float, grid_bits: int, rng: np.random.Generator,
+                 jitter: float = 0.1, inside_by_vertices: bool = False):
+    """Jittered Freudenthal lattice restricted to {sdf < 0}, cleaned to a manifold.
+
+    Returns (integer vertex coordinates int64[nv,3], tets int64[nt,4]) with every
+    tet positively oriented.
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    n = np.maximum(np.ceil((hi - lo) / h).astype(np.int64), 1)
+    nx, ny, nz = (int(v) for v in n)
+    gi, gj, gk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing='ij')
+    idx = np.stack([gi.ravel(), gj.ravel(), gk.ravel()], axis=1)
+    p = lo + h * idx + rng.uniform(-jitter * h, jitter * h, size=idx.shape)
+    q = snap(p, grid_bits)
+    if np.abs(q).max() > MAX_COORD:
+        raise ValueError("coordinates exceed the integer grid bound; lower grid_bits")
+    vid = lambda i, j, k: (i * (ny + 1) + j) * (nz + 1) + k
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing='ij')
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    corners = np.stack([vid(ci + (c & 1), cj + ((c >> 1) & 1), ck + ((c >> 2) & 1)) for c in range(8)], axis=1)
+    scale = 1.0 / float(1 << grid_bits)
+    if inside_by_vertices:
+        sv = sdf(q * scale)
+    keep_t = []
+    chunk = 1 << 18
+    for s in range(0, len(corners), chunk):
+        cc = corners[s:s + chunk]
+        tt = cc[:, KUHN].reshape(-1, 4)
+        if inside_by_vertices:
+            inside = sv[tt].mean(axis=1) < 0
+        else:
+            cen = q[tt].mean(axis=1) * scale
+            inside = sdf(cen) < 0
+        keep_t.append(tt[inside])
+    tets = np.concatenate(keep_t, axis=0)
+    o = orient_int(q, tets)
+    if np.any(o == 0):
+        raise ValueError("flat tetrahedron after jitter")
+    neg = o < 0
+    tets[neg] = tets[neg][:, [0, 1, 3, 2]]
+    tets = make_manifold(tets, len(q))
+    q, tets = compact(q, tets)
+    return q, tets

@@ -1,0 +1,140 @@
+"""Analytic shapes and seeded medial-sphere samplers (input generator only).
+
+Each shape has a signed distance function ``sdf(x)`` (negative inside) used to
+carve the lattice mesh, and a sampler that places spheres near the shape's
+medial axis with radius equal to the distance to the boundary, in the spirit of
+the paper's medial spheres (Sec. 3.1).  Nothing here computes any part of the
+restricted power diagram.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ----------------------------------------------------------------- solid torus
+def torus_sdf(R: float, r: float):
+    def f(x):
+        x = np.asarray(x, dtype=np.float64)
+        q = np.hypot(x[..., 0], x[..., 1]) - R
+        return np.hypot(q, x[..., 2]) - r
+    return f
+
+
+def torus_core_spheres(n: int, rng: np.random.Generator, R: float = 1.0,
+                       sigma: float = 0.02, rmin: float = 0.3, rmax: float = 0.4,
+                       phase: float = 0.1234):
+    """Centres on the core circle plus N(0, sigma^2) jitter, radii U(rmin, rmax)."""
+    th = 2.0 * np.pi * np.arange(n) / n + phase
+    c = np.stack([R * np.cos(th), R * np.sin(th), np.zeros(n)], axis=1)
+    c = c + rng.normal(0.0, sigma, size=c.shape)
+    rad = rng.uniform(rmin, rmax, size=n)
+    return c, rad
+
+
+# ------------------------------------------------- genus-3 block (CAD-like)
+BLOCK_HALF = np.array([2.0, 1.0, 0.5])
+HOLES_X = (-1.2, 0.0, 1.2)
+HOLE_R = 0.3
+
+
+def _block_prims(x):
+    """Distances from interior points to each primitive surface: 6 box planes
+    and 3 z-through cylinders.  Shape (..., 9)."""
+    x = np.asarray(x, dtype=np.float64)
+    d = [BLOCK_HALF[a] - x[..., a] for a in range(3)] + [BLOCK_HALF[a] + x[..., a] for a in range(3)]
+    for cx in HOLES_X:
+        d.append(np.hypot(x[..., 0] - cx, x[..., 1]) - HOLE_R)
+    return np.stack(d, axis=-1)
+
+
+def block_sdf(x):
+    return -_block_prims(x).min(axis=-1)
+
+
+def block_medial_spheres(n: int, rng: np.random.Generator, tol: float = 0.02):
+    """Rejection-sample interior points whose two nearest primitives are within
+    ``tol`` of each other (near-medial); radius = distance to the boundary."""
+    out = []
+    total = 0
+    while total < n:
+        p = rng.uniform(-BLOCK_HALF, BLOCK_HALF, size=(65536, 3))
+        d = _block_prims(p)
+        ok = d.min(axis=-1) > 0
+        ds = np.sort(d, axis=-1)
+        ok &= (ds[:, 1] - ds[:, 0]) < tol
+        p = p[ok]
+        out.append(np.concatenate([p, ds[ok][:, :1]], axis=1))
+        total += len(p)
+    s = np.concatenate(out, axis=0)[:n]
+    return s[:, :3].copy(), s[:, 3].copy()
+
+
+# ------------------------------------------------------ organic ellipsoid blob
+def random_rotations(n: int, rng: np.random.Generator):
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)], -1),
+        np.stack([2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)], -1),
+        np.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], -1),
+    ], axis=1)
+
+
+class EllipsoidBlob:
+    """Union of ellipsoids with axes U(amin, amax), random rotations and centres
+    from a seeded random walk (consecutive centres overlap, so the union is
+    connected).  The signed distance is approximated per ellipsoid by the scaled
+    radial distance (|D^-1 R^T (x-m)| - 1) * min(axes)."""
+
+    def __init__(self, n: int, rng: np.random.Generator, amin: float = 0.1, amax: float = 0.5,
+                 step: float = 0.25):
+        self.axes = rng.uniform(amin, amax, size=(n, 3))
+        self.rot = random_rotations(n, rng)
+        c = np.zeros((n, 3))
+        for k in range(1, n):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            c[k] = c[rng.integers(0, k)] + step * d
+        self.centers = c - c.mean(axis=0)
+        rad = self.axes.max(axis=1)
+        self.lo = (self.centers - rad[:, None]).min(axis=0)
+        self.hi = (self.centers + rad[:, None]).max(axis=0)
+
+    def sdf(self, x, chunk: int = 1 << 16):
+        x = np.asarray(x, dtype=np.float64)
+        shp = x.shape[:-1]
+        x = x.reshape(-1, 3)
+        out = np.empty(len(x))
+        amin = self.axes.min(axis=1)
+        for s in range(0, len(x), chunk):
+            xs = x[s:s + chunk]
+            best = np.full(len(xs), np.inf)
+            for e in range(len(self.axes)):
+                y = (xs - self.centers[e]) @ self.rot[e]
+                g = (np.linalg.norm(y / self.axes[e], axis=1) - 1.0) * amin[e]
+                np.minimum(best, g, out=best)
+            out[s:s + chunk] = best
+        return out.reshape(shp)
+
+    def medial_spheres(self, n: int, rng: np.random.Generator, eps: float = 0.01, gmax: float = 0.6):
+        """Interior points where the finite-difference gradient of the depth is
+        small (ridge of the distance field); radius = depth."""
+        out = []
+        total = 0
+        while total < n:
+            p = rng.uniform(self.lo, self.hi, size=(16384, 3))
+            dep = -self.sdf(p)
+            p, dep = p[dep > 0.02], dep[dep > 0.02]
+            if len(p) == 0:
+                continue
+            g2 = np.zeros(len(p))
+            for a in range(3):
+                e = np.zeros(3)
+                e[a] = eps
+                g2 += ((self.sdf(p + e) - self.sdf(p - e)) / (2 * eps)) ** 2
+            ok = np.sqrt(g2) < gmax
+            out.append(np.concatenate([p[ok], dep[ok][:, None]], axis=1))
+            total += int(ok.sum())
+        s = np.concatenate(out, axis=0)[:n]
+        return s[:, :3].copy(), s[:, 3].copy()
