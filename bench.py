@@ -1,0 +1,282 @@
+"""Benchmark: restricted (tet, sphere) pieces per second, including the
+fractional Euler characteristic, connected components and contractibility of
+every RPC/RPF/RPE/RPV, on one GB300.
+
+One step = rpd_build + rpd_euler/rpd_components/rpd_contractible for every
+element kind (all of the hot path) on the genus-3 block workload (4x2x1 box
+with three through-holes, ~200k tets, 2k near-medial spheres, FP32-filtered
+clipping with FP64/exact fallback, k = 32).  Inputs are seeded and synthetic.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config block_c2|torus_c1|blob_c3] [--precision fp32|fp64]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "restricted (tet,sphere) pieces/sec incl. Euler+components; FP32-filtered vs FP64"
+UNIT = "pieces/s"
+WORKLOADS = {
+    "block_c2": "genus-3 block 4x2x1 with 3 through-holes, ~200k tets, 2000 near-medial spheres, k=32",
+    "torus_c1": "solid torus R=1 r=0.4, ~5k tets, 64 core-circle spheres, k=16",
+    "blob_c3": "union of 200 ellipsoids, ~2M tets, 20000 near-medial spheres, k=32",
+}
+
+
+def make_workload(name):
+    import rpd_inputs
+    return rpd_inputs.CONFIGS[name]()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(w, frac, seed=20240318, nthreads=None):
+    """Time the oracle (as it stands) on a seeded tet sample of the workload."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    n = max(1, int(round(frac * w.nt)))
+    sub = np.sort(rng.choice(w.nt, size=n, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    o = oracle.run(w, subset=sub, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return dict(value=len(o["tet"]) / dt, unit=UNIT, cores=o["nthreads"], kind="oracle",
+                sample=f"{n} of {w.nt} tets ({100 * frac:.1f}%, seed {seed}), all {w.ns} spheres, "
+                       f"brute-force C oracle; {len(o['tet'])} pieces in {dt:.2f} s"), dt
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    frac = args.ref_frac
+    times = []
+    pieces = 0
+    for s in range(args.warmup + args.steps):
+        import oracle
+        rng = np.random.default_rng(1000 + s)
+        sub = np.sort(rng.choice(w.nt, size=max(1, int(frac * w.nt)), replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        o = oracle.run(w, subset=sub)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            pieces += len(o["tet"])
+            cores = o["nthreads"]
+    value = pieces / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOADS[args.config], "precision": "fp64 + exact predicates",
+                       "sample_fraction": frac},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{frac * 100:.1f}% seeded tet sample per step, all spheres"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="block_c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--cpu-frac", type=float, default=0.05)
+    ap.add_argument("--ref-frac", type=float, default=0.01)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    w = make_workload(args.config)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2403_18761_gb300 import rpd_build
+    from paper_2403_18761_gb300.rpd import rpd_stats
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    precision = args.precision or w.precision
+    stream = torch.cuda.Stream(device=dev)
+
+    V = torch.as_tensor(w.verts, dtype=torch.float64, device=dev)
+    T = torch.as_tensor(w.tets, dtype=torch.int32, device=dev)
+    C = torch.as_tensor(w.centers, dtype=torch.float64, device=dev)
+    R = torch.as_tensor(w.radii, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step(Vd, Td, Cd, Rd):
+        ctx = rpd_build(Vd, Td, Cd, Rd, precision=precision, k=w.k, grid_bits=w.grid_bits, stream=stream)
+        outs = []
+        for kind in (1, 2, 3, 4):
+            outs.append(ctx.rpd_euler(kind))
+            outs.append(ctx.rpd_components(kind))
+            outs.append(ctx.rpd_contractible(kind))
+        return ctx, outs
+
+    # ---- device-resident timing
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx, _ = step(V, T, C, R)
+            ctx.rpd_destroy()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms, stage, pieces = [], [], 0
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx, outs = step(V, T, C, R)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                st = ctx.rpd_stats_get()
+                stage.append(st)
+                pieces += st["n_pieces"]
+                ctx.rpd_destroy()
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    t_step = max(ms)
+    if world > 1:
+        tt = torch.tensor([sum(ms)], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    else:
+        total_ms = sum(ms)
+    value = pieces * world / (total_ms / 1e3)
+
+    # ---- end to end through the C-ABI from pinned host buffers
+    hV = torch.as_tensor(w.verts, dtype=torch.float64).pin_memory()
+    hT = torch.as_tensor(w.tets, dtype=torch.int32).pin_memory()
+    hC = torch.as_tensor(w.centers, dtype=torch.float64).pin_memory()
+    hR = torch.as_tensor(w.radii, dtype=torch.float64).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in (hV, hT, hC, hR))
+    e2e_ms, d2h = [], 0
+    with torch.cuda.stream(stream):
+        for s in range(args.warmup + args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Vd, Td, Cd, Rd = (x.to(dev, non_blocking=True) for x in (hV, hT, hC, hR))
+            ctx, outs = step(Vd, Td, Cd, Rd)
+            host = [o.cpu() for pair in outs for o in pair]
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                e2e_ms.append(dt * 1e3)
+                d2h = sum(x.numel() * x.element_size() for x in host)
+                npieces = ctx.rpd_stats_get()["n_pieces"]
+            ctx.rpd_destroy()
+    e2e_value = npieces * len(e2e_ms) / (sum(e2e_ms) / 1e3) * world
+
+    st_mean = {k: float(np.mean([s[k] for s in stage])) for k in ("ms_prep", "ms_knn", "ms_cand", "ms_clip")}
+    st_mean["ms_finalize"] = [float(np.mean([s["ms_finalize"][k] for s in stage])) for k in range(4)]
+    last = stage[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "precision": precision, "tets": int(w.nt),
+                   "spheres": int(w.ns), "pieces_per_step": int(last["n_pieces"]),
+                   "l2": "256 MB buffer written between timed steps", "parallelism": "replicas"},
+        "stages_ms": st_mean,
+        "predicates": {"fast": last["pred_fast"], "fp64": last["pred_fp64"], "exact": last["pred_exact"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "clocks": clocks,
+        "step_ms_max": t_step,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _ = oracle_baseline(w, args.cpu_frac)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

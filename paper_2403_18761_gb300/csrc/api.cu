@@ -1,0 +1,491 @@
+// C-ABI of librpd: context lifecycle, orchestration of the stages, outputs.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "prim.cuh"
+#include "rpd.h"
+
+namespace {
+
+thread_local std::string g_build_error;
+
+// Optional host-side allocation-failure injection for tests:
+// RPD_FAIL_ALLOC_AFTER=N makes the (N+1)-th device allocation of a build fail.
+long long g_alloc_budget = -2;
+
+long long alloc_budget() {
+    if (g_alloc_budget == -2) {
+        const char* e = getenv("RPD_FAIL_ALLOC_AFTER");
+        g_alloc_budget = e ? atoll(e) : -1;
+    }
+    return g_alloc_budget;
+}
+
+}  // namespace
+
+struct rpd_ctx {
+    cudaStream_t stream = nullptr;
+    rpd_options opt{};
+    long long nv = 0, nt = 0, ns = 0, npairs = 0;
+    int key_bits = 1;
+    int K = 16;
+    std::string last_error;
+    std::vector<void*> allocs;
+    long long nalloc = 0;
+    bool failed_alloc = false;
+
+    // device state
+    DevState* st = nullptr;
+    int32_t *Xi = nullptr, *Ci = nullptr;
+    long long* W = nullptr;
+    int32_t* adj = nullptr;
+    uint32_t* own = nullptr;
+    int32_t* tets = nullptr;
+    GridParams* gp = nullptr;
+    int64_t* cell_start = nullptr;
+    int32_t* cell_ids = nullptr;
+    long long* cell_wmax = nullptr;
+    int32_t* knn = nullptr;
+    long long* dplus = nullptr;
+    int32_t *cand_cnt = nullptr, *cand = nullptr, *fb_list = nullptr, *fb_count = nullptr;
+    int64_t* pair_off = nullptr;
+    int32_t *pair_tet = nullptr, *bins = nullptr, *bin_count = nullptr;
+    ClipArgs clip{};
+    unsigned long long* rcount = nullptr;
+    long long nrec[3] = {0, 0, 0};
+    // finalised elements per kind (index kind-1)
+    long long nkeys[4] = {0, 0, 0, 0};
+    bool kind_ok[4] = {true, true, true, true};
+    uint64_t* ukey[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t* uchi[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t* ubeta[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t* piece_off = nullptr;
+    long long npieces = 0;
+    rpd_stats stats{};
+    cudaEvent_t ev[10] = {};
+
+    template <typename T>
+    T* alloc(size_t count) {
+        size_t bytes = sizeof(T) * (count ? count : 1);
+        long long budget = alloc_budget();
+        if (budget >= 0 && nalloc >= budget) {
+            failed_alloc = true;
+            return nullptr;
+        }
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            failed_alloc = true;
+            return nullptr;
+        }
+        nalloc++;
+        allocs.push_back(p);
+        return (T*)p;
+    }
+    void release_all() {
+        for (void* p : allocs) cudaFreeAsync(p, stream);
+        allocs.clear();
+    }
+};
+
+namespace {
+
+rpd_status fail(rpd_ctx* c, rpd_status s, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return s;
+}
+
+const char* dev_reason(int code, const unsigned long long* cnt) {
+    switch (code) {
+        case RPD_E_INVALID: return "invalid input: coordinate or radius off the supported grid range, NaN, index out of range, or a tet that is not positively oriented";
+        case RPD_E_NONMANIFOLD: return "non-manifold mesh: a triangle is shared by more than two tets";
+        case RPD_E_DEGENERATE:
+            return cnt[CNT_LINK_MISSING] ? "inconsistent restricted element across a shared tet face (input not in generic position)"
+                                         : "input not in generic position: an exact predicate is zero (a vertex lies on a radical plane)";
+        case RPD_E_OVERFLOW: return "more than 32 candidate spheres for one tet";
+        case RPD_E_TIMEOUT: return "union-find iteration bound reached";
+        default: return "device error";
+    }
+}
+
+// Read the device status block; returns RPD_OK or the first device error.
+rpd_status check_device(rpd_ctx* c) {
+    DevState h;
+    if (cudaMemcpyAsync(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, RPD_E_CUDA, "CUDA error while reading the device status");
+    }
+    c->stats.pred_fast = (int64_t)h.cnt[CNT_PRED_FAST];
+    c->stats.pred_fp64 = (int64_t)h.cnt[CNT_PRED_FP64];
+    c->stats.pred_exact = (int64_t)h.cnt[CNT_PRED_EXACT];
+    c->stats.cand_fallback = (int64_t)h.cnt[CNT_CAND_FALLBACK];
+    c->stats.whole_tets = (int64_t)h.cnt[CNT_WHOLE];
+    if (h.err != 0) return fail(c, (rpd_status)h.err, dev_reason(h.err, h.cnt));
+    return RPD_OK;
+}
+
+rpd_status cuda_check(rpd_ctx* c, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, RPD_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return RPD_OK;
+}
+
+int bits_for(long long ns) {
+    int b = 1;
+    while ((1ll << b) - 1 <= ns) b++;   // index ns-1 < 2^b - 1 leaves a sentinel
+    return b;
+}
+
+#define TRY(expr)                         \
+    do {                                  \
+        rpd_status _s = (expr);           \
+        if (_s != RPD_OK) return _s;      \
+    } while (0)
+
+#define NEED(ptr)                                                             \
+    do {                                                                      \
+        if (!(ptr)) return fail(c, RPD_E_OOM, "device allocation failed");    \
+    } while (0)
+
+rpd_status run_clip(rpd_ctx* c) {
+    cudaStream_t s = c->stream;
+    ClipArgs& a = c->clip;
+    cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
+    launch_whole_tets(a, c->bins, c->bin_count, c->npairs, s);
+    for (int b = 1; b < RPD_NBINS; b++)
+        launch_clip(a, b, c->opt.precision, c->bins + (long long)b * c->npairs, c->bin_count + b, c->npairs, s);
+    return cuda_check(c, "clip launch");
+}
+
+rpd_status finalize_kind(rpd_ctx* c, int kind, void* tmp, uint64_t* kbuf, uint32_t* pbuf, uint64_t* kout,
+                         uint32_t* pout, int32_t* parent, int64_t* d_nseg) {
+    cudaStream_t s = c->stream;
+    int b = c->key_bits;
+    long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
+    if (kind == 4 && 4 * b > 64) {
+        c->kind_ok[3] = false;
+        cudaMemsetAsync(d_nseg, 0, sizeof(int64_t), s);
+        return RPD_OK;
+    }
+    uint64_t* ukey = c->alloc<uint64_t>(n);
+    int32_t* chi = c->alloc<int32_t>(n);
+    int32_t* beta = c->alloc<int32_t>(n);
+    NEED(ukey && chi && beta);
+    c->ukey[kind - 1] = ukey;
+    c->uchi[kind - 1] = chi;
+    c->ubeta[kind - 1] = beta;
+    const uint64_t* keys;
+    uint64_t sentinel;
+    if (kind == 1) {
+        sentinel = (1ull << b) - 1;
+        launch_components_cells(c->clip, n, parent, pbuf, kbuf, b, sentinel, s);
+        keys = kbuf;
+    } else {
+        sentinel = ~0ull;
+        launch_components_records(c->clip, kind - 2, n, parent, pbuf, s);
+        keys = c->clip.rkey[kind - 2];
+    }
+    radix_sort_pairs(keys, pbuf, kout, pout, n, kind * b, tmp, s);
+    segmented_reduce(kout, pout, n, sentinel, ukey, chi, beta, d_nseg, tmp, s);
+    return cuda_check(c, "finalize launch");
+}
+
+void record(rpd_ctx* c, int k) { cudaEventRecord(c->ev[k], c->stream); }
+
+float elapsed(rpd_ctx* c, int a, int b) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return ms;
+}
+
+rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const double* d_centers,
+                 const double* d_radii) {
+    cudaStream_t s = c->stream;
+    const long long nv = c->nv, nt = c->nt, ns = c->ns;
+    for (int k = 0; k < 10; k++)
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
+    record(c, 0);
+    c->st = c->alloc<DevState>(1);
+    c->Xi = c->alloc<int32_t>(3 * nv);
+    c->Ci = c->alloc<int32_t>(3 * ns);
+    c->W = c->alloc<long long>(ns);
+    c->adj = c->alloc<int32_t>(4 * nt);
+    c->own = c->alloc<uint32_t>(nt);
+    c->tets = c->alloc<int32_t>(4 * nt);
+    NEED(c->st && c->Xi && c->Ci && c->W && c->adj && c->own && c->tets);
+    cudaMemsetAsync(c->st, 0, sizeof(DevState), s);
+    cudaMemcpyAsync(c->tets, d_tets, sizeof(int32_t) * 4 * nt, cudaMemcpyDeviceToDevice, s);
+    // ---- A0
+    launch_snap(d_verts, nv, d_centers, d_radii, ns, c->opt.grid_bits, c->Xi, c->Ci, c->W, c->st, s);
+    size_t tmp_bytes = prep_tmp_bytes(nt, nv);
+    void* tmp = c->alloc<char>(tmp_bytes);
+    NEED(tmp);
+    launch_prep_mesh(c->tets, nt, nv, c->Xi, c->adj, c->own, tmp, c->st, s);
+    TRY(cuda_check(c, "prep launch"));
+    record(c, 1);
+    // ---- A1
+    long long ncap = 2 * ns + 64;
+    c->gp = c->alloc<GridParams>(1);
+    c->cell_start = c->alloc<int64_t>(ncap + 1);
+    c->cell_ids = c->alloc<int32_t>(ns);
+    c->cell_wmax = c->alloc<long long>(ncap);
+    void* gtmp = c->alloc<char>(grid_tmp_bytes(ns, ncap));
+    c->knn = c->alloc<int32_t>(nv * c->K);
+    c->dplus = c->alloc<long long>(nv);
+    NEED(c->gp && c->cell_start && c->cell_ids && c->cell_wmax && gtmp && c->knn && c->dplus);
+    launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, c->cell_wmax, gtmp, s);
+    launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, c->cell_ids, c->cell_wmax, c->K, c->knn, c->dplus, s);
+    TRY(cuda_check(c, "knn launch"));
+    record(c, 2);
+    // ---- A2
+    c->cand_cnt = c->alloc<int32_t>(nt);
+    c->cand = c->alloc<int32_t>(nt * RPD_MAXC);
+    c->fb_list = c->alloc<int32_t>(nt);
+    c->fb_count = c->alloc<int32_t>(1);
+    c->pair_off = c->alloc<int64_t>(nt + 1);
+    void* stmp = c->alloc<char>(scan_tmp_bytes(nt + 1));
+    NEED(c->cand_cnt && c->cand && c->fb_list && c->fb_count && c->pair_off && stmp);
+    launch_candidates(c->tets, nt, nv, c->Xi, c->Ci, c->W, c->knn, c->dplus, c->K, c->gp, c->cell_start,
+                      c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->fb_list, c->fb_count, c->st, s);
+    scan_excl(c->cand_cnt, c->pair_off, nt, stmp, s);
+    TRY(cuda_check(c, "candidate launch"));
+    record(c, 3);
+    long long npairs = 0;
+    cudaMemcpyAsync(&npairs, c->pair_off + nt, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    TRY(check_device(c));   // synchronises: validation errors stop the build here
+    c->npairs = npairs;
+    c->stats.n_pairs = npairs;
+    // ---- A3-A4
+    c->pair_tet = c->alloc<int32_t>(npairs);
+    c->bins = c->alloc<int32_t>(RPD_NBINS * npairs);
+    c->bin_count = c->alloc<int32_t>(RPD_NBINS);
+    c->rcount = c->alloc<unsigned long long>(3);
+    ClipArgs& a = c->clip;
+    a.tets = c->tets;
+    a.Xi = c->Xi;
+    a.Ci = c->Ci;
+    a.W = c->W;
+    a.own = c->own;
+    a.adj = c->adj;
+    a.cand_cnt = c->cand_cnt;
+    a.cand = c->cand;
+    a.pair_off = c->pair_off;
+    a.pair_tet = c->pair_tet;
+    a.unit = ldexp(1.0, -c->opt.grid_bits);
+    a.pflag = c->alloc<uint8_t>(npairs);
+    a.c_val = c->alloc<int32_t>(npairs);
+    a.c_link = c->alloc<uint8_t>(npairs);
+    a.p_vol = c->alloc<double>(npairs);
+    a.p_mom = c->alloc<double>(3 * npairs);
+    a.f_off = c->alloc<int32_t>(npairs);
+    a.f_cnt = c->alloc<uint8_t>(npairs);
+    a.e_off = c->alloc<int32_t>(npairs);
+    a.e_cnt = c->alloc<uint8_t>(npairs);
+    a.rcount = c->rcount;
+    a.key_bits = c->key_bits;
+    a.force_slow = c->opt.debug_checks & 3;
+    a.st = c->st;
+    NEED(c->pair_tet && c->bins && c->bin_count && c->rcount && a.pflag && a.c_val && a.c_link && a.p_vol &&
+         a.p_mom && a.f_off && a.f_cnt && a.e_off && a.e_cnt);
+    launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, npairs, c->bin_count, s);
+    long long cap[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
+    for (int attempt = 0; attempt < 2; attempt++) {
+        for (int k = 0; k < 3; k++) {
+            a.rcap[k] = cap[k];
+            a.rkey[k] = c->alloc<uint64_t>(cap[k]);
+            a.rtet[k] = c->alloc<int32_t>(cap[k]);
+            a.rval[k] = c->alloc<int16_t>(cap[k]);
+            a.rlink[k] = c->alloc<uint8_t>(cap[k]);
+            NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
+        }
+        TRY(run_clip(c));
+        unsigned long long cnt[3];
+        cudaMemcpyAsync(cnt, c->rcount, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+        TRY(check_device(c));
+        bool fits = true;
+        for (int k = 0; k < 3; k++) {
+            c->nrec[k] = (long long)cnt[k];
+            if ((long long)cnt[k] > cap[k]) {
+                fits = false;
+                cap[k] = (long long)cnt[k] + 1024;
+            }
+        }
+        if (fits) break;
+        if (attempt == 1) return fail(c, RPD_E_OVERFLOW, "record buffers overflowed twice");
+    }
+    record(c, 4);
+    for (int k = 0; k < 3; k++) c->stats.n_records[k + 1] = c->nrec[k];
+    // ---- A5-A7 for every kind
+    long long nmax = npairs;
+    for (int k = 0; k < 3; k++) nmax = nmax > c->nrec[k] ? nmax : c->nrec[k];
+    size_t ftmp_bytes = radix_tmp_bytes(nmax);
+    size_t sr = segreduce_tmp_bytes(nmax);
+    if (sr > ftmp_bytes) ftmp_bytes = sr;
+    void* ftmp = c->alloc<char>(ftmp_bytes);
+    uint64_t* kbuf = c->alloc<uint64_t>(nmax);
+    uint32_t* pbuf = c->alloc<uint32_t>(nmax);
+    uint64_t* kout = c->alloc<uint64_t>(nmax);
+    uint32_t* pout = c->alloc<uint32_t>(nmax);
+    int32_t* parent = c->alloc<int32_t>(nmax);
+    int64_t* d_nseg = c->alloc<int64_t>(4);
+    c->piece_off = c->alloc<int64_t>(npairs + 1);
+    void* ptmp = c->alloc<char>(scan_tmp_bytes(npairs + 1));
+    NEED(ftmp && kbuf && pbuf && kout && pout && parent && d_nseg && c->piece_off && ptmp);
+    for (int kind = 1; kind <= 4; kind++) {
+        TRY(finalize_kind(c, kind, ftmp, kbuf, pbuf, kout, pout, parent, d_nseg + kind - 1));
+        record(c, 4 + kind);
+    }
+    scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
+    long long h[5];
+    cudaMemcpyAsync(h, d_nseg, sizeof(long long) * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 4, c->piece_off + npairs, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    TRY(check_device(c));
+    for (int k = 0; k < 4; k++) {
+        c->nkeys[k] = h[k];
+        c->stats.n_keys[k] = h[k];
+    }
+    c->npieces = h[4];
+    c->stats.n_pieces = h[4];
+    c->stats.n_records[0] = h[4];
+    c->stats.ms_prep = elapsed(c, 0, 1);
+    c->stats.ms_knn = elapsed(c, 1, 2);
+    c->stats.ms_cand = elapsed(c, 2, 3);
+    c->stats.ms_clip = elapsed(c, 3, 4);
+    for (int k = 0; k < 4; k++) c->stats.ms_finalize[k] = elapsed(c, 4 + k, 5 + k);
+    return RPD_OK;
+}
+
+rpd_status check_kind(rpd_ctx* c, int kind) {
+    if (!c) return RPD_E_INVALID;
+    if (kind < 1 || kind > 4) return fail(c, RPD_E_INVALID, "kind must be 1..4");
+    if (!c->kind_ok[kind - 1]) return fail(c, RPD_E_OVERFLOW, "RPV keys need at most 2^16 - 1 spheres");
+    return RPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rpd_default_options(rpd_options* opt) {
+    if (!opt) return;
+    opt->precision = RPD_FP32_FILTERED;
+    opt->k = 16;
+    opt->grid_bits = 20;
+    opt->debug_checks = 0;
+}
+
+rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt, const double* d_centers,
+                     const double* d_radii, int64_t ns, const rpd_options* opt, void* cuda_stream, rpd_ctx** out) {
+    if (!out) return RPD_E_INVALID;
+    *out = nullptr;
+    rpd_options o;
+    rpd_default_options(&o);
+    if (opt) o = *opt;
+    auto reject = [](const char* m) {
+        g_build_error = m;
+        return RPD_E_INVALID;
+    };
+    if (nv < 4 || nv >= (1ll << 21)) return reject("nv must be in [4, 2^21)");
+    if (nt < 1 || nt >= (1ll << 31) / RPD_MAXC) return reject("nt must be in [1, 2^26)");
+    if (ns < 1 || ns >= (1ll << 21)) return reject("ns must be in [1, 2^21)");
+    if (!d_verts || !d_tets || !d_centers || !d_radii) return reject("null input pointer");
+    if (o.k < 1 || o.k > RPD_MAXK) return reject("k must be in [1, 32]");
+    if (o.grid_bits < 0 || o.grid_bits > 40) return reject("grid_bits must be in [0, 40]");
+    if (o.precision != RPD_FP64 && o.precision != RPD_FP32_FILTERED) return reject("unknown precision");
+    rpd_ctx* c = new rpd_ctx();
+    c->stream = (cudaStream_t)cuda_stream;
+    c->opt = o;
+    c->nv = nv;
+    c->nt = nt;
+    c->ns = ns;
+    c->K = o.k;
+    c->key_bits = bits_for(ns);
+    rpd_status st = build(c, d_verts, d_tets, d_centers, d_radii);
+    if (st != RPD_OK) {
+        g_build_error = c->last_error.empty() ? "build failed" : c->last_error;
+        rpd_destroy(c);
+        return st;
+    }
+    g_build_error.clear();
+    *out = c;
+    return RPD_OK;
+}
+
+static rpd_status copy_common(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, const int32_t* src, int32_t* d_dst,
+                              int64_t cap, int64_t* n) {
+    TRY(check_kind(ctx, kind));
+    long long m = ctx->nkeys[kind - 1];
+    if (n) *n = m;
+    if (!d_keys && !d_dst) return RPD_OK;
+    if (cap < m) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of elements");
+    if (d_keys) launch_unpack_keys(ctx->ukey[kind - 1], m, kind, ctx->key_bits, d_keys, ctx->stream);
+    if (d_dst && m) cudaMemcpyAsync(d_dst, src, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, ctx->stream);
+    return cuda_check(ctx, "output copy");
+}
+
+rpd_status rpd_euler(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, int32_t* d_chi, int64_t cap, int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    TRY(check_kind(ctx, kind));
+    return copy_common(ctx, kind, d_keys, ctx->uchi[kind - 1], d_chi, cap, n);
+}
+
+rpd_status rpd_components(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, int32_t* d_beta0, int64_t cap, int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    TRY(check_kind(ctx, kind));
+    return copy_common(ctx, kind, d_keys, ctx->ubeta[kind - 1], d_beta0, cap, n);
+}
+
+rpd_status rpd_contractible(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, uint8_t* d_flag, int64_t cap, int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    TRY(check_kind(ctx, kind));
+    long long m = ctx->nkeys[kind - 1];
+    if (n) *n = m;
+    if (!d_keys && !d_flag) return RPD_OK;
+    if (cap < m) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of elements");
+    if (d_keys) launch_unpack_keys(ctx->ukey[kind - 1], m, kind, ctx->key_bits, d_keys, ctx->stream);
+    if (d_flag) launch_flags(ctx->uchi[kind - 1], ctx->ubeta[kind - 1], m, d_flag, ctx->stream);
+    return cuda_check(ctx, "flag launch");
+}
+
+rpd_status rpd_pieces(rpd_ctx* ctx, int32_t* d_tet, int32_t* d_sphere, double* d_vol, double* d_moment3, int64_t cap,
+                      int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n) *n = ctx->npieces;
+    if (!d_tet && !d_sphere && !d_vol && !d_moment3) return RPD_OK;
+    if (cap < ctx->npieces) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of pieces");
+    launch_compact_pieces(ctx->clip, ctx->npairs, ctx->piece_off, d_tet, d_sphere, d_vol, d_moment3, ctx->stream);
+    return cuda_check(ctx, "piece launch");
+}
+
+rpd_status rpd_stats_get(const rpd_ctx* ctx, rpd_stats* out) {
+    if (!ctx || !out) return RPD_E_INVALID;
+    *out = ctx->stats;
+    return RPD_OK;
+}
+
+const char* rpd_last_error(const rpd_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+const char* rpd_build_error(void) { return g_build_error.c_str(); }
+
+void rpd_destroy(rpd_ctx* ctx) {
+    if (!ctx) return;
+    ctx->release_all();
+    cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < 10; k++)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

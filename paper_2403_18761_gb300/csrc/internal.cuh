@@ -1,0 +1,103 @@
+// Host-side launchers shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+// Uniform grid over the sphere centres (computed on the device).
+struct GridParams {
+    int3 org;          // minimum corner (grid units)
+    int cell;          // cell edge length (grid units)
+    int3 dim;          // cells per axis
+    int ncell;
+    long long wmax;    // largest power weight r^2
+};
+
+// ---------------------------------------------------------------- prep.cu
+// Round coordinates and radii to the integer grid and validate them.
+void launch_snap(const double* d_verts, long long nv, const double* d_centers, const double* d_radii,
+                 long long ns, int grid_bits, int32_t* Xi, int32_t* Ci, long long* W, DevState* st,
+                 cudaStream_t s);
+// Validate tets (index range, exact orientation) and build adjacency and the
+// 14 ownership bits per tet (4 corners, 6 edges, 4 faces: bit set when this
+// tet is the lowest-numbered tet containing that mesh face).
+size_t prep_tmp_bytes(long long nt, long long nv);
+void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, int32_t* adj,
+                      uint32_t* own, void* tmp, DevState* st, cudaStream_t s);
+
+// ----------------------------------------------------------------- knn.cu
+size_t grid_tmp_bytes(long long ns, long long ncap);
+void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
+                        int64_t* cell_start, int32_t* cell_ids, long long* cell_wmax, void* tmp,
+                        cudaStream_t s);
+// k nearest spheres in power distance of every mesh vertex, with D+ = a lower
+// bound of the power distance of every sphere left out of the list.
+void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
+                const int64_t* cell_start, const int32_t* cell_ids, const long long* cell_wmax, int K,
+                int32_t* knn, long long* dplus, cudaStream_t s);
+// Candidate spheres of every tet (superset of the spheres whose cell meets
+// the tet with positive volume), sorted by index, at most RPD_MAXC.
+void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
+                       const long long* W, const int32_t* knn, const long long* dplus, int K,
+                       const GridParams* gp, const int64_t* cell_start, const int32_t* cell_ids,
+                       const long long* cell_wmax, int32_t* cand_cnt, int32_t* cand, int32_t* fb_list,
+                       int32_t* fb_count, DevState* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- clip.cu
+struct ClipArgs {
+    const int32_t* tets;
+    const int32_t* Xi;
+    const int32_t* Ci;
+    const long long* W;
+    const uint32_t* own;
+    const int32_t* adj;
+    const int32_t* cand_cnt;   // [nt]
+    const int32_t* cand;       // [nt * RPD_MAXC]
+    const int64_t* pair_off;   // [nt + 1]
+    const int32_t* pair_tet;   // [npairs]
+    double unit;               // 2^-grid_bits
+    // per-pair outputs
+    uint8_t* pflag;            // 1 = nonempty piece
+    int32_t* c_val;            // RPC contribution (owner rule)
+    uint8_t* c_link;           // tet faces crossed by the piece
+    double* p_vol;
+    double* p_mom;             // [npairs * 3]
+    int32_t* f_off;
+    uint8_t* f_cnt;
+    int32_t* e_off;
+    uint8_t* e_cnt;
+    // element records (RPF, RPE, RPV): key, tet, contribution, links
+    uint64_t* rkey[3];
+    int32_t* rtet[3];
+    int16_t* rval[3];
+    uint8_t* rlink[3];
+    long long rcap[3];
+    unsigned long long* rcount;   // [3] device counters
+    int key_bits;                 // bits per sphere index in packed keys
+    int force_slow;               // 0; 1 = skip the first-stage filter; 2 = exact only
+    DevState* st;
+};
+// Split pairs into bins by the candidate count of their tet; bins[b] lists
+// pair ids, bin_count[b] their number.  Bin 0: one candidate (whole tet).
+#define RPD_NBINS 5
+void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet,
+                      int32_t* bins, long long bin_stride, int32_t* bin_count, cudaStream_t s);
+// Pair counts are read on the device (d_n); n/nmax only size the grid.
+void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s);
+void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,
+                 cudaStream_t s);
+
+// ---------------------------------------------------------------- topo.cu
+// Union-find over the nodes of one element kind; writes root flags into the
+// payload (bit 16) next to the 16-bit contribution.
+void launch_components_cells(const ClipArgs& a, long long npairs, int32_t* parent, uint32_t* pay,
+                             uint64_t* keys, int key_bits, uint64_t sentinel, cudaStream_t s);
+void launch_components_records(const ClipArgs& a, int which, long long nrec, int32_t* parent, uint32_t* pay,
+                               cudaStream_t s);
+void launch_unpack_keys(const uint64_t* ukey, long long n, int kind, int key_bits, int32_t* out,
+                        cudaStream_t s);
+void launch_flags(const int32_t* chi, const int32_t* beta0, long long n, uint8_t* flag, cudaStream_t s);
+void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet,
+                           int32_t* d_sphere, double* d_vol, double* d_mom, cudaStream_t s);

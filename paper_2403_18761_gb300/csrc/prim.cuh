@@ -1,0 +1,30 @@
+// Device primitives: exclusive scan, LSD radix sort, segmented warp-shuffle
+// reduction, stream compaction.  All stream-ordered, no host synchronisation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Exclusive scan: out[i] = sum_{j<i} in[j] for i < n, and out[n] = total.
+// tmp must hold scan_tmp_bytes(n).
+size_t scan_tmp_bytes(long long n);
+void scan_excl(const int32_t* in, int64_t* out, long long n, void* tmp, cudaStream_t s);
+void scan_excl(const uint8_t* in, int64_t* out, long long n, void* tmp, cudaStream_t s);
+void scan_excl(const int64_t* in, int64_t* out, long long n, void* tmp, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys, 8 bits per pass.  Reads keys_in/vals_in, writes keys_out/vals_out.
+// tmp must hold radix_tmp_bytes(n).
+size_t radix_tmp_bytes(long long n);
+void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                      uint32_t* vals_out, long long n, int bits, void* tmp, cudaStream_t s);
+
+// Segmented reduction over runs of equal keys (keys sorted; runs whose key is
+// `sentinel` are ignored).  Payload bits 0..15 hold a signed contribution to
+// chi, bit 16 a root flag counted into beta0.  Outputs (capacity n) receive
+// one entry per run in key order; *d_nseg (device) the number of runs.
+// tmp must hold segreduce_tmp_bytes(n).
+size_t segreduce_tmp_bytes(long long n);
+void segmented_reduce(const uint64_t* keys, const uint32_t* pay, long long n, uint64_t sentinel,
+                      uint64_t* ukey, int32_t* chi, int32_t* beta0, int64_t* d_nseg, void* tmp,
+                      cudaStream_t s);

@@ -1,0 +1,233 @@
+"""Python binding of librpd (argument marshalling only).
+
+Every function mirrors a C entry point of ``include/rpd.h``.  PyTorch provides
+device memory and the CUDA stream; all computation runs in the library's CUDA
+kernels.  There is no CPU fallback: without the compiled library or a CUDA
+device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librpd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rpd.h")
+
+RPD_OK, RPD_E_INVALID, RPD_E_NONMANIFOLD, RPD_E_DEGENERATE = 0, 1, 2, 3
+RPD_E_OOM, RPD_E_CUDA, RPD_E_OVERFLOW, RPD_E_TIMEOUT = 4, 5, 6, 7
+STATUS_NAMES = {0: "RPD_OK", 1: "RPD_E_INVALID", 2: "RPD_E_NONMANIFOLD", 3: "RPD_E_DEGENERATE",
+                4: "RPD_E_OOM", 5: "RPD_E_CUDA", 6: "RPD_E_OVERFLOW", 7: "RPD_E_TIMEOUT"}
+RPD_CELL, RPD_FACE, RPD_EDGE, RPD_VERTEX = 1, 2, 3, 4
+RPD_FP64, RPD_FP32_FILTERED = 0, 1
+PRECISION = {"fp64": RPD_FP64, "fp32": RPD_FP32_FILTERED}
+
+
+class RpdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rpd_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("k", ctypes.c_int32), ("grid_bits", ctypes.c_int32),
+                ("debug_checks", ctypes.c_int32)]
+
+
+class rpd_stats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_records", ctypes.c_int64 * 4),
+                ("n_keys", ctypes.c_int64 * 4), ("pred_fast", ctypes.c_int64), ("pred_fp64", ctypes.c_int64),
+                ("pred_exact", ctypes.c_int64), ("cand_fallback", ctypes.c_int64), ("whole_tets", ctypes.c_int64),
+                ("ms_prep", ctypes.c_float), ("ms_knn", ctypes.c_float), ("ms_cand", ctypes.c_float),
+                ("ms_clip", ctypes.c_float), ("ms_finalize", ctypes.c_float * 4)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librpd.so (building it in-tree first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        from .build import build
+        build()
+    lib = ctypes.CDLL(path)
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    lib.rpd_default_options.argtypes = [ctypes.POINTER(rpd_options)]
+    lib.rpd_default_options.restype = None
+    lib.rpd_build.argtypes = [P, I64, P, I64, P, P, I64, ctypes.POINTER(rpd_options), P, ctypes.POINTER(P)]
+    lib.rpd_build.restype = ctypes.c_int
+    for name in ("rpd_euler", "rpd_components", "rpd_contractible"):
+        f = getattr(lib, name)
+        f.argtypes = [P, ctypes.c_int, P, P, I64, ctypes.POINTER(I64)]
+        f.restype = ctypes.c_int
+    lib.rpd_pieces.argtypes = [P, P, P, P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_pieces.restype = ctypes.c_int
+    lib.rpd_stats_get.argtypes = [P, ctypes.POINTER(rpd_stats)]
+    lib.rpd_stats_get.restype = ctypes.c_int
+    lib.rpd_last_error.argtypes = [P]
+    lib.rpd_last_error.restype = ctypes.c_char_p
+    lib.rpd_build_error.argtypes = []
+    lib.rpd_build_error.restype = ctypes.c_char_p
+    lib.rpd_destroy.argtypes = [P]
+    lib.rpd_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def header_symbols(path: str = HEADER):
+    """Entry points declared in include/rpd.h."""
+    with open(path) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(rpd_[a-z_]+)\s*\(", text)))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev_f64(x, dev):
+    t = torch.as_tensor(x, dtype=torch.float64)
+    return t.to(dev).contiguous()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream), stream
+
+
+class Ctx:
+    """Owns one rpd_ctx (device workspace and results)."""
+
+    def __init__(self, handle, stream, device, keep):
+        self.handle = handle
+        self.stream = stream
+        self.device = device
+        self._keep = keep
+
+    def _check(self, st):
+        if st != RPD_OK:
+            raise RpdError(st, load().rpd_last_error(self.handle).decode())
+
+    def _query(self, fn, kind):
+        n = ctypes.c_int64(0)
+        self._check(fn(self.handle, kind, None, None, 0, ctypes.byref(n)))
+        return n.value
+
+    def rpd_euler(self, kind):
+        """(keys int32[n, kind], chi int32[n]) on the device."""
+        lib = load()
+        n = self._query(lib.rpd_euler, kind)
+        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
+        chi = torch.empty(n, dtype=torch.int32, device=self.device)
+        out = ctypes.c_int64(0)
+        self._check(lib.rpd_euler(self.handle, kind, _ptr(keys), _ptr(chi), n, ctypes.byref(out)))
+        return keys, chi
+
+    def rpd_components(self, kind):
+        lib = load()
+        n = self._query(lib.rpd_components, kind)
+        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
+        beta = torch.empty(n, dtype=torch.int32, device=self.device)
+        out = ctypes.c_int64(0)
+        self._check(lib.rpd_components(self.handle, kind, _ptr(keys), _ptr(beta), n, ctypes.byref(out)))
+        return keys, beta
+
+    def rpd_contractible(self, kind):
+        lib = load()
+        n = self._query(lib.rpd_contractible, kind)
+        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
+        flag = torch.empty(n, dtype=torch.uint8, device=self.device)
+        out = ctypes.c_int64(0)
+        self._check(lib.rpd_contractible(self.handle, kind, _ptr(keys), _ptr(flag), n, ctypes.byref(out)))
+        return keys, flag
+
+    def rpd_pieces(self):
+        """(tet int32[n], sphere int32[n], vol f64[n], moment f64[n,3]) sorted by (tet, sphere)."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        self._check(lib.rpd_pieces(self.handle, None, None, None, None, 0, ctypes.byref(n)))
+        m = n.value
+        t = torch.empty(m, dtype=torch.int32, device=self.device)
+        s = torch.empty(m, dtype=torch.int32, device=self.device)
+        v = torch.empty(m, dtype=torch.float64, device=self.device)
+        mo = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+        self._check(lib.rpd_pieces(self.handle, _ptr(t), _ptr(s), _ptr(v), _ptr(mo), m, ctypes.byref(n)))
+        return t, s, v, mo
+
+    def rpd_stats_get(self):
+        st = rpd_stats()
+        self._check(load().rpd_stats_get(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def rpd_destroy(self):
+        if self.handle:
+            load().rpd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.rpd_destroy()
+        except Exception:
+            pass
+
+
+def rpd_build(verts, tets, centers, radii, precision="fp32", k=16, grid_bits=20, stream=None,
+              device="cuda", debug=0) -> Ctx:
+    """Build the restricted power diagram.  Inputs may be host arrays or device
+    tensors; host inputs are copied to the device first."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("librpd needs a CUDA device; there is no CPU fallback")
+    lib = load()
+    dev = torch.device(device)
+    V = _dev_f64(verts, dev)
+    T = torch.as_tensor(tets, dtype=torch.int32).to(dev).contiguous()
+    C = _dev_f64(centers, dev)
+    R = _dev_f64(radii, dev)
+    opt = rpd_options()
+    lib.rpd_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    opt.k = int(k)
+    opt.grid_bits = int(grid_bits)
+    opt.debug_checks = int(debug)
+    sh, stream = _stream_handle(stream)
+    out = ctypes.c_void_p()
+    st = lib.rpd_build(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(C), _ptr(R), R.shape[0],
+                       ctypes.byref(opt), sh, ctypes.byref(out))
+    if st != RPD_OK:
+        raise RpdError(st, lib.rpd_build_error().decode())
+    return Ctx(out, stream, dev, (V, T, C, R))
+
+
+def build_workload(w, precision=None, k=None, stream=None, debug=0):
+    """rpd_build on a seeded workload (see rpd_inputs)."""
+    return rpd_build(w.verts, w.tets, w.centers, w.radii, precision=precision or w.precision,
+                     k=k or w.k, grid_bits=w.grid_bits, stream=stream, debug=debug)
+
+
+def collect(ctx):
+    """All outputs of a context as host numpy arrays (for tests and checks)."""
+    out = {"kinds": {}}
+    for kind in (RPD_CELL, RPD_FACE, RPD_EDGE, RPD_VERTEX):
+        keys, chi = ctx.rpd_euler(kind)
+        _, beta = ctx.rpd_components(kind)
+        _, flag = ctx.rpd_contractible(kind)
+        out["kinds"][kind] = dict(keys=keys.cpu().numpy(), chi=chi.cpu().numpy(), beta0=beta.cpu().numpy(),
+                                  flag=flag.cpu().numpy())
+    t, s, v, m = ctx.rpd_pieces()
+    out.update(tet=t.cpu().numpy(), sphere=s.cpu().numpy(), vol=v.cpu().numpy(), moment=m.cpu().numpy())
+    out["stats"] = ctx.rpd_stats_get()
+    return out
