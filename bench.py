@@ -156,9 +156,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="block_c2", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--k", type=int, default=None, help="power neighbours kept per mesh vertex")
     ap.add_argument("--cpu-frac", type=float, default=0.05)
     ap.add_argument("--ref-frac", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -186,8 +188,10 @@ def main():
     R = torch.as_tensor(w.radii, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
+    kk = args.k or w.k
+
     def step(Vd, Td, Cd, Rd):
-        ctx = rpd_build(Vd, Td, Cd, Rd, precision=precision, k=w.k, grid_bits=w.grid_bits, stream=stream)
+        ctx = rpd_build(Vd, Td, Cd, Rd, precision=precision, k=kk, grid_bits=w.grid_bits, stream=stream)
         outs = []
         for kind in (1, 2, 3, 4):
             outs.append(ctx.rpd_euler(kind))
@@ -234,9 +238,9 @@ def main():
     hC = torch.as_tensor(w.centers, dtype=torch.float64).pin_memory()
     hR = torch.as_tensor(w.radii, dtype=torch.float64).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in (hV, hT, hC, hR))
-    e2e_ms, d2h = [], 0
+    e2e_ms, d2h, npieces = [], 0, 0
     with torch.cuda.stream(stream):
-        for s in range(args.warmup + args.steps):
+        for s in range(0 if args.no_e2e else args.warmup + args.steps):
             flush.fill_(1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -250,7 +254,7 @@ def main():
                 d2h = sum(x.numel() * x.element_size() for x in host)
                 npieces = ctx.rpd_stats_get()["n_pieces"]
             ctx.rpd_destroy()
-    e2e_value = npieces * len(e2e_ms) / (sum(e2e_ms) / 1e3) * world
+    e2e_value = npieces * len(e2e_ms) / (sum(e2e_ms) / 1e3) * world if e2e_ms else None
 
     st_mean = {k: float(np.mean([s[k] for s in stage])) for k in ("ms_prep", "ms_knn", "ms_cand", "ms_clip")}
     st_mean["ms_finalize"] = [float(np.mean([s["ms_finalize"][k] for s in stage])) for k in range(4)]
@@ -265,6 +269,8 @@ def main():
                    "l2": "256 MB buffer written between timed steps", "parallelism": "replicas"},
         "stages_ms": st_mean,
         "predicates": {"fast": last["pred_fast"], "fp64": last["pred_fp64"], "exact": last["pred_exact"]},
+        "pairs": {"total": last["n_pairs"], "by_bin": last["bin_pairs"], "cut_by_bin": last["bin_cut"],
+                  "whole_tets": last["whole_tets"], "cand_fallback": last["cand_fallback"], "k": kk},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
         "step_ms_max": t_step,

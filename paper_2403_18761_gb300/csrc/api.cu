@@ -55,8 +55,14 @@ struct rpd_ctx {
     int32_t* knn = nullptr;
     long long* dplus = nullptr;
     int32_t *cand_cnt = nullptr, *cand = nullptr, *fb_list = nullptr, *fb_count = nullptr;
+    uint8_t* cand_ord = nullptr;
     int64_t* pair_off = nullptr;
-    int32_t *pair_tet = nullptr, *bins = nullptr, *bin_count = nullptr;
+    int32_t *pair_tet = nullptr, *bins = nullptr, *bin_count = nullptr, *bin_fill = nullptr;
+    long long hbin[RPD_NBINS] = {};
+    int32_t* qpair[RPD_NBINS] = {};
+    uint8_t* qnv[RPD_NBINS] = {};
+    uint32_t* qtrip[RPD_NBINS] = {};
+    unsigned long long* qcount = nullptr;
     ClipArgs clip{};
     unsigned long long* rcount = nullptr;
     long long nrec[3] = {0, 0, 0};
@@ -157,11 +163,24 @@ int bits_for(long long ns) {
 
 rpd_status run_clip(rpd_ctx* c) {
     cudaStream_t s = c->stream;
-    ClipArgs& a = c->clip;
+    ClipArgs a = c->clip;
     cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
-    launch_whole_tets(a, c->bins, c->bin_count, c->npairs, s);
-    for (int b = 1; b < RPD_NBINS; b++)
-        launch_clip(a, b, c->opt.precision, c->bins + (long long)b * c->npairs, c->bin_count + b, c->npairs, s);
+    cudaMemsetAsync(c->qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
+    long long off = 0;
+    for (int b = 0; b < RPD_NBINS; b++) {
+        long long n = c->hbin[b];
+        if (b == 0) {
+            launch_whole_tets(a, c->bins, c->bin_count, n, s);
+        } else if (n > 0) {
+            a.qpair = c->qpair[b];
+            a.qnv = c->qnv[b];
+            a.qtrip = c->qtrip[b];
+            a.qcap = n;
+            a.qcount = c->qcount + b;
+            launch_clip(a, b, c->opt.precision, c->bins + off, c->bin_count + b, n, s);
+        }
+        off += n;
+    }
     return cuda_check(c, "clip launch");
 }
 
@@ -251,26 +270,43 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     // ---- A2
     c->cand_cnt = c->alloc<int32_t>(nt);
     c->cand = c->alloc<int32_t>(nt * RPD_MAXC);
+    c->cand_ord = c->alloc<uint8_t>(nt * RPD_MAXC);
     c->fb_list = c->alloc<int32_t>(nt);
     c->fb_count = c->alloc<int32_t>(1);
     c->pair_off = c->alloc<int64_t>(nt + 1);
     void* stmp = c->alloc<char>(scan_tmp_bytes(nt + 1));
-    NEED(c->cand_cnt && c->cand && c->fb_list && c->fb_count && c->pair_off && stmp);
+    c->bin_count = c->alloc<int32_t>(RPD_NBINS);
+    c->bin_fill = c->alloc<int32_t>(RPD_NBINS);
+    NEED(c->cand_cnt && c->cand && c->cand_ord && c->fb_list && c->fb_count && c->pair_off && stmp && c->bin_count &&
+         c->bin_fill);
     launch_candidates(c->tets, nt, nv, c->Xi, c->Ci, c->W, c->knn, c->dplus, c->K, c->gp, c->cell_start,
-                      c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->fb_list, c->fb_count, c->st, s);
+                      c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->cand_ord, c->fb_list, c->fb_count, c->st, s);
     scan_excl(c->cand_cnt, c->pair_off, nt, stmp, s);
+    launch_bin_count(c->cand_cnt, nt, c->bin_count, s);
     TRY(cuda_check(c, "candidate launch"));
     record(c, 3);
     long long npairs = 0;
+    int32_t hb[RPD_NBINS];
     cudaMemcpyAsync(&npairs, c->pair_off + nt, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hb, c->bin_count, sizeof(hb), cudaMemcpyDeviceToHost, s);
     TRY(check_device(c));   // synchronises: validation errors stop the build here
     c->npairs = npairs;
     c->stats.n_pairs = npairs;
+    for (int b = 0; b < RPD_NBINS; b++) c->stats.bin_pairs[b] = c->hbin[b] = hb[b];
     // ---- A3-A4
     c->pair_tet = c->alloc<int32_t>(npairs);
-    c->bins = c->alloc<int32_t>(RPD_NBINS * npairs);
-    c->bin_count = c->alloc<int32_t>(RPD_NBINS);
+    c->bins = c->alloc<int32_t>(npairs);
     c->rcount = c->alloc<unsigned long long>(3);
+    c->qcount = c->alloc<unsigned long long>(RPD_NBINS);
+    NEED(c->pair_tet && c->bins && c->rcount && c->qcount);
+    for (int b = 1; b < RPD_NBINS; b++) {
+        long long n = c->hbin[b];
+        if (n == 0) continue;
+        c->qpair[b] = c->alloc<int32_t>(n);
+        c->qnv[b] = c->alloc<uint8_t>(n);
+        c->qtrip[b] = c->alloc<uint32_t>(2 * n * clip_vmax(b));
+        NEED(c->qpair[b] && c->qnv[b] && c->qtrip[b]);
+    }
     ClipArgs& a = c->clip;
     a.tets = c->tets;
     a.Xi = c->Xi;
@@ -280,6 +316,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     a.adj = c->adj;
     a.cand_cnt = c->cand_cnt;
     a.cand = c->cand;
+    a.cand_ord = c->cand_ord;
     a.pair_off = c->pair_off;
     a.pair_tet = c->pair_tet;
     a.unit = ldexp(1.0, -c->opt.grid_bits);
@@ -296,9 +333,8 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     a.key_bits = c->key_bits;
     a.force_slow = c->opt.debug_checks & 3;
     a.st = c->st;
-    NEED(c->pair_tet && c->bins && c->bin_count && c->rcount && a.pflag && a.c_val && a.c_link && a.p_vol &&
-         a.p_mom && a.f_off && a.f_cnt && a.e_off && a.e_cnt);
-    launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, npairs, c->bin_count, s);
+    NEED(a.pflag && a.c_val && a.c_link && a.p_vol && a.p_mom && a.f_off && a.f_cnt && a.e_off && a.e_cnt);
+    launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, s);
     long long cap[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
     for (int attempt = 0; attempt < 2; attempt++) {
         for (int k = 0; k < 3; k++) {
@@ -310,9 +346,11 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
         }
         TRY(run_clip(c));
-        unsigned long long cnt[3];
+        unsigned long long cnt[3], qc[RPD_NBINS];
         cudaMemcpyAsync(cnt, c->rcount, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(qc, c->qcount, sizeof(qc), cudaMemcpyDeviceToHost, s);
         TRY(check_device(c));
+        for (int b = 0; b < RPD_NBINS; b++) c->stats.bin_cut[b] = (int64_t)qc[b];
         bool fits = true;
         for (int k = 0; k < 3; k++) {
             c->nrec[k] = (long long)cnt[k];

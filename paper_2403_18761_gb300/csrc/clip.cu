@@ -4,11 +4,12 @@
 // Sec. 5.2 (Tet-Cell): the piece P(t,i) = t cap cell_i is computed for every
 // (tet, sphere) pair independently, by clipping t with the radical
 // half-spaces {pd(x,i) <= pd(x,k)} of the other spheres k (Sec. 4.1.2).  The
-// polytope is stored as in the paper's data structure (Sec. 5.2): a list of
-// planes and one integer triplet of plane ids per vertex.  Triplets are kept
-// consistently oriented so that they form a closed triangulated surface in
-// the dual; a clip removes the triangles of the outside vertices and closes
-// the hole with a fan of new triplets on the new plane.
+// polytope is stored as in the paper's data structure (Sec. 5.2): one integer
+// triplet of plane ids per vertex.  Triplets are oriented so that they form a
+// closed triangulated surface in the dual; each vertex also keeps its three
+// dual neighbours (the vertex across each of its edges), so a clip removes
+// the outside vertices, walks the boundary of the removed region once and
+// closes it with a fan of new vertices on the new plane, all in O(V).
 //
 // Geometry lives in the barycentric coordinates of the tet.  Plane ids 0..3
 // are the tet faces (face f opposite corner f, i.e. beta_f = 0); id 4+s is the
@@ -31,6 +32,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
+#include "dfloat.cuh"
 #include "exact.cuh"
 #include "internal.cuh"
 
@@ -42,14 +46,16 @@ template <typename Real>
 struct PrecTraits;
 template <>
 struct PrecTraits<float> {
-    static constexpr int VW = 7;   // words per vertex: trip, C0..C3, bound, spare
+    static constexpr int VW = 7;   // words per slot: trip, nb, C0..C3, bound
     __device__ static float u() { return 0x1p-24f; }
 };
 template <>
 struct PrecTraits<double> {
-    static constexpr int VW = 11;  // trip, C0..C3 (8 words), bound (2 words)
+    static constexpr int VW = 12;  // trip, nb, C0..C3 (8 words), bound (2 words)
     __device__ static double u() { return 0x1p-53; }
 };
+
+constexpr uint32_t DEAD = 0xff000000u;   // flag in the triplet word of a free slot
 
 // ---------------------------------------------------------------- lane state
 struct Lane {
@@ -72,40 +78,76 @@ __device__ __forceinline__ void row_i64(const Lane& L, const int32_t* __restrict
     for (int k = 0; k < 4; k++) F[k] = L.di[k] - pd_exact(L.X[k], c, w);
 }
 
-// Scale a row by a power of two so that every |entry| < 1.
+// Scale a row by a power of two so that every |entry| <= 1, with an absolute
+// error below the unit roundoff u of Real per entry.
 template <typename Real>
-__device__ __forceinline__ void scale_row(const long long F[4], Real R[4]) {
+__device__ __forceinline__ void scale_row(const long long F[4], Real R[4]);
+
+template <>
+__device__ __forceinline__ void scale_row<double>(const long long F[4], double R[4]) {
+    unsigned long long m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) m = max(m, (unsigned long long)(F[k] < 0 ? -F[k] : F[k]));
+    int e = m ? 64 - __clzll(m) : 0;                  // |F| < 2^e <= 2^48: exact in FP64
+    double sc = __longlong_as_double((long long)(1023 - e) << 52);
+#pragma unroll
+    for (int k = 0; k < 4; k++) R[k] = (double)F[k] * sc;
+}
+
+// FP32 without FP64 or 64-bit conversions: drop the low e-24 bits with an
+// arithmetic shift (floor, error < 2^(e-24)), convert the 24-bit integer
+// exactly, scale by 2^-24 (exact); the result differs from F 2^-e by < 2^-24.
+template <>
+__device__ __forceinline__ void scale_row<float>(const long long F[4], float R[4]) {
     unsigned long long m = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) m = max(m, (unsigned long long)(F[k] < 0 ? -F[k] : F[k]));
     int e = m ? 64 - __clzll(m) : 0;
-    Real sc = (Real)ldexp(1.0, -e);
+    if (e <= 24) {
+        float sc = __int_as_float((127 - e) << 23);
 #pragma unroll
-    for (int k = 0; k < 4; k++) R[k] = (Real)F[k] * sc;
+        for (int k = 0; k < 4; k++) R[k] = __int2float_rn((int)F[k]) * sc;
+    } else {
+        int sh = e - 24;
+#pragma unroll
+        for (int k = 0; k < 4; k++) R[k] = __int2float_rn((int)(F[k] >> sh)) * 0x1p-24f;
+    }
 }
 
-// Decode a triplet word: plane ids in bytes 0..2.
-__device__ __forceinline__ void unpack3(uint32_t tw, int& a, int& b, int& c) {
-    a = tw & 0xff;
-    b = (tw >> 8) & 0xff;
-    c = (tw >> 16) & 0xff;
-}
+// Triplet word: plane ids in bytes 0..2 (byte 3 = 0xff marks a free slot).
+// Neighbour word: byte k = slot across dual edge trip[k] -> trip[k+1].
+__device__ __forceinline__ int tb(uint32_t tw, int k) { return (tw >> (8 * k)) & 0xff; }
 __device__ __forceinline__ uint32_t pack3(int a, int b, int c) { return (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)c << 16); }
+__device__ __forceinline__ bool is_dead(uint32_t tw) { return (tw & DEAD) == DEAD; }
+
+// Register-friendly access to 4-vectors with a run-time index (selects
+// instead of local-memory indexing).
+template <typename T>
+__device__ __forceinline__ T get4(const T v[4], int i) {
+    return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+template <typename T>
+__device__ __forceinline__ void set4(T v[4], int i, T x) {
+    v[0] = i == 0 ? x : v[0];
+    v[1] = i == 1 ? x : v[1];
+    v[2] = i == 2 ? x : v[2];
+    v[3] = i == 3 ? x : v[3];
+}
 
 // Free columns (ascending) and bisector planes of a triplet; returns m.
 __device__ __forceinline__ int split_planes(int a, int b, int c, int* fc, int* bis) {
-    int pl[3] = {a, b, c};
-    unsigned fmask = 0;
-    int m = 0;
+    const unsigned fmask = (a < 4 ? 1u << a : 0u) | (b < 4 ? 1u << b : 0u) | (c < 4 ? 1u << c : 0u);
+    const int m = (a >= 4) + (b >= 4) + (c >= 4);
+    // bisectors in (a, b, c) order
+    bis[0] = a >= 4 ? a : (b >= 4 ? b : c);
+    bis[1] = (a >= 4 && b >= 4) ? b : c;
+    bis[2] = c;
+    unsigned fr = (~fmask) & 15u;
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        if (pl[k] < 4) fmask |= 1u << pl[k];
-        else bis[m++] = pl[k];
+    for (int k = 0; k < 4; k++) {
+        fc[k] = fr ? __ffs(fr) - 1 : 3;
+        fr &= fr - 1;
     }
-    int nf = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-        if (!(fmask & (1u << k))) fc[nf++] = k;
     return m;
 }
 
@@ -115,20 +157,18 @@ template <typename Real>
 __device__ __forceinline__ void cof_real(int m, const Real (*R)[4], const int* fc, Real C[4]) {
     C[0] = C[1] = C[2] = C[3] = (Real)0;
     if (m == 1) {
-        C[fc[0]] = R[0][fc[1]];
-        C[fc[1]] = -R[0][fc[0]];
+        set4(C, fc[0], get4(R[0], fc[1]));
+        set4(C, fc[1], -get4(R[0], fc[0]));
     } else if (m == 2) {
-        Real x0 = R[0][fc[0]], x1 = R[0][fc[1]], x2 = R[0][fc[2]];
-        Real y0 = R[1][fc[0]], y1 = R[1][fc[1]], y2 = R[1][fc[2]];
-        C[fc[0]] = fma(x1, y2, -(x2 * y1));
-        C[fc[1]] = fma(x2, y0, -(x0 * y2));
-        C[fc[2]] = fma(x0, y1, -(x1 * y0));
+        const Real x0 = get4(R[0], fc[0]), x1 = get4(R[0], fc[1]), x2 = get4(R[0], fc[2]);
+        const Real y0 = get4(R[1], fc[0]), y1 = get4(R[1], fc[1]), y2 = get4(R[1], fc[2]);
+        set4(C, fc[0], fma(x1, y2, -(x2 * y1)));
+        set4(C, fc[1], fma(x2, y0, -(x0 * y2)));
+        set4(C, fc[2], fma(x0, y1, -(x1 * y0)));
     } else {
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            int c0 = k == 0 ? 1 : 0;
-            int c1 = k <= 1 ? 2 : 1;
-            int c2 = k <= 2 ? 3 : 2;
+            const int c0 = k == 0 ? 1 : 0, c1 = k <= 1 ? 2 : 1, c2 = k <= 2 ? 3 : 2;
             Real m0 = fma(R[1][c1], R[2][c2], -(R[1][c2] * R[2][c1]));
             Real m1 = fma(R[1][c0], R[2][c2], -(R[1][c2] * R[2][c0]));
             Real m2 = fma(R[1][c0], R[2][c1], -(R[1][c1] * R[2][c0]));
@@ -138,14 +178,14 @@ __device__ __forceinline__ void cof_real(int m, const Real (*R)[4], const int* f
     }
 }
 
-// Absolute error bound of each cofactor entry for rows with |entry| < 1.
+// Absolute error bound of each cofactor entry for rows with |entry| <= 1.
 template <typename Real>
 __device__ __forceinline__ Real cof_err(int m) {
     const Real u = PrecTraits<Real>::u();
     return m == 1 ? 2 * u : (m == 2 ? 16 * u : 96 * u);
 }
 
-// Bound on |computed F.C - exact| for a scaled row F (|F| < 1).
+// Bound on |computed F.C - exact| for a scaled row F (|F| <= 1).
 template <typename Real>
 __device__ __forceinline__ Real dot_bound(int m, const Real C[4]) {
     const Real u = PrecTraits<Real>::u();
@@ -160,11 +200,19 @@ struct Slow {
     DevState* st;
 };
 
+struct Row4 {
+    long long v[4];
+};
+
 // Exact-or-FP64 sign of (F_u . C) * sign(sum C) for the vertex on planes
-// (a,b,c); F_u == nullptr asks for sign(sum C) alone.  Returns 0 only when the
-// exact value is zero (degenerate input).
-__device__ __noinline__ int slow_sign(const Lane& L, const Slow& S, int a, int b, int c, const long long* Fu,
-                                      bool try_fp64, unsigned& n64, unsigned& nex) {
+// (a,b,c); has_u == false asks for sign(sum C) alone.  Returns 0 only when
+// the exact value is zero (degenerate input).  Arguments are passed by value
+// so that the caller's lane state stays in registers.
+__device__ __noinline__ int slow_sign_impl(Lane L, Slow S, int a, int b, int c, Row4 U, bool has_u, bool try_fp64,
+                                           unsigned* cnt) {
+    const long long* Fu = has_u ? U.v : nullptr;
+    unsigned& n64 = cnt[0];
+    unsigned& nex = cnt[1];
     int fc[4], bis[3];
     int m = split_planes(a, b, c, fc, bis);
     long long R[3][4];
@@ -203,39 +251,43 @@ __device__ __noinline__ int slow_sign(const Lane& L, const Slow& S, int a, int b
     return i256_sign(v) * ss;
 }
 
+__device__ __forceinline__ int slow_sign(const Lane& L, const Slow& S, int a, int b, int c, const long long* Fu,
+                                         bool try_fp64, unsigned& n64, unsigned& nex) {
+    Row4 U;
+    if (Fu)
+        for (int k = 0; k < 4; k++) U.v[k] = Fu[k];
+    else
+        for (int k = 0; k < 4; k++) U.v[k] = 0;
+    unsigned cnt[2] = {0, 0};
+    const int r = slow_sign_impl(L, S, a, b, c, U, Fu != nullptr, try_fp64, cnt);
+    n64 += cnt[0];
+    nex += cnt[1];
+    return r;
+}
+
 // ------------------------------------------------------------ smem access
+// Per warp: [VMAX][VW][32] slot words followed by [VMAX][32] scratch words.
 template <typename Real, int VMAX>
 struct Store {
-    uint32_t* base;   // this warp's region: [VMAX][VW][32]
+    uint32_t* base;
     int lane;
     static constexpr int VW = PrecTraits<Real>::VW;
     __device__ __forceinline__ uint32_t& w(int v, int k) const { return base[(v * VW + k) * 32 + lane]; }
+    __device__ __forceinline__ uint32_t& scratch(int j) const { return base[(VMAX * VW + j) * 32 + lane]; }
     __device__ __forceinline__ uint32_t trip(int v) const { return w(v, 0); }
     __device__ __forceinline__ void set_trip(int v, uint32_t t) const { w(v, 0) = t; }
-    __device__ __forceinline__ void put_real(int v, int k, float x) const { w(v, 1 + k) = __float_as_uint(x); }
+    __device__ __forceinline__ uint32_t nb(int v) const { return w(v, 1); }
+    __device__ __forceinline__ void set_nb(int v, uint32_t t) const { w(v, 1) = t; }
+    __device__ __forceinline__ void put_real(int v, int k, float x) const { w(v, 2 + k) = __float_as_uint(x); }
     __device__ __forceinline__ void put_real(int v, int k, double x) const {
         unsigned long long b = __double_as_longlong(x);
-        w(v, 1 + 2 * k) = (uint32_t)b;
-        w(v, 2 + 2 * k) = (uint32_t)(b >> 32);
+        w(v, 2 + 2 * k) = (uint32_t)b;
+        w(v, 3 + 2 * k) = (uint32_t)(b >> 32);
     }
-    __device__ __forceinline__ void get_real(int v, int k, float& x) const { x = __uint_as_float(w(v, 1 + k)); }
+    __device__ __forceinline__ void get_real(int v, int k, float& x) const { x = __uint_as_float(w(v, 2 + k)); }
     __device__ __forceinline__ void get_real(int v, int k, double& x) const {
-        unsigned long long b = (unsigned long long)w(v, 1 + 2 * k) | ((unsigned long long)w(v, 2 + 2 * k) << 32);
+        unsigned long long b = (unsigned long long)w(v, 2 + 2 * k) | ((unsigned long long)w(v, 3 + 2 * k) << 32);
         x = __longlong_as_double(b);
-    }
-    // chart coordinates (3 doubles) reuse words 1..6
-    __device__ __forceinline__ void put_beta(int v, int k, double x) const {
-        unsigned long long b = __double_as_longlong(x);
-        w(v, 1 + 2 * k) = (uint32_t)b;
-        w(v, 2 + 2 * k) = (uint32_t)(b >> 32);
-    }
-    __device__ __forceinline__ double get_beta(int v, int k) const {
-        unsigned long long b = (unsigned long long)w(v, 1 + 2 * k) | ((unsigned long long)w(v, 2 + 2 * k) << 32);
-        return __longlong_as_double(b);
-    }
-    __device__ __forceinline__ void copy(int dst, int src) const {
-#pragma unroll
-        for (int k = 0; k < VW; k++) w(dst, k) = w(src, k);
     }
 };
 
@@ -255,12 +307,8 @@ __device__ __forceinline__ int carrier_weight(unsigned fmask, uint32_t own) {
 }
 
 __device__ __forceinline__ unsigned fbits(int p) { return p < 4 ? (1u << p) : 0u; }
-
-// Does triplet (a,b,c) contain the directed edge x -> y?
-__device__ __forceinline__ bool has_dir(int a, int b, int c, int x, int y) {
-    return (a == x && b == y) || (b == x && c == y) || (c == x && a == y);
-}
-__device__ __forceinline__ bool has_plane(int a, int b, int c, int p) { return a == p || b == p || c == p; }
+__device__ __forceinline__ unsigned tfbits(uint32_t tw) { return fbits(tb(tw, 0)) | fbits(tb(tw, 1)) | fbits(tb(tw, 2)); }
+__device__ __forceinline__ int pos_of(uint32_t tw, int p) { return tb(tw, 0) == p ? 0 : (tb(tw, 1) == p ? 1 : (tb(tw, 2) == p ? 2 : -1)); }
 
 __device__ __forceinline__ double tet_volume6(const int3* X) {
     long long ax = X[1].x - X[0].x, ay = X[1].y - X[0].y, az = X[1].z - X[0].z;
@@ -288,13 +336,17 @@ __device__ __forceinline__ long long warp_reserve(unsigned cnt, unsigned long lo
     return (long long)base + (inc - cnt);
 }
 
+__device__ __forceinline__ bool bit(unsigned long long m0, unsigned long long m1, int v) {
+    return v < 64 ? ((m0 >> v) & 1) : ((m1 >> (v - 64)) & 1);
+}
+
 // ----------------------------------------------------------- clip kernel
 template <typename Real, int VMAX>
 __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __restrict__ pairs, long long q, bool active,
                                          const Store<Real, VMAX>& V) {
     Lane L;
     long long p = 0;
-    int nv = 0;
+    int nslot = 0, nlive = 0;
     bool alive = active, whole = true, degenerate = false;
     unsigned nfast = 0, n64 = 0, nex = 0;
     const Slow S{A.Ci, A.W, A.st};
@@ -306,29 +358,35 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
         L.cand = A.cand + L.t * RPD_MAXC;
         L.i = L.cand[L.si];
         L.own = A.own[L.t];
-        int3 ci = ld_int3(A.Ci, L.i);
-        long long wi = A.W[L.i];
+        const int3 ci = ld_int3(A.Ci, L.i);
+        const long long wi = A.W[L.i];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             L.X[k] = ld_int3(A.Xi, A.tets[4 * L.t + k]);
             L.di[k] = pd_exact(L.X[k], ci, wi);
         }
-        // the tet: corner a lies on the three faces != a (oriented triplets)
+        // the tet: corner a lies on the three faces != a; neighbours across
+        // the dual edges trip[0]->trip[1], trip[1]->trip[2], trip[2]->trip[0]
         V.set_trip(0, pack3(1, 2, 3));
+        V.set_nb(0, pack3(3, 1, 2));
         V.set_trip(1, pack3(0, 3, 2));
+        V.set_nb(1, pack3(2, 0, 3));
         V.set_trip(2, pack3(0, 1, 3));
+        V.set_nb(2, pack3(3, 0, 1));
         V.set_trip(3, pack3(0, 2, 1));
-        nv = 4;
+        V.set_nb(3, pack3(1, 0, 2));
+        nslot = nlive = 4;
     }
     // ---------------------------------------------------------- clipping
-    for (int s = 0; alive && s < L.n; s++) {
+    const uint8_t* ord = active ? A.cand_ord + L.t * RPD_MAXC : nullptr;
+    for (int k = 0; alive && k < L.n; k++) {
+        const int s = ord[k];
         if (s == L.si) continue;
         long long F[4];
         row_i64(L, A.Ci, A.W, s, F);
-        bool allneg = F[0] < 0 && F[1] < 0 && F[2] < 0 && F[3] < 0;
-        if (allneg) continue;                            // plane misses the tet
-        if (F[0] > 0 && F[1] > 0 && F[2] > 0 && F[3] > 0) {
-            alive = false;                               // tet entirely in cell s
+        if (F[0] < 0 && F[1] < 0 && F[2] < 0 && F[3] < 0) continue;   // plane misses the tet
+        if (F[0] > 0 && F[1] > 0 && F[2] > 0 && F[3] > 0) {            // tet inside cell s
+            alive = false;
             break;
         }
         Real Fr[4];
@@ -336,12 +394,13 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
         const int l = 4 + s;
         unsigned long long out0 = 0, out1 = 0;
         int nout = 0;
-        for (int v = 0; v < nv; v++) {
-            int a, b, c;
-            unpack3(V.trip(v), a, b, c);
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            const int a = tb(tw, 0), b = tb(tw, 1), c = tb(tw, 2);
             int sg;
             if (a < 4 && b < 4 && c < 4) {
-                long long fv = F[6 - a - b - c];
+                const long long fv = get4(F, 6 - a - b - c);
                 sg = (fv > 0) - (fv < 0);
             } else {
                 Real C0, C1, C2, C3, B;
@@ -350,7 +409,7 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
                 V.get_real(v, 2, C2);
                 V.get_real(v, 3, C3);
                 V.get_real(v, 4, B);
-                Real val = fma(Fr[0], C0, fma(Fr[1], C1, fma(Fr[2], C2, Fr[3] * C3)));
+                const Real val = fma(Fr[0], C0, fma(Fr[1], C1, fma(Fr[2], C2, Fr[3] * C3)));
                 if (fabs(val) > B && !A.force_slow) {
                     sg = val > 0 ? 1 : -1;
                     nfast++;
@@ -373,91 +432,125 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
             break;
         }
         if (nout == 0) continue;
-        if (nout == nv) {
+        if (nout == nlive) {
             alive = false;
             break;
         }
         whole = false;
-        // boundary edges of the removed region -> new vertices (x, y, l)
-        int nnew = 0;
-        for (int r = 0; r < nv && alive; r++) {
-            bool isout = r < 64 ? ((out0 >> r) & 1) : ((out1 >> (r - 64)) & 1);
-            if (!isout) continue;
-            int a, b, c;
-            unpack3(V.trip(r), a, b, c);
-            const int ex[3] = {a, b, c}, ey[3] = {b, c, a};
+        // boundary of the removed region: dual edges x->y of removed vertices
+        // whose neighbour w is kept; one new vertex (x, y, l) each
+        int nbd = 0;
+        for (int r = 0; r < nslot; r++) {
+            if (!bit(out0, out1, r)) continue;
+            const uint32_t tw = V.trip(r), nw = V.nb(r);
+#pragma unroll
             for (int e = 0; e < 3; e++) {
-                int x = ex[e], y = ey[e];
-                int twin = -1;
-                for (int w = 0; w < nv; w++) {
-                    int a2, b2, c2;
-                    unpack3(V.trip(w), a2, b2, c2);
-                    if (has_dir(a2, b2, c2, y, x)) {
-                        twin = w;
-                        break;
-                    }
-                }
-                if (twin < 0) continue;
-                bool twin_out = twin < 64 ? ((out0 >> twin) & 1) : ((out1 >> (twin - 64)) & 1);
-                if (twin_out) continue;
-                int dst = nv + nnew;
-                if (dst >= VMAX) {
-                    dev_fail(A.st, RPD_E_OVERFLOW, CNT_CAPACITY);
-                    alive = false;
+                const int w = tb(nw, e);
+                if (bit(out0, out1, w)) continue;
+                if (nbd == VMAX) {
+                    nbd = VMAX + 1;
                     break;
                 }
-                nnew++;
-                V.set_trip(dst, pack3(x, y, l));
-                // homogeneous barycentric coordinates of the new vertex
-                int fc[4], bis[3];
-                int m = split_planes(x, y, l, fc, bis);
-                Real R[3][4];
-                for (int k = 0; k < m; k++) {
-                    if (bis[k] == l) {
-                        for (int z = 0; z < 4; z++) R[k][z] = Fr[z];
-                    } else {
-                        long long Fk[4];
-                        row_i64(L, A.Ci, A.W, bis[k] - 4, Fk);
-                        scale_row<Real>(Fk, R[k]);
-                    }
-                }
-                Real C[4];
-                cof_real<Real>(m, R, fc, C);
-                const Real u = PrecTraits<Real>::u();
-                Real sum = C[0] + C[1] + C[2] + C[3];
-                Real sa = fabs(C[0]) + fabs(C[1]) + fabs(C[2]) + fabs(C[3]);
-                Real bs = ((Real)(m + 1) * cof_err<Real>(m) + 4 * u * sa) * (1 + 8 * u);
-                int ss;
-                if (fabs(sum) > bs && !A.force_slow) {
-                    ss = sum > 0 ? 1 : -1;
-                    nfast++;
-                } else {
-                    ss = slow_sign(L, S, x, y, l, nullptr, sizeof(Real) == 4 && A.force_slow < 2, n64, nex);
-                }
-                if (ss == 0) {
-                    degenerate = true;
-                    alive = false;
-                    break;
-                }
-                if (ss < 0)
-                    for (int z = 0; z < 4; z++) C[z] = -C[z];
-                for (int z = 0; z < 4; z++) V.put_real(dst, z, C[z]);
-                V.put_real(dst, 4, dot_bound<Real>(m, C));
+                V.scratch(nbd++) = (uint32_t)tb(tw, e) | ((uint32_t)tb(tw, (e + 1) % 3) << 8) | ((uint32_t)w << 16);
             }
+            V.set_trip(r, DEAD);
+        }
+        if (nbd > VMAX) {
+            dev_fail(A.st, RPD_E_OVERFLOW, CNT_CAPACITY);
+            alive = false;
+            break;
+        }
+        // slots: free slots first, then append
+        int cur = 0;
+        for (int j = 0; j < nbd; j++) {
+            while (cur < nslot && !is_dead(V.trip(cur))) cur++;
+            int h;
+            if (cur < nslot) {
+                h = cur++;
+            } else {
+                h = nslot++;
+                cur = nslot;
+            }
+            if (h >= VMAX) {
+                dev_fail(A.st, RPD_E_OVERFLOW, CNT_CAPACITY);
+                alive = false;
+                break;
+            }
+            V.scratch(j) |= (uint32_t)h << 24;
+            V.set_trip(h, DEAD | 0x00ffffffu);   // reserved (still free for the scan below)
         }
         if (!alive) break;
-        // compact: keep inside vertices and append the new ones
-        int wpos = 0;
-        for (int r = 0; r < nv + nnew; r++) {
-            bool isout = r < nv && (r < 64 ? ((out0 >> r) & 1) : ((out1 >> (r - 64)) & 1));
-            if (isout) continue;
-            if (r != wpos) V.copy(wpos, r);
-            wpos++;
+        for (int j = 0; j < nbd; j++) {
+            const uint32_t e = V.scratch(j);
+            const int x = e & 0xff, y = (e >> 8) & 0xff, w = (e >> 16) & 0xff, h = e >> 24;
+            int n1 = -1, n2 = -1;
+            for (int j2 = 0; j2 < nbd; j2++) {
+                const uint32_t e2 = V.scratch(j2);
+                if ((int)(e2 & 0xff) == y) n1 = e2 >> 24;          // next: starts at y
+                if ((int)((e2 >> 8) & 0xff) == x) n2 = e2 >> 24;   // previous: ends at x
+            }
+            // w held the dual edge y -> x towards the removed vertex
+            const uint32_t tww = V.trip(w);
+            const int kk = (tb(tww, 0) == y && tb(tww, 1) == x)   ? 0
+                           : (tb(tww, 1) == y && tb(tww, 2) == x) ? 1
+                           : (tb(tww, 2) == y && tb(tww, 0) == x) ? 2
+                                                                  : -1;
+            if (n1 < 0 || n2 < 0 || kk < 0) {   // not a closed dual surface: cannot happen for exact signs
+                dev_fail(A.st, RPD_E_DEGENERATE, CNT_CAPACITY);
+                degenerate = true;
+                alive = false;
+                break;
+            }
+            V.set_trip(h, pack3(x, y, l));
+            V.set_nb(h, pack3(w, n1, n2));
+            V.set_nb(w, (V.nb(w) & ~(0xffu << (8 * kk))) | ((uint32_t)h << (8 * kk)));
+            // homogeneous barycentric coordinates of the new vertex
+            int fc[4], bis[3];
+            const int m = split_planes(x, y, l, fc, bis);
+            Real R[3][4];
+#pragma unroll
+            for (int z = 0; z < 3; z++) {
+                if (z >= m) break;
+                if (bis[z] == l) {
+#pragma unroll
+                    for (int c = 0; c < 4; c++) R[z][c] = Fr[c];
+                } else {
+                    long long Fk[4];
+                    row_i64(L, A.Ci, A.W, bis[z] - 4, Fk);
+                    scale_row<Real>(Fk, R[z]);
+                }
+            }
+            Real C[4];
+            cof_real<Real>(m, R, fc, C);
+            const Real u = PrecTraits<Real>::u();
+            const Real sum = C[0] + C[1] + C[2] + C[3];
+            const Real sa = fabs(C[0]) + fabs(C[1]) + fabs(C[2]) + fabs(C[3]);
+            const Real bs = ((Real)(m + 1) * cof_err<Real>(m) + 4 * u * sa) * (1 + 8 * u);
+            int ss;
+            if (fabs(sum) > bs && !A.force_slow) {
+                ss = sum > 0 ? 1 : -1;
+                nfast++;
+            } else {
+                ss = slow_sign(L, S, x, y, l, nullptr, sizeof(Real) == 4 && A.force_slow < 2, n64, nex);
+            }
+            if (ss == 0) {
+                degenerate = true;
+                alive = false;
+                break;
+            }
+            if (ss < 0) {
+#pragma unroll
+                for (int z = 0; z < 4; z++) C[z] = -C[z];
+            }
+#pragma unroll
+            for (int z = 0; z < 4; z++) V.put_real(h, z, C[z]);
+            V.put_real(h, 4, dot_bound<Real>(m, C));
         }
-        nv = wpos;
+        if (!alive) break;
+        nlive += nbd - nout;
     }
     if (degenerate) dev_fail(A.st, RPD_E_DEGENERATE, CNT_DEGENERATE);
-    if (active && nv < 4) alive = false;
+    if (active && nlive < 4) alive = false;
     dev_count(A.st, CNT_PRED_FAST, nfast);
     dev_count(A.st, CNT_PRED_FP64, n64);
     dev_count(A.st, CNT_PRED_EXACT, nex);
@@ -467,23 +560,35 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     unsigned long long fmask = 0;   // planes present as faces
     unsigned nF = 0, nE = 0, nV = 0;
     if (alive) {
-        for (int v = 0; v < nv; v++) {
-            int a, bb, c;
-            unpack3(V.trip(v), a, bb, c);
-            fmask |= (1ull << a) | (1ull << bb) | (1ull << c);
-            // radical vertex (3 bisectors, all of larger index)
-            if (a >= 4 && bb >= 4 && c >= 4 && L.cand[a - 4] > L.i && L.cand[bb - 4] > L.i && L.cand[c - 4] > L.i) nV++;
-            // radical edges x<y (directed edge counted once)
-            const int ex[3] = {a, bb, c}, ey[3] = {bb, c, a};
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            const int x0 = tb(tw, 0), x1 = tb(tw, 1), x2 = tb(tw, 2);
+            fmask |= (1ull << x0) | (1ull << x1) | (1ull << x2);
+            if (x0 >= 4 && x1 >= 4 && x2 >= 4 && L.cand[x0 - 4] > L.i && L.cand[x1 - 4] > L.i && L.cand[x2 - 4] > L.i)
+                nV++;
+            const int ex[3] = {x0, x1, x2}, ey[3] = {x1, x2, x0};
+#pragma unroll
             for (int e = 0; e < 3; e++)
                 if (ex[e] < ey[e] && ex[e] >= 4 && L.cand[ex[e] - 4] > L.i && L.cand[ey[e] - 4] > L.i) nE++;
         }
         for (int pl = 4; pl < 4 + L.n; pl++)
             if (((fmask >> pl) & 1) && L.cand[pl - 4] > L.i) nF++;
     }
-    long long fb = warp_reserve(nF, &A.rcount[0]);
-    long long eb = warp_reserve(nE, &A.rcount[1]);
-    long long vb = warp_reserve(nV, &A.rcount[2]);
+    const long long fb = warp_reserve(nF, &A.rcount[0]);
+    const long long eb = warp_reserve(nE, &A.rcount[1]);
+    const long long vb = warp_reserve(nV, &A.rcount[2]);
+    // cut pieces go to the volume queue of this bin
+    const bool queued = alive && !whole;
+    const long long qb = warp_reserve(queued ? 1u : 0u, A.qcount);
+    if (queued && qb < A.qcap) {
+        A.qpair[qb] = (int32_t)p;
+        A.qnv[qb] = (uint8_t)nslot;
+        for (int v = 0; v < nslot; v++) {
+            A.qtrip[(2LL * v) * A.qcap + qb] = V.trip(v);
+            A.qtrip[(2LL * v + 1) * A.qcap + qb] = V.nb(v);
+        }
+    }
     if (active) {
         A.pflag[p] = alive ? 1 : 0;
         A.f_off[p] = (int32_t)fb;
@@ -501,16 +606,18 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
         return;
     }
     const int32_t* adj = A.adj + 4 * L.t;
-    // RPC contribution and links
+    // RPC contribution V - E + F - C and links through tet faces
     {
         int sv = 0, se = 0, sf = 0;
-        for (int v = 0; v < nv; v++) {
-            int a, bb, c;
-            unpack3(V.trip(v), a, bb, c);
-            sv += carrier_weight(fbits(a) | fbits(bb) | fbits(c), L.own);
-            const int ex[3] = {a, bb, c}, ey[3] = {bb, c, a};
-            for (int e = 0; e < 3; e++)
-                if (ex[e] < ey[e]) se += carrier_weight(fbits(ex[e]) | fbits(ey[e]), L.own);
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            sv += carrier_weight(tfbits(tw), L.own);
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3);
+                if (x < y) se += carrier_weight(fbits(x) | fbits(y), L.own);
+            }
         }
         unsigned lk = 0;
         for (int f = 0; f < 4; f++)
@@ -522,84 +629,74 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
         A.c_val[p] = sv - se + sf - 1;
         A.c_link[p] = (uint8_t)lk;
     }
-    // RPF records: face on the radical plane of sphere j > i
+    // RPF records: walk the polygon on the radical plane of each sphere j > i
     {
-        long long w = fb;
+        long long wr = fb;
         for (int pl = 4; pl < 4 + L.n; pl++) {
             if (!((fmask >> pl) & 1)) continue;
-            int j = L.cand[pl - 4];
+            const int j = L.cand[pl - 4];
             if (j <= L.i) continue;
-            int sv = 0, se = 0;
+            int v0 = 0;
+            while (is_dead(V.trip(v0)) || pos_of(V.trip(v0), pl) < 0) v0++;
+            int sv = 0, se = 0, v = v0;
             unsigned lk = 0;
-            for (int v = 0; v < nv; v++) {
-                int a, bb, c;
-                unpack3(V.trip(v), a, bb, c);
-                if (!has_plane(a, bb, c, pl)) continue;
-                sv += carrier_weight(fbits(a) | fbits(bb) | fbits(c), L.own);
-                const int ex[3] = {a, bb, c}, ey[3] = {bb, c, a};
-                for (int e = 0; e < 3; e++) {
-                    int x = ex[e], y = ey[e];
-                    if (x < y && (x == pl || y == pl)) {
-                        int other = x == pl ? y : x;
-                        se += carrier_weight(fbits(other), L.own);
-                        if (other < 4 && adj[other] >= 0) lk |= 1u << other;
-                    }
-                }
+            for (int guard = 0; guard < VMAX; guard++) {
+                const uint32_t tw = V.trip(v);
+                const int kp = pos_of(tw, pl);
+                const int r = tb(tw, (kp + 2) % 3);          // edge (r -> pl) leads to the next vertex
+                sv += carrier_weight(tfbits(tw), L.own);
+                se += carrier_weight(fbits(r), L.own);
+                if (r < 4 && adj[r] >= 0) lk |= 1u << r;
+                v = tb(V.nb(v), (kp + 2) % 3);
+                if (v == v0) break;
             }
-            if (w < A.rcap[0]) {
-                A.rkey[0][w] = ((unsigned long long)L.i << b) | (unsigned long long)j;
-                A.rtet[0][w] = (int32_t)L.t;
-                A.rval[0][w] = (int16_t)(sv - se + 1);
-                A.rlink[0][w] = (uint8_t)lk;
+            if (wr < A.rcap[0]) {
+                A.rkey[0][wr] = ((unsigned long long)L.i << b) | (unsigned long long)j;
+                A.rtet[0][wr] = (int32_t)L.t;
+                A.rval[0][wr] = (int16_t)(sv - se + 1);
+                A.rlink[0][wr] = (uint8_t)lk;
             }
-            w++;
+            wr++;
         }
     }
     // RPE records (edges on two radical planes) and RPV records
     {
-        long long w = eb, wv = vb;
-        for (int v = 0; v < nv; v++) {
-            int a, bb, c;
-            unpack3(V.trip(v), a, bb, c);
-            const int ex[3] = {a, bb, c}, ey[3] = {bb, c, a}, ez[3] = {c, a, bb};
+        long long we = eb, wv = vb;
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            const uint32_t nw = V.nb(v);
+#pragma unroll
             for (int e = 0; e < 3; e++) {
-                int x = ex[e], y = ey[e];
+                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3), z = tb(tw, (e + 2) % 3);
                 if (!(x < y && x >= 4)) continue;
-                int j = L.cand[x - 4], k = L.cand[y - 4];
+                const int j = L.cand[x - 4], k = L.cand[y - 4];
                 if (j <= L.i || k <= L.i) continue;
-                // the other endpoint holds the directed edge y -> x
-                int twin = -1, tz = -1;
-                for (int u2 = 0; u2 < nv && twin < 0; u2++) {
-                    int a2, b2, c2;
-                    unpack3(V.trip(u2), a2, b2, c2);
-                    if (has_dir(a2, b2, c2, y, x)) {
-                        twin = u2;
-                        tz = (a2 != x && a2 != y) ? a2 : ((b2 != x && b2 != y) ? b2 : c2);
-                    }
-                }
-                if (twin < 0) continue;
-                int z = ez[e];
-                int sv = carrier_weight(fbits(z), L.own) + carrier_weight(fbits(tz), L.own);
+                const uint32_t tw2 = V.trip(tb(nw, e));       // other end point (holds y -> x)
+                const int tz = tb(tw2, 0) + tb(tw2, 1) + tb(tw2, 2) - x - y;
+                const int sv = carrier_weight(fbits(z), L.own) + carrier_weight(fbits(tz), L.own);
                 unsigned lk = 0;
                 if (z < 4 && adj[z] >= 0) lk |= 1u << z;
-                if (tz >= 0 && tz < 4 && adj[tz] >= 0) lk |= 1u << tz;
-                int lo = min(j, k), hi = max(j, k);
-                if (w < A.rcap[1]) {
-                    A.rkey[1][w] = ((unsigned long long)L.i << (2 * b)) | ((unsigned long long)lo << b) |
-                                   (unsigned long long)hi;
-                    A.rtet[1][w] = (int32_t)L.t;
-                    A.rval[1][w] = (int16_t)(sv - 1);
-                    A.rlink[1][w] = (uint8_t)lk;
+                if (tz < 4 && adj[tz] >= 0) lk |= 1u << tz;
+                const int lo = min(j, k), hi = max(j, k);
+                if (we < A.rcap[1]) {
+                    A.rkey[1][we] = ((unsigned long long)L.i << (2 * b)) | ((unsigned long long)lo << b) |
+                                    (unsigned long long)hi;
+                    A.rtet[1][we] = (int32_t)L.t;
+                    A.rval[1][we] = (int16_t)(sv - 1);
+                    A.rlink[1][we] = (uint8_t)lk;
                 }
-                w++;
+                we++;
             }
-            if (a >= 4 && bb >= 4 && c >= 4) {
-                int j = L.cand[a - 4], k = L.cand[bb - 4], m3 = L.cand[c - 4];
+            const int x0 = tb(tw, 0), x1 = tb(tw, 1), x2 = tb(tw, 2);
+            if (x0 >= 4 && x1 >= 4 && x2 >= 4) {
+                const int j = L.cand[x0 - 4], k = L.cand[x1 - 4], m3 = L.cand[x2 - 4];
                 if (j > L.i && k > L.i && m3 > L.i) {
-                    int s0 = min(j, min(k, m3)), s2 = max(j, max(k, m3)), s1 = j + k + m3 - s0 - s2;
+                    const int s0 = min(j, min(k, m3)), s2 = max(j, max(k, m3)), s1 = j + k + m3 - s0 - s2;
                     if (wv < A.rcap[2] && 4 * b <= 64) {
-                        A.rkey[2][wv] = ((unsigned long long)L.i << (3 * b)) | ((unsigned long long)s0 << (2 * b)) |
-                                        ((unsigned long long)s1 << b) | (unsigned long long)s2;
+                        A.rkey[2][wv] = ((unsigned long long)L.i << (3 * b)) |
+                                        ((unsigned long long)s0 << (2 * b)) | ((unsigned long long)s1 << b) |
+                                        (unsigned long long)s2;
                         A.rtet[2][wv] = (int32_t)L.t;
                         A.rval[2][wv] = 1;
                         A.rlink[2][wv] = 0;
@@ -609,86 +706,14 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
             }
         }
     }
-    // ------------------------------------------------ volume and moment (FP64)
-    const double vol6 = tet_volume6(L.X);    // 6 vol(t), grid units
-    const double u3 = A.unit * A.unit * A.unit;
+    // whole tets: volume and moment in closed form; cut pieces were queued
     if (whole) {
-        double vt = vol6 / 6.0;
+        const double vt = tet_volume6(L.X) / 6.0;
+        const double u3 = A.unit * A.unit * A.unit;
         A.p_vol[p] = vt * u3;
-        for (int k = 0; k < 3; k++) {
-            double cx = 0.25 * ((double)(&L.X[0].x)[k] + (&L.X[1].x)[k] + (&L.X[2].x)[k] + (&L.X[3].x)[k]);
-            A.p_mom[3 * p + k] = vt * cx * u3 * A.unit;
-        }
-        return;
-    }
-    // chart coordinates beta_1..3 of every vertex (exact rows, FP64 cofactors)
-    for (int v = 0; v < nv; v++) {
-        int a, bb, c;
-        unpack3(V.trip(v), a, bb, c);
-        double beta[4] = {0, 0, 0, 0};
-        int fc[4], bis[3];
-        int m = split_planes(a, bb, c, fc, bis);
-        if (m == 0) {
-            beta[6 - a - bb - c] = 1.0;
-        } else {
-            double Rd[3][4], Cd[4];
-            for (int k = 0; k < m; k++) {
-                long long Fk[4];
-                row_i64(L, A.Ci, A.W, bis[k] - 4, Fk);
-                scale_row<double>(Fk, Rd[k]);
-            }
-            cof_real<double>(m, Rd, fc, Cd);
-            double sum = Cd[0] + Cd[1] + Cd[2] + Cd[3];
-            double inv = 1.0 / sum;
-            for (int z = 0; z < 4; z++) beta[z] = Cd[z] * inv;
-        }
-        V.put_beta(v, 0, beta[1]);
-        V.put_beta(v, 1, beta[2]);
-        V.put_beta(v, 2, beta[3]);
-    }
-    int a0, b0, c0;
-    unpack3(V.trip(0), a0, b0, c0);
-    const double O[3] = {V.get_beta(0, 0), V.get_beta(0, 1), V.get_beta(0, 2)};
-    double S0 = 0, S1 = 0, S2 = 0, S3 = 0;
-    for (int v = 1; v < nv; v++) {
-        int a, bb, c;
-        unpack3(V.trip(v), a, bb, c);
-        const int ex[3] = {a, bb, c}, ey[3] = {bb, c, a};
-        for (int e = 0; e < 3; e++) {
-            int pf = ex[e], qf = ey[e];
-            if (has_plane(a0, b0, c0, pf)) continue;          // face through the apex
-            int R = -1, twin = -1;
-            for (int u2 = 0; u2 < nv && (R < 0 || twin < 0); u2++) {
-                int a2, b2, c2;
-                unpack3(V.trip(u2), a2, b2, c2);
-                if (R < 0 && has_plane(a2, b2, c2, pf)) R = u2;
-                if (twin < 0 && has_dir(a2, b2, c2, qf, pf)) twin = u2;
-            }
-            if (v == R || twin == R || twin < 0) continue;
-            double P1[3], P2[3], P3[3];
-            for (int k = 0; k < 3; k++) {
-                P1[k] = V.get_beta(v, k) - O[k];
-                P2[k] = V.get_beta(twin, k) - O[k];
-                P3[k] = V.get_beta(R, k) - O[k];
-            }
-            double d = P1[0] * (P2[1] * P3[2] - P2[2] * P3[1]) - P1[1] * (P2[0] * P3[2] - P2[2] * P3[0]) +
-                       P1[2] * (P2[0] * P3[1] - P2[1] * P3[0]);
-            S0 += d;
-            S1 += d * (4 * O[0] + P1[0] + P2[0] + P3[0]);
-            S2 += d * (4 * O[1] + P1[1] + P2[1] + P3[1]);
-            S3 += d * (4 * O[2] + P1[2] + P2[2] + P3[2]);
-        }
-    }
-    double sgn = S0 < 0 ? -1.0 : 1.0;
-    double vt = vol6 / 6.0;
-    double vol = vt * fabs(S0);
-    const double Sc[3] = {S1 * sgn, S2 * sgn, S3 * sgn};
-    A.p_vol[p] = vol * u3;
-    for (int k = 0; k < 3; k++) {
-        double x0 = (double)(&L.X[0].x)[k];
-        double acc = vol * x0;
-        for (int cc = 1; cc <= 3; cc++) acc += vt * ((double)(&L.X[cc].x)[k] - x0) * Sc[cc - 1] * 0.25;
-        A.p_mom[3 * p + k] = acc * u3 * A.unit;
+        A.p_mom[3 * p + 0] = vt * 0.25 * ((double)L.X[0].x + L.X[1].x + L.X[2].x + L.X[3].x) * u3 * A.unit;
+        A.p_mom[3 * p + 1] = vt * 0.25 * ((double)L.X[0].y + L.X[1].y + L.X[2].y + L.X[3].y) * u3 * A.unit;
+        A.p_mom[3 * p + 2] = vt * 0.25 * ((double)L.X[0].z + L.X[1].z + L.X[2].z + L.X[3].z) * u3 * A.unit;
     }
 }
 
@@ -697,21 +722,268 @@ __global__ void __launch_bounds__(128) k_clip(ClipArgs A, const int32_t* __restr
                                               const int32_t* __restrict__ d_n) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Store<Real, VMAX> V{smem + (size_t)warp * VMAX * PrecTraits<Real>::VW * 32, lane};
+    const Store<Real, VMAX> V{smem + (size_t)warp * VMAX * (PrecTraits<Real>::VW + 1) * 32, lane};
     const long long n = *d_n;
     // grid-stride over pairs; q0 is warp-uniform so warp collectives stay converged
     for (long long q0 = (long long)blockIdx.x * blockDim.x + warp * 32; q0 < n;
          q0 += (long long)gridDim.x * blockDim.x) {
-        long long q = q0 + lane;
+        const long long q = q0 + lane;
         clip_one<Real, VMAX>(A, pairs, q, q < n, V);
         __syncwarp();
     }
 }
 
+// ------------------------------------------------------ volume and moment
+// Chart coordinates of the tet: x = X0 + sum_{c=1..3} beta_c (X_c - X0), with
+// Jacobian 6 vol(t).  With P_v = beta_v - beta_a (chart, relative to an apex
+// vertex a of the piece), the piece is the union of the tets (a, R, v, v')
+// over the fan triangles (R, v, v') of every face not through a, R being the
+// face's first vertex; faces are walked through the dual adjacency.
+//   vol(P) = vol(t) |sum d|,  d = det(P_R, P_v, P_v')
+//   int_P x = vol(P) X0 + vol(t) sum_c (X_c - X0) (beta_a,c |sum d| + sign * sum d (P_R+P_v+P_v')_c / 4)
+template <typename Real>
+struct VolAcc;
+
+// Double-float accumulation (FP32 pipes) for the FP32-filtered mode.
+template <>
+struct VolAcc<float> {
+    df s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
+    static __device__ __forceinline__ void beta(const Lane& L, const ClipArgs& A, int a, int b, int c, df out[3]) {
+        int fc[4], bis[3];
+        const int m = split_planes(a, b, c, fc, bis);
+        df be[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        if (m == 0) {
+            set4(be, 6 - a - b - c, df_make(1.0f));
+        } else {
+            df R[3][4];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= m) break;
+                long long F[4];
+                row_i64(L, A.Ci, A.W, bis[k] - 4, F);
+                unsigned long long mx = 0;
+#pragma unroll
+                for (int z = 0; z < 4; z++) mx = max(mx, (unsigned long long)(F[z] < 0 ? -F[z] : F[z]));
+                const int e = mx ? 64 - __clzll(mx) : 0;
+                const float sc = __int_as_float((127 - e) << 23);
+#pragma unroll
+                for (int z = 0; z < 4; z++) R[k][z] = df_scale(df_from_i64(F[z]), sc);
+            }
+            df C[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            if (m == 1) {
+                set4(C, fc[0], get4(R[0], fc[1]));
+                set4(C, fc[1], df_neg(get4(R[0], fc[0])));
+            } else if (m == 2) {
+                const df x0 = get4(R[0], fc[0]), x1 = get4(R[0], fc[1]), x2 = get4(R[0], fc[2]);
+                const df y0 = get4(R[1], fc[0]), y1 = get4(R[1], fc[1]), y2 = get4(R[1], fc[2]);
+                set4(C, fc[0], df_sub(df_mul(x1, y2), df_mul(x2, y1)));
+                set4(C, fc[1], df_sub(df_mul(x2, y0), df_mul(x0, y2)));
+                set4(C, fc[2], df_sub(df_mul(x0, y1), df_mul(x1, y0)));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int c0 = k == 0 ? 1 : 0, c1 = k <= 1 ? 2 : 1, c2 = k <= 2 ? 3 : 2;
+                    const df m0 = df_sub(df_mul(R[1][c1], R[2][c2]), df_mul(R[1][c2], R[2][c1]));
+                    const df m1 = df_sub(df_mul(R[1][c0], R[2][c2]), df_mul(R[1][c2], R[2][c0]));
+                    const df m2 = df_sub(df_mul(R[1][c0], R[2][c1]), df_mul(R[1][c1], R[2][c0]));
+                    const df d = df_add(df_sub(df_mul(R[0][c0], m0), df_mul(R[0][c1], m1)), df_mul(R[0][c2], m2));
+                    C[k] = (k & 1) ? df_neg(d) : d;
+                }
+            }
+            const df sum = df_add(df_add(C[0], C[1]), df_add(C[2], C[3]));
+#pragma unroll
+            for (int z = 1; z < 4; z++) be[z] = df_div(C[z], sum);
+        }
+        out[0] = be[1];
+        out[1] = be[2];
+        out[2] = be[3];
+    }
+    __device__ __forceinline__ void term(const df* P1, const df* P2, const df* P3) {
+        const df c0 = df_sub(df_mul(P2[1], P3[2]), df_mul(P2[2], P3[1]));
+        const df c1 = df_sub(df_mul(P2[2], P3[0]), df_mul(P2[0], P3[2]));
+        const df c2 = df_sub(df_mul(P2[0], P3[1]), df_mul(P2[1], P3[0]));
+        const df d = df_add(df_add(df_mul(P1[0], c0), df_mul(P1[1], c1)), df_mul(P1[2], c2));
+        s0 = df_add(s0, d);
+        s1 = df_add(s1, df_mul(d, df_add(df_add(P1[0], P2[0]), P3[0])));
+        s2 = df_add(s2, df_mul(d, df_add(df_add(P1[1], P2[1]), P3[1])));
+        s3 = df_add(s3, df_mul(d, df_add(df_add(P1[2], P2[2]), P3[2])));
+    }
+    __device__ __forceinline__ void result(double* S) const {
+        S[0] = df_to_double(s0);
+        S[1] = df_to_double(s1);
+        S[2] = df_to_double(s2);
+        S[3] = df_to_double(s3);
+    }
+};
+
+// Native FP64 for the FP64 mode.
+template <>
+struct VolAcc<double> {
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    static __device__ __forceinline__ void beta(const Lane& L, const ClipArgs& A, int a, int b, int c, double out[3]) {
+        int fc[4], bis[3];
+        const int m = split_planes(a, b, c, fc, bis);
+        double be[4] = {0, 0, 0, 0};
+        if (m == 0) {
+            set4(be, 6 - a - b - c, 1.0);
+        } else {
+            double Rd[3][4], Cd[4];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k >= m) break;
+                long long Fk[4];
+                row_i64(L, A.Ci, A.W, bis[k] - 4, Fk);
+                scale_row<double>(Fk, Rd[k]);
+            }
+            cof_real<double>(m, Rd, fc, Cd);
+            const double inv = 1.0 / (Cd[0] + Cd[1] + Cd[2] + Cd[3]);
+#pragma unroll
+            for (int z = 0; z < 4; z++) be[z] = Cd[z] * inv;
+        }
+        out[0] = be[1];
+        out[1] = be[2];
+        out[2] = be[3];
+    }
+    __device__ __forceinline__ void term(const double* P1, const double* P2, const double* P3) {
+        const double d = P1[0] * (P2[1] * P3[2] - P2[2] * P3[1]) - P1[1] * (P2[0] * P3[2] - P2[2] * P3[0]) +
+                         P1[2] * (P2[0] * P3[1] - P2[1] * P3[0]);
+        s0 += d;
+        s1 += d * (P1[0] + P2[0] + P3[0]);
+        s2 += d * (P1[1] + P2[1] + P3[1]);
+        s3 += d * (P1[2] + P2[2] + P3[2]);
+    }
+    __device__ __forceinline__ void result(double* S) const {
+        S[0] = s0;
+        S[1] = s1;
+        S[2] = s2;
+        S[3] = s3;
+    }
+};
+
+// Volume-kernel storage per warp: [vmax][8][32] words: trip, nb, P (3 values).
+template <typename T>
+struct VStore {
+    uint32_t* base;
+    int lane;
+    __device__ __forceinline__ uint32_t& w(int v, int k) const { return base[(v * 8 + k) * 32 + lane]; }
+    __device__ __forceinline__ void put(int v, int k, df x) const {
+        w(v, 2 + 2 * k) = __float_as_uint(x.hi);
+        w(v, 3 + 2 * k) = __float_as_uint(x.lo);
+    }
+    __device__ __forceinline__ void put(int v, int k, double x) const {
+        unsigned long long b = __double_as_longlong(x);
+        w(v, 2 + 2 * k) = (uint32_t)b;
+        w(v, 3 + 2 * k) = (uint32_t)(b >> 32);
+    }
+    __device__ __forceinline__ void get(int v, int k, df& x) const {
+        x.hi = __uint_as_float(w(v, 2 + 2 * k));
+        x.lo = __uint_as_float(w(v, 3 + 2 * k));
+    }
+    __device__ __forceinline__ void get(int v, int k, double& x) const {
+        x = __longlong_as_double((long long)((unsigned long long)w(v, 2 + 2 * k) |
+                                             ((unsigned long long)w(v, 3 + 2 * k) << 32)));
+    }
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax) {
+    typedef typename std::conditional<sizeof(Real) == 4, df, double>::type T;
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const VStore<T> V{smem + (size_t)warp * vmax * 8 * 32, lane};
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)*A.qcount;
+    if (q >= n || q >= A.qcap) return;
+    const long long p = A.qpair[q];
+    const int nslot = A.qnv[q];
+    Lane L;
+    L.t = A.pair_tet[p];
+    L.si = (int)(p - A.pair_off[L.t]);
+    L.n = A.cand_cnt[L.t];
+    L.cand = A.cand + L.t * RPD_MAXC;
+    L.i = L.cand[L.si];
+    const int3 ci = ld_int3(A.Ci, L.i);
+    const long long wi = A.W[L.i];
+    for (int k = 0; k < 4; k++) {
+        L.X[k] = ld_int3(A.Xi, A.tets[4 * L.t + k]);
+        L.di[k] = pd_exact(L.X[k], ci, wi);
+    }
+    int apex = -1;
+    for (int v = 0; v < nslot; v++) {
+        V.w(v, 0) = A.qtrip[(2LL * v) * A.qcap + q];
+        V.w(v, 1) = A.qtrip[(2LL * v + 1) * A.qcap + q];
+        if (apex < 0 && !is_dead(V.w(v, 0))) apex = v;
+    }
+    // chart coordinates relative to the apex vertex
+    T O[3];
+    const uint32_t ta = V.w(apex, 0);
+    VolAcc<Real>::beta(L, A, tb(ta, 0), tb(ta, 1), tb(ta, 2), O);
+    unsigned long long fm = 0;
+    for (int v = 0; v < nslot; v++) {
+        const uint32_t tw = V.w(v, 0);
+        if (is_dead(tw) || v == apex) continue;
+        fm |= (1ull << tb(tw, 0)) | (1ull << tb(tw, 1)) | (1ull << tb(tw, 2));
+        T be[3];
+        VolAcc<Real>::beta(L, A, tb(tw, 0), tb(tw, 1), tb(tw, 2), be);
+        for (int k = 0; k < 3; k++) {
+            if constexpr (sizeof(Real) == 4) V.put(v, k, df_sub(be[k], O[k]));
+            else V.put(v, k, be[k] - O[k]);
+        }
+    }
+    fm &= ~((1ull << tb(ta, 0)) | (1ull << tb(ta, 1)) | (1ull << tb(ta, 2)));   // faces through the apex
+    VolAcc<Real> acc;
+    while (fm) {
+        const int pl = __ffsll((long long)fm) - 1;
+        fm &= fm - 1;
+        int R = 0;
+        while (is_dead(V.w(R, 0)) || pos_of(V.w(R, 0), pl) < 0) R++;
+        // successor around face pl: across the dual edge (r -> pl)
+        auto next = [&](int v) {
+            const int kp = pos_of(V.w(v, 0), pl);
+            return (int)tb(V.w(v, 1), (kp + 2) % 3);
+        };
+        T PR[3];
+        for (int k = 0; k < 3; k++) V.get(R, k, PR[k]);
+        int prev = next(R);
+        int cur = next(prev);
+        for (int guard = 0; guard < vmax && cur != R; guard++) {
+            T P2[3], P3[3];
+            for (int k = 0; k < 3; k++) {
+                V.get(prev, k, P2[k]);
+                V.get(cur, k, P3[k]);
+            }
+            acc.term(PR, P2, P3);
+            prev = cur;
+            cur = next(cur);
+        }
+    }
+    double S[4];
+    acc.result(S);
+    double Od[3];
+    for (int k = 0; k < 3; k++) {
+        if constexpr (sizeof(Real) == 4) Od[k] = df_to_double(O[k]);
+        else Od[k] = O[k];
+    }
+    const double sgn = S[0] < 0 ? -1.0 : 1.0;
+    const double vt = tet_volume6(L.X) / 6.0;
+    const double frac = fabs(S[0]);
+    const double u3 = A.unit * A.unit * A.unit;
+    A.p_vol[p] = vt * frac * u3;
+    const int xs[4][3] = {{L.X[0].x, L.X[0].y, L.X[0].z}, {L.X[1].x, L.X[1].y, L.X[1].z},
+                          {L.X[2].x, L.X[2].y, L.X[2].z}, {L.X[3].x, L.X[3].y, L.X[3].z}};
+    for (int k = 0; k < 3; k++) {
+        const double x0 = (double)xs[0][k];
+        double m = vt * frac * x0;
+        for (int cc = 1; cc <= 3; cc++)
+            m += vt * ((double)xs[cc][k] - x0) * (Od[cc - 1] * frac + sgn * S[cc] * 0.25);
+        A.p_mom[3 * p + k] = m * u3 * A.unit;
+    }
+}
+
 // Whole-tet pieces: a tet with a single candidate lies inside one cell.
 __device__ __forceinline__ void whole_one(const ClipArgs& A, long long p) {
-    long long t = A.pair_tet[p];
-    uint32_t own = A.own[t];
+    const long long t = A.pair_tet[p];
+    const uint32_t own = A.own[t];
     int3 X[4];
     for (int k = 0; k < 4; k++) X[k] = ld_int3(A.Xi, A.tets[4 * t + k]);
     const int32_t* adj = A.adj + 4 * t;
@@ -725,8 +997,8 @@ __device__ __forceinline__ void whole_one(const ClipArgs& A, long long p) {
     A.f_cnt[p] = 0;
     A.e_off[p] = 0;
     A.e_cnt[p] = 0;
-    double vt = tet_volume6(X) / 6.0;
-    double u3 = A.unit * A.unit * A.unit;
+    const double vt = tet_volume6(X) / 6.0;
+    const double u3 = A.unit * A.unit * A.unit;
     A.p_vol[p] = vt * u3;
     A.p_mom[3 * p + 0] = vt * 0.25 * ((double)X[0].x + X[1].x + X[2].x + X[3].x) * u3 * A.unit;
     A.p_mom[3 * p + 1] = vt * 0.25 * ((double)X[0].y + X[1].y + X[2].y + X[3].y) * u3 * A.unit;
@@ -743,38 +1015,57 @@ __global__ void k_whole(ClipArgs A, const int32_t* __restrict__ pairs, const int
     dev_count(A.st, CNT_WHOLE, cnt);
 }
 
+// Bins by candidate count n: 0: n = 1 (whole tet), 1..3: n = 2..4,
+// 4: 5-6, 5: 7-8, 6: 9-16, 7: 17-32.
 __device__ __forceinline__ int bin_of(int n) {
-    return n <= 1 ? 0 : (n <= 4 ? 1 : (n <= 8 ? 2 : (n <= 16 ? 3 : 4)));
+    return n <= 4 ? n - 1 : (n <= 6 ? 4 : (n <= 8 ? 5 : (n <= 16 ? 6 : 7)));
 }
 
-__global__ void k_bin_pairs(const int32_t* __restrict__ cand_cnt, const int64_t* __restrict__ pair_off, long long nt,
-                            int32_t* __restrict__ pair_tet, int32_t* __restrict__ bins, long long stride,
-                            int32_t* __restrict__ bin_count) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int n = t < nt ? cand_cnt[t] : 0;
-    int b = bin_of(n);
-    // warp-aggregated reservation per bin
-    unsigned peers = __match_any_sync(0xffffffffu, n > 0 ? b : -1);
-    int lane = threadIdx.x & 31;
-    unsigned lt = peers & ((1u << lane) - 1u);
-    // prefix of n over lower peers
+// Warp-aggregated atomicAdd of n on counter[b] (lanes with n <= 0 skip);
+// returns this lane's base.
+__device__ __forceinline__ int warp_bin_add(int n, int b, int32_t* counter) {
+    const unsigned peers = __match_any_sync(0xffffffffu, n > 0 ? b : -1);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = peers & ((1u << lane) - 1u);
     int pre = 0, tot = 0;
     for (int k = 0; k < 32; k++) {
-        int nk = __shfl_sync(0xffffffffu, n, k);
+        const int nk = __shfl_sync(0xffffffffu, n, k);
         if ((peers >> k) & 1) {
             tot += nk;
             if ((lt >> k) & 1) pre += nk;
         }
     }
-    int leader = __ffs(peers) - 1;
+    const int leader = __ffs(peers) - 1;
     int base = 0;
-    if (lane == leader && n > 0 && tot > 0) base = atomicAdd(&bin_count[b], tot);
+    if (lane == leader && n > 0 && tot > 0) base = atomicAdd(&counter[b], tot);
     base = __shfl_sync(0xffffffffu, base, leader);
+    return base + pre;
+}
+
+__global__ void k_bin_count(const int32_t* __restrict__ cand_cnt, long long nt, int32_t* __restrict__ bin_count) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = t < nt ? cand_cnt[t] : 0;
+    warp_bin_add(n, n > 0 ? bin_of(n) : 0, bin_count);
+}
+
+__global__ void k_bin_prefix(const int32_t* __restrict__ bin_count, int32_t* __restrict__ bin_fill) {
+    int run = 0;
+    for (int b = 0; b < RPD_NBINS; b++) {
+        bin_fill[b] = run;
+        run += bin_count[b];
+    }
+}
+
+__global__ void k_bin_pairs(const int32_t* __restrict__ cand_cnt, const int64_t* __restrict__ pair_off, long long nt,
+                            int32_t* __restrict__ pair_tet, int32_t* __restrict__ bins, int32_t* __restrict__ bin_fill) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = t < nt ? cand_cnt[t] : 0;
+    const int base = warp_bin_add(n, n > 0 ? bin_of(n) : 0, bin_fill);
     if (n <= 0) return;
-    long long off = pair_off[t];
+    const long long off = pair_off[t];
     for (int k = 0; k < n; k++) {
         pair_tet[off + k] = (int32_t)t;
-        bins[(long long)b * stride + base + pre + k] = (int32_t)(off + k);
+        bins[base + k] = (int32_t)(off + k);
     }
 }
 
@@ -788,7 +1079,7 @@ inline unsigned grid_for(long long n, int tpb) {
 template <typename Real, int VMAX, int WARPS>
 void launch_clip_t(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long n, cudaStream_t s) {
     if (n <= 0) return;
-    size_t smem = (size_t)WARPS * VMAX * PrecTraits<Real>::VW * 32 * sizeof(uint32_t);
+    const size_t smem = (size_t)WARPS * VMAX * (PrecTraits<Real>::VW + 1) * 32 * sizeof(uint32_t);
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(k_clip<Real, VMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -797,13 +1088,39 @@ void launch_clip_t(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, 
     k_clip<Real, VMAX><<<grid_for(n, 32 * WARPS), 32 * WARPS, smem, s>>>(a, pairs, d_n);
 }
 
+template <typename Real>
+void launch_volume_t(const ClipArgs& a, int vmax, int warps, long long nmax, cudaStream_t s) {
+    if (nmax <= 0) return;
+    const size_t smem = (size_t)warps * vmax * 8 * 32 * sizeof(uint32_t);
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaFuncSetAttribute(k_volume<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    k_volume<Real><<<nblk(nmax, 32 * warps), 32 * warps, smem, s>>>(a, vmax);
+}
+
 }  // namespace
 
-void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet, int32_t* bins,
-                      long long bin_stride, int32_t* bin_count, cudaStream_t s) {
+// Slot capacity per bin: a piece of a tet with n candidates is a simple
+// polytope with at most n + 3 faces, hence at most 2(n + 3) - 4 = 2n + 2
+// vertices; new vertices fill freed slots first, so 2n + 2 slots suffice.
+int clip_vmax(int bin) {
+    static const int v[RPD_NBINS] = {4, 6, 8, 10, 14, 18, 34, 66};
+    return v[bin];
+}
+
+void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s) {
     cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * RPD_NBINS, s);
     if (nt == 0) return;
-    k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_stride, bin_count);
+    k_bin_count<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, nt, bin_count);
+}
+
+void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet, int32_t* bins,
+                      const int32_t* bin_count, int32_t* bin_fill, cudaStream_t s) {
+    if (nt == 0) return;
+    k_bin_prefix<<<1, 1, 0, s>>>(bin_count, bin_fill);
+    k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_fill);
 }
 
 void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s) {
@@ -811,24 +1128,30 @@ void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d
     k_whole<<<grid_for(nmax, 256), 256, 0, s>>>(a, pairs, d_n);
 }
 
-// Vertex capacity per bin: a piece of a tet with n candidates has at most
-// 2n vertices before a clip and the new face adds at most n + 2, so 3n + 2
-// slots always suffice.
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,
                  cudaStream_t s) {
+    const int vw = bin <= 5 ? 4 : (bin == 6 ? 2 : 1);
     if (precision == RPD_FP32_FILTERED) {
         switch (bin) {
-            case 1: launch_clip_t<float, 14, 4>(a, pairs, d_n, n, s); break;
-            case 2: launch_clip_t<float, 26, 4>(a, pairs, d_n, n, s); break;
-            case 3: launch_clip_t<float, 50, 2>(a, pairs, d_n, n, s); break;
-            case 4: launch_clip_t<float, 98, 1>(a, pairs, d_n, n, s); break;
+            case 1: launch_clip_t<float, 6, 4>(a, pairs, d_n, n, s); break;
+            case 2: launch_clip_t<float, 8, 4>(a, pairs, d_n, n, s); break;
+            case 3: launch_clip_t<float, 10, 4>(a, pairs, d_n, n, s); break;
+            case 4: launch_clip_t<float, 14, 4>(a, pairs, d_n, n, s); break;
+            case 5: launch_clip_t<float, 18, 4>(a, pairs, d_n, n, s); break;
+            case 6: launch_clip_t<float, 34, 2>(a, pairs, d_n, n, s); break;
+            case 7: launch_clip_t<float, 66, 1>(a, pairs, d_n, n, s); break;
         }
+        if (bin >= 1) launch_volume_t<float>(a, clip_vmax(bin), vw, n, s);
     } else {
         switch (bin) {
-            case 1: launch_clip_t<double, 14, 4>(a, pairs, d_n, n, s); break;
-            case 2: launch_clip_t<double, 26, 2>(a, pairs, d_n, n, s); break;
-            case 3: launch_clip_t<double, 50, 1>(a, pairs, d_n, n, s); break;
-            case 4: launch_clip_t<double, 98, 1>(a, pairs, d_n, n, s); break;
+            case 1: launch_clip_t<double, 6, 4>(a, pairs, d_n, n, s); break;
+            case 2: launch_clip_t<double, 8, 4>(a, pairs, d_n, n, s); break;
+            case 3: launch_clip_t<double, 10, 4>(a, pairs, d_n, n, s); break;
+            case 4: launch_clip_t<double, 14, 2>(a, pairs, d_n, n, s); break;
+            case 5: launch_clip_t<double, 18, 2>(a, pairs, d_n, n, s); break;
+            case 6: launch_clip_t<double, 34, 1>(a, pairs, d_n, n, s); break;
+            case 7: launch_clip_t<double, 66, 1>(a, pairs, d_n, n, s); break;
         }
+        if (bin >= 1) launch_volume_t<double>(a, clip_vmax(bin), vw, n, s);
     }
 }

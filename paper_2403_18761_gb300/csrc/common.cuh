@@ -49,8 +49,8 @@ __device__ __forceinline__ void dev_count(DevState* st, int counter, unsigned v)
 // Exact power distance pd(x, m) = |x - c|^2 - w on the integer grid.
 // |x|,|c| <= 2^21 so |x-c|^2 <= 3*2^44 and w <= 2^44: |pd| < 2^46.
 __device__ __forceinline__ long long pd_exact(int3 x, int3 c, long long w) {
-    long long dx = (long long)x.x - c.x, dy = (long long)x.y - c.y, dz = (long long)x.z - c.z;
-    return dx * dx + dy * dy + dz * dz - w;
+    int dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;   // |d| <= 2^22: 32-bit exact
+    return (long long)dx * dx + (long long)dy * dy + (long long)dz * dz - w;
 }
 
 __device__ __forceinline__ int3 ld_int3(const int32_t* p, long long i) {

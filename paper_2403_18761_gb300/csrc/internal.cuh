@@ -42,8 +42,8 @@ void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long l
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
                        const long long* W, const int32_t* knn, const long long* dplus, int K,
                        const GridParams* gp, const int64_t* cell_start, const int32_t* cell_ids,
-                       const long long* cell_wmax, int32_t* cand_cnt, int32_t* cand, int32_t* fb_list,
-                       int32_t* fb_count, DevState* st, cudaStream_t s);
+                       const long long* cell_wmax, int32_t* cand_cnt, int32_t* cand, uint8_t* cand_ord,
+                       int32_t* fb_list, int32_t* fb_count, DevState* st, cudaStream_t s);
 
 // ---------------------------------------------------------------- clip.cu
 struct ClipArgs {
@@ -54,7 +54,8 @@ struct ClipArgs {
     const uint32_t* own;
     const int32_t* adj;
     const int32_t* cand_cnt;   // [nt]
-    const int32_t* cand;       // [nt * RPD_MAXC]
+    const int32_t* cand;       // [nt * RPD_MAXC], sorted by sphere index
+    const uint8_t* cand_ord;   // [nt * RPD_MAXC], slots in clip order
     const int64_t* pair_off;   // [nt + 1]
     const int32_t* pair_tet;   // [npairs]
     double unit;               // 2^-grid_bits
@@ -78,12 +79,21 @@ struct ClipArgs {
     int key_bits;                 // bits per sphere index in packed keys
     int force_slow;               // 0; 1 = skip the first-stage filter; 2 = exact only
     DevState* st;
+    // volume queue of the bin being launched (cut pieces)
+    int32_t* qpair;               // [qcap] pair ids
+    uint8_t* qnv;                 // [qcap] vertex counts
+    uint32_t* qtrip;              // [vmax * qcap] triplets, vertex-major
+    long long qcap;
+    unsigned long long* qcount;   // device counter
 };
-// Split pairs into bins by the candidate count of their tet; bins[b] lists
-// pair ids, bin_count[b] their number.  Bin 0: one candidate (whole tet).
-#define RPD_NBINS 5
+// Pairs are grouped into bins by the candidate count n of their tet
+// (0: n = 1, whole tet; 1..3: n = 2..4; 4: 5-6; 5: 7-8; 6: 9-16; 7: 17-32).
+#define RPD_NBINS 8
+int clip_vmax(int bin);
+void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s);
+// bins: one array of npairs pair ids, bin b starting at sum of earlier counts.
 void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet,
-                      int32_t* bins, long long bin_stride, int32_t* bin_count, cudaStream_t s);
+                      int32_t* bins, const int32_t* bin_count, int32_t* bin_fill, cudaStream_t s);
 // Pair counts are read on the device (d_n); n/nmax only size the grid.
 void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s);
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,

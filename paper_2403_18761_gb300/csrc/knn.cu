@@ -240,10 +240,12 @@ struct Gathered {
 
 // Keep the gathered spheres that pass the exact corner test against every
 // other gathered sphere; write them sorted by index.
+// Also writes the clip order: slots sorted by power distance at the tet
+// centroid (sum_a pd(X_a, s) = 4 pd(centroid, s) + a sphere-independent term).
 template <int CAP>
 __device__ void finish_candidates(Gathered* G, int n, long long t, int32_t* __restrict__ cand_cnt,
-                                  int32_t* __restrict__ cand, DevState* st) {
-    int kept[RPD_MAXC];
+                                  int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st) {
+    int kept[RPD_MAXC];   // indices into G, sorted by sphere index
     int nk = 0;
     for (int s = 0; s < n; s++) {
         bool ok = true;
@@ -260,15 +262,29 @@ __device__ void finish_candidates(Gathered* G, int n, long long t, int32_t* __re
             cand_cnt[t] = 0;
             return;
         }
-        // insertion by sphere index
-        int id = G[s].id, p = nk++;
-        while (p > 0 && kept[p - 1] > id) {
+        int p = nk++;
+        while (p > 0 && G[kept[p - 1]].id > G[s].id) {
             kept[p] = kept[p - 1];
             p--;
         }
-        kept[p] = id;
+        kept[p] = s;
     }
-    for (int j = 0; j < nk; j++) cand[t * RPD_MAXC + j] = kept[j];
+    uint8_t ord[RPD_MAXC];
+    for (int j = 0; j < nk; j++) {
+        cand[t * RPD_MAXC + j] = G[kept[j]].id;
+        const Gathered& g = G[kept[j]];
+        long long key = g.D[0] + g.D[1] + g.D[2] + g.D[3];
+        int p = j;
+        while (p > 0) {
+            const Gathered& h = G[kept[ord[p - 1]]];
+            long long hk = h.D[0] + h.D[1] + h.D[2] + h.D[3];
+            if (hk <= key) break;
+            ord[p] = ord[p - 1];
+            p--;
+        }
+        ord[p] = (uint8_t)j;
+    }
+    for (int j = 0; j < nk; j++) cand_ord[t * RPD_MAXC + j] = ord[j];
     cand_cnt[t] = nk;
 }
 
@@ -286,7 +302,7 @@ __global__ void __launch_bounds__(128) k_candidates(const int32_t* __restrict__ 
                              const int32_t* __restrict__ Xi, const int32_t* __restrict__ Ci,
                              const long long* __restrict__ W, const int32_t* __restrict__ knn,
                              const long long* __restrict__ dplus, int K, int32_t* __restrict__ cand_cnt,
-                             int32_t* __restrict__ cand, int32_t* __restrict__ fb_list,
+                             int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, int32_t* __restrict__ fb_list,
                              int32_t* __restrict__ fb_count, DevState* st) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
@@ -352,7 +368,7 @@ __global__ void __launch_bounds__(128) k_candidates(const int32_t* __restrict__ 
             n++;
         }
     }
-    finish_candidates<RPD_GATHER>(G, n, t, cand_cnt, cand, st);
+    finish_candidates<RPD_GATHER>(G, n, t, cand_cnt, cand, cand_ord, st);
 }
 
 #define RPD_FB_GATHER 128
@@ -362,7 +378,7 @@ __device__ void fallback_one(const int32_t* __restrict__ T, long long nv, const 
                              const int32_t* __restrict__ knn, int K, const GridParams* __restrict__ gp,
                              const int64_t* __restrict__ start, const int32_t* __restrict__ ids,
                              const long long* __restrict__ cwmax, long long t, int32_t* __restrict__ cand_cnt,
-                             int32_t* __restrict__ cand, DevState* st);
+                             int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st);
 
 __global__ void __launch_bounds__(64) k_candidates_fallback(const int32_t* __restrict__ T, long long nv,
                                       const int32_t* __restrict__ Xi, const int32_t* __restrict__ Ci,
@@ -370,11 +386,12 @@ __global__ void __launch_bounds__(64) k_candidates_fallback(const int32_t* __res
                                       const GridParams* __restrict__ gp, const int64_t* __restrict__ start,
                                       const int32_t* __restrict__ ids, const long long* __restrict__ cwmax,
                                       const int32_t* __restrict__ fb_list, const int32_t* __restrict__ fb_count,
-                                      int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand, DevState* st) {
+                                      int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand,
+                                      uint8_t* __restrict__ cand_ord, DevState* st) {
     const long long nfb = *fb_count;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nfb;
          q += (long long)gridDim.x * blockDim.x)
-        fallback_one(T, nv, Xi, Ci, W, knn, K, gp, start, ids, cwmax, fb_list[q], cand_cnt, cand, st);
+        fallback_one(T, nv, Xi, Ci, W, knn, K, gp, start, ids, cwmax, fb_list[q], cand_cnt, cand, cand_ord, st);
 }
 
 __device__ void fallback_one(const int32_t* __restrict__ T, long long nv, const int32_t* __restrict__ Xi,
@@ -382,7 +399,7 @@ __device__ void fallback_one(const int32_t* __restrict__ T, long long nv, const 
                              const int32_t* __restrict__ knn, int K, const GridParams* __restrict__ gp,
                              const int64_t* __restrict__ start, const int32_t* __restrict__ ids,
                              const long long* __restrict__ cwmax, long long t, int32_t* __restrict__ cand_cnt,
-                             int32_t* __restrict__ cand, DevState* st) {
+                             int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st) {
     int v[4];
     int3 X[4];
     if (!load_tet(T, t, nv, Xi, v, X)) return;
@@ -436,7 +453,7 @@ __device__ void fallback_one(const int32_t* __restrict__ T, long long nv, const 
         return;
     }
     atomicAdd(&st->cnt[CNT_CAND_FALLBACK], 1ull);
-    finish_candidates<RPD_FB_GATHER>(G, n, t, cand_cnt, cand, st);
+    finish_candidates<RPD_FB_GATHER>(G, n, t, cand_cnt, cand, cand_ord, st);
 }
 
 }  // namespace
@@ -470,12 +487,12 @@ void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long l
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
                        const long long* W, const int32_t* knn, const long long* dplus, int K, const GridParams* gp,
                        const int64_t* cell_start, const int32_t* cell_ids, const long long* cell_wmax,
-                       int32_t* cand_cnt, int32_t* cand, int32_t* fb_list, int32_t* fb_count, DevState* st,
-                       cudaStream_t s) {
+                       int32_t* cand_cnt, int32_t* cand, uint8_t* cand_ord, int32_t* fb_list, int32_t* fb_count,
+                       DevState* st, cudaStream_t s) {
     if (nt == 0) return;
     cudaMemsetAsync(fb_count, 0, sizeof(int32_t), s);
-    k_candidates<<<nblk(nt, 128), 128, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand, fb_list,
-                                               fb_count, st);
+    k_candidates<<<nblk(nt, 128), 128, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand, cand_ord,
+                                               fb_list, fb_count, st);
     k_candidates_fallback<<<152, 64, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids, cell_wmax,
-                                             fb_list, fb_count, cand_cnt, cand, st);
+                                             fb_list, fb_count, cand_cnt, cand, cand_ord, st);
 }
