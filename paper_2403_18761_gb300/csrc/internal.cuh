@@ -29,14 +29,16 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
 
 // ----------------------------------------------------------------- knn.cu
 size_t grid_tmp_bytes(long long ns, long long ncap);
+// Counting sort of the spheres into grid cells: cell_start (ncap + 1
+// offsets), and per sorted slot the sphere id, (centre, id) and weight.
 void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
-                        int64_t* cell_start, int32_t* cell_ids, long long* cell_wmax, void* tmp,
-                        cudaStream_t s);
+                        int64_t* cell_start, int32_t* cell_ids, int4* cell_sph, long long* cell_w,
+                        long long* cell_wmax, void* tmp, cudaStream_t s);
 // k nearest spheres in power distance of every mesh vertex, with D+ = a lower
 // bound of the power distance of every sphere left out of the list.
 void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
-                const int64_t* cell_start, const int32_t* cell_ids, const long long* cell_wmax, int K,
-                int32_t* knn, long long* dplus, cudaStream_t s);
+                const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, int K, int32_t* knn,
+                long long* dplus, cudaStream_t s);
 // Candidate spheres of every tet (superset of the spheres whose cell meets
 // the tet with positive volume), sorted by index, at most RPD_MAXC.
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,

@@ -164,72 +164,200 @@ __global__ void k_cell_count(const int32_t* __restrict__ Ci, const long long* __
     atomicMax((unsigned long long*)&cwmax[q], (unsigned long long)W[i]);
 }
 
-__global__ void k_cell_fill(const int32_t* __restrict__ Ci, long long ns, const GridParams* __restrict__ gp,
-                            const int64_t* __restrict__ start, int32_t* __restrict__ fill, int32_t* __restrict__ ids) {
+// Cell-sorted copy of the spheres: ids, (centre, id) and weight per slot.
+__global__ void k_cell_fill(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns,
+                            const GridParams* __restrict__ gp, const int64_t* __restrict__ start,
+                            int32_t* __restrict__ fill, int32_t* __restrict__ ids, int4* __restrict__ sph,
+                            long long* __restrict__ sw) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     GridParams g = *gp;
-    int3 c = cell_of(ld_int3(Ci, i), g);
-    int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
+    int3 c = ld_int3(Ci, i);
+    int3 cc = cell_of(c, g);
+    int q = (cc.z * g.dim.y + cc.y) * g.dim.x + cc.x;
     int slot = atomicAdd(&fill[q], 1);
-    ids[start[q] + slot] = (int32_t)i;
+    long long pos = start[q] + slot;
+    ids[pos] = (int32_t)i;
+    sph[pos] = make_int4(c.x, c.y, c.z, (int)i);
+    sw[pos] = W[i];
 }
 
 // ---------------------------------------------------------------- kNN
-__global__ void __launch_bounds__(128) k_knn(const int32_t* __restrict__ Xi, long long nv, const int32_t* __restrict__ Ci,
-                      const long long* __restrict__ W, const GridParams* __restrict__ gp,
-                      const int64_t* __restrict__ start, const int32_t* __restrict__ ids,
-                      const long long* __restrict__ cwmax, int K, int32_t* __restrict__ knn,
-                      long long* __restrict__ dplus) {
-    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
+// One warp per mesh vertex.  The current K best (power distance, sphere)
+// pairs live one per lane, sorted by lane; the spheres of a grid cell are
+// evaluated 32 at a time, bitonic-sorted across the lanes and merged into
+// the list.  Every sphere or cell left out contributes to D+.
+__device__ __forceinline__ bool pair_less(long long d1, int i1, long long d2, int i2) {
+    return d1 < d2 || (d1 == d2 && i1 < i2);
+}
+
+// Bitonic compare-exchange with the lane at distance j; `up` = ascending block.
+__device__ __forceinline__ void cmpx(long long& d, int& id, int j, bool up) {
+    const int lane = threadIdx.x & 31;
+    const long long od = __shfl_xor_sync(0xffffffffu, d, j);
+    const int oi = __shfl_xor_sync(0xffffffffu, id, j);
+    const bool lower = (lane & j) == 0;
+    const bool want_min = (lower == up);
+    const bool other_smaller = pair_less(od, oi, d, id);
+    if (want_min ? other_smaller : (!other_smaller && (od != d || oi != id))) {
+        d = od;
+        id = oi;
+    }
+}
+
+__device__ __forceinline__ void warp_sort32(long long& d, int& id) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) cmpx(d, id, j, (lane & k) == 0 || k == 32);
+}
+
+// L (sorted) <- the 32 smallest of L and B (sorted); returns the smallest
+// distance that was dropped (LLONG_MAX if none).
+__device__ __forceinline__ long long warp_merge32(long long& d, int& id, long long bd, int bi) {
+    const int lane = threadIdx.x & 31;
+    const long long rd = __shfl_sync(0xffffffffu, bd, 31 - lane);
+    const int ri = __shfl_sync(0xffffffffu, bi, 31 - lane);
+    long long dropped;
+    if (pair_less(rd, ri, d, id)) {
+        dropped = d;
+        d = rd;
+        id = ri;
+    } else {
+        dropped = rd;
+    }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) cmpx(d, id, j, true);
+    long long m = dropped;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, off));
+    return m;
+}
+
+__global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, long long nv,
+                                                   const int32_t* __restrict__ Ci, const long long* __restrict__ W,
+                                                   const GridParams* __restrict__ gp,
+                                                   const int64_t* __restrict__ start, const int4* __restrict__ sph,
+                                                   const long long* __restrict__ sw, int K,
+                                                   int32_t* __restrict__ knn, long long* __restrict__ dplus) {
+    const int lane = threadIdx.x & 31;
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (v >= nv) return;   // warp-uniform
     const GridParams g = *gp;
     const int3 x = ld_int3(Xi, v);
     const int3 c = cell_of(x, g);
-    long long bd[RPD_MAXK];
-    int bi[RPD_MAXK];
-    int cnt = 0;
+    long long d = LLONG_MAX;
+    int id = 0x7fffffff;
     long long dp = LLONG_MAX;
-    for (int r = 0;; r++) {
-        if (r > 0) {
-            long long lb2 = ring_lb2(x, g, c, r);
-            if (lb2 == LLONG_MAX) break;                 // every cell visited
-            long long plb = lb2 - g.wmax;
-            if (cnt == K && plb > bd[K - 1]) {
-                dp = min(dp, plb);
+    long long kd = LLONG_MAX;   // K-th distance (warp-uniform)
+    int ki = 0x7fffffff;
+    // Bands of Chebyshev shells r_lo < r <= r_hi around c; the lanes stride
+    // over the cells of the band's bounding box.
+    int r_done = -1;
+    for (int iter = 0; iter < 64; iter++) {
+        // next band: while the list is short grow by one ring, otherwise take
+        // every ring that can still hold a sphere closer than the K-th
+        const int rn = r_done + 1;   // first unexplored ring
+        if (rn > 0) {
+            const long long lb2 = ring_lb2(x, g, c, rn);
+            if (lb2 == LLONG_MAX) break;                          // no cells left
+            if (kd != LLONG_MAX && lb2 - g.wmax > kd) {
+                dp = min(dp, lb2 - g.wmax);
                 break;
             }
         }
-        for_shell(g, c, r, [&](int qx, int qy, int qz) {
-            int q = (qz * g.dim.y + qy) * g.dim.x + qx;
-            long long s0 = start[q], s1 = start[q + 1];
-            if (s0 == s1) return;
-            long long plb = box_dist2(x, g, qx, qy, qz) - cwmax[q];
-            if (cnt == K && plb > bd[K - 1]) {
-                dp = min(dp, plb);
-                return;
+        int r_hi;
+        if (kd == LLONG_MAX) {
+            r_hi = rn == 0 ? 1 : 2 * rn + 1;                      // list still short: grow geometrically
+        } else {
+            r_hi = rn;
+            while (r_hi < 4096) {
+                const long long nb2 = ring_lb2(x, g, c, r_hi + 1);
+                if (nb2 == LLONG_MAX || nb2 - g.wmax > kd) break;
+                r_hi++;
             }
-            for (long long e = s0; e < s1; e++) {
-                int s = ids[e];
-                long long d = pd_exact(x, ld_int3(Ci, s), W[s]);
-                if (cnt < K || d < bd[K - 1] || (d == bd[K - 1] && s < bi[K - 1])) {
-                    if (cnt == K) dp = min(dp, bd[K - 1]);
-                    int p = cnt < K ? cnt++ : K - 1;
-                    while (p > 0 && (bd[p - 1] > d || (bd[p - 1] == d && bi[p - 1] > s))) {
-                        bd[p] = bd[p - 1];
-                        bi[p] = bi[p - 1];
-                        p--;
+        }
+        const int x0 = max(-r_hi, -c.x), x1 = min(r_hi, g.dim.x - 1 - c.x);
+        const int y0 = max(-r_hi, -c.y), y1 = min(r_hi, g.dim.y - 1 - c.y);
+        const int z0 = max(-r_hi, -c.z), z1 = min(r_hi, g.dim.z - 1 - c.z);
+        const int ey = y1 - y0 + 1;
+        const int nrow = ey * (z1 - z0 + 1);
+        // A row (dy, dz) of cells is one contiguous run of the cell-sorted
+        // sphere array; rows inside the explored cube split into two runs.
+        int j = lane - 32, seg = 2;
+        long long e = 0, e1 = 0;
+        bool done = false;
+        for (int round = 0; round < (1 << 20); round++) {
+            // advance to this lane's next candidate
+            long long sd = LLONG_MAX;
+            int si = 0x7fffffff;
+            bool cand = false;
+            while (!done && !cand) {
+                if (e < e1) {
+                    const int4 cs = sph[e];
+                    const long long ds = pd_exact(x, make_int3(cs.x, cs.y, cs.z), sw[e]);
+                    e++;
+                    if (kd == LLONG_MAX || pair_less(ds, cs.w, kd, ki)) {
+                        sd = ds;
+                        si = cs.w;
+                        cand = true;
+                    } else {
+                        dp = min(dp, ds);
                     }
-                    bd[p] = d;
-                    bi[p] = s;
-                } else {
-                    dp = min(dp, d);
+                    continue;
                 }
+                if (seg >= 2) {
+                    j += 32;
+                    if (j >= nrow) {
+                        done = true;
+                        break;
+                    }
+                    seg = 0;
+                }
+                const int dy = y0 + j % ey, dz = z0 + j / ey;
+                const bool inner = abs(dy) <= r_done && abs(dz) <= r_done;
+                int xa, xb;
+                if (!inner) {
+                    xa = x0;
+                    xb = x1;
+                    seg = 2;
+                } else if (seg == 0) {
+                    xa = x0;
+                    xb = -r_done - 1;
+                    seg = 1;
+                } else {
+                    xa = r_done + 1;
+                    xb = x1;
+                    seg = 2;
+                }
+                if (xa > xb) continue;
+                const int qrow = ((c.z + dz) * g.dim.y + (c.y + dy)) * g.dim.x + c.x;
+                e = start[qrow + xa];
+                e1 = start[qrow + xb + 1];
             }
-        });
+            if (!__any_sync(0xffffffffu, cand)) {
+                if (__all_sync(0xffffffffu, done)) break;
+                continue;
+            }
+            warp_sort32(sd, si);
+            dp = min(dp, warp_merge32(d, id, sd, si));
+            kd = __shfl_sync(0xffffffffu, d, K - 1);
+            ki = __shfl_sync(0xffffffffu, id, K - 1);
+        }
+        r_done = r_hi;
     }
-    for (int j = 0; j < K; j++) knn[v * K + j] = j < cnt ? bi[j] : -1;
-    dplus[v] = dp;
+    {   // whatever was not explored is bounded by the next ring
+        const long long lbu = ring_lb2(x, g, c, r_done + 1);
+        if (lbu != LLONG_MAX) dp = min(dp, lbu - g.wmax);
+    }
+    // entries beyond the K-th are left out too
+    long long tail = (lane >= K) ? d : LLONG_MAX;
+    dp = min(dp, tail);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) dp = min(dp, __shfl_xor_sync(0xffffffffu, dp, off));
+    if (lane < K) knn[v * K + lane] = d == LLONG_MAX ? -1 : id;
+    if (lane == 0) dplus[v] = dp;
 }
 
 // ---------------------------------------------------------- candidates
@@ -298,39 +426,48 @@ __device__ __forceinline__ bool load_tet(const int32_t* __restrict__ T, long lon
     return true;
 }
 
-__global__ void __launch_bounds__(128) k_candidates(const int32_t* __restrict__ T, long long nt, long long nv,
-                             const int32_t* __restrict__ Xi, const int32_t* __restrict__ Ci,
-                             const long long* __restrict__ W, const int32_t* __restrict__ knn,
-                             const long long* __restrict__ dplus, int K, int32_t* __restrict__ cand_cnt,
-                             int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, int32_t* __restrict__ fb_list,
-                             int32_t* __restrict__ fb_count, DevState* st) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+// One warp per tet: the gathered spheres live one per lane.
+__global__ void __launch_bounds__(256) k_candidates_warp(
+    const int32_t* __restrict__ T, long long nt, long long nv, const int32_t* __restrict__ Xi,
+    const int32_t* __restrict__ Ci, const long long* __restrict__ W, const int32_t* __restrict__ knn,
+    const long long* __restrict__ dplus, int K, int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand,
+    uint8_t* __restrict__ cand_ord, int32_t* __restrict__ fb_list, int32_t* __restrict__ fb_count, DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;   // warp-uniform
     int v[4];
     int3 X[4];
     if (!load_tet(T, t, nv, Xi, v, X)) {
-        cand_cnt[t] = 0;
+        if (lane == 0) cand_cnt[t] = 0;
         return;
     }
     int o[4];
-    long long dp[4], M[4][4];
+    long long dp[4];
+#pragma unroll
     for (int a = 0; a < 4; a++) {
         o[a] = knn[(long long)v[a] * K];
         dp[a] = dplus[v[a]];
     }
-    for (int b = 0; b < 4; b++) {
-        int3 cb = ld_int3(Ci, o[b]);
-        long long wb = W[o[b]];
-        for (int a = 0; a < 4; a++) M[a][b] = pd_exact(X[a], cb, wb);
+    // M(a, b) = pd(X_a, owner of corner b), one entry per lane 0..15
+    long long Ml = 0;
+    if (lane < 16) {
+        const int a = lane >> 2, b = lane & 3;
+        const int ob = b == 0 ? o[0] : (b == 1 ? o[1] : (b == 2 ? o[2] : o[3]));
+        const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
+        Ml = pd_exact(xa, ld_int3(Ci, ob), W[ob]);
     }
     int bstar = -1;
     long long best = LLONG_MAX;
+#pragma unroll
     for (int b = 0; b < 4; b++) {
         bool complete = true;
         long long score = 0;
+#pragma unroll
         for (int a = 0; a < 4; a++) {
-            complete &= dp[a] > M[a][b];
-            score = max(score, M[a][b] - M[a][a]);
+            const long long mab = __shfl_sync(0xffffffffu, Ml, a * 4 + b);
+            const long long maa = __shfl_sync(0xffffffffu, Ml, a * 4 + a);
+            complete &= dp[a] > mab;
+            score = max(score, mab - maa);
         }
         if (complete && score < best) {
             best = score;
@@ -338,37 +475,67 @@ __global__ void __launch_bounds__(128) k_candidates(const int32_t* __restrict__ 
         }
     }
     if (bstar < 0) {
-        int slot = atomicAdd(fb_count, 1);
-        fb_list[slot] = (int32_t)t;
-        cand_cnt[t] = 0;
+        if (lane == 0) {
+            fb_list[atomicAdd(fb_count, 1)] = (int32_t)t;
+            cand_cnt[t] = 0;
+        }
         return;
     }
-    Gathered G[RPD_GATHER];
-    int n = 0;
+    int sid = -1, nheld = 0;
+#pragma unroll
     for (int a = 0; a < 4; a++) {
-        long long thr = M[a][bstar];
-        for (int j = 0; j < K; j++) {
-            int s = knn[(long long)v[a] * K + j];
-            if (s < 0) break;
-            int3 cs = ld_int3(Ci, s);
-            long long ws = W[s];
-            long long d = pd_exact(X[a], cs, ws);
-            if (d > thr) break;                       // lists are sorted by distance
-            bool dup = false;
-            for (int q = 0; q < n && !dup; q++) dup = (G[q].id == s);
-            if (dup) continue;
-            if (n == RPD_GATHER) {
-                int slot = atomicAdd(fb_count, 1);
-                fb_list[slot] = (int32_t)t;
+        const long long thr = __shfl_sync(0xffffffffu, Ml, a * 4 + bstar);
+        const int s = lane < K ? knn[(long long)v[a] * K + lane] : -1;
+        bool in = false;
+        if (s >= 0) in = pd_exact(X[a], ld_int3(Ci, s), W[s]) <= thr;
+        for (int h = 0; h < nheld; h++)
+            if (__shfl_sync(0xffffffffu, sid, h) == s) in = false;
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+        const int cnt = __popc(mask);
+        if (nheld + cnt > 32) {
+            if (lane == 0) {
+                fb_list[atomicAdd(fb_count, 1)] = (int32_t)t;
                 cand_cnt[t] = 0;
-                return;
             }
-            G[n].id = s;
-            for (int c = 0; c < 4; c++) G[n].D[c] = pd_exact(X[c], cs, ws);
-            n++;
+            return;
         }
+        const bool take = lane >= nheld && lane < nheld + cnt;
+        const int src = take ? __fns(mask, 0, lane - nheld + 1) : 0;
+        const int sn = __shfl_sync(0xffffffffu, s, src);
+        if (take) sid = sn;
+        nheld += cnt;
     }
-    finish_candidates<RPD_GATHER>(G, n, t, cand_cnt, cand, cand_ord, st);
+    const bool held = lane < nheld;
+    long long D[4] = {0, 0, 0, 0};
+    if (held) {
+        const int3 cs = ld_int3(Ci, sid);
+        const long long ws = W[sid];
+#pragma unroll
+        for (int c = 0; c < 4; c++) D[c] = pd_exact(X[c], cs, ws);
+    }
+    // exact corner filter against every other gathered sphere
+    bool ok = held;
+    for (int j = 0; j < nheld; j++) {
+        bool some = false;
+#pragma unroll
+        for (int c = 0; c < 4; c++) some |= D[c] <= __shfl_sync(0xffffffffu, D[c], j);
+        if (j != lane) ok = ok && some;
+    }
+    const unsigned kmask = __ballot_sync(0xffffffffu, ok);
+    const long long key = D[0] + D[1] + D[2] + D[3];
+    int rank = 0, rank2 = 0;
+    for (unsigned m = kmask; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const int sj = __shfl_sync(0xffffffffu, sid, j);
+        const long long kj = __shfl_sync(0xffffffffu, key, j);
+        rank += sj < sid;
+        rank2 += (kj < key) || (kj == key && sj < sid);
+    }
+    if (ok) {
+        cand[t * RPD_MAXC + rank] = sid;
+        cand_ord[t * RPD_MAXC + rank2] = (uint8_t)rank;
+    }
+    if (lane == 0) cand_cnt[t] = __popc(kmask);
 }
 
 #define RPD_FB_GATHER 128
@@ -463,7 +630,8 @@ size_t grid_tmp_bytes(long long ns, long long ncap) {
 }
 
 void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
-                        int64_t* cell_start, int32_t* cell_ids, long long* cell_wmax, void* tmp, cudaStream_t s) {
+                        int64_t* cell_start, int32_t* cell_ids, int4* cell_sph, long long* cell_w,
+                        long long* cell_wmax, void* tmp, cudaStream_t s) {
     char* p = (char*)tmp;
     int32_t* count = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
     int32_t* fill = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
@@ -474,14 +642,14 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
     cudaMemsetAsync(cell_wmax, 0, sizeof(long long) * ncap, s);
     k_cell_count<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, count, cell_wmax);
     scan_excl(count, cell_start, ncap, stmp, s);
-    k_cell_fill<<<nblk(ns, 256), 256, 0, s>>>(Ci, ns, gp, cell_start, fill, cell_ids);
+    k_cell_fill<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, cell_start, fill, cell_ids, cell_sph, cell_w);
 }
 
 void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
-                const int64_t* cell_start, const int32_t* cell_ids, const long long* cell_wmax, int K,
-                int32_t* knn, long long* dplus, cudaStream_t s) {
+                const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, int K, int32_t* knn,
+                long long* dplus, cudaStream_t s) {
     if (nv == 0) return;
-    k_knn<<<nblk(nv, 128), 128, 0, s>>>(Xi, nv, Ci, W, gp, cell_start, cell_ids, cell_wmax, K, knn, dplus);
+    k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nv, Ci, W, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
 }
 
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
@@ -491,7 +659,8 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
                        DevState* st, cudaStream_t s) {
     if (nt == 0) return;
     cudaMemsetAsync(fb_count, 0, sizeof(int32_t), s);
-    k_candidates<<<nblk(nt, 128), 128, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand, cand_ord,
+    k_candidates_warp<<<nblk(32 * nt, 256), 256, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand,
+                                                          cand_ord,
                                                fb_list, fb_count, st);
     k_candidates_fallback<<<152, 64, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids, cell_wmax,
                                              fb_list, fb_count, cand_cnt, cand, cand_ord, st);

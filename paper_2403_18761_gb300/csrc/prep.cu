@@ -72,7 +72,8 @@ __device__ __forceinline__ void sort3(unsigned long long& a, unsigned long long&
 }
 
 // Face f of a tet is the triangle opposite local vertex f.
-__global__ void k_face_keys(const int32_t* __restrict__ T, long long nt, uint64_t* __restrict__ key,
+// Vertex ids use vb bits (nv <= 2^vb), so a face key has 3 vb bits.
+__global__ void k_face_keys(const int32_t* __restrict__ T, long long nt, int vb, uint64_t* __restrict__ key,
                             uint32_t* __restrict__ val) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * nt) return;
@@ -81,22 +82,23 @@ __global__ void k_face_keys(const int32_t* __restrict__ T, long long nt, uint64_
     unsigned long long v[3];
     int n = 0;
     for (int c = 0; c < 4; c++)
-        if (c != f) v[n++] = (unsigned)T[4 * t + c];
+        if (c != f) v[n++] = (unsigned)T[4 * t + c] & ((1u << vb) - 1u);
     sort3(v[0], v[1], v[2]);
-    key[i] = (v[0] << 42) | (v[1] << 21) | v[2];
+    key[i] = (v[0] << (2 * vb)) | (v[1] << vb) | v[2];
     val[i] = (uint32_t)i;
 }
 
-__global__ void k_edge_keys(const int32_t* __restrict__ T, long long nt, uint64_t* __restrict__ key,
+__global__ void k_edge_keys(const int32_t* __restrict__ T, long long nt, int vb, uint64_t* __restrict__ key,
                             uint32_t* __restrict__ val) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 6 * nt) return;
     long long t = i / 6;
     int e = (int)(i - 6 * t);
     const int EA[6] = {0, 0, 0, 1, 1, 2}, EB[6] = {1, 2, 3, 2, 3, 3};
-    unsigned long long a = (unsigned)T[4 * t + EA[e]], b = (unsigned)T[4 * t + EB[e]];
+    unsigned long long a = (unsigned)T[4 * t + EA[e]] & ((1u << vb) - 1u);
+    unsigned long long b = (unsigned)T[4 * t + EB[e]] & ((1u << vb) - 1u);
     if (a > b) { unsigned long long s = a; a = b; b = s; }
-    key[i] = (a << 21) | b;
+    key[i] = (a << vb) | b;
     val[i] = (uint32_t)i;
 }
 
@@ -194,13 +196,15 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
     k_check_tets<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, Xi, st);
     cudaMemsetAsync(own, 0, sizeof(uint32_t) * nt, s);
     cudaMemsetAsync(adj, 0xff, sizeof(int32_t) * 4 * nt, s);
+    int vb = 1;
+    while ((1ll << vb) < nv) vb++;
     // faces
-    k_face_keys<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, k0, v0);
-    radix_sort_pairs(k0, v0, k1, v1, 4 * nt, 63, rtmp, s);
+    k_face_keys<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
+    radix_sort_pairs(k0, v0, k1, v1, 4 * nt, 3 * vb, rtmp, s);
     k_face_runs<<<nblk(4 * nt, T), T, 0, s>>>(k1, v1, 4 * nt, adj, own, st);
     // edges
-    k_edge_keys<<<nblk(n6, T), T, 0, s>>>(d_tets, nt, k0, v0);
-    radix_sort_pairs(k0, v0, k1, v1, n6, 42, rtmp, s);
+    k_edge_keys<<<nblk(n6, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
+    radix_sort_pairs(k0, v0, k1, v1, n6, 2 * vb, rtmp, s);
     k_edge_runs<<<nblk(n6, T), T, 0, s>>>(k1, v1, n6, own);
     // vertices
     k_fill_i32<<<nblk(nv, T), T, 0, s>>>(vmin, nv, 0x7fffffff);

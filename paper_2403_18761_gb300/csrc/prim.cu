@@ -125,7 +125,45 @@ __global__ void rs_hist(const uint64_t* __restrict__ keys, long long n, int shif
         if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
     }
     __syncthreads();
-    hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    hist[(long long)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
+}
+
+// Global offsets per (block, digit): digit-major exclusive scan of the
+// block-major histogram, one thread per digit (256 threads, one block).
+__global__ void rs_scan_hist(const uint32_t* __restrict__ hist, int nblocks, int64_t* __restrict__ hoff) {
+    __shared__ long long base[256];
+    const int d = threadIdx.x;
+    long long s = 0;
+    for (int b = 0; b < nblocks; b++) s += hist[(long long)b * 256 + d];
+    base[d] = s;
+    __syncthreads();
+    if (d < 32) {
+        // exclusive scan of the 256 digit totals by one warp (8 per lane)
+        long long v[8], run = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            v[k] = base[d * 8 + k];
+            run += v[k];
+        }
+        long long inc = run;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            long long o = __shfl_up_sync(0xffffffffu, inc, off);
+            if (d >= off) inc += o;
+        }
+        long long pre = inc - run;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            base[d * 8 + k] = pre;
+            pre += v[k];
+        }
+    }
+    __syncthreads();
+    s = base[d];
+    for (int b = 0; b < nblocks; b++) {
+        hoff[(long long)b * 256 + d] = s;
+        s += hist[(long long)b * 256 + d];
+    }
 }
 
 __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
@@ -135,7 +173,7 @@ __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __r
     __shared__ int64_t goff[256];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < RS_WARPS * 256; k += RS_THREADS) (&wh[0][0])[k] = 0;
-    goff[threadIdx.x] = hoff[(long long)threadIdx.x * nblocks + blockIdx.x];
+    goff[threadIdx.x] = hoff[(long long)blockIdx.x * 256 + threadIdx.x];
     __syncthreads();
     long long base = (long long)blockIdx.x * RS_TILE + (long long)w * (RS_TILE / RS_WARPS);
     uint64_t key[RS_ROUNDS];
@@ -269,7 +307,6 @@ void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t
     uint32_t* vb = (uint32_t*)p; p += align256(sizeof(uint32_t) * n);
     uint32_t* hist = (uint32_t*)p; p += align256(sizeof(uint32_t) * nh);
     int64_t* hoff = (int64_t*)p; p += align256(sizeof(int64_t) * (nh + 1));
-    void* stmp = p;
     const uint64_t* ksrc = keys_in;
     const uint32_t* vsrc = vals_in;
     for (int q = 0; q < passes; q++) {
@@ -278,7 +315,7 @@ void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t
         uint32_t* vdst = lastp ? vals_out : ((q & 1) ? vb : va);
         int shift = 8 * q;
         rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, n, shift, hist, (int)nb);
-        scan_impl<int32_t>((const int32_t*)hist, hoff, nh, stmp, s);
+        rs_scan_hist<<<1, 256, 0, s>>>(hist, (int)nb, hoff);
         rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, vsrc, kdst, vdst, n, shift, hoff, (int)nb);
         ksrc = kdst;
         vsrc = vdst;
