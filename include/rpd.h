@@ -145,6 +145,32 @@ const char* rpd_build_error(void);
 /* Release the context and all its device memory (synchronises its stream). */
 void rpd_destroy(rpd_ctx* ctx);
 
+/*
+ * rpd_build + rpd_euler in one call that allocates no device memory.  The
+ * paper has no counterpart; this is a convenience of the library.
+ *
+ * For callers that cannot call cudaMalloc when they need the result: work
+ * recorded into a CUDA graph (allocation is illegal during stream capture),
+ * or pipelines that fix their device-memory budget up front.  All workspace
+ * comes from one file-scope device array of 32 MiB that every GPU loading the
+ * library holds until the process exits (enough for roughly 30k tets; larger
+ * problems are rejected with RPD_E_OVERFLOW before the stage that would need
+ * more).  No cudaMalloc, cudaFree or other allocating routine is called.
+ *   inputs  as rpd_build (caller-owned device memory; opt may be NULL)
+ *   kind    element kind whose chi is returned
+ *   d_keys  i32[n*kind], d_chi i32[n]: caller-owned outputs, cap >= n; both
+ *           NULL only sets *n
+ *   n       host pointer, receives the number of elements
+ * The first call on a device looks up the array's device address: make it
+ * before any stream capture.  Every call reuses the same array (it is
+ * cleared as needed), so calls that overlap on the GPU race: serialise them.
+ * Synchronises the stream.  Errors are reported by status only.
+ */
+rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt,
+                            const double* d_centers, const double* d_radii, int64_t ns, const rpd_options* opt,
+                            void* cuda_stream, rpd_kind kind, int32_t* d_keys, int32_t* d_chi, int64_t cap,
+                            int64_t* n);
+
 #ifdef __cplusplus
 }
 #endif
