@@ -28,6 +28,27 @@ long long alloc_budget() {
     return g_alloc_budget;
 }
 
+// One stream-ordered memory pool per device, owned by the library, that keeps
+// freed workspace cached (release threshold = max) so that repeated builds
+// reuse it instead of mapping fresh memory at every synchronisation.
+cudaMemPool_t library_pool() {
+    static cudaMemPool_t pools[64];
+    static bool ready[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ready[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) return nullptr;
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+        ready[dev] = true;
+    }
+    return pools[dev];
+}
+
 }  // namespace
 
 struct rpd_ctx {
@@ -86,7 +107,8 @@ struct rpd_ctx {
             return nullptr;
         }
         void* p = nullptr;
-        if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaMemPool_t pool = library_pool();
+        if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) {
             cudaGetLastError();
             failed_alloc = true;
             return nullptr;

@@ -183,181 +183,149 @@ __global__ void k_cell_fill(const int32_t* __restrict__ Ci, const long long* __r
 }
 
 // ---------------------------------------------------------------- kNN
-// One warp per mesh vertex.  The current K best (power distance, sphere)
-// pairs live one per lane, sorted by lane; the spheres of a grid cell are
-// evaluated 32 at a time, bitonic-sorted across the lanes and merged into
-// the list.  Every sphere or cell left out contributes to D+.
+// Tiled form: one lane per mesh vertex, 32 consecutive vertices per warp.
+// The warp walks box shells around the bounding box of its vertices' cells;
+// each row run of the cell-sorted spheres is loaded 32 at a time (coalesced)
+// and broadcast by shuffles, and every lane tests every sphere against its
+// own vertex.  Each lane keeps its K best (distance, id) sorted in shared
+// memory; everything it rejects, evicts or leaves unexplored lowers its D+.
+// A lane is done once the next shell's distance bound minus max r^2 exceeds
+// its K-th distance; the warp stops when all lanes are done.
+
 __device__ __forceinline__ bool pair_less(long long d1, int i1, long long d2, int i2) {
     return d1 < d2 || (d1 == d2 && i1 < i2);
 }
 
-// Bitonic compare-exchange with the lane at distance j; `up` = ascending block.
-__device__ __forceinline__ void cmpx(long long& d, int& id, int j, bool up) {
-    const int lane = threadIdx.x & 31;
-    const long long od = __shfl_xor_sync(0xffffffffu, d, j);
-    const int oi = __shfl_xor_sync(0xffffffffu, id, j);
-    const bool lower = (lane & j) == 0;
-    const bool want_min = (lower == up);
-    const bool other_smaller = pair_less(od, oi, d, id);
-    if (want_min ? other_smaller : (!other_smaller && (od != d || oi != id))) {
-        d = od;
-        id = oi;
+// Lower bound of |x - y|^2 over cells outside the box [lo, hi] (cell
+// indices); LLONG_MAX when the box covers the whole grid.
+__device__ __forceinline__ long long outside_box_lb2(int3 x, const GridParams& g, int3 lo, int3 hi) {
+    long long best = LLONG_MAX;
+    const int xs[3] = {x.x, x.y, x.z}, ls[3] = {lo.x, lo.y, lo.z}, hs[3] = {hi.x, hi.y, hi.z},
+              ds[3] = {g.dim.x, g.dim.y, g.dim.z}, os[3] = {g.org.x, g.org.y, g.org.z};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (hs[a] + 1 <= ds[a] - 1) {
+            long long start = (long long)os[a] + (long long)(hs[a] + 1) * g.cell;
+            best = min(best, max(0LL, start - xs[a]));
+        }
+        if (ls[a] - 1 >= 0) {
+            long long end = (long long)os[a] + (long long)ls[a] * g.cell - 1;
+            best = min(best, max(0LL, (long long)xs[a] - end));
+        }
     }
+    return best == LLONG_MAX ? LLONG_MAX : best * best;
 }
 
-__device__ __forceinline__ void warp_sort32(long long& d, int& id) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) cmpx(d, id, j, (lane & k) == 0 || k == 32);
-}
-
-// L (sorted) <- the 32 smallest of L and B (sorted); returns the smallest
-// distance that was dropped (LLONG_MAX if none).
-__device__ __forceinline__ long long warp_merge32(long long& d, int& id, long long bd, int bi) {
-    const int lane = threadIdx.x & 31;
-    const long long rd = __shfl_sync(0xffffffffu, bd, 31 - lane);
-    const int ri = __shfl_sync(0xffffffffu, bi, 31 - lane);
-    long long dropped;
-    if (pair_less(rd, ri, d, id)) {
-        dropped = d;
-        d = rd;
-        id = ri;
-    } else {
-        dropped = rd;
-    }
-#pragma unroll
-    for (int j = 16; j > 0; j >>= 1) cmpx(d, id, j, true);
-    long long m = dropped;
-#pragma unroll
-    for (int off = 16; off; off >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, off));
-    return m;
-}
-
-__global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, long long nv,
-                                                   const int32_t* __restrict__ Ci, const long long* __restrict__ W,
+template <int KMAX>
+__global__ void __launch_bounds__(128) k_knn_tile(const int32_t* __restrict__ Xi, long long nv,
                                                    const GridParams* __restrict__ gp,
                                                    const int64_t* __restrict__ start, const int4* __restrict__ sph,
                                                    const long long* __restrict__ sw, int K,
                                                    int32_t* __restrict__ knn, long long* __restrict__ dplus) {
-    const int lane = threadIdx.x & 31;
-    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (v >= nv) return;   // warp-uniform
+    __shared__ long long sd_all[4][KMAX][32];
+    __shared__ int si_all[4][KMAX][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long(*sd)[32] = sd_all[warp];
+    int(*si)[32] = si_all[warp];
+    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const long long vbase = v - lane;
+    if (vbase >= nv) return;   // warp-uniform
+    const bool valid = v < nv;
     const GridParams g = *gp;
-    const int3 x = ld_int3(Xi, v);
+    const int3 x = valid ? ld_int3(Xi, v) : ld_int3(Xi, vbase);
     const int3 c = cell_of(x, g);
-    long long d = LLONG_MAX;
-    int id = 0x7fffffff;
-    long long dp = LLONG_MAX;
-    long long kd = LLONG_MAX;   // K-th distance (warp-uniform)
+    // bounding box of the warp's cells
+    int3 lo, hi;
+    lo.x = __reduce_min_sync(0xffffffffu, c.x);
+    lo.y = __reduce_min_sync(0xffffffffu, c.y);
+    lo.z = __reduce_min_sync(0xffffffffu, c.z);
+    hi.x = __reduce_max_sync(0xffffffffu, c.x);
+    hi.y = __reduce_max_sync(0xffffffffu, c.y);
+    hi.z = __reduce_max_sync(0xffffffffu, c.z);
+    int cnt = 0;                 // entries in this lane's list
+    long long kd = LLONG_MAX;    // this lane's K-th distance (LLONG_MAX while short)
     int ki = 0x7fffffff;
-    // Bands of Chebyshev shells r_lo < r <= r_hi around c; the lanes stride
-    // over the cells of the band's bounding box.
-    int r_done = -1;
-    for (int iter = 0; iter < 64; iter++) {
-        // next band: while the list is short grow by one ring, otherwise take
-        // every ring that can still hold a sphere closer than the K-th
-        const int rn = r_done + 1;   // first unexplored ring
-        if (rn > 0) {
-            const long long lb2 = ring_lb2(x, g, c, rn);
-            if (lb2 == LLONG_MAX) break;                          // no cells left
-            if (kd != LLONG_MAX && lb2 - g.wmax > kd) {
+    long long dp = LLONG_MAX;
+    bool done = !valid;
+    int3 plo = make_int3(1, 1, 1), phi = make_int3(0, 0, 0);   // processed box (empty)
+    for (int r = 0; r < 4096; r++) {
+        const int3 blo = make_int3(max(lo.x - r, 0), max(lo.y - r, 0), max(lo.z - r, 0));
+        const int3 bhi = make_int3(min(hi.x + r, g.dim.x - 1), min(hi.y + r, g.dim.y - 1), min(hi.z + r, g.dim.z - 1));
+        // rows (y, z) of the new shell: whole rows outside the processed
+        // box's (y, z) range, else the parts left and right of it
+        for (int zz = blo.z; zz <= bhi.z; zz++) {
+            for (int yy = blo.y; yy <= bhi.y; yy++) {
+                const bool inner = zz >= plo.z && zz <= phi.z && yy >= plo.y && yy <= phi.y;
+                for (int part = 0; part < (inner ? 2 : 1); part++) {
+                    int xa = blo.x, xb = bhi.x;
+                    if (inner) {
+                        if (part == 0) xb = plo.x - 1;
+                        else xa = phi.x + 1;
+                    }
+                    if (xa > xb) continue;
+                    const int qrow = (zz * g.dim.y + yy) * g.dim.x;
+                    const long long e0 = start[qrow + xa], e1 = start[qrow + xb + 1];
+                    for (long long eb = e0; eb < e1; eb += 32) {
+                        const long long e = eb + lane;
+                        int4 cs = make_int4(0, 0, 0, 0);
+                        long long ws = 0;
+                        if (e < e1) {
+                            cs = sph[e];
+                            ws = sw[e];
+                        }
+                        const int nb = (int)min(32LL, e1 - eb);
+                        for (int jj = 0; jj < nb; jj++) {
+                            const int3 cj = make_int3(__shfl_sync(0xffffffffu, cs.x, jj), __shfl_sync(0xffffffffu, cs.y, jj),
+                                                      __shfl_sync(0xffffffffu, cs.z, jj));
+                            const int idj = __shfl_sync(0xffffffffu, cs.w, jj);
+                            const long long wj = __shfl_sync(0xffffffffu, ws, jj);
+                            if (done) continue;
+                            const long long d = pd_exact(x, cj, wj);
+                            if (cnt == K && !pair_less(d, idj, kd, ki)) {
+                                dp = min(dp, d);
+                                continue;
+                            }
+                            // insert into the sorted list (evicting the K-th when full)
+                            int pos = cnt < K ? cnt : K - 1;
+                            if (cnt == K) dp = min(dp, sd[K - 1][lane]);
+                            while (pos > 0 && pair_less(d, idj, sd[pos - 1][lane], si[pos - 1][lane])) {
+                                sd[pos][lane] = sd[pos - 1][lane];
+                                si[pos][lane] = si[pos - 1][lane];
+                                pos--;
+                            }
+                            sd[pos][lane] = d;
+                            si[pos][lane] = idj;
+                            if (cnt < K) cnt++;
+                            if (cnt == K) {
+                                kd = sd[K - 1][lane];
+                                ki = si[K - 1][lane];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        plo = blo;
+        phi = bhi;
+        // lane termination: the next shell cannot hold a sphere within kd
+        const long long lb2 = outside_box_lb2(x, g, blo, bhi);
+        if (!done) {
+            if (lb2 == LLONG_MAX) {
+                done = true;
+            } else if (cnt == K && lb2 - g.wmax > kd) {
                 dp = min(dp, lb2 - g.wmax);
-                break;
+                done = true;
             }
         }
-        int r_hi;
-        if (kd == LLONG_MAX) {
-            r_hi = rn == 0 ? 1 : 2 * rn + 1;                      // list still short: grow geometrically
-        } else {
-            r_hi = rn;
-            while (r_hi < 4096) {
-                const long long nb2 = ring_lb2(x, g, c, r_hi + 1);
-                if (nb2 == LLONG_MAX || nb2 - g.wmax > kd) break;
-                r_hi++;
-            }
-        }
-        const int x0 = max(-r_hi, -c.x), x1 = min(r_hi, g.dim.x - 1 - c.x);
-        const int y0 = max(-r_hi, -c.y), y1 = min(r_hi, g.dim.y - 1 - c.y);
-        const int z0 = max(-r_hi, -c.z), z1 = min(r_hi, g.dim.z - 1 - c.z);
-        const int ey = y1 - y0 + 1;
-        const int nrow = ey * (z1 - z0 + 1);
-        // A row (dy, dz) of cells is one contiguous run of the cell-sorted
-        // sphere array; rows inside the explored cube split into two runs.
-        int j = lane - 32, seg = 2;
-        long long e = 0, e1 = 0;
-        bool done = false;
-        for (int round = 0; round < (1 << 20); round++) {
-            // advance to this lane's next candidate
-            long long sd = LLONG_MAX;
-            int si = 0x7fffffff;
-            bool cand = false;
-            while (!done && !cand) {
-                if (e < e1) {
-                    const int4 cs = sph[e];
-                    const long long ds = pd_exact(x, make_int3(cs.x, cs.y, cs.z), sw[e]);
-                    e++;
-                    if (kd == LLONG_MAX || pair_less(ds, cs.w, kd, ki)) {
-                        sd = ds;
-                        si = cs.w;
-                        cand = true;
-                    } else {
-                        dp = min(dp, ds);
-                    }
-                    continue;
-                }
-                if (seg >= 2) {
-                    j += 32;
-                    if (j >= nrow) {
-                        done = true;
-                        break;
-                    }
-                    seg = 0;
-                }
-                const int dy = y0 + j % ey, dz = z0 + j / ey;
-                const bool inner = abs(dy) <= r_done && abs(dz) <= r_done;
-                int xa, xb;
-                if (!inner) {
-                    xa = x0;
-                    xb = x1;
-                    seg = 2;
-                } else if (seg == 0) {
-                    xa = x0;
-                    xb = -r_done - 1;
-                    seg = 1;
-                } else {
-                    xa = r_done + 1;
-                    xb = x1;
-                    seg = 2;
-                }
-                if (xa > xb) continue;
-                const int qrow = ((c.z + dz) * g.dim.y + (c.y + dy)) * g.dim.x + c.x;
-                e = start[qrow + xa];
-                e1 = start[qrow + xb + 1];
-            }
-            if (!__any_sync(0xffffffffu, cand)) {
-                if (__all_sync(0xffffffffu, done)) break;
-                continue;
-            }
-            warp_sort32(sd, si);
-            dp = min(dp, warp_merge32(d, id, sd, si));
-            kd = __shfl_sync(0xffffffffu, d, K - 1);
-            ki = __shfl_sync(0xffffffffu, id, K - 1);
-        }
-        r_done = r_hi;
+        if (__all_sync(0xffffffffu, done)) break;
     }
-    {   // whatever was not explored is bounded by the next ring
-        const long long lbu = ring_lb2(x, g, c, r_done + 1);
+    if (!valid) return;
+    {   // whatever was not explored is bounded by the last box
+        const long long lbu = outside_box_lb2(x, g, plo, phi);
         if (lbu != LLONG_MAX) dp = min(dp, lbu - g.wmax);
     }
-    // entries beyond the K-th are left out too
-    long long tail = (lane >= K) ? d : LLONG_MAX;
-    dp = min(dp, tail);
-#pragma unroll
-    for (int off = 16; off; off >>= 1) dp = min(dp, __shfl_xor_sync(0xffffffffu, dp, off));
-    if (lane < K) knn[v * K + lane] = d == LLONG_MAX ? -1 : id;
-    if (lane == 0) dplus[v] = dp;
+    for (int j = 0; j < K; j++) knn[v * K + j] = j < cnt ? si[j][lane] : -1;
+    dplus[v] = dp;
 }
 
 // ---------------------------------------------------------- candidates
@@ -649,7 +617,7 @@ void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long l
                 const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, int K, int32_t* knn,
                 long long* dplus, cudaStream_t s) {
     if (nv == 0) return;
-    k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nv, Ci, W, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
+    k_knn_tile<RPD_MAXK><<<nblk(nv, 128), 128, 0, s>>>(Xi, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
 }
 
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
