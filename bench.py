@@ -33,6 +33,47 @@ WORKLOADS = {
 }
 
 
+# Algorithmic FP32 work of the clip stage (Tet-Cell clipping, Sec. 5.2):
+# one filtered sign test F.C of a live polytope vertex against a new radical
+# plane is 3 FMA + 1 MUL = 7 flop (its error bound is stored with the vertex);
+# one vertex constructed on a new plane is four 3x3 cofactors (4 x 14 flop),
+# the orientation test with its bound (10 flop) and the stored bound (7 flop).
+FLOP_SIGN_TEST = 7
+FLOP_NEW_VERTEX = 73
+FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per clip stage from one ncu capture of the
+# current clip kernels on this workload; None until captured for this code.
+CLIP_TRAFFIC_BYTES = None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def clip_roofline(stage, n_sm):
+    """FP32 ALU roofline of the clip stage, from the counters of the timed steps."""
+    peaks = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    flop, ms = [], []
+    for s in stage:
+        tests = s["pred_fast"] + s["pred_fp64"] + s["pred_exact"]
+        nv = s["clip_vertices"]
+        flop.append(FLOP_SIGN_TEST * max(tests - nv, 0) + FLOP_NEW_VERTEX * nv)
+        ms.append(s["ms_clip"])
+    achieved = float(np.mean(flop)) / (float(np.mean(ms)) * 1e-3) / 1e12
+    return {"kernel": "k_clip (all candidate-count bins) + k_whole: the clip stage",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": CLIP_TRAFFIC_BYTES, "flop_per_launch": float(np.mean(flop)),
+            "ms_per_launch": float(np.mean(ms)),
+            "peak_source": f"derived FP32: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz:.0f} MHz "
+                           "(sm_max_mhz of MEASURED_PEAKS.json)"}
+
+
 def make_workload(name):
     import rpd_inputs
     return rpd_inputs.CONFIGS[name]()
@@ -171,7 +212,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2403_18761_gb300 import rpd_build
+    from paper_2403_18761_gb300 import rpd_build, rpd_launch_count
     from paper_2403_18761_gb300.rpd import rpd_stats
 
     rank, world, local = dist_env()
@@ -208,6 +249,7 @@ def main():
         if world > 1:
             dist.barrier()
         ms, stage, pieces = [], [], 0
+        launches0 = rpd_launch_count()
         with ClockSampler(local) as clk:
             for _ in range(args.steps):
                 flush.fill_(1)
@@ -222,6 +264,7 @@ def main():
                 pieces += st["n_pieces"]
                 ctx.rpd_destroy()
         torch.cuda.synchronize()
+    launches = rpd_launch_count() - launches0
     clocks = clk.summary()
     t_step = max(ms)
     if world > 1:
@@ -268,11 +311,15 @@ def main():
                    "spheres": int(w.ns), "pieces_per_step": int(last["n_pieces"]),
                    "l2": "256 MB buffer written between timed steps", "parallelism": "replicas"},
         "stages_ms": st_mean,
-        "predicates": {"fast": last["pred_fast"], "fp64": last["pred_fp64"], "exact": last["pred_exact"]},
+        "predicates": {"fast": last["pred_fast"], "fp64": last["pred_fp64"], "exact": last["pred_exact"],
+                       "vertices_constructed": last["clip_vertices"]},
         "pairs": {"total": last["n_pairs"], "by_bin": last["bin_pairs"], "cut_by_bin": last["bin_cut"],
                   "whole_tets": last["whole_tets"], "cand_fallback": last["cand_fallback"], "k": kk},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps,
+        "roofline": clip_roofline(stage, torch.cuda.get_device_properties(dev).multi_processor_count),
         "step_ms_max": t_step,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -78,6 +78,7 @@ typedef struct {
     int64_t pred_exact;       /* ... by exact 256-bit integer arithmetic          */
     int64_t cand_fallback;    /* tets whose candidate set needed the grid search  */
     int64_t whole_tets;       /* tets inside a single cell (no clipping)          */
+    int64_t clip_vertices;    /* polytope vertices constructed by clipping        */
     int64_t bin_pairs[8];     /* candidate pairs by candidate count of their tet:
                                  1, 2, 3, 4, 5-6, 7-8, 9-16, 17-32                */
     int64_t bin_cut[8];       /* nonempty pieces that were cut, per bin           */
@@ -144,6 +145,11 @@ const char* rpd_build_error(void);
 
 /* Release the context and all its device memory (synchronises its stream). */
 void rpd_destroy(rpd_ctx* ctx);
+
+/* Number of kernel launches the library has issued in this process so far
+ * (all contexts, all devices; a host-side counter, no synchronisation).  The
+ * difference around a call counts that call's launches. */
+int64_t rpd_launch_count(void);
 
 /*
  * rpd_build + rpd_euler in one call that allocates no device memory.  The

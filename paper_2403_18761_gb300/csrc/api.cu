@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,6 +30,8 @@ long long alloc_budget() {
     return g_alloc_budget;
 }
 
+std::atomic<long long> g_launches{0};
+
 // One stream-ordered memory pool per device, owned by the library, that keeps
 // freed workspace cached (release threshold = max) so that repeated builds
 // reuse it instead of mapping fresh memory at every synchronisation.
@@ -50,6 +54,8 @@ cudaMemPool_t library_pool() {
 }
 
 }  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct rpd_ctx {
     cudaStream_t stream = nullptr;
@@ -156,6 +162,7 @@ rpd_status check_device(rpd_ctx* c) {
     c->stats.pred_exact = (int64_t)h.cnt[CNT_PRED_EXACT];
     c->stats.cand_fallback = (int64_t)h.cnt[CNT_CAND_FALLBACK];
     c->stats.whole_tets = (int64_t)h.cnt[CNT_WHOLE];
+    c->stats.clip_vertices = (int64_t)h.cnt[CNT_NEWVERT];
     if (h.err != 0) return fail(c, (rpd_status)h.err, dev_reason(h.err, h.cnt));
     return RPD_OK;
 }
@@ -183,25 +190,66 @@ int bits_for(long long ns) {
         if (!(ptr)) return fail(c, RPD_E_OOM, "device allocation failed");    \
     } while (0)
 
+// Library-owned side streams (one per bin) and events, per device, used to
+// run the clip bins concurrently: the few heavy pairs of the high bins are
+// latency-bound and overlap with the throughput-bound low bins.
+struct BinStreams {
+    bool ready = false;
+    cudaStream_t s[RPD_NBINS];
+    cudaEvent_t fork, join[RPD_NBINS];
+};
+
+BinStreams* bin_streams() {
+    static BinStreams per_dev[64];
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    BinStreams& b = per_dev[dev];
+    if (!b.ready) {
+        for (int k = 0; k < RPD_NBINS; k++)
+            if (cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming) != cudaSuccess)
+                return nullptr;
+        if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        b.ready = true;
+    }
+    return &b;
+}
+
 rpd_status run_clip(rpd_ctx* c) {
     cudaStream_t s = c->stream;
-    ClipArgs a = c->clip;
     cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
     cudaMemsetAsync(c->qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
-    long long off = 0;
-    for (int b = 0; b < RPD_NBINS; b++) {
-        long long n = c->hbin[b];
+    long long off[RPD_NBINS + 1];
+    off[0] = 0;
+    for (int b = 0; b < RPD_NBINS; b++) off[b + 1] = off[b] + c->hbin[b];
+    BinStreams* bs = bin_streams();
+    if (bs) cudaEventRecord(bs->fork, s);
+    // heaviest bins first
+    for (int b = RPD_NBINS - 1; b >= 0; b--) {
+        const long long n = c->hbin[b];
+        if (n == 0) continue;
+        cudaStream_t sb = s;
+        if (bs) {
+            sb = bs->s[b];
+            cudaStreamWaitEvent(sb, bs->fork, 0);
+        }
+        ClipArgs a = c->clip;
         if (b == 0) {
-            launch_whole_tets(a, c->bins, c->bin_count, n, s);
-        } else if (n > 0) {
+            launch_whole_tets(a, c->bins, c->bin_count, n, sb);
+        } else {
             a.qpair = c->qpair[b];
             a.qnv = c->qnv[b];
             a.qtrip = c->qtrip[b];
             a.qcap = n;
             a.qcount = c->qcount + b;
-            launch_clip(a, b, c->opt.precision, c->bins + off, c->bin_count + b, n, s);
+            launch_clip(a, b, c->opt.precision, c->bins + off[b], c->bin_count + b, n, sb);
         }
-        off += n;
+        if (bs) {
+            cudaEventRecord(bs->join[b], sb);
+            cudaStreamWaitEvent(s, bs->join[b], 0);
+        }
     }
     return cuda_check(c, "clip launch");
 }
@@ -531,6 +579,8 @@ rpd_status rpd_pieces(rpd_ctx* ctx, int32_t* d_tet, int32_t* d_sphere, double* d
     launch_compact_pieces(ctx->clip, ctx->npairs, ctx->piece_off, d_tet, d_sphere, d_vol, d_moment3, ctx->stream);
     return cuda_check(ctx, "piece launch");
 }
+
+int64_t rpd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 rpd_status rpd_stats_get(const rpd_ctx* ctx, rpd_stats* out) {
     if (!ctx || !out) return RPD_E_INVALID;

@@ -348,7 +348,7 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     long long p = 0;
     int nslot = 0, nlive = 0;
     bool alive = active, whole = true, degenerate = false;
-    unsigned nfast = 0, n64 = 0, nex = 0;
+    unsigned nfast = 0, n64 = 0, nex = 0, nvert = 0;
     const Slow S{A.Ci, A.W, A.st};
     if (active) {
         p = pairs[q];
@@ -547,6 +547,7 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
             V.put_real(h, 4, dot_bound<Real>(m, C));
         }
         if (!alive) break;
+        nvert += nbd;
         nlive += nbd - nout;
     }
     if (degenerate) dev_fail(A.st, RPD_E_DEGENERATE, CNT_DEGENERATE);
@@ -554,6 +555,7 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     dev_count(A.st, CNT_PRED_FAST, nfast);
     dev_count(A.st, CNT_PRED_FP64, n64);
     dev_count(A.st, CNT_PRED_EXACT, nex);
+    dev_count(A.st, CNT_NEWVERT, nvert);
 
     // --------------------------------------------- fractional Euler records
     const int b = A.key_bits;
@@ -1086,6 +1088,7 @@ void launch_clip_t(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, 
         configured = true;
     }
     k_clip<Real, VMAX><<<grid_for(n, 32 * WARPS), 32 * WARPS, smem, s>>>(a, pairs, d_n);
+    note_launch();
 }
 
 template <typename Real>
@@ -1098,6 +1101,7 @@ void launch_volume_t(const ClipArgs& a, int vmax, int warps, long long nmax, cud
         configured = smem;
     }
     k_volume<Real><<<nblk(nmax, 32 * warps), 32 * warps, smem, s>>>(a, vmax);
+    note_launch();
 }
 
 }  // namespace
@@ -1114,18 +1118,22 @@ void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count,
     cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * RPD_NBINS, s);
     if (nt == 0) return;
     k_bin_count<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, nt, bin_count);
+    note_launch();
 }
 
 void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet, int32_t* bins,
                       const int32_t* bin_count, int32_t* bin_fill, cudaStream_t s) {
     if (nt == 0) return;
     k_bin_prefix<<<1, 1, 0, s>>>(bin_count, bin_fill);
+    note_launch();
     k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_fill);
+    note_launch();
 }
 
 void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s) {
     if (nmax <= 0) return;
     k_whole<<<grid_for(nmax, 256), 256, 0, s>>>(a, pairs, d_n);
+    note_launch();
 }
 
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "prim.cuh"
 #include "rpd.h"
 
 #define RPD_MAXC 32          // candidate spheres per tet (one warp of lanes)
@@ -25,6 +26,7 @@ enum {
     CNT_PRED_EXACT,       // decided by exact integers
     CNT_CAND_FALLBACK,    // tets resolved by the grid-search fallback
     CNT_WHOLE,            // whole-tet pieces
+    CNT_NEWVERT,          // polytope vertices constructed by clipping
     CNT_NUM
 };
 

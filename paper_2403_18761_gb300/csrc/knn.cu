@@ -605,12 +605,15 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
     int32_t* fill = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
     void* stmp = p;
     k_bbox<<<1, 1024, 0, s>>>(Ci, W, ns, ncap, gp);
+    note_launch();
     cudaMemsetAsync(count, 0, sizeof(int32_t) * ncap, s);
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncap, s);
     cudaMemsetAsync(cell_wmax, 0, sizeof(long long) * ncap, s);
     k_cell_count<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, count, cell_wmax);
+    note_launch();
     scan_excl(count, cell_start, ncap, stmp, s);
     k_cell_fill<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, cell_start, fill, cell_ids, cell_sph, cell_w);
+    note_launch();
 }
 
 void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
@@ -618,6 +621,7 @@ void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long l
                 long long* dplus, cudaStream_t s) {
     if (nv == 0) return;
     k_knn_tile<RPD_MAXK><<<nblk(nv, 128), 128, 0, s>>>(Xi, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
+    note_launch();
 }
 
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
@@ -630,6 +634,8 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
     k_candidates_warp<<<nblk(32 * nt, 256), 256, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand,
                                                           cand_ord,
                                                fb_list, fb_count, st);
+    note_launch();
     k_candidates_fallback<<<152, 64, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids, cell_wmax,
                                              fb_list, fb_count, cand_cnt, cand, cand_ord, st);
+    note_launch();
 }

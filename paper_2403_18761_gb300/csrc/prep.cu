@@ -169,10 +169,15 @@ void launch_snap(const double* d_verts, long long nv, const double* d_centers, c
                  int grid_bits, int32_t* Xi, int32_t* Ci, long long* W, DevState* st, cudaStream_t s) {
     double scale = ldexp(1.0, grid_bits);
     const int T = 256;
-    if (nv) k_snap_points<<<nblk(3 * nv, T), T, 0, s>>>(d_verts, 3 * nv, scale, Xi, st);
+    if (nv) {
+        k_snap_points<<<nblk(3 * nv, T), T, 0, s>>>(d_verts, 3 * nv, scale, Xi, st);
+        note_launch();
+    }
     if (ns) {
         k_snap_points<<<nblk(3 * ns, T), T, 0, s>>>(d_centers, 3 * ns, scale, Ci, st);
+        note_launch();
         k_snap_radii<<<nblk(ns, T), T, 0, s>>>(d_radii, ns, scale, W, st);
+        note_launch();
     }
 }
 
@@ -194,20 +199,28 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
     int32_t* vmin = (int32_t*)p; p += al(sizeof(int32_t) * nv);
     void* rtmp = p;
     k_check_tets<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, Xi, st);
+    note_launch();
     cudaMemsetAsync(own, 0, sizeof(uint32_t) * nt, s);
     cudaMemsetAsync(adj, 0xff, sizeof(int32_t) * 4 * nt, s);
     int vb = 1;
     while ((1ll << vb) < nv) vb++;
     // faces
     k_face_keys<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
+    note_launch();
     radix_sort_pairs(k0, v0, k1, v1, 4 * nt, 3 * vb, rtmp, s);
     k_face_runs<<<nblk(4 * nt, T), T, 0, s>>>(k1, v1, 4 * nt, adj, own, st);
+    note_launch();
     // edges
     k_edge_keys<<<nblk(n6, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
+    note_launch();
     radix_sort_pairs(k0, v0, k1, v1, n6, 2 * vb, rtmp, s);
     k_edge_runs<<<nblk(n6, T), T, 0, s>>>(k1, v1, n6, own);
+    note_launch();
     // vertices
     k_fill_i32<<<nblk(nv, T), T, 0, s>>>(vmin, nv, 0x7fffffff);
+    note_launch();
     k_vertex_min<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, nv, vmin);
+    note_launch();
     k_vertex_own<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, vmin, own);
+    note_launch();
 }

@@ -98,14 +98,17 @@ void scan_impl(const T* in, int64_t* out, long long n, void* tmp, cudaStream_t s
     int64_t* toff = tsum + t + 1;
     void* rest = toff + t + 1;
     scan_tiles<T><<<(unsigned)t, SCAN_THREADS, 0, s>>>(in, out, n, tsum);
+    note_launch();
     if (t == 1) {
         cudaMemsetAsync(toff, 0, sizeof(int64_t), s);
         cudaMemcpyAsync(toff + 1, tsum, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     } else {
         scan_impl<int64_t>(tsum, toff, t, rest, s);
         scan_add<<<(unsigned)t, SCAN_THREADS, 0, s>>>(out, n, toff);
+        note_launch();
     }
     scan_total<<<1, 1, 0, s>>>(out, n, toff, t);
+    note_launch();
 }
 
 // ------------------------------------------------------------- radix sort
@@ -315,8 +318,11 @@ void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t
         uint32_t* vdst = lastp ? vals_out : ((q & 1) ? vb : va);
         int shift = 8 * q;
         rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, n, shift, hist, (int)nb);
+        note_launch();
         rs_scan_hist<<<1, 256, 0, s>>>(hist, (int)nb, hoff);
+        note_launch();
         rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, vsrc, kdst, vdst, n, shift, hoff, (int)nb);
+        note_launch();
         ksrc = kdst;
         vsrc = vdst;
     }
@@ -339,9 +345,12 @@ void segmented_reduce(const uint64_t* keys, const uint32_t* pay, long long n, ui
     void* stmp = p;
     const int T = 256;
     seg_heads<<<div_up_ll(n, T), T, 0, s>>>(keys, n, sentinel, head);
+    note_launch();
     scan_impl<uint8_t>(head, excl, n, stmp, s);
     cudaMemsetAsync(chi, 0, sizeof(int32_t) * n, s);
     cudaMemsetAsync(beta0, 0, sizeof(int32_t) * n, s);
     seg_reduce<<<div_up_ll(n, T), T, 0, s>>>(keys, pay, n, sentinel, head, excl, ukey, chi, beta0);
+    note_launch();
     seg_count<<<1, 1, 0, s>>>(excl, n, d_nseg);
+    note_launch();
 }

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Host-side count of kernel launches issued by the library (rpd_launch_count).
+void note_launch();
+
 // Exclusive scan: out[i] = sum_{j<i} in[j] for i < n, and out[n] = total.
 // tmp must hold scan_tmp_bytes(n).
 size_t scan_tmp_bytes(long long n);

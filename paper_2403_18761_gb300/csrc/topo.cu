@@ -181,8 +181,11 @@ void launch_components_cells(const ClipArgs& a, long long npairs, int32_t* paren
     (void)key_bits;
     if (npairs <= 0) return;
     k_iota<<<nblk(npairs, 256), 256, 0, s>>>(parent, npairs);
+    note_launch();
     k_link_cells<<<nblk(npairs, 256), 256, 0, s>>>(a, npairs, parent);
+    note_launch();
     k_cell_payload<<<nblk(npairs, 256), 256, 0, s>>>(a, npairs, parent, pay, keys, sentinel);
+    note_launch();
 }
 
 void launch_components_records(const ClipArgs& a, int which, long long nrec, int32_t* parent, uint32_t* pay,
@@ -190,25 +193,32 @@ void launch_components_records(const ClipArgs& a, int which, long long nrec, int
     if (nrec <= 0) return;
     if (which < 2) {
         k_iota<<<nblk(nrec, 256), 256, 0, s>>>(parent, nrec);
+        note_launch();
         k_link_records<<<nblk(nrec, 256), 256, 0, s>>>(a, which, nrec, parent);
+        note_launch();
         k_record_payload<<<nblk(nrec, 256), 256, 0, s>>>(a, which, nrec, parent, pay);
+        note_launch();
     } else {
         k_record_payload<<<nblk(nrec, 256), 256, 0, s>>>(a, which, nrec, nullptr, pay);
+        note_launch();
     }
 }
 
 void launch_unpack_keys(const uint64_t* ukey, long long n, int kind, int key_bits, int32_t* out, cudaStream_t s) {
     if (n <= 0) return;
     k_unpack<<<nblk(n, 256), 256, 0, s>>>(ukey, n, kind, key_bits, out);
+    note_launch();
 }
 
 void launch_flags(const int32_t* chi, const int32_t* beta0, long long n, uint8_t* flag, cudaStream_t s) {
     if (n <= 0) return;
     k_flags<<<nblk(n, 256), 256, 0, s>>>(chi, beta0, n, flag);
+    note_launch();
 }
 
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet, int32_t* d_sphere,
                            double* d_vol, double* d_mom, cudaStream_t s) {
     if (npairs <= 0) return;
     k_compact_pieces<<<nblk(npairs, 256), 256, 0, s>>>(a, npairs, off, d_tet, d_sphere, d_vol, d_mom);
+    note_launch();
 }

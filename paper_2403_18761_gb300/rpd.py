@@ -41,6 +41,7 @@ class rpd_stats(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_records", ctypes.c_int64 * 4),
                 ("n_keys", ctypes.c_int64 * 4), ("pred_fast", ctypes.c_int64), ("pred_fp64", ctypes.c_int64),
                 ("pred_exact", ctypes.c_int64), ("cand_fallback", ctypes.c_int64), ("whole_tets", ctypes.c_int64),
+                ("clip_vertices", ctypes.c_int64),
                 ("bin_pairs", ctypes.c_int64 * 8), ("bin_cut", ctypes.c_int64 * 8), ("ms_prep", ctypes.c_float), ("ms_knn", ctypes.c_float), ("ms_cand", ctypes.c_float),
                 ("ms_clip", ctypes.c_float), ("ms_finalize", ctypes.c_float * 4)]
 
@@ -83,8 +84,15 @@ def load(path: str = LIB_PATH):
     lib.rpd_build_error.restype = ctypes.c_char_p
     lib.rpd_destroy.argtypes = [P]
     lib.rpd_destroy.restype = None
+    lib.rpd_launch_count.argtypes = []
+    lib.rpd_launch_count.restype = I64
     _lib = lib
     return lib
+
+
+def rpd_launch_count():
+    """Kernel launches the library has issued in this process so far."""
+    return int(load().rpd_launch_count())
 
 
 def header_symbols(path: str = HEADER):
