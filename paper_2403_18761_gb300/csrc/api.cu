@@ -335,10 +335,11 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     NEED(c->gp && c->cell_start && c->cell_ids && c->cell_wmax && gtmp && c->knn && c->dplus);
     int4* cell_sph = c->alloc<int4>(ns);
     long long* cell_w = c->alloc<long long>(ns);
-    NEED(cell_sph && cell_w);
+    void* ktmp = c->alloc<char>(knn_tmp_bytes(nv));
+    NEED(cell_sph && cell_w && ktmp);
     launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
                        gtmp, s);
-    launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, cell_sph, cell_w, c->K, c->knn, c->dplus, s);
+    launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp, s);
     TRY(cuda_check(c, "knn launch"));
     record(c, 2);
     // ---- A2

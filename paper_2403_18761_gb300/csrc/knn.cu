@@ -24,6 +24,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "prim.cuh"
 
@@ -183,14 +185,23 @@ __global__ void k_cell_fill(const int32_t* __restrict__ Ci, const long long* __r
 }
 
 // ---------------------------------------------------------------- kNN
-// Tiled form: one lane per mesh vertex, 32 consecutive vertices per warp.
-// The warp walks box shells around the bounding box of its vertices' cells;
-// each row run of the cell-sorted spheres is loaded 32 at a time (coalesced)
-// and broadcast by shuffles, and every lane tests every sphere against its
-// own vertex.  Each lane keeps its K best (distance, id) sorted in shared
-// memory; everything it rejects, evicts or leaves unexplored lowers its D+.
-// A lane is done once the next shell's distance bound minus max r^2 exceeds
-// its K-th distance; the warp stops when all lanes are done.
+// Tiled form: eight mesh vertices per warp, four lanes per vertex.  Vertices
+// are processed in the order of their sphere-grid cell (a stable sort by cell
+// index), so the vertices of a warp lie in a few neighbouring cells.  The
+// warp walks box shells around the bounding box of its vertices' cells; each
+// row run of the cell-sorted spheres is loaded 32 at a time (coalesced), and
+// sphere j of a chunk goes to lane j mod 4 of every vertex group, so each
+// lane sees a quarter of the stream.  Each lane keeps the K best (distance,
+// id) pairs of its quarter in a binary max-heap in shared memory.  A sphere
+// farther than the root of a full heap of its group cannot be among the K
+// best and is rejected.  Per chunk, every lane first marks the spheres that
+// survive this test; the marked spheres are then inserted in rounds in which
+// all lanes that still hold one insert together (one heap update each, log2 K
+// levels).  Once a lane's or its group's bound proves that no unexplored
+// sphere can enter, the group is done; at the end the four heaps of a vertex
+// are sorted and merged.  Everything rejected, evicted, left out of the
+// merge or left unexplored lowers D+.  The walk stops once the distance to
+// the next shell minus max r^2 exceeds the group's K-th distance bound.
 
 __device__ __forceinline__ bool pair_less(long long d1, int i1, long long d2, int i2) {
     return d1 < d2 || (d1 == d2 && i1 < i2);
@@ -216,116 +227,247 @@ __device__ __forceinline__ long long outside_box_lb2(int3 x, const GridParams& g
     return best == LLONG_MAX ? LLONG_MAX : best * best;
 }
 
+// Sift (d, id) down from the root of a max-heap of size m held in column
+// `lane` of hd/hi.
 template <int KMAX>
-__global__ void __launch_bounds__(128) k_knn_tile(const int32_t* __restrict__ Xi, long long nv,
-                                                   const GridParams* __restrict__ gp,
-                                                   const int64_t* __restrict__ start, const int4* __restrict__ sph,
-                                                   const long long* __restrict__ sw, int K,
-                                                   int32_t* __restrict__ knn, long long* __restrict__ dplus) {
-    __shared__ long long sd_all[4][KMAX][32];
-    __shared__ int si_all[4][KMAX][32];
+__device__ __forceinline__ void heap_sift_down(long long (*hd)[32], int (*hi)[32], int lane, int m, long long d,
+                                               int id) {
+    int p = 0;
+    while (true) {
+        int ch = 2 * p + 1;
+        if (ch >= m) break;
+        long long cd = hd[ch][lane];
+        int ci = hi[ch][lane];
+        if (ch + 1 < m) {
+            const long long c2 = hd[ch + 1][lane];
+            const int i2 = hi[ch + 1][lane];
+            if (pair_less(cd, ci, c2, i2)) {
+                ch++;
+                cd = c2;
+                ci = i2;
+            }
+        }
+        if (!pair_less(d, id, cd, ci)) break;
+        hd[p][lane] = cd;
+        hi[p][lane] = ci;
+        p = ch;
+    }
+    hd[p][lane] = d;
+    hi[p][lane] = id;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
+                                                    long long nv, const GridParams* __restrict__ gp,
+                                                    const int64_t* __restrict__ start, const int4* __restrict__ sph,
+                                                    const long long* __restrict__ sw, int K,
+                                                    int32_t* __restrict__ knn, long long* __restrict__ dplus) {
+    const unsigned FULL = 0xffffffffu;
+    __shared__ long long hd_all[4][KMAX][32];
+    __shared__ int hi_all[4][KMAX][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long(*sd)[32] = sd_all[warp];
-    int(*si)[32] = si_all[warp];
-    const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x);
-    const long long vbase = v - lane;
-    if (vbase >= nv) return;   // warp-uniform
-    const bool valid = v < nv;
+    const int sub = lane & 3;   // quarter of the stream this lane sees
+    long long(*hd)[32] = hd_all[warp];
+    int(*hi)[32] = hi_all[warp];
+    const long long wbase = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 8;
+    if (wbase >= nv) return;   // warp-uniform
+    const long long idx = wbase + (lane >> 2);
+    const bool valid = idx < nv;
+    const long long v = vorder[valid ? idx : wbase];
     const GridParams g = *gp;
-    const int3 x = valid ? ld_int3(Xi, v) : ld_int3(Xi, vbase);
+    const int3 x = ld_int3(Xi, v);
     const int3 c = cell_of(x, g);
-    // bounding box of the warp's cells
-    int3 lo, hi;
-    lo.x = __reduce_min_sync(0xffffffffu, c.x);
-    lo.y = __reduce_min_sync(0xffffffffu, c.y);
-    lo.z = __reduce_min_sync(0xffffffffu, c.z);
-    hi.x = __reduce_max_sync(0xffffffffu, c.x);
-    hi.y = __reduce_max_sync(0xffffffffu, c.y);
-    hi.z = __reduce_max_sync(0xffffffffu, c.z);
-    int cnt = 0;                 // entries in this lane's list
-    long long kd = LLONG_MAX;    // this lane's K-th distance (LLONG_MAX while short)
-    int ki = 0x7fffffff;
+    int3 lo, hi3;
+    lo.x = __reduce_min_sync(FULL, c.x);
+    lo.y = __reduce_min_sync(FULL, c.y);
+    lo.z = __reduce_min_sync(FULL, c.z);
+    hi3.x = __reduce_max_sync(FULL, c.x);
+    hi3.y = __reduce_max_sync(FULL, c.y);
+    hi3.z = __reduce_max_sync(FULL, c.z);
+    int cnt = 0;                 // size of this lane's heap
+    long long kd = LLONG_MAX;    // its root once full
+    int ki = INT_MAX;
+    long long gmin = LLONG_MAX;  // smallest full-heap root distance in the group
     long long dp = LLONG_MAX;
     bool done = !valid;
     int3 plo = make_int3(1, 1, 1), phi = make_int3(0, 0, 0);   // processed box (empty)
-    for (int r = 0; r < 4096; r++) {
+    for (int r = 0; r < (1 << 22); r++) {
         const int3 blo = make_int3(max(lo.x - r, 0), max(lo.y - r, 0), max(lo.z - r, 0));
-        const int3 bhi = make_int3(min(hi.x + r, g.dim.x - 1), min(hi.y + r, g.dim.y - 1), min(hi.z + r, g.dim.z - 1));
-        // rows (y, z) of the new shell: whole rows outside the processed
-        // box's (y, z) range, else the parts left and right of it
-        for (int zz = blo.z; zz <= bhi.z; zz++) {
-            for (int yy = blo.y; yy <= bhi.y; yy++) {
+        const int3 bhi =
+            make_int3(min(hi3.x + r, g.dim.x - 1), min(hi3.y + r, g.dim.y - 1), min(hi3.z + r, g.dim.z - 1));
+        // rows (y, z) of the new shell, one per lane: the whole row outside
+        // the processed box's (y, z) range, else the parts left and right of
+        // it; their spheres are concatenated and processed 32 at a time
+        const int ny = bhi.y - blo.y + 1, nrow = ny * (bhi.z - blo.z + 1);
+        for (int rb = 0; rb < nrow; rb += 32) {
+            long long a0 = 0, b0 = 0;
+            int na = 0, nbb = 0;
+            if (rb + lane < nrow) {
+                const int yy = blo.y + (rb + lane) % ny, zz = blo.z + (rb + lane) / ny;
+                const int qrow = (zz * g.dim.y + yy) * g.dim.x;
                 const bool inner = zz >= plo.z && zz <= phi.z && yy >= plo.y && yy <= phi.y;
-                for (int part = 0; part < (inner ? 2 : 1); part++) {
-                    int xa = blo.x, xb = bhi.x;
-                    if (inner) {
-                        if (part == 0) xb = plo.x - 1;
-                        else xa = phi.x + 1;
-                    }
-                    if (xa > xb) continue;
-                    const int qrow = (zz * g.dim.y + yy) * g.dim.x;
-                    const long long e0 = start[qrow + xa], e1 = start[qrow + xb + 1];
-                    for (long long eb = e0; eb < e1; eb += 32) {
-                        const long long e = eb + lane;
-                        int4 cs = make_int4(0, 0, 0, 0);
-                        long long ws = 0;
-                        if (e < e1) {
-                            cs = sph[e];
-                            ws = sw[e];
+                if (inner) {
+                    a0 = start[qrow + blo.x];
+                    na = (int)(start[qrow + plo.x] - a0);
+                    b0 = start[qrow + phi.x + 1];
+                    nbb = (int)(start[qrow + bhi.x + 1] - b0);
+                } else {
+                    a0 = start[qrow + blo.x];
+                    na = (int)(start[qrow + bhi.x + 1] - a0);
+                }
+            }
+            const int m = na + nbb;
+            int incl = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int ntot = __shfl_sync(FULL, incl, 31);
+            for (int pb = 0; pb < ntot; pb += 32) {
+                const int item = pb + lane;
+                int j = 0;   // first lane whose inclusive count exceeds item
+#pragma unroll
+                for (int step = 16; step; step >>= 1) {
+                    const int probe = __shfl_sync(FULL, incl, j + step - 1);
+                    if (probe <= item) j += step;
+                }
+                j = min(j, 31);
+                const int oj = item - __shfl_sync(FULL, incl - m, j);
+                const int naj = __shfl_sync(FULL, na, j);
+                const long long a0j = __shfl_sync(FULL, a0, j), b0j = __shfl_sync(FULL, b0, j);
+                int4 cs = make_int4(0, 0, 0, 0);
+                long long ws = 0;
+                if (item < ntot) {
+                    const long long e = oj < naj ? a0j + oj : b0j + (oj - naj);
+                    cs = sph[e];
+                    ws = sw[e];
+                }
+                const int nb = min(32, ntot - pb);
+                // pass 1: spheres sub, sub + 4, ... of the chunk that may enter
+                unsigned mark = 0;
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const int jj = 4 * t + sub;
+                    const int3 cj = make_int3(__shfl_sync(FULL, cs.x, jj), __shfl_sync(FULL, cs.y, jj),
+                                              __shfl_sync(FULL, cs.z, jj));
+                    const int idj = __shfl_sync(FULL, cs.w, jj);
+                    const long long wj = __shfl_sync(FULL, ws, jj);
+                    if (done || jj >= nb) continue;
+                    const long long d = pd_exact(x, cj, wj);
+                    if (d <= gmin && (cnt < K || pair_less(d, idj, kd, ki))) mark |= 1u << t;
+                    else dp = min(dp, d);
+                }
+                // pass 2: insert the marked spheres, one per lane per round
+                while (__any_sync(FULL, mark != 0)) {
+                    const bool has = mark != 0;
+                    const int jj = has ? 4 * (__ffs(mark) - 1) + sub : 0;
+                    mark &= mark - 1;
+                    const int3 cj = make_int3(__shfl_sync(FULL, cs.x, jj), __shfl_sync(FULL, cs.y, jj),
+                                              __shfl_sync(FULL, cs.z, jj));
+                    const int id = __shfl_sync(FULL, cs.w, jj);
+                    const long long wj = __shfl_sync(FULL, ws, jj);
+                    if (!has) continue;
+                    const long long d = pd_exact(x, cj, wj);
+                    if (cnt < K) {   // push and sift up
+                        int p = cnt++;
+                        while (p > 0) {
+                            const int q = (p - 1) >> 1;
+                            const long long qd = hd[q][lane];
+                            const int qi = hi[q][lane];
+                            if (!pair_less(qd, qi, d, id)) break;
+                            hd[p][lane] = qd;
+                            hi[p][lane] = qi;
+                            p = q;
                         }
-                        const int nb = (int)min(32LL, e1 - eb);
-                        for (int jj = 0; jj < nb; jj++) {
-                            const int3 cj = make_int3(__shfl_sync(0xffffffffu, cs.x, jj), __shfl_sync(0xffffffffu, cs.y, jj),
-                                                      __shfl_sync(0xffffffffu, cs.z, jj));
-                            const int idj = __shfl_sync(0xffffffffu, cs.w, jj);
-                            const long long wj = __shfl_sync(0xffffffffu, ws, jj);
-                            if (done) continue;
-                            const long long d = pd_exact(x, cj, wj);
-                            if (cnt == K && !pair_less(d, idj, kd, ki)) {
-                                dp = min(dp, d);
-                                continue;
-                            }
-                            // insert into the sorted list (evicting the K-th when full)
-                            int pos = cnt < K ? cnt : K - 1;
-                            if (cnt == K) dp = min(dp, sd[K - 1][lane]);
-                            while (pos > 0 && pair_less(d, idj, sd[pos - 1][lane], si[pos - 1][lane])) {
-                                sd[pos][lane] = sd[pos - 1][lane];
-                                si[pos][lane] = si[pos - 1][lane];
-                                pos--;
-                            }
-                            sd[pos][lane] = d;
-                            si[pos][lane] = idj;
-                            if (cnt < K) cnt++;
-                            if (cnt == K) {
-                                kd = sd[K - 1][lane];
-                                ki = si[K - 1][lane];
-                            }
+                        hd[p][lane] = d;
+                        hi[p][lane] = id;
+                        if (cnt == K) {
+                            kd = hd[0][lane];
+                            ki = hi[0][lane];
                         }
+                    } else if (pair_less(d, id, kd, ki)) {   // replace the root
+                        dp = min(dp, kd);
+                        heap_sift_down<KMAX>(hd, hi, lane, K, d, id);
+                        kd = hd[0][lane];
+                        ki = hi[0][lane];
+                    } else {
+                        dp = min(dp, d);
                     }
                 }
+                // group bound: smallest root among the group's full heaps
+                long long gr = cnt == K ? kd : LLONG_MAX;
+                gr = min(gr, __shfl_xor_sync(FULL, gr, 1));
+                gr = min(gr, __shfl_xor_sync(FULL, gr, 2));
+                gmin = min(gmin, gr);
             }
         }
         plo = blo;
         phi = bhi;
-        // lane termination: the next shell cannot hold a sphere within kd
         const long long lb2 = outside_box_lb2(x, g, blo, bhi);
-        if (!done) {
+        if (!done) {   // uniform over the group: same x and gmin
             if (lb2 == LLONG_MAX) {
                 done = true;
-            } else if (cnt == K && lb2 - g.wmax > kd) {
+            } else if (gmin != LLONG_MAX && lb2 - g.wmax > gmin) {
                 dp = min(dp, lb2 - g.wmax);
                 done = true;
             }
         }
-        if (__all_sync(0xffffffffu, done)) break;
+        if (__all_sync(FULL, done)) break;
     }
-    if (!valid) return;
-    {   // whatever was not explored is bounded by the last box
+    if (valid) {   // whatever was not explored is bounded by the last box
         const long long lbu = outside_box_lb2(x, g, plo, phi);
         if (lbu != LLONG_MAX) dp = min(dp, lbu - g.wmax);
     }
-    for (int j = 0; j < K; j++) knn[v * K + j] = j < cnt ? si[j][lane] : -1;
-    dplus[v] = dp;
+    // heap sort each lane's column into ascending order
+    for (int n = cnt; n > 1; n--) {
+        const long long rd = hd[0][lane];
+        const int ri = hi[0][lane];
+        heap_sift_down<KMAX>(hd, hi, lane, n - 1, hd[n - 1][lane], hi[n - 1][lane]);
+        hd[n - 1][lane] = rd;
+        hi[n - 1][lane] = ri;
+    }
+    __syncwarp();
+    // merge the four sorted columns of each vertex: the K smallest go to the
+    // list, the smallest left out bounds D+
+    const int n0 = __shfl_sync(FULL, cnt, lane & ~3), n1 = __shfl_sync(FULL, cnt, (lane & ~3) + 1),
+              n2 = __shfl_sync(FULL, cnt, (lane & ~3) + 2), n3 = __shfl_sync(FULL, cnt, (lane & ~3) + 3);
+    long long dmin = dp;
+    if (valid && sub == 0) {
+        int p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+        const int l0 = lane;
+        for (int j = 0; j < K; j++) {
+            long long bd = LLONG_MAX;
+            int bi = INT_MAX, bc = -1;
+            if (p0 < n0 && pair_less(hd[p0][l0], hi[p0][l0], bd, bi)) { bd = hd[p0][l0]; bi = hi[p0][l0]; bc = 0; }
+            if (p1 < n1 && pair_less(hd[p1][l0 + 1], hi[p1][l0 + 1], bd, bi)) { bd = hd[p1][l0 + 1]; bi = hi[p1][l0 + 1]; bc = 1; }
+            if (p2 < n2 && pair_less(hd[p2][l0 + 2], hi[p2][l0 + 2], bd, bi)) { bd = hd[p2][l0 + 2]; bi = hi[p2][l0 + 2]; bc = 2; }
+            if (p3 < n3 && pair_less(hd[p3][l0 + 3], hi[p3][l0 + 3], bd, bi)) { bd = hd[p3][l0 + 3]; bi = hi[p3][l0 + 3]; bc = 3; }
+            knn[v * K + j] = bc < 0 ? -1 : bi;
+            p0 += bc == 0;
+            p1 += bc == 1;
+            p2 += bc == 2;
+            p3 += bc == 3;
+        }
+        if (p0 < n0) dmin = min(dmin, hd[p0][l0]);
+        if (p1 < n1) dmin = min(dmin, hd[p1][l0 + 1]);
+        if (p2 < n2) dmin = min(dmin, hd[p2][l0 + 2]);
+        if (p3 < n3) dmin = min(dmin, hd[p3][l0 + 3]);
+    }
+    dmin = min(dmin, __shfl_xor_sync(FULL, dmin, 1));
+    dmin = min(dmin, __shfl_xor_sync(FULL, dmin, 2));
+    if (valid && sub == 0) dplus[v] = dmin;
+}
+
+// Sort key of a vertex: the index of its sphere-grid cell.
+__global__ void k_vertex_cells(const int32_t* __restrict__ Xi, long long nv, const GridParams* __restrict__ gp,
+                               uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const GridParams g = *gp;
+    const int3 c = cell_of(ld_int3(Xi, v), g);
+    key[v] = (uint64_t)((c.z * g.dim.y + c.y) * g.dim.x + c.x);
+    val[v] = (uint32_t)v;
 }
 
 // ---------------------------------------------------------- candidates
@@ -616,11 +758,25 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
     note_launch();
 }
 
+size_t knn_tmp_bytes(long long nv) {
+    return 2 * al(sizeof(uint64_t) * nv) + 2 * al(sizeof(uint32_t) * nv) + radix_tmp_bytes(nv);
+}
+
 void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
-                const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, int K, int32_t* knn,
-                long long* dplus, cudaStream_t s) {
+                const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, long long ncap, int K,
+                int32_t* knn, long long* dplus, void* tmp, cudaStream_t s) {
     if (nv == 0) return;
-    k_knn_tile<RPD_MAXK><<<nblk(nv, 128), 128, 0, s>>>(Xi, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
+    char* p = (char*)tmp;
+    uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
+    uint64_t* k1 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
+    uint32_t* v0 = (uint32_t*)p; p += al(sizeof(uint32_t) * nv);
+    uint32_t* v1 = (uint32_t*)p; p += al(sizeof(uint32_t) * nv);
+    int bits = 1;
+    while ((1ll << bits) < ncap) bits++;
+    k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
+    note_launch();
+    radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, s);
+    k_knn_group<RPD_MAXK><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
     note_launch();
 }
 
