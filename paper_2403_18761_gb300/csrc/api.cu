@@ -282,7 +282,7 @@ rpd_status finalize_kind(rpd_ctx* c, int kind, void* tmp, uint64_t* kbuf, uint32
         launch_components_records(c->clip, kind - 2, n, parent, pbuf, s);
         keys = c->clip.rkey[kind - 2];
     }
-    radix_sort_pairs(keys, pbuf, kout, pout, n, kind * b, tmp, s);
+    radix_sort_pairs(keys, pbuf, kout, pout, n, kind * b, tmp, &c->st->err, s);
     segmented_reduce(kout, pout, n, sentinel, ukey, chi, beta, d_nseg, tmp, s);
     return cuda_check(c, "finalize launch");
 }
@@ -339,7 +339,8 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     NEED(cell_sph && cell_w && ktmp);
     launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
                        gtmp, s);
-    launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp, s);
+    launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp,
+               &c->st->err, s);
     TRY(cuda_check(c, "knn launch"));
     record(c, 2);
     // ---- A2

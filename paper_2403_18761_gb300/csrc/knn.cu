@@ -764,7 +764,7 @@ size_t knn_tmp_bytes(long long nv) {
 
 void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
                 const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, long long ncap, int K,
-                int32_t* knn, long long* dplus, void* tmp, cudaStream_t s) {
+                int32_t* knn, long long* dplus, void* tmp, int* d_err, cudaStream_t s) {
     if (nv == 0) return;
     char* p = (char*)tmp;
     uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
@@ -775,7 +775,7 @@ void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long l
     while ((1ll << bits) < ncap) bits++;
     k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
     note_launch();
-    radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, s);
+    radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, d_err, s);
     k_knn_group<RPD_MAXK><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
     note_launch();
 }

@@ -207,13 +207,13 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
     // faces
     k_face_keys<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
     note_launch();
-    radix_sort_pairs(k0, v0, k1, v1, 4 * nt, 3 * vb, rtmp, s);
+    radix_sort_pairs(k0, v0, k1, v1, 4 * nt, 3 * vb, rtmp, &st->err, s);
     k_face_runs<<<nblk(4 * nt, T), T, 0, s>>>(k1, v1, 4 * nt, adj, own, st);
     note_launch();
     // edges
     k_edge_keys<<<nblk(n6, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
     note_launch();
-    radix_sort_pairs(k0, v0, k1, v1, n6, 2 * vb, rtmp, s);
+    radix_sort_pairs(k0, v0, k1, v1, n6, 2 * vb, rtmp, &st->err, s);
     k_edge_runs<<<nblk(n6, T), T, 0, s>>>(k1, v1, n6, own);
     note_launch();
     // vertices

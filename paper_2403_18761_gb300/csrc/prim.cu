@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "rpd.h"
+
 namespace {
 
 inline unsigned div_up_ll(long long a, int b) { return (unsigned)((a + b - 1) / b); }
@@ -112,91 +116,105 @@ void scan_impl(const T* in, int64_t* out, long long n, void* tmp, cudaStream_t s
 }
 
 // ------------------------------------------------------------- radix sort
+// Onesweep LSD radix sort (8-bit digits): one kernel builds the digit
+// histograms of every pass, one scans them, then one kernel per pass ranks
+// and scatters a tile of 4096 keys.  Tiles take their index from an atomic
+// counter in launch order, publish their digit counts, and obtain their
+// global offsets by decoupled look-back over the preceding tiles (a waiting
+// tile only ever waits for a tile that is already running).  Every wait is
+// bounded; on timeout the pass records RPD_E_TIMEOUT and drops the writes it
+// cannot place.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 4096 keys per block
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 4096 keys per tile
+constexpr int RS_MAXPASS = 8;
+constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1;
+constexpr int LB_SPIN_LIMIT = 1 << 22;
 
-__global__ void rs_hist(const uint64_t* __restrict__ keys, long long n, int shift, uint32_t* __restrict__ hist,
-                        int nblocks) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    long long base = (long long)blockIdx.x * RS_TILE;
-    for (int k = threadIdx.x; k < RS_TILE; k += RS_THREADS) {
-        long long i = base + k;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
-    }
-    __syncthreads();
-    hist[(long long)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
-}
+__device__ __forceinline__ long long rs_count(const long long* d_n, long long n) { return d_n ? *d_n : n; }
 
-// Global offsets per (block, digit): digit-major exclusive scan of the
-// block-major histogram, one thread per digit (256 threads, one block).
-__global__ void rs_scan_hist(const uint32_t* __restrict__ hist, int nblocks, int64_t* __restrict__ hoff) {
-    __shared__ long long base[256];
-    const int d = threadIdx.x;
-    long long s = 0;
-    for (int b = 0; b < nblocks; b++) s += hist[(long long)b * 256 + d];
-    base[d] = s;
+__global__ void rs_hist_all(const uint64_t* __restrict__ keys, const long long* __restrict__ d_n, long long n_host,
+                            int passes, uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[RS_MAXPASS][256];
+    for (int k = threadIdx.x; k < RS_MAXPASS * 256; k += RS_THREADS) (&h[0][0])[k] = 0;
     __syncthreads();
-    if (d < 32) {
-        // exclusive scan of the 256 digit totals by one warp (8 per lane)
-        long long v[8], run = 0;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            v[k] = base[d * 8 + k];
-            run += v[k];
-        }
-        long long inc = run;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            long long o = __shfl_up_sync(0xffffffffu, inc, off);
-            if (d >= off) inc += o;
-        }
-        long long pre = inc - run;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            base[d * 8 + k] = pre;
-            pre += v[k];
+    const long long n = rs_count(d_n, n_host);
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * RS_TILE; base < n; base += (long long)gridDim.x * RS_TILE) {
+        for (int k = threadIdx.x; k < RS_TILE; k += RS_THREADS) {
+            const long long i = base + k;
+            const bool ok = i < n;
+            const uint64_t key = ok ? keys[i] : 0;
+            for (int q = 0; q < passes; q++) {
+                const int d = ok ? (int)((key >> (8 * q)) & 255) : 256;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                if (d < 256 && lane == __ffs(peers) - 1) atomicAdd(&h[q][d], (uint32_t)__popc(peers));
+            }
         }
     }
     __syncthreads();
-    s = base[d];
-    for (int b = 0; b < nblocks; b++) {
-        hoff[(long long)b * 256 + d] = s;
-        s += hist[(long long)b * 256 + d];
+    for (int q = 0; q < passes; q++) {
+        const uint32_t v = h[q][threadIdx.x];
+        if (v) atomicAdd(&ghist[q * 256 + threadIdx.x], v);
     }
 }
 
-__global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, long long n, int shift,
-                           const int64_t* __restrict__ hoff, int nblocks) {
+// Exclusive scan over the 256 digits of every pass (one block).
+__global__ void rs_scan_all(const uint32_t* __restrict__ ghist, int passes, uint32_t* __restrict__ gbase) {
+    __shared__ uint32_t wsum[RS_WARPS];
+    const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+    for (int q = 0; q < passes; q++) {
+        const uint32_t v = ghist[q * 256 + d];
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int k = 0; k < w; k++) off += wsum[k];
+        gbase[q * 256 + d] = off + inc - v;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                     uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                     const long long* __restrict__ d_n, long long n_host, int shift,
+                                                     const uint32_t* __restrict__ gbase, uint32_t* look,
+                                                     uint32_t* tcnt, int* err) {
     __shared__ uint32_t wh[RS_WARPS][256];
-    __shared__ int64_t goff[256];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ uint32_t dbase[256];
+    __shared__ int tile_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(tcnt, 1u);
     for (int k = threadIdx.x; k < RS_WARPS * 256; k += RS_THREADS) (&wh[0][0])[k] = 0;
-    goff[threadIdx.x] = hoff[(long long)blockIdx.x * 256 + threadIdx.x];
     __syncthreads();
-    long long base = (long long)blockIdx.x * RS_TILE + (long long)w * (RS_TILE / RS_WARPS);
+    const long long n = rs_count(d_n, n_host);
+    const long long tile = tile_s;
+    if (tile * RS_TILE >= n) return;   // block-uniform
+    const long long base = tile * RS_TILE + (long long)w * (RS_TILE / RS_WARPS);
     uint64_t key[RS_ROUNDS];
     uint32_t val[RS_ROUNDS];
     uint32_t pos[RS_ROUNDS];
     int dig[RS_ROUNDS];
-    unsigned lt = (1u << lane) - 1u;
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; r++) {
-        long long i = base + r * 32 + lane;
-        bool ok = i < n;
+        const long long i = base + r * 32 + lane;
+        const bool ok = i < n;
         key[r] = ok ? kin[i] : 0;
         val[r] = ok ? vin[i] : 0;
         dig[r] = ok ? (int)((key[r] >> shift) & 255) : 256;
     }
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; r++) {
-        int d = dig[r];
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
+        const int d = dig[r];
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (lane == leader && d < 256) old = wh[w][d];
         old = __shfl_sync(0xffffffffu, old, leader);
@@ -206,22 +224,53 @@ __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __r
     }
     __syncthreads();
     {
-        int d = threadIdx.x;   // 256 threads = 256 digits
+        const int d = threadIdx.x;   // 256 threads = 256 digits
         uint32_t run = 0;
         for (int q = 0; q < RS_WARPS; q++) {
-            uint32_t t = wh[q][d];
+            const uint32_t t = wh[q][d];
             wh[q][d] = run;
             run += t;
         }
+        // publish this tile's count, then look back for its offset
+        volatile uint32_t* L = look;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            atomicExch(&look[d], LB_PRE | run);
+        } else {
+            atomicExch(&look[tile * 256 + d], LB_AGG | run);
+            long long t = tile - 1;
+            int spins = 0;
+            while (true) {
+                const uint32_t v = L[t * 256 + d];
+                if (v & LB_PRE) {
+                    excl += v & LB_VAL;
+                    break;
+                }
+                if (v & LB_AGG) {
+                    excl += v & LB_VAL;
+                    t--;
+                    continue;
+                }
+                if (++spins > LB_SPIN_LIMIT) {
+                    atomicCAS(err, 0, (int)RPD_E_TIMEOUT);
+                    excl = 0x80000000u;   // marks the digit as unplaceable
+                    break;
+                }
+            }
+            if (excl != 0x80000000u) atomicExch(&look[tile * 256 + d], LB_PRE | (excl + run));
+        }
+        dbase[d] = excl == 0x80000000u ? 0xffffffffu : gbase[d] + excl;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; r++) {
-        int d = dig[r];
-        if (d < 256) {
-            long long dst = goff[d] + wh[w][d] + pos[r];
-            kout[dst] = key[r];
-            vout[dst] = val[r];
+        const int d = dig[r];
+        if (d < 256 && dbase[d] != 0xffffffffu) {
+            const long long dst = (long long)dbase[d] + wh[w][d] + pos[r];
+            if (dst < n) {
+                kout[dst] = key[r];
+                vout[dst] = val[r];
+            }
         }
     }
 }
@@ -287,45 +336,63 @@ void scan_excl(const int64_t* in, int64_t* out, long long n, void* tmp, cudaStre
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+static long long rs_tiles(long long n) { return n > 0 ? (n + RS_TILE - 1) / RS_TILE : 1; }
+
 size_t radix_tmp_bytes(long long n) {
-    long long nb = (n + RS_TILE - 1) / RS_TILE;
-    if (nb < 1) nb = 1;
-    long long nh = 256 * nb;
-    return 2 * align256(sizeof(uint64_t) * (size_t)n) + 2 * align256(sizeof(uint32_t) * (size_t)n) +
-           align256(sizeof(uint32_t) * (size_t)nh) + align256(sizeof(int64_t) * (size_t)(nh + 1)) +
-           align256(scan_tmp_bytes(nh));
+    const long long nt = rs_tiles(n);
+    return 2 * align256(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1)) +
+           2 * align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)) +
+           align256(sizeof(uint32_t) * (size_t)(2 * RS_MAXPASS * 256 + RS_MAXPASS)) +
+           align256(sizeof(uint32_t) * (size_t)(RS_MAXPASS * nt * 256));
 }
 
-void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                      long long n, int bits, void* tmp, cudaStream_t s) {
-    if (n <= 0) return;
+static void radix_sort_impl(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                            const long long* d_n, long long nmax, int bits, void* tmp, int* d_err, cudaStream_t s) {
+    if (nmax <= 0) return;
     int passes = (bits + 7) / 8;
     if (passes < 1) passes = 1;
-    long long nb = (n + RS_TILE - 1) / RS_TILE;
-    long long nh = 256 * nb;
+    if (passes > RS_MAXPASS) passes = RS_MAXPASS;
+    const long long nt = rs_tiles(nmax);
     char* p = (char*)tmp;
-    uint64_t* ka = (uint64_t*)p; p += align256(sizeof(uint64_t) * n);
-    uint64_t* kb = (uint64_t*)p; p += align256(sizeof(uint64_t) * n);
-    uint32_t* va = (uint32_t*)p; p += align256(sizeof(uint32_t) * n);
-    uint32_t* vb = (uint32_t*)p; p += align256(sizeof(uint32_t) * n);
-    uint32_t* hist = (uint32_t*)p; p += align256(sizeof(uint32_t) * nh);
-    int64_t* hoff = (int64_t*)p; p += align256(sizeof(int64_t) * (nh + 1));
+    uint64_t* ka = (uint64_t*)p; p += align256(sizeof(uint64_t) * nmax);
+    uint64_t* kb = (uint64_t*)p; p += align256(sizeof(uint64_t) * nmax);
+    uint32_t* va = (uint32_t*)p; p += align256(sizeof(uint32_t) * nmax);
+    uint32_t* vb = (uint32_t*)p; p += align256(sizeof(uint32_t) * nmax);
+    uint32_t* ctl = (uint32_t*)p; p += align256(sizeof(uint32_t) * (2 * RS_MAXPASS * 256 + RS_MAXPASS));
+    uint32_t* look = (uint32_t*)p;
+    uint32_t* ghist = ctl;
+    uint32_t* gbase = ctl + RS_MAXPASS * 256;
+    uint32_t* tcnt = ctl + 2 * RS_MAXPASS * 256;
+    // histograms, tile counters and look-back words start at zero
+    cudaMemsetAsync(ctl, 0, sizeof(uint32_t) * (2 * RS_MAXPASS * 256 + RS_MAXPASS), s);
+    cudaMemsetAsync(look, 0, sizeof(uint32_t) * (size_t)(passes * nt * 256), s);
+    const unsigned hb = (unsigned)std::min<long long>(nt, 152LL * 8);
+    rs_hist_all<<<hb, RS_THREADS, 0, s>>>(keys_in, d_n, nmax, passes, ghist);
+    note_launch();
+    rs_scan_all<<<1, 256, 0, s>>>(ghist, passes, gbase);
+    note_launch();
     const uint64_t* ksrc = keys_in;
     const uint32_t* vsrc = vals_in;
     for (int q = 0; q < passes; q++) {
-        bool lastp = (q == passes - 1);
+        const bool lastp = (q == passes - 1);
         uint64_t* kdst = lastp ? keys_out : ((q & 1) ? kb : ka);
         uint32_t* vdst = lastp ? vals_out : ((q & 1) ? vb : va);
-        int shift = 8 * q;
-        rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, n, shift, hist, (int)nb);
-        note_launch();
-        rs_scan_hist<<<1, 256, 0, s>>>(hist, (int)nb, hoff);
-        note_launch();
-        rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(ksrc, vsrc, kdst, vdst, n, shift, hoff, (int)nb);
+        rs_pass<<<(unsigned)nt, RS_THREADS, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, nmax, 8 * q, gbase + q * 256,
+                                                     look + (size_t)q * nt * 256, tcnt + q, d_err);
         note_launch();
         ksrc = kdst;
         vsrc = vdst;
     }
+}
+
+void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                      long long n, int bits, void* tmp, int* d_err, cudaStream_t s) {
+    radix_sort_impl(keys_in, vals_in, keys_out, vals_out, nullptr, n, bits, tmp, d_err, s);
+}
+
+void radix_sort_pairs_dn(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                         const long long* d_n, long long nmax, int bits, void* tmp, int* d_err, cudaStream_t s) {
+    radix_sort_impl(keys_in, vals_in, keys_out, vals_out, d_n, nmax, bits, tmp, d_err, s);
 }
 
 size_t segreduce_tmp_bytes(long long n) {

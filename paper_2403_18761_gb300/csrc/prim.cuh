@@ -16,11 +16,17 @@ void scan_excl(const uint8_t* in, int64_t* out, long long n, void* tmp, cudaStre
 void scan_excl(const int64_t* in, int64_t* out, long long n, void* tmp, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
-// keys, 8 bits per pass.  Reads keys_in/vals_in, writes keys_out/vals_out.
-// tmp must hold radix_tmp_bytes(n).
+// keys (at most 64), 8 bits per pass; n < 2^30.  Reads keys_in/vals_in,
+// writes keys_out/vals_out.  tmp must hold radix_tmp_bytes(n).  A pass whose
+// bounded look-back wait runs out sets *d_err to RPD_E_TIMEOUT (if it is 0).
 size_t radix_tmp_bytes(long long n);
 void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
-                      uint32_t* vals_out, long long n, int bits, void* tmp, cudaStream_t s);
+                      uint32_t* vals_out, long long n, int bits, void* tmp, int* d_err, cudaStream_t s);
+// Same with the element count read on the device from *d_n (<= nmax); tmp
+// must hold radix_tmp_bytes(nmax).
+void radix_sort_pairs_dn(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                         uint32_t* vals_out, const long long* d_n, long long nmax, int bits, void* tmp, int* d_err,
+                         cudaStream_t s);
 
 // Segmented reduction over runs of equal keys (keys sorted; runs whose key is
 // `sentinel` are ignored).  Payload bits 0..15 hold a signed contribution to
