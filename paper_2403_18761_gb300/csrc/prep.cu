@@ -41,27 +41,56 @@ __global__ void k_snap_radii(const double* __restrict__ r, long long n, double s
     W[i] = q * q;
 }
 
-// Exact orientation: det[p1-p0, p2-p0, p3-p0] > 0 with 128-bit integers.
-__global__ void k_check_tets(const int32_t* __restrict__ T, long long nt, long long nv, const int32_t* __restrict__ Xi,
-                             DevState* st) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    int v[4];
-    for (int a = 0; a < 4; a++) {
-        v[a] = T[4 * t + a];
-        if (v[a] < 0 || v[a] >= nv) {
-            dev_fail(st, RPD_E_INVALID, CNT_INVALID);
-            return;
+// Mesh combinatorics by hashing: every tet inserts its 4 faces (sorted vertex
+// triples) and 6 edges (sorted pairs) into open-addressing tables keyed by the
+// packed vertex ids; per face the table counts the tets and keeps the lowest
+// and highest (tet, face) index, per edge the lowest (tet, edge) index, per
+// vertex the lowest tet.  A second pass looks every entry up again: face
+// adjacency, ownership by the lowest-numbered tet, and > 2 tets per face as a
+// non-manifold error.  The results do not depend on the insertion order.
+constexpr uint64_t HEMPTY = ~0ull;
+
+struct MeshTables {
+    uint64_t* fk;   // face keys
+    uint32_t* fc;   // tets per face
+    uint32_t* fmin;
+    uint32_t* fmax;
+    uint64_t* ek;   // edge keys
+    uint32_t* emin;
+    uint32_t* vmin;   // lowest tet per vertex
+    unsigned long long fmask, emask;
+    int fshift, eshift;
+    int vb;
+};
+
+__device__ __forceinline__ unsigned long long hslot(uint64_t key, int shift) {
+    return (key * 0x9E3779B97F4A7C15ull) >> shift;
+}
+
+// Slot holding `key` (inserted if absent), or -1 if the table is full.
+__device__ __forceinline__ long long table_insert(uint64_t* tk, unsigned long long mask, int shift, uint64_t key) {
+    unsigned long long h = hslot(key, shift);
+    for (unsigned long long it = 0; it <= mask; it++) {
+        const uint64_t k = tk[h];
+        if (k == key) return (long long)h;
+        if (k == HEMPTY) {
+            const uint64_t old = atomicCAS((unsigned long long*)&tk[h], HEMPTY, key);
+            if (old == HEMPTY || old == key) return (long long)h;
         }
+        h = (h + 1) & mask;
     }
-    int3 p0 = ld_int3(Xi, v[0]), p1 = ld_int3(Xi, v[1]), p2 = ld_int3(Xi, v[2]), p3 = ld_int3(Xi, v[3]);
-    long long ax = p1.x - p0.x, ay = p1.y - p0.y, az = p1.z - p0.z;
-    long long bx = p2.x - p0.x, by = p2.y - p0.y, bz = p2.z - p0.z;
-    long long cx = p3.x - p0.x, cy = p3.y - p0.y, cz = p3.z - p0.z;
-    __int128 d = (__int128)ax * ((__int128)by * cz - (__int128)bz * cy) -
-                 (__int128)ay * ((__int128)bx * cz - (__int128)bz * cx) +
-                 (__int128)az * ((__int128)bx * cy - (__int128)by * cx);
-    if (d <= 0) dev_fail(st, RPD_E_INVALID, CNT_INVALID);
+    return -1;
+}
+
+__device__ __forceinline__ long long table_find(const uint64_t* tk, unsigned long long mask, int shift, uint64_t key) {
+    unsigned long long h = hslot(key, shift);
+    for (unsigned long long it = 0; it <= mask; it++) {
+        const uint64_t k = tk[h];
+        if (k == key) return (long long)h;
+        if (k == HEMPTY) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
 }
 
 __device__ __forceinline__ void sort3(unsigned long long& a, unsigned long long& b, unsigned long long& c) {
@@ -72,92 +101,124 @@ __device__ __forceinline__ void sort3(unsigned long long& a, unsigned long long&
 }
 
 // Face f of a tet is the triangle opposite local vertex f.
-// Vertex ids use vb bits (nv <= 2^vb), so a face key has 3 vb bits.
-__global__ void k_face_keys(const int32_t* __restrict__ T, long long nt, int vb, uint64_t* __restrict__ key,
-                            uint32_t* __restrict__ val) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 4 * nt) return;
-    long long t = i >> 2;
-    int f = (int)(i & 3);
-    unsigned long long v[3];
+__device__ __forceinline__ uint64_t face_key(const int v[4], int f, int vb) {
+    unsigned long long w[3];
     int n = 0;
+#pragma unroll
     for (int c = 0; c < 4; c++)
-        if (c != f) v[n++] = (unsigned)T[4 * t + c] & ((1u << vb) - 1u);
-    sort3(v[0], v[1], v[2]);
-    key[i] = (v[0] << (2 * vb)) | (v[1] << vb) | v[2];
-    val[i] = (uint32_t)i;
+        if (c != f) w[n++] = (unsigned)v[c];
+    sort3(w[0], w[1], w[2]);
+    return (w[0] << (2 * vb)) | (w[1] << vb) | w[2];
 }
 
-__global__ void k_edge_keys(const int32_t* __restrict__ T, long long nt, int vb, uint64_t* __restrict__ key,
-                            uint32_t* __restrict__ val) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 6 * nt) return;
-    long long t = i / 6;
-    int e = (int)(i - 6 * t);
-    const int EA[6] = {0, 0, 0, 1, 1, 2}, EB[6] = {1, 2, 3, 2, 3, 3};
-    unsigned long long a = (unsigned)T[4 * t + EA[e]] & ((1u << vb) - 1u);
-    unsigned long long b = (unsigned)T[4 * t + EB[e]] & ((1u << vb) - 1u);
-    if (a > b) { unsigned long long s = a; a = b; b = s; }
-    key[i] = (a << vb) | b;
-    val[i] = (uint32_t)i;
+__device__ __forceinline__ uint64_t edge_key(const int v[4], int e, int vb) {
+    const int ea = e < 3 ? 0 : (e < 5 ? 1 : 2);
+    const int eb = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+    unsigned long long a = (unsigned)v[ea], b = (unsigned)v[eb];
+    if (a > b) {
+        const unsigned long long t = a;
+        a = b;
+        b = t;
+    }
+    return (a << vb) | b;
 }
 
-// Runs of equal face keys: adjacency, face ownership, > 2 tets -> error.
-__global__ void k_face_runs(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val, long long n,
-                            int32_t* __restrict__ adj, uint32_t* __restrict__ own, DevState* st) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint64_t k = key[i];
-    bool first = (i == 0) || key[i - 1] != k;
-    if (!first) return;
-    long long j = i + 1;
-    while (j < n && key[j] == k && j - i < 3) j++;
-    long long cnt = j - i;
-    if (cnt > 2) {
-        dev_fail(st, RPD_E_NONMANIFOLD, CNT_NONMANIFOLD);
+__device__ __forceinline__ bool load_tet_ids(const int32_t* __restrict__ T, long long t, long long nv, int v[4]) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        v[a] = T[4 * t + a];
+        ok &= v[a] >= 0 && v[a] < nv;
+    }
+    return ok;
+}
+
+// Exact orientation (det[p1-p0, p2-p0, p3-p0] > 0 with 128-bit integers) and
+// table insertion.
+__global__ void k_mesh_insert(const int32_t* __restrict__ T, long long nt, long long nv,
+                              const int32_t* __restrict__ Xi, MeshTables M, DevState* st) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int v[4];
+    if (!load_tet_ids(T, t, nv, v)) {
+        dev_fail(st, RPD_E_INVALID, CNT_INVALID);
         return;
     }
-    uint32_t a = val[i];
-    atomicOr(&own[a >> 2], 1u << (10 + (a & 3)));
-    if (cnt == 2) {
-        uint32_t b = val[i + 1];
-        adj[a] = (int32_t)(b >> 2);
-        adj[b] = (int32_t)(a >> 2);
+    const int3 p0 = ld_int3(Xi, v[0]), p1 = ld_int3(Xi, v[1]), p2 = ld_int3(Xi, v[2]), p3 = ld_int3(Xi, v[3]);
+    const long long ax = p1.x - p0.x, ay = p1.y - p0.y, az = p1.z - p0.z;
+    const long long bx = p2.x - p0.x, by = p2.y - p0.y, bz = p2.z - p0.z;
+    const long long cx = p3.x - p0.x, cy = p3.y - p0.y, cz = p3.z - p0.z;
+    const __int128 d = (__int128)ax * ((__int128)by * cz - (__int128)bz * cy) -
+                       (__int128)ay * ((__int128)bx * cz - (__int128)bz * cx) +
+                       (__int128)az * ((__int128)bx * cy - (__int128)by * cx);
+    if (d <= 0) {
+        dev_fail(st, RPD_E_INVALID, CNT_INVALID);
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++) atomicMin(&M.vmin[v[a]], (uint32_t)t);
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+        const long long h = table_insert(M.fk, M.fmask, M.fshift, face_key(v, f, M.vb));
+        if (h < 0) {
+            dev_fail(st, RPD_E_OVERFLOW, CNT_CAPACITY);
+            continue;
+        }
+        const uint32_t i = (uint32_t)(4 * t + f);
+        atomicAdd(&M.fc[h], 1u);
+        atomicMin(&M.fmin[h], i);
+        atomicMax(&M.fmax[h], i);
+    }
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        const long long h = table_insert(M.ek, M.emask, M.eshift, edge_key(v, e, M.vb));
+        if (h < 0) {
+            dev_fail(st, RPD_E_OVERFLOW, CNT_CAPACITY);
+            continue;
+        }
+        atomicMin(&M.emin[h], (uint32_t)(6 * t + e));
     }
 }
 
-__global__ void k_edge_runs(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val, long long n,
-                            uint32_t* __restrict__ own) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (i == 0 || key[i - 1] != key[i]) {
-        uint32_t a = val[i];   // stable sort: lowest tet first
-        atomicOr(&own[a / 6], 1u << (4 + a % 6));
-    }
-}
-
-__global__ void k_vertex_min(const int32_t* __restrict__ T, long long nt, long long nv, int32_t* __restrict__ vmin) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 4 * nt) return;
-    int v = T[i];
-    if (v >= 0 && v < nv) atomicMin(&vmin[v], (int32_t)(i >> 2));
-}
-
-__global__ void k_vertex_own(const int32_t* __restrict__ T, long long nt, long long nv,
-                             const int32_t* __restrict__ vmin, uint32_t* __restrict__ own) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Adjacency (adj[4t+f] = tet across face f, or -1) and ownership bits:
+// 0..3 vertices, 4..9 edges, 10..13 faces.
+__global__ void k_mesh_finish(const int32_t* __restrict__ T, long long nt, long long nv, MeshTables M,
+                              int32_t* __restrict__ adj, uint32_t* __restrict__ own, DevState* st) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
-    uint32_t b = 0;
-    for (int a = 0; a < 4; a++) {
-        int v = T[4 * t + a];
-        if (v >= 0 && v < nv && vmin[v] == (int32_t)t) b |= 1u << a;
+    int v[4];
+    if (!load_tet_ids(T, t, nv, v)) {
+        own[t] = 0;
+#pragma unroll
+        for (int f = 0; f < 4; f++) adj[4 * t + f] = -1;
+        return;
     }
-    atomicOr(&own[t], b);
-}
-
-__global__ void k_fill_i32(int32_t* p, long long n, int32_t v) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = v;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+        if (M.vmin[v[a]] == (uint32_t)t) bits |= 1u << a;
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+        const uint32_t i = (uint32_t)(4 * t + f);
+        int32_t nb = -1;
+        const long long h = table_find(M.fk, M.fmask, M.fshift, face_key(v, f, M.vb));
+        if (h >= 0) {
+            const uint32_t c = M.fc[h], mn = M.fmin[h];
+            if (c > 2) {
+                dev_fail(st, RPD_E_NONMANIFOLD, CNT_NONMANIFOLD);
+            } else {
+                if (mn == i) bits |= 1u << (10 + f);
+                if (c == 2) nb = (int32_t)((mn == i ? M.fmax[h] : mn) >> 2);
+            }
+        }
+        adj[4 * t + f] = nb;
+    }
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        const long long h = table_find(M.ek, M.emask, M.eshift, edge_key(v, e, M.vb));
+        if (h >= 0 && M.emin[h] == (uint32_t)(6 * t + e)) bits |= 1u << (4 + e);
+    }
+    own[t] = bits;
 }
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -181,46 +242,47 @@ void launch_snap(const double* d_verts, long long nv, const double* d_centers, c
     }
 }
 
+static int log2_cap(long long n) {
+    int b = 4;
+    while ((1ll << b) < n) b++;
+    return b;
+}
+
 size_t prep_tmp_bytes(long long nt, long long nv) {
-    long long n = 6 * nt;
-    return 2 * al(sizeof(uint64_t) * n) + 2 * al(sizeof(uint32_t) * n) + al(sizeof(int32_t) * nv) +
-           al(radix_tmp_bytes(n));
+    const long long cf = 1ll << log2_cap(6 * nt), ce = 1ll << log2_cap(8 * nt);
+    return al(sizeof(uint64_t) * (cf + ce)) + al(sizeof(uint32_t) * (cf + ce + nv)) +
+           al(sizeof(uint32_t) * 2 * cf);
 }
 
 void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, int32_t* adj,
                       uint32_t* own, void* tmp, DevState* st, cudaStream_t s) {
+    if (nt <= 0) return;
     const int T = 256;
-    long long n6 = 6 * nt;
+    const int bf = log2_cap(6 * nt), be = log2_cap(8 * nt);
+    const long long cf = 1ll << bf, ce = 1ll << be;
     char* p = (char*)tmp;
-    uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * n6);
-    uint64_t* k1 = (uint64_t*)p; p += al(sizeof(uint64_t) * n6);
-    uint32_t* v0 = (uint32_t*)p; p += al(sizeof(uint32_t) * n6);
-    uint32_t* v1 = (uint32_t*)p; p += al(sizeof(uint32_t) * n6);
-    int32_t* vmin = (int32_t*)p; p += al(sizeof(int32_t) * nv);
-    void* rtmp = p;
-    k_check_tets<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, Xi, st);
-    note_launch();
-    cudaMemsetAsync(own, 0, sizeof(uint32_t) * nt, s);
-    cudaMemsetAsync(adj, 0xff, sizeof(int32_t) * 4 * nt, s);
+    MeshTables M;
+    M.fk = (uint64_t*)p;
+    M.ek = M.fk + cf;
+    p += al(sizeof(uint64_t) * (cf + ce));
+    M.fmin = (uint32_t*)p;
+    M.emin = M.fmin + cf;
+    M.vmin = M.emin + ce;
+    p += al(sizeof(uint32_t) * (cf + ce + nv));
+    M.fc = (uint32_t*)p;
+    M.fmax = M.fc + cf;
+    M.fmask = (unsigned long long)(cf - 1);
+    M.emask = (unsigned long long)(ce - 1);
+    M.fshift = 64 - bf;
+    M.eshift = 64 - be;
     int vb = 1;
     while ((1ll << vb) < nv) vb++;
-    // faces
-    k_face_keys<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
+    M.vb = vb;
+    cudaMemsetAsync(M.fk, 0xff, sizeof(uint64_t) * (cf + ce), s);
+    cudaMemsetAsync(M.fmin, 0xff, sizeof(uint32_t) * (cf + ce + nv), s);
+    cudaMemsetAsync(M.fc, 0, sizeof(uint32_t) * 2 * cf, s);
+    k_mesh_insert<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, Xi, M, st);
     note_launch();
-    radix_sort_pairs(k0, v0, k1, v1, 4 * nt, 3 * vb, rtmp, &st->err, s);
-    k_face_runs<<<nblk(4 * nt, T), T, 0, s>>>(k1, v1, 4 * nt, adj, own, st);
-    note_launch();
-    // edges
-    k_edge_keys<<<nblk(n6, T), T, 0, s>>>(d_tets, nt, vb, k0, v0);
-    note_launch();
-    radix_sort_pairs(k0, v0, k1, v1, n6, 2 * vb, rtmp, &st->err, s);
-    k_edge_runs<<<nblk(n6, T), T, 0, s>>>(k1, v1, n6, own);
-    note_launch();
-    // vertices
-    k_fill_i32<<<nblk(nv, T), T, 0, s>>>(vmin, nv, 0x7fffffff);
-    note_launch();
-    k_vertex_min<<<nblk(4 * nt, T), T, 0, s>>>(d_tets, nt, nv, vmin);
-    note_launch();
-    k_vertex_own<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, vmin, own);
+    k_mesh_finish<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, M, adj, own, st);
     note_launch();
 }
