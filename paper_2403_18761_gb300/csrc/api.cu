@@ -96,9 +96,7 @@ struct rpd_ctx {
     // finalised elements per kind (index kind-1)
     long long nkeys[4] = {0, 0, 0, 0};
     bool kind_ok[4] = {true, true, true, true};
-    uint64_t* ukey[4] = {nullptr, nullptr, nullptr, nullptr};
-    int32_t* uchi[4] = {nullptr, nullptr, nullptr, nullptr};
-    int32_t* ubeta[4] = {nullptr, nullptr, nullptr, nullptr};
+    FinalOut fout[4] = {};
     int64_t* piece_off = nullptr;
     long long npieces = 0;
     rpd_stats stats{};
@@ -254,36 +252,25 @@ rpd_status run_clip(rpd_ctx* c) {
     return cuda_check(c, "clip launch");
 }
 
-rpd_status finalize_kind(rpd_ctx* c, int kind, void* tmp, uint64_t* kbuf, uint32_t* pbuf, uint64_t* kout,
-                         uint32_t* pout, int32_t* parent, int64_t* d_nseg) {
+rpd_status finalize_kind(rpd_ctx* c, int kind, long long* d_count) {
     cudaStream_t s = c->stream;
-    int b = c->key_bits;
-    long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
+    const int b = c->key_bits;
+    const long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
+    FinalOut& o = c->fout[kind - 1];
+    o.count = d_count;
     if (kind == 4 && 4 * b > 64) {
         c->kind_ok[3] = false;
-        cudaMemsetAsync(d_nseg, 0, sizeof(int64_t), s);
+        cudaMemsetAsync(d_count, 0, sizeof(long long), s);
         return RPD_OK;
     }
-    uint64_t* ukey = c->alloc<uint64_t>(n);
-    int32_t* chi = c->alloc<int32_t>(n);
-    int32_t* beta = c->alloc<int32_t>(n);
-    NEED(ukey && chi && beta);
-    c->ukey[kind - 1] = ukey;
-    c->uchi[kind - 1] = chi;
-    c->ubeta[kind - 1] = beta;
-    const uint64_t* keys;
-    uint64_t sentinel;
-    if (kind == 1) {
-        sentinel = (1ull << b) - 1;
-        launch_components_cells(c->clip, n, parent, pbuf, kbuf, b, sentinel, s);
-        keys = kbuf;
-    } else {
-        sentinel = ~0ull;
-        launch_components_records(c->clip, kind - 2, n, parent, pbuf, s);
-        keys = c->clip.rkey[kind - 2];
-    }
-    radix_sort_pairs(keys, pbuf, kout, pout, n, kind * b, tmp, &c->st->err, s);
-    segmented_reduce(kout, pout, n, sentinel, ukey, chi, beta, d_nseg, tmp, s);
+    const long long rows = kind == 1 ? c->ns : n;
+    o.keys = c->alloc<int32_t>(rows * kind);
+    o.chi = c->alloc<int32_t>(rows);
+    o.beta = c->alloc<int32_t>(rows);
+    o.flag = c->alloc<uint8_t>(rows);
+    void* tmp = c->alloc<char>(finalize_tmp_bytes(kind, n, c->ns));
+    NEED(o.keys && o.chi && o.beta && o.flag && tmp);
+    launch_finalize(c->clip, kind, n, c->ns, b, o, tmp, s);
     return cuda_check(c, "finalize launch");
 }
 
@@ -441,23 +428,12 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     record(c, 4);
     for (int k = 0; k < 3; k++) c->stats.n_records[k + 1] = c->nrec[k];
     // ---- A5-A7 for every kind
-    long long nmax = npairs;
-    for (int k = 0; k < 3; k++) nmax = nmax > c->nrec[k] ? nmax : c->nrec[k];
-    size_t ftmp_bytes = radix_tmp_bytes(nmax);
-    size_t sr = segreduce_tmp_bytes(nmax);
-    if (sr > ftmp_bytes) ftmp_bytes = sr;
-    void* ftmp = c->alloc<char>(ftmp_bytes);
-    uint64_t* kbuf = c->alloc<uint64_t>(nmax);
-    uint32_t* pbuf = c->alloc<uint32_t>(nmax);
-    uint64_t* kout = c->alloc<uint64_t>(nmax);
-    uint32_t* pout = c->alloc<uint32_t>(nmax);
-    int32_t* parent = c->alloc<int32_t>(nmax);
-    int64_t* d_nseg = c->alloc<int64_t>(4);
+    long long* d_nseg = c->alloc<long long>(4);
     c->piece_off = c->alloc<int64_t>(npairs + 1);
     void* ptmp = c->alloc<char>(scan_tmp_bytes(npairs + 1));
-    NEED(ftmp && kbuf && pbuf && kout && pout && parent && d_nseg && c->piece_off && ptmp);
+    NEED(d_nseg && c->piece_off && ptmp);
     for (int kind = 1; kind <= 4; kind++) {
-        TRY(finalize_kind(c, kind, ftmp, kbuf, pbuf, kout, pout, parent, d_nseg + kind - 1));
+        TRY(finalize_kind(c, kind, d_nseg + kind - 1));
         record(c, 4 + kind);
     }
     scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
@@ -536,40 +512,38 @@ rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, i
     return RPD_OK;
 }
 
-static rpd_status copy_common(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, const int32_t* src, int32_t* d_dst,
-                              int64_t cap, int64_t* n) {
+// Copy the finalised rows of one kind: keys [m, kind] and one value array.
+static rpd_status copy_rows(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, const void* src, void* d_dst,
+                            size_t elem, int64_t cap, int64_t* n) {
     TRY(check_kind(ctx, kind));
-    long long m = ctx->nkeys[kind - 1];
+    const long long m = ctx->nkeys[kind - 1];
     if (n) *n = m;
     if (!d_keys && !d_dst) return RPD_OK;
     if (cap < m) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of elements");
-    if (d_keys) launch_unpack_keys(ctx->ukey[kind - 1], m, kind, ctx->key_bits, d_keys, ctx->stream);
-    if (d_dst && m) cudaMemcpyAsync(d_dst, src, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (m == 0) return RPD_OK;
+    const FinalOut& o = ctx->fout[kind - 1];
+    if (d_keys)
+        cudaMemcpyAsync(d_keys, o.keys, sizeof(int32_t) * m * kind, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (d_dst) cudaMemcpyAsync(d_dst, src, elem * m, cudaMemcpyDeviceToDevice, ctx->stream);
     return cuda_check(ctx, "output copy");
 }
 
 rpd_status rpd_euler(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, int32_t* d_chi, int64_t cap, int64_t* n) {
     if (!ctx) return RPD_E_INVALID;
     TRY(check_kind(ctx, kind));
-    return copy_common(ctx, kind, d_keys, ctx->uchi[kind - 1], d_chi, cap, n);
+    return copy_rows(ctx, kind, d_keys, ctx->fout[kind - 1].chi, d_chi, sizeof(int32_t), cap, n);
 }
 
 rpd_status rpd_components(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, int32_t* d_beta0, int64_t cap, int64_t* n) {
     if (!ctx) return RPD_E_INVALID;
     TRY(check_kind(ctx, kind));
-    return copy_common(ctx, kind, d_keys, ctx->ubeta[kind - 1], d_beta0, cap, n);
+    return copy_rows(ctx, kind, d_keys, ctx->fout[kind - 1].beta, d_beta0, sizeof(int32_t), cap, n);
 }
 
 rpd_status rpd_contractible(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, uint8_t* d_flag, int64_t cap, int64_t* n) {
     if (!ctx) return RPD_E_INVALID;
     TRY(check_kind(ctx, kind));
-    long long m = ctx->nkeys[kind - 1];
-    if (n) *n = m;
-    if (!d_keys && !d_flag) return RPD_OK;
-    if (cap < m) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of elements");
-    if (d_keys) launch_unpack_keys(ctx->ukey[kind - 1], m, kind, ctx->key_bits, d_keys, ctx->stream);
-    if (d_flag) launch_flags(ctx->uchi[kind - 1], ctx->ubeta[kind - 1], m, d_flag, ctx->stream);
-    return cuda_check(ctx, "flag launch");
+    return copy_rows(ctx, kind, d_keys, ctx->fout[kind - 1].flag, d_flag, sizeof(uint8_t), cap, n);
 }
 
 rpd_status rpd_pieces(rpd_ctx* ctx, int32_t* d_tet, int32_t* d_sphere, double* d_vol, double* d_moment3, int64_t cap,

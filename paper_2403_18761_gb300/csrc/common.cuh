@@ -66,3 +66,41 @@ __device__ __forceinline__ int tet_edge_index(int a, int b) {
 }
 
 static inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------ open-addressing hash sets
+// 64-bit keys (~0 marks an empty slot and is never a valid key), linear
+// probing, capacity a power of two with mask = capacity - 1 and shift = 64 -
+// log2(capacity).  Keys are only ever inserted, so a slot once set never
+// changes; a stale empty read is settled by the compare-and-swap.
+constexpr uint64_t HEMPTY = ~0ull;
+
+__device__ __forceinline__ unsigned long long hslot(uint64_t key, int shift) {
+    return (key * 0x9E3779B97F4A7C15ull) >> shift;
+}
+
+// Slot holding `key` (inserted if absent), or -1 if the table is full.
+__device__ __forceinline__ long long table_insert(uint64_t* tk, unsigned long long mask, int shift, uint64_t key) {
+    unsigned long long h = hslot(key, shift);
+    for (unsigned long long it = 0; it <= mask; it++) {
+        const uint64_t k = tk[h];
+        if (k == key) return (long long)h;
+        if (k == HEMPTY) {
+            const uint64_t old = atomicCAS((unsigned long long*)&tk[h], HEMPTY, key);
+            if (old == HEMPTY || old == key) return (long long)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Slot holding `key`, or -1.
+__device__ __forceinline__ long long table_find(const uint64_t* tk, unsigned long long mask, int shift, uint64_t key) {
+    unsigned long long h = hslot(key, shift);
+    for (unsigned long long it = 0; it <= mask; it++) {
+        const uint64_t k = tk[h];
+        if (k == key) return (long long)h;
+        if (k == HEMPTY) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}

@@ -106,12 +106,19 @@ void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs
 // ---------------------------------------------------------------- topo.cu
 // Union-find over the nodes of one element kind; writes root flags into the
 // payload (bit 16) next to the 16-bit contribution.
-void launch_components_cells(const ClipArgs& a, long long npairs, int32_t* parent, uint32_t* pay,
-                             uint64_t* keys, int key_bits, uint64_t sentinel, cudaStream_t s);
-void launch_components_records(const ClipArgs& a, int which, long long nrec, int32_t* parent, uint32_t* pay,
-                               cudaStream_t s);
-void launch_unpack_keys(const uint64_t* ukey, long long n, int kind, int key_bits, int32_t* out,
-                        cudaStream_t s);
-void launch_flags(const int32_t* chi, const int32_t* beta0, long long n, uint8_t* flag, cudaStream_t s);
+// A5-A7 for one element kind (1 = cells from the pieces, 2..4 = records):
+// union-find components, chi and beta0 per key, sorted unique keys unpacked
+// to int32 rows, contractibility flags.  Outputs hold up to n (kind 1: ns)
+// rows; *count (device) receives the number of keys.
+struct FinalOut {
+    int32_t* keys;    // [count, kind]
+    int32_t* chi;
+    int32_t* beta;
+    uint8_t* flag;
+    long long* count;
+};
+size_t finalize_tmp_bytes(int kind, long long n, long long ns);
+void launch_finalize(const ClipArgs& a, int kind, long long n, long long ns, int key_bits, const FinalOut& out,
+                     void* tmp, cudaStream_t s);
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet,
                            int32_t* d_sphere, double* d_vol, double* d_mom, cudaStream_t s);

@@ -48,8 +48,6 @@ __global__ void k_snap_radii(const double* __restrict__ r, long long n, double s
 // vertex the lowest tet.  A second pass looks every entry up again: face
 // adjacency, ownership by the lowest-numbered tet, and > 2 tets per face as a
 // non-manifold error.  The results do not depend on the insertion order.
-constexpr uint64_t HEMPTY = ~0ull;
-
 struct MeshTables {
     uint64_t* fk;   // face keys
     uint32_t* fc;   // tets per face
@@ -62,36 +60,6 @@ struct MeshTables {
     int fshift, eshift;
     int vb;
 };
-
-__device__ __forceinline__ unsigned long long hslot(uint64_t key, int shift) {
-    return (key * 0x9E3779B97F4A7C15ull) >> shift;
-}
-
-// Slot holding `key` (inserted if absent), or -1 if the table is full.
-__device__ __forceinline__ long long table_insert(uint64_t* tk, unsigned long long mask, int shift, uint64_t key) {
-    unsigned long long h = hslot(key, shift);
-    for (unsigned long long it = 0; it <= mask; it++) {
-        const uint64_t k = tk[h];
-        if (k == key) return (long long)h;
-        if (k == HEMPTY) {
-            const uint64_t old = atomicCAS((unsigned long long*)&tk[h], HEMPTY, key);
-            if (old == HEMPTY || old == key) return (long long)h;
-        }
-        h = (h + 1) & mask;
-    }
-    return -1;
-}
-
-__device__ __forceinline__ long long table_find(const uint64_t* tk, unsigned long long mask, int shift, uint64_t key) {
-    unsigned long long h = hslot(key, shift);
-    for (unsigned long long it = 0; it <= mask; it++) {
-        const uint64_t k = tk[h];
-        if (k == key) return (long long)h;
-        if (k == HEMPTY) return -1;
-        h = (h + 1) & mask;
-    }
-    return -1;
-}
 
 __device__ __forceinline__ void sort3(unsigned long long& a, unsigned long long& b, unsigned long long& c) {
     unsigned long long t;

@@ -1,4 +1,4 @@
-// Device primitives: scan, radix sort, segmented warp-shuffle reduction.
+// Device primitives: exclusive scan and onesweep radix sort.
 #include "prim.cuh"
 
 #include <cuda_runtime.h>
@@ -275,51 +275,6 @@ __global__ void __launch_bounds__(RS_THREADS) rs_pass(const uint64_t* __restrict
     }
 }
 
-// -------------------------------------------------------- segmented reduce
-__global__ void seg_heads(const uint64_t* __restrict__ keys, long long n, uint64_t sentinel,
-                          uint8_t* __restrict__ head) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint64_t k = keys[i];
-    head[i] = (k != sentinel) && (i == 0 || keys[i - 1] != k);
-}
-
-__global__ void seg_reduce(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ pay, long long n,
-                           uint64_t sentinel, const uint8_t* __restrict__ head, const int64_t* __restrict__ excl,
-                           uint64_t* __restrict__ ukey, int32_t* __restrict__ chi, int32_t* __restrict__ beta) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int lane = threadIdx.x & 31;
-    bool valid = i < n && keys[i] != sentinel;
-    long long seg = -1;
-    int c = 0, b = 0;
-    if (valid) {
-        seg = excl[i] + head[i] - 1;
-        uint32_t p = pay[i];
-        c = (int)(int16_t)(p & 0xffffu);
-        b = (int)((p >> 16) & 1u);
-        if (head[i]) ukey[seg] = keys[i];
-    }
-    // segmented inclusive scan across the warp (segments are contiguous runs)
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        long long s2 = __shfl_up_sync(0xffffffffu, seg, off);
-        int c2 = __shfl_up_sync(0xffffffffu, c, off);
-        int b2 = __shfl_up_sync(0xffffffffu, b, off);
-        if (lane >= off && s2 == seg) {
-            c += c2;
-            b += b2;
-        }
-    }
-    long long nxt = __shfl_down_sync(0xffffffffu, seg, 1);
-    bool last = (lane == 31) || (nxt != seg);
-    if (valid && last) {
-        atomicAdd(&chi[seg], c);
-        atomicAdd(&beta[seg], b);
-    }
-}
-
-__global__ void seg_count(const int64_t* excl, long long n, int64_t* d_nseg) { *d_nseg = excl[n]; }
-
 }  // namespace
 
 size_t scan_tmp_bytes(long long n) { return scan_tmp_rec(n) + 64; }
@@ -393,31 +348,4 @@ void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t
 void radix_sort_pairs_dn(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                          const long long* d_n, long long nmax, int bits, void* tmp, int* d_err, cudaStream_t s) {
     radix_sort_impl(keys_in, vals_in, keys_out, vals_out, d_n, nmax, bits, tmp, d_err, s);
-}
-
-size_t segreduce_tmp_bytes(long long n) {
-    return align256((size_t)(n > 0 ? n : 1)) + align256(sizeof(int64_t) * (size_t)(n + 1)) +
-           align256(scan_tmp_bytes(n));
-}
-
-void segmented_reduce(const uint64_t* keys, const uint32_t* pay, long long n, uint64_t sentinel, uint64_t* ukey,
-                      int32_t* chi, int32_t* beta0, int64_t* d_nseg, void* tmp, cudaStream_t s) {
-    if (n <= 0) {
-        cudaMemsetAsync(d_nseg, 0, sizeof(int64_t), s);
-        return;
-    }
-    char* p = (char*)tmp;
-    uint8_t* head = (uint8_t*)p; p += align256((size_t)n);
-    int64_t* excl = (int64_t*)p; p += align256(sizeof(int64_t) * (n + 1));
-    void* stmp = p;
-    const int T = 256;
-    seg_heads<<<div_up_ll(n, T), T, 0, s>>>(keys, n, sentinel, head);
-    note_launch();
-    scan_impl<uint8_t>(head, excl, n, stmp, s);
-    cudaMemsetAsync(chi, 0, sizeof(int32_t) * n, s);
-    cudaMemsetAsync(beta0, 0, sizeof(int32_t) * n, s);
-    seg_reduce<<<div_up_ll(n, T), T, 0, s>>>(keys, pay, n, sentinel, head, excl, ukey, chi, beta0);
-    note_launch();
-    seg_count<<<1, 1, 0, s>>>(excl, n, d_nseg);
-    note_launch();
 }

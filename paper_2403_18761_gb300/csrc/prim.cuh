@@ -1,5 +1,5 @@
-// Device primitives: exclusive scan, LSD radix sort, segmented warp-shuffle
-// reduction, stream compaction.  All stream-ordered, no host synchronisation.
+// Device primitives: exclusive scan and LSD radix sort.  All stream-ordered,
+// no host synchronisation.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,12 +28,3 @@ void radix_sort_pairs_dn(const uint64_t* keys_in, const uint32_t* vals_in, uint6
                          uint32_t* vals_out, const long long* d_n, long long nmax, int bits, void* tmp, int* d_err,
                          cudaStream_t s);
 
-// Segmented reduction over runs of equal keys (keys sorted; runs whose key is
-// `sentinel` are ignored).  Payload bits 0..15 hold a signed contribution to
-// chi, bit 16 a root flag counted into beta0.  Outputs (capacity n) receive
-// one entry per run in key order; *d_nseg (device) the number of runs.
-// tmp must hold segreduce_tmp_bytes(n).
-size_t segreduce_tmp_bytes(long long n);
-void segmented_reduce(const uint64_t* keys, const uint32_t* pay, long long n, uint64_t sentinel,
-                      uint64_t* ukey, int32_t* chi, int32_t* beta0, int64_t* d_nseg, void* tmp,
-                      cudaStream_t s);

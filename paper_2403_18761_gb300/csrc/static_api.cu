@@ -244,41 +244,26 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
     TRY_S(read_status(st, s));
     for (int k = 0; k < 3; k++)
         if ((long long)cnt[k] > rc[k]) return fail_static(RPD_E_OVERFLOW, "element records exceed their capacity");
-    // ---- A5: chi of the requested kind (segmented warp-shuffle sums)
+    // ---- A5-A7 for the requested kind
     const long long n = kind == 1 ? npairs : (long long)cnt[kind - 2];
-    void* ftmp = ar.take<char>(radix_tmp_bytes(n) > segreduce_tmp_bytes(n) ? radix_tmp_bytes(n)
-                                                                           : segreduce_tmp_bytes(n));
-    uint64_t* kbuf = ar.take<uint64_t>(n);
-    uint32_t* pbuf = ar.take<uint32_t>(n);
-    uint64_t* kout = ar.take<uint64_t>(n);
-    uint32_t* pout = ar.take<uint32_t>(n);
-    int32_t* parent = ar.take<int32_t>(n);
-    uint64_t* ukey = ar.take<uint64_t>(n);
-    int32_t* chi = ar.take<int32_t>(n);
-    int32_t* beta = ar.take<int32_t>(n);
-    int64_t* d_nseg = ar.take<int64_t>(1);
+    const long long rows = kind == 1 ? ns : n;
+    FinalOut fo;
+    fo.keys = ar.take<int32_t>(rows * kind);
+    fo.chi = ar.take<int32_t>(rows);
+    fo.beta = ar.take<int32_t>(rows);
+    fo.flag = ar.take<uint8_t>(rows);
+    fo.count = ar.take<long long>(1);
+    void* ftmp = ar.take<char>(finalize_tmp_bytes(kind, n, ns));
     NEED_S(!ar.full);
-    const uint64_t* keys;
-    uint64_t sentinel;
-    if (kind == 1) {
-        sentinel = (1ull << b) - 1;
-        launch_components_cells(a, n, parent, pbuf, kbuf, b, sentinel, s);
-        keys = kbuf;
-    } else {
-        sentinel = ~0ull;
-        launch_components_records(a, kind - 2, n, parent, pbuf, s);
-        keys = a.rkey[kind - 2];
-    }
-    radix_sort_pairs(keys, pbuf, kout, pout, n, kind * b, ftmp, &st->err, s);
-    segmented_reduce(kout, pout, n, sentinel, ukey, chi, beta, d_nseg, ftmp, s);
+    launch_finalize(a, kind, n, ns, b, fo, ftmp, s);
     long long m = 0;
-    cudaMemcpyAsync(&m, d_nseg, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&m, fo.count, sizeof(long long), cudaMemcpyDeviceToHost, s);
     TRY_S(read_status(st, s));
     *n_out = m;
     if (!d_keys && !d_chi) return RPD_OK;
     if (cap < m) return fail_static(RPD_E_INVALID, "cap is smaller than the number of elements");
-    if (d_keys) launch_unpack_keys(ukey, m, kind, b, d_keys, s);
-    if (d_chi && m) cudaMemcpyAsync(d_chi, chi, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s);
+    if (d_keys && m) cudaMemcpyAsync(d_keys, fo.keys, sizeof(int32_t) * m * kind, cudaMemcpyDeviceToDevice, s);
+    if (d_chi && m) cudaMemcpyAsync(d_chi, fo.chi, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return fail_static(RPD_E_CUDA, "CUDA error in rpd_euler_static");

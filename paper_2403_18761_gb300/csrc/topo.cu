@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
+#include "prim.cuh"
 
 namespace {
 
@@ -123,42 +124,88 @@ __global__ void k_link_records(ClipArgs A, int which, long long nrec, int32_t* _
     }
 }
 
-__global__ void k_cell_payload(ClipArgs A, long long npairs, int32_t* __restrict__ parent, uint32_t* __restrict__ pay,
-                               uint64_t* __restrict__ keys, uint64_t sentinel) {
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npairs) return;
-    if (A.pflag[p] != 1) {
-        keys[p] = sentinel;
-        pay[p] = 0;
+// ------------------------------------------------------ aggregation (A5-A7)
+// Cells: chi and root counts summed straight into per-sphere slots.
+__global__ void k_cell_agg(ClipArgs A, long long npairs, int32_t* __restrict__ parent, int32_t* __restrict__ cchi,
+                           int32_t* __restrict__ cbeta, uint8_t* __restrict__ cpres) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs || A.pflag[p] != 1) return;
+    const long long t = A.pair_tet[p];
+    const int i = A.cand[t * RPD_MAXC + (p - A.pair_off[t])];
+    const bool root = uf_find(parent, (int)p) == (int)p;
+    atomicAdd(&cchi[i], (int)A.c_val[p]);
+    if (root) atomicAdd(&cbeta[i], 1);
+    cpres[i] = 1;
+}
+
+__global__ void k_cell_emit(long long ns, const uint8_t* __restrict__ cpres, const int64_t* __restrict__ pos,
+                            const int32_t* __restrict__ cchi, const int32_t* __restrict__ cbeta,
+                            int32_t* __restrict__ keys, int32_t* __restrict__ chi, int32_t* __restrict__ beta,
+                            uint8_t* __restrict__ flag, long long* __restrict__ count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *count = pos[ns];
+    if (i >= ns || !cpres[i]) return;
+    const long long q = pos[i];
+    const int c = cchi[i], b = cbeta[i];
+    keys[q] = (int32_t)i;
+    chi[q] = c;
+    beta[q] = b;
+    flag[q] = (b == 1 && c == 1) ? 1 : 0;
+}
+
+// Faces, edges, vertices: records hashed by key; chi and root counts summed
+// into the key's slot.
+__global__ void k_rec_agg(ClipArgs A, int which, long long nrec, int32_t* __restrict__ parent, uint64_t* __restrict__ tk,
+                          int32_t* __restrict__ tchi, int32_t* __restrict__ tbeta, unsigned long long mask,
+                          int shift) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    const uint64_t key = A.rkey[which][r];
+    const bool root = parent ? uf_find(parent, (int)r) == (int)r : true;
+    const long long h = table_insert(tk, mask, shift, key);
+    if (h < 0) {   // cannot happen: capacity >= 2 * records
+        dev_fail(A.st, RPD_E_OVERFLOW, CNT_CAPACITY);
         return;
     }
-    long long t = A.pair_tet[p];
-    int i = A.cand[t * RPD_MAXC + (p - A.pair_off[t])];
-    int root = uf_find(parent, (int)p) == (int)p;
-    keys[p] = (uint64_t)i;
-    pay[p] = ((uint32_t)(uint16_t)(int16_t)A.c_val[p]) | ((uint32_t)root << 16);
+    atomicAdd(&tchi[h], (int)A.rval[which][r]);
+    if (root) atomicAdd(&tbeta[h], 1);
 }
 
-__global__ void k_record_payload(ClipArgs A, int which, long long nrec, int32_t* __restrict__ parent,
-                                 uint32_t* __restrict__ pay) {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrec) return;
-    int root = parent ? (uf_find(parent, (int)r) == (int)r) : 1;
-    pay[r] = ((uint32_t)(uint16_t)A.rval[which][r]) | ((uint32_t)root << 16);
+// Occupied slots appended (warp-aggregated) to (key, slot) lists.
+__global__ void k_table_compact(const uint64_t* __restrict__ tk, long long cap, uint64_t* __restrict__ ck,
+                                uint32_t* __restrict__ cs, unsigned long long* __restrict__ count) {
+    const long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint64_t key = h < cap ? tk[h] : HEMPTY;
+    const bool occ = key != HEMPTY;
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    if (!m) return;
+    unsigned long long base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (occ) {
+        const unsigned long long q = base + __popc(m & ((1u << lane) - 1u));
+        ck[q] = key;
+        cs[q] = (uint32_t)h;
+    }
 }
 
-__global__ void k_unpack(const uint64_t* __restrict__ ukey, long long n, int kind, int b, int32_t* __restrict__ out) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint64_t k = ukey[i];
-    uint64_t mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
-    for (int j = 0; j < kind; j++) out[i * kind + j] = (int32_t)((k >> (b * (kind - 1 - j))) & mask);
-}
-
-__global__ void k_flags(const int32_t* __restrict__ chi, const int32_t* __restrict__ beta, long long n,
-                        uint8_t* __restrict__ flag) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = (beta[i] == 1 && chi[i] == 1) ? 1 : 0;
+__global__ void k_rec_emit(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ ss,
+                           const unsigned long long* __restrict__ count, long long nmax, int kind, int b,
+                           const int32_t* __restrict__ tchi, const int32_t* __restrict__ tbeta,
+                           int32_t* __restrict__ keys, int32_t* __restrict__ chi, int32_t* __restrict__ beta,
+                           uint8_t* __restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)*count;
+    if (i >= n || i >= nmax) return;
+    const uint64_t k = sk[i];
+    const uint32_t h = ss[i];
+    const uint64_t mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
+    for (int j = 0; j < kind; j++) keys[i * kind + j] = (int32_t)((k >> (b * (kind - 1 - j))) & mask);
+    const int c = tchi[h], bb = tbeta[h];
+    chi[i] = c;
+    beta[i] = bb;
+    flag[i] = (bb == 1 && c == 1) ? 1 : 0;
 }
 
 __global__ void k_compact_pieces(ClipArgs A, long long npairs, const int64_t* __restrict__ off, int32_t* d_tet,
@@ -176,44 +223,95 @@ __global__ void k_compact_pieces(ClipArgs A, long long npairs, const int64_t* __
 
 }  // namespace
 
-void launch_components_cells(const ClipArgs& a, long long npairs, int32_t* parent, uint32_t* pay, uint64_t* keys,
-                             int key_bits, uint64_t sentinel, cudaStream_t s) {
-    (void)key_bits;
-    if (npairs <= 0) return;
-    k_iota<<<nblk(npairs, 256), 256, 0, s>>>(parent, npairs);
-    note_launch();
-    k_link_cells<<<nblk(npairs, 256), 256, 0, s>>>(a, npairs, parent);
-    note_launch();
-    k_cell_payload<<<nblk(npairs, 256), 256, 0, s>>>(a, npairs, parent, pay, keys, sentinel);
-    note_launch();
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int table_bits(long long n) {
+    int b = 4;
+    while ((1ll << b) < 2 * n) b++;
+    return b;
 }
 
-void launch_components_records(const ClipArgs& a, int which, long long nrec, int32_t* parent, uint32_t* pay,
-                               cudaStream_t s) {
-    if (nrec <= 0) return;
-    if (which < 2) {
-        k_iota<<<nblk(nrec, 256), 256, 0, s>>>(parent, nrec);
+size_t finalize_tmp_bytes(int kind, long long n, long long ns) {
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    if (kind == 1) {
+        return al256(sizeof(int32_t) * m) + al256(sizeof(int32_t) * 2 * ns) + al256((size_t)ns) +
+               al256(sizeof(int64_t) * (ns + 1)) + al256(scan_tmp_bytes(ns));
+    }
+    const size_t cap = (size_t)1 << table_bits(n);
+    return al256(sizeof(int32_t) * m) + al256(sizeof(uint64_t) * cap) + al256(sizeof(int32_t) * 2 * cap) +
+           al256(sizeof(unsigned long long)) + 2 * al256(sizeof(uint64_t) * m) + 2 * al256(sizeof(uint32_t) * m) +
+           al256(radix_tmp_bytes(n));
+}
+
+void launch_finalize(const ClipArgs& a, int kind, long long n, long long ns, int key_bits, const FinalOut& out,
+                     void* tmp, cudaStream_t s) {
+    char* p = (char*)tmp;
+    int32_t* parent = (int32_t*)p;
+    p += al256(sizeof(int32_t) * (n > 0 ? n : 1));
+    if (kind == 1) {
+        int32_t* cchi = (int32_t*)p;
+        int32_t* cbeta = cchi + ns;
+        p += al256(sizeof(int32_t) * 2 * ns);
+        uint8_t* cpres = (uint8_t*)p;
+        p += al256((size_t)ns);
+        int64_t* pos = (int64_t*)p;
+        p += al256(sizeof(int64_t) * (ns + 1));
+        cudaMemsetAsync(cchi, 0, sizeof(int32_t) * 2 * ns, s);
+        cudaMemsetAsync(cpres, 0, (size_t)ns, s);
+        if (n > 0) {
+            k_iota<<<nblk(n, 256), 256, 0, s>>>(parent, n);
+            note_launch();
+            k_link_cells<<<nblk(n, 256), 256, 0, s>>>(a, n, parent);
+            note_launch();
+            k_cell_agg<<<nblk(n, 256), 256, 0, s>>>(a, n, parent, cchi, cbeta, cpres);
+            note_launch();
+        }
+        scan_excl(cpres, pos, ns, p, s);
+        k_cell_emit<<<nblk(ns, 256), 256, 0, s>>>(ns, cpres, pos, cchi, cbeta, out.keys, out.chi, out.beta, out.flag,
+                                                  out.count);
         note_launch();
-        k_link_records<<<nblk(nrec, 256), 256, 0, s>>>(a, which, nrec, parent);
-        note_launch();
-        k_record_payload<<<nblk(nrec, 256), 256, 0, s>>>(a, which, nrec, parent, pay);
-        note_launch();
-    } else {
-        k_record_payload<<<nblk(nrec, 256), 256, 0, s>>>(a, which, nrec, nullptr, pay);
+        return;
+    }
+    const int which = kind - 2;
+    const int tb = table_bits(n);
+    const long long cap = 1ll << tb;
+    uint64_t* tk = (uint64_t*)p;
+    p += al256(sizeof(uint64_t) * cap);
+    int32_t* tchi = (int32_t*)p;
+    int32_t* tbeta = tchi + cap;
+    p += al256(sizeof(int32_t) * 2 * cap);
+    unsigned long long* cnt = (unsigned long long*)p;
+    p += al256(sizeof(unsigned long long));
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    uint64_t* ck = (uint64_t*)p; p += al256(sizeof(uint64_t) * m);
+    uint64_t* sk = (uint64_t*)p; p += al256(sizeof(uint64_t) * m);
+    uint32_t* cs = (uint32_t*)p; p += al256(sizeof(uint32_t) * m);
+    uint32_t* ss = (uint32_t*)p; p += al256(sizeof(uint32_t) * m);
+    cudaMemsetAsync(tk, 0xff, sizeof(uint64_t) * cap, s);
+    cudaMemsetAsync(tchi, 0, sizeof(int32_t) * 2 * cap, s);
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+    if (n > 0) {
+        int32_t* par = nullptr;
+        if (which < 2) {   // faces and edges have components across tets; vertices are points
+            k_iota<<<nblk(n, 256), 256, 0, s>>>(parent, n);
+            note_launch();
+            k_link_records<<<nblk(n, 256), 256, 0, s>>>(a, which, n, parent);
+            note_launch();
+            par = parent;
+        }
+        k_rec_agg<<<nblk(n, 256), 256, 0, s>>>(a, which, n, par, tk, tchi, tbeta, (unsigned long long)(cap - 1),
+                                               64 - tb);
         note_launch();
     }
-}
-
-void launch_unpack_keys(const uint64_t* ukey, long long n, int kind, int key_bits, int32_t* out, cudaStream_t s) {
-    if (n <= 0) return;
-    k_unpack<<<nblk(n, 256), 256, 0, s>>>(ukey, n, kind, key_bits, out);
+    k_table_compact<<<nblk(cap, 256), 256, 0, s>>>(tk, cap, ck, cs, cnt);
     note_launch();
-}
-
-void launch_flags(const int32_t* chi, const int32_t* beta0, long long n, uint8_t* flag, cudaStream_t s) {
-    if (n <= 0) return;
-    k_flags<<<nblk(n, 256), 256, 0, s>>>(chi, beta0, n, flag);
-    note_launch();
+    radix_sort_pairs_dn(ck, cs, sk, ss, (const long long*)cnt, n, kind * key_bits, p, &a.st->err, s);
+    if (n > 0) {
+        k_rec_emit<<<nblk(n, 256), 256, 0, s>>>(sk, ss, cnt, n, kind, key_bits, tchi, tbeta, out.keys, out.chi,
+                                                out.beta, out.flag);
+        note_launch();
+    }
+    cudaMemcpyAsync(out.count, cnt, sizeof(long long), cudaMemcpyDeviceToDevice, s);
 }
 
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet, int32_t* d_sphere,

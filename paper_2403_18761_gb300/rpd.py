@@ -125,12 +125,15 @@ class Ctx:
         self.stream = stream
         self.device = device
         self._keep = keep
+        self._nkeys = list(self.rpd_stats_get()["n_keys"])   # element counts per kind (fixed after the build)
 
     def _check(self, st):
         if st != RPD_OK:
             raise RpdError(st, load().rpd_last_error(self.handle).decode())
 
     def _query(self, fn, kind):
+        if 1 <= kind <= 4:
+            return self._nkeys[kind - 1]
         n = ctypes.c_int64(0)
         self._check(fn(self.handle, kind, None, None, 0, ctypes.byref(n)))
         return n.value
