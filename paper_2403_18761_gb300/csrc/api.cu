@@ -100,7 +100,7 @@ struct rpd_ctx {
     int64_t* piece_off = nullptr;
     long long npieces = 0;
     rpd_stats stats{};
-    cudaEvent_t ev[10] = {};
+    cudaEvent_t ev[16] = {};
 
     template <typename T>
     T* alloc(size_t count) {
@@ -252,15 +252,15 @@ rpd_status run_clip(rpd_ctx* c) {
     return cuda_check(c, "clip launch");
 }
 
-rpd_status finalize_kind(rpd_ctx* c, int kind, long long* d_count) {
-    cudaStream_t s = c->stream;
+// Output and workspace buffers of one kind's finalisation.
+rpd_status finalize_alloc(rpd_ctx* c, int kind, long long* d_count, void** tmp) {
     const int b = c->key_bits;
     const long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
     FinalOut& o = c->fout[kind - 1];
     o.count = d_count;
+    *tmp = nullptr;
     if (kind == 4 && 4 * b > 64) {
         c->kind_ok[3] = false;
-        cudaMemsetAsync(d_count, 0, sizeof(long long), s);
         return RPD_OK;
     }
     const long long rows = kind == 1 ? c->ns : n;
@@ -268,10 +268,9 @@ rpd_status finalize_kind(rpd_ctx* c, int kind, long long* d_count) {
     o.chi = c->alloc<int32_t>(rows);
     o.beta = c->alloc<int32_t>(rows);
     o.flag = c->alloc<uint8_t>(rows);
-    void* tmp = c->alloc<char>(finalize_tmp_bytes(kind, n, c->ns));
-    NEED(o.keys && o.chi && o.beta && o.flag && tmp);
-    launch_finalize(c->clip, kind, n, c->ns, b, o, tmp, s);
-    return cuda_check(c, "finalize launch");
+    *tmp = c->alloc<char>(finalize_tmp_bytes(kind, n, c->ns));
+    NEED(o.keys && o.chi && o.beta && o.flag && *tmp);
+    return RPD_OK;
 }
 
 void record(rpd_ctx* c, int k) { cudaEventRecord(c->ev[k], c->stream); }
@@ -289,8 +288,12 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
                  const double* d_radii) {
     cudaStream_t s = c->stream;
     const long long nv = c->nv, nt = c->nt, ns = c->ns;
-    for (int k = 0; k < 10; k++)
+    for (int k = 0; k < 16; k++)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
+    // side streams: mesh combinatorics next to the sphere grid and kNN, the
+    // clip bins, and the four element kinds of the finalisation
+    BinStreams* bs = bin_streams();
+    if (!bs) return fail(c, RPD_E_CUDA, "stream creation failed");
     record(c, 0);
     c->st = c->alloc<DevState>(1);
     c->Xi = c->alloc<int32_t>(3 * nv);
@@ -307,9 +310,11 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     size_t tmp_bytes = prep_tmp_bytes(nt, nv);
     void* tmp = c->alloc<char>(tmp_bytes);
     NEED(tmp);
-    launch_prep_mesh(c->tets, nt, nv, c->Xi, c->adj, c->own, tmp, c->st, s);
-    TRY(cuda_check(c, "prep launch"));
     record(c, 1);
+    cudaStreamWaitEvent(bs->s[0], c->ev[1], 0);
+    launch_prep_mesh(c->tets, nt, nv, c->Xi, c->adj, c->own, tmp, c->st, bs->s[0]);
+    cudaEventRecord(c->ev[2], bs->s[0]);
+    TRY(cuda_check(c, "prep launch"));
     // ---- A1
     long long ncap = 2 * ns + 64;
     c->gp = c->alloc<GridParams>(1);
@@ -329,7 +334,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp,
                &c->st->err, s);
     TRY(cuda_check(c, "knn launch"));
-    record(c, 2);
+    record(c, 3);
     // ---- A2
     c->cand_cnt = c->alloc<int32_t>(nt);
     c->cand = c->alloc<int32_t>(nt * RPD_MAXC);
@@ -347,7 +352,8 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     scan_excl(c->cand_cnt, c->pair_off, nt, stmp, s);
     launch_bin_count(c->cand_cnt, nt, c->bin_count, s);
     TRY(cuda_check(c, "candidate launch"));
-    record(c, 3);
+    record(c, 4);
+    cudaStreamWaitEvent(s, c->ev[2], 0);   // mesh combinatorics done
     long long npairs = 0;
     int32_t hb[RPD_NBINS];
     cudaMemcpyAsync(&npairs, c->pair_off + nt, sizeof(long long), cudaMemcpyDeviceToHost, s);
@@ -425,18 +431,29 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         if (fits) break;
         if (attempt == 1) return fail(c, RPD_E_OVERFLOW, "record buffers overflowed twice");
     }
-    record(c, 4);
     for (int k = 0; k < 3; k++) c->stats.n_records[k + 1] = c->nrec[k];
-    // ---- A5-A7 for every kind
+    // ---- A5-A7 for every kind, the four kinds side by side
     long long* d_nseg = c->alloc<long long>(4);
     c->piece_off = c->alloc<int64_t>(npairs + 1);
     void* ptmp = c->alloc<char>(scan_tmp_bytes(npairs + 1));
     NEED(d_nseg && c->piece_off && ptmp);
+    void* ftmp[4];
+    for (int kind = 1; kind <= 4; kind++) TRY(finalize_alloc(c, kind, d_nseg + kind - 1, &ftmp[kind - 1]));
+    record(c, 5);
     for (int kind = 1; kind <= 4; kind++) {
-        TRY(finalize_kind(c, kind, d_nseg + kind - 1));
-        record(c, 4 + kind);
+        cudaStream_t sk = bs->s[kind - 1];
+        cudaStreamWaitEvent(sk, c->ev[5], 0);
+        if (c->kind_ok[kind - 1]) {
+            const long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
+            launch_finalize(c->clip, kind, n, c->ns, c->key_bits, c->fout[kind - 1], ftmp[kind - 1], sk);
+        } else {
+            cudaMemsetAsync(d_nseg + kind - 1, 0, sizeof(long long), sk);
+        }
+        cudaEventRecord(c->ev[6 + kind - 1], sk);
     }
+    TRY(cuda_check(c, "finalize launch"));
     scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
+    for (int kind = 1; kind <= 4; kind++) cudaStreamWaitEvent(s, c->ev[6 + kind - 1], 0);
     long long h[5];
     cudaMemcpyAsync(h, d_nseg, sizeof(long long) * 4, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h + 4, c->piece_off + npairs, sizeof(long long), cudaMemcpyDeviceToHost, s);
@@ -448,11 +465,11 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->npieces = h[4];
     c->stats.n_pieces = h[4];
     c->stats.n_records[0] = h[4];
-    c->stats.ms_prep = elapsed(c, 0, 1);
-    c->stats.ms_knn = elapsed(c, 1, 2);
-    c->stats.ms_cand = elapsed(c, 2, 3);
-    c->stats.ms_clip = elapsed(c, 3, 4);
-    for (int k = 0; k < 4; k++) c->stats.ms_finalize[k] = elapsed(c, 4 + k, 5 + k);
+    c->stats.ms_prep = elapsed(c, 0, 2);   // snapping + mesh combinatorics (beside the kNN)
+    c->stats.ms_knn = elapsed(c, 1, 3);
+    c->stats.ms_cand = elapsed(c, 3, 4);
+    c->stats.ms_clip = elapsed(c, 4, 5);
+    for (int k = 0; k < 4; k++) c->stats.ms_finalize[k] = elapsed(c, 5, 6 + k);   // the kinds run side by side
     return RPD_OK;
 }
 
