@@ -35,11 +35,13 @@ WORKLOADS = {
 
 # Algorithmic FP32 work of the clip stage (Tet-Cell clipping, Sec. 5.2):
 # one filtered sign test F.C of a live polytope vertex against a new radical
-# plane is 3 FMA + 1 MUL = 7 flop (its error bound is stored with the vertex);
-# one vertex constructed on a new plane is four 3x3 cofactors (4 x 14 flop),
-# the orientation test with its bound (10 flop) and the stored bound (7 flop).
+# plane is 3 FMA + 1 MUL = 7 flop (its error bound is stored with the vertex).
+# A vertex constructed on a new plane takes the cofactors of its m radical-plane
+# rows (m = 1: a selection, 0 flop; m = 2: three 2x2 minors, 9 flop; m = 3:
+# four 3x3 cofactors, 56 flop) plus its orientation test and stored bound
+# (17 flop).
 FLOP_SIGN_TEST = 7
-FLOP_NEW_VERTEX = 73
+FLOP_NEW_VERTEX = (17, 26, 73)   # by m = 1, 2, 3
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per clip stage from one ncu capture of the
 # current clip kernels on this workload; None until captured for this code.
@@ -63,7 +65,7 @@ def clip_roofline(stage, n_sm):
     for s in stage:
         tests = s["pred_fast"] + s["pred_fp64"] + s["pred_exact"]
         nv = s["clip_vertices"]
-        flop.append(FLOP_SIGN_TEST * max(tests - nv, 0) + FLOP_NEW_VERTEX * nv)
+        flop.append(FLOP_SIGN_TEST * max(tests - sum(nv), 0) + sum(f * n for f, n in zip(FLOP_NEW_VERTEX, nv)))
         ms.append(s["ms_clip"])
     achieved = float(np.mean(flop)) / (float(np.mean(ms)) * 1e-3) / 1e12
     return {"kernel": "k_clip (all candidate-count bins) + k_whole: the clip stage",

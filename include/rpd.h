@@ -78,7 +78,8 @@ typedef struct {
     int64_t pred_exact;       /* ... by exact 256-bit integer arithmetic          */
     int64_t cand_fallback;    /* tets whose candidate set needed the grid search  */
     int64_t whole_tets;       /* tets inside a single cell (no clipping)          */
-    int64_t clip_vertices;    /* polytope vertices constructed by clipping        */
+    int64_t clip_vertices[3]; /* polytope vertices constructed by clipping, by the
+                                 number of radical planes through them (1, 2, 3) */
     int64_t bin_pairs[8];     /* candidate pairs by candidate count of their tet:
                                  1, 2, 3, 4, 5-6, 7-8, 9-16, 17-32                */
     int64_t bin_cut[8];       /* nonempty pieces that were cut, per bin           */

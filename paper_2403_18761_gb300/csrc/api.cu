@@ -160,7 +160,7 @@ rpd_status check_device(rpd_ctx* c) {
     c->stats.pred_exact = (int64_t)h.cnt[CNT_PRED_EXACT];
     c->stats.cand_fallback = (int64_t)h.cnt[CNT_CAND_FALLBACK];
     c->stats.whole_tets = (int64_t)h.cnt[CNT_WHOLE];
-    c->stats.clip_vertices = (int64_t)h.cnt[CNT_NEWVERT];
+    for (int k = 0; k < 3; k++) c->stats.clip_vertices[k] = (int64_t)h.cnt[CNT_NEWVERT1 + k];
     if (h.err != 0) return fail(c, (rpd_status)h.err, dev_reason(h.err, h.cnt));
     return RPD_OK;
 }

@@ -348,7 +348,8 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     long long p = 0;
     int nslot = 0, nlive = 0;
     bool alive = active, whole = true, degenerate = false;
-    unsigned nfast = 0, n64 = 0, nex = 0, nvert = 0;
+    unsigned nfast = 0, n64 = 0, nex = 0;
+    unsigned nvp = 0;   // constructed vertices with m = 1, 2, 3 radical planes, 10 bits each
     const Slow S{A.Ci, A.W, A.st};
     if (active) {
         p = pairs[q];
@@ -507,6 +508,7 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
             // homogeneous barycentric coordinates of the new vertex
             int fc[4], bis[3];
             const int m = split_planes(x, y, l, fc, bis);
+            nvp += 1u << (10 * (m - 1));
             Real R[3][4];
 #pragma unroll
             for (int z = 0; z < 3; z++) {
@@ -547,7 +549,6 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
             V.put_real(h, 4, dot_bound<Real>(m, C));
         }
         if (!alive) break;
-        nvert += nbd;
         nlive += nbd - nout;
     }
     if (degenerate) dev_fail(A.st, RPD_E_DEGENERATE, CNT_DEGENERATE);
@@ -555,7 +556,9 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     dev_count(A.st, CNT_PRED_FAST, nfast);
     dev_count(A.st, CNT_PRED_FP64, n64);
     dev_count(A.st, CNT_PRED_EXACT, nex);
-    dev_count(A.st, CNT_NEWVERT, nvert);
+    dev_count(A.st, CNT_NEWVERT1, nvp & 1023u);
+    dev_count(A.st, CNT_NEWVERT2, (nvp >> 10) & 1023u);
+    dev_count(A.st, CNT_NEWVERT3, nvp >> 20);
 
     // --------------------------------------------- fractional Euler records
     const int b = A.key_bits;

@@ -26,7 +26,9 @@ enum {
     CNT_PRED_EXACT,       // decided by exact integers
     CNT_CAND_FALLBACK,    // tets resolved by the grid-search fallback
     CNT_WHOLE,            // whole-tet pieces
-    CNT_NEWVERT,          // polytope vertices constructed by clipping
+    CNT_NEWVERT1,         // polytope vertices constructed by clipping, by the number
+    CNT_NEWVERT2,         //   of radical planes through them (1, 2, 3)
+    CNT_NEWVERT3,
     CNT_NUM
 };
 

@@ -41,7 +41,7 @@ class rpd_stats(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_records", ctypes.c_int64 * 4),
                 ("n_keys", ctypes.c_int64 * 4), ("pred_fast", ctypes.c_int64), ("pred_fp64", ctypes.c_int64),
                 ("pred_exact", ctypes.c_int64), ("cand_fallback", ctypes.c_int64), ("whole_tets", ctypes.c_int64),
-                ("clip_vertices", ctypes.c_int64),
+                ("clip_vertices", ctypes.c_int64 * 3),
                 ("bin_pairs", ctypes.c_int64 * 8), ("bin_cut", ctypes.c_int64 * 8), ("ms_prep", ctypes.c_float), ("ms_knn", ctypes.c_float), ("ms_cand", ctypes.c_float),
                 ("ms_clip", ctypes.c_float), ("ms_finalize", ctypes.c_float * 4)]
 
