@@ -43,9 +43,10 @@ WORKLOADS = {
 FLOP_SIGN_TEST = 7
 FLOP_NEW_VERTEX = (17, 26, 73)   # by m = 1, 2, 3
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per clip stage from one ncu capture of the
-# current clip kernels on this workload; None until captured for this code.
-CLIP_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of the clip kernels of one step (k_clip over all
+# bins + k_whole) on block_c2, from one ncu capture of the current kernels
+# (profiles/clip_block_c2.md); None once the kernels change.
+CLIP_TRAFFIC_BYTES = {("block_c2", "fp32"): 80.44e6}
 
 
 def measured_peaks():
@@ -56,8 +57,10 @@ def measured_peaks():
         return {}
 
 
-def clip_roofline(stage, n_sm):
-    """FP32 ALU roofline of the clip stage, from the counters of the timed steps."""
+def clip_roofline(stage, n_sm, workload, precision):
+    """FP32 ALU roofline of the clip kernels, from the counters of the timed
+    steps and the clip-kernel span timed by the library's CUDA events on the
+    launching streams."""
     peaks = measured_peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -66,11 +69,11 @@ def clip_roofline(stage, n_sm):
         tests = s["pred_fast"] + s["pred_fp64"] + s["pred_exact"]
         nv = s["clip_vertices"]
         flop.append(FLOP_SIGN_TEST * max(tests - sum(nv), 0) + sum(f * n for f, n in zip(FLOP_NEW_VERTEX, nv)))
-        ms.append(s["ms_clip"])
+        ms.append(s["ms_clip_kernels"])
     achieved = float(np.mean(flop)) / (float(np.mean(ms)) * 1e-3) / 1e12
-    return {"kernel": "k_clip (all candidate-count bins) + k_whole: the clip stage",
+    return {"kernel": "k_clip over all candidate-count bins (side by side on the bin streams) + k_whole",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": CLIP_TRAFFIC_BYTES, "flop_per_launch": float(np.mean(flop)),
+            "traffic": CLIP_TRAFFIC_BYTES.get((workload, precision)), "flop_per_launch": float(np.mean(flop)),
             "ms_per_launch": float(np.mean(ms)),
             "peak_source": f"derived FP32: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz:.0f} MHz "
                            "(sm_max_mhz of MEASURED_PEAKS.json)"}
@@ -301,7 +304,8 @@ def main():
             ctx.rpd_destroy()
     e2e_value = npieces * len(e2e_ms) / (sum(e2e_ms) / 1e3) * world if e2e_ms else None
 
-    st_mean = {k: float(np.mean([s[k] for s in stage])) for k in ("ms_prep", "ms_knn", "ms_cand", "ms_clip")}
+    st_mean = {k: float(np.mean([s[k] for s in stage]))
+               for k in ("ms_prep", "ms_knn", "ms_cand", "ms_clip", "ms_clip_kernels", "ms_clip_span")}
     st_mean["ms_finalize"] = [float(np.mean([s["ms_finalize"][k] for s in stage])) for k in range(4)]
     last = stage[-1]
     line = {
@@ -321,7 +325,8 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
-        "roofline": clip_roofline(stage, torch.cuda.get_device_properties(dev).multi_processor_count),
+        "roofline": clip_roofline(stage, torch.cuda.get_device_properties(dev).multi_processor_count, args.config,
+                                  precision),
         "step_ms_max": t_step,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

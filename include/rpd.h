@@ -84,6 +84,9 @@ typedef struct {
                                  1, 2, 3, 4, 5-6, 7-8, 9-16, 17-32                */
     int64_t bin_cut[8];       /* nonempty pieces that were cut, per bin           */
     float ms_prep, ms_knn, ms_cand, ms_clip, ms_finalize[4];
+    float ms_clip_kernels;    /* from the start of the clip launches to the end of
+                                 the last clip kernel (volume pass excluded)      */
+    float ms_clip_span;       /* same start to the end of the last volume kernel  */
 } rpd_stats;
 
 typedef struct rpd_ctx rpd_ctx;   /* opaque; owns all device workspace and results */

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -101,6 +102,8 @@ struct rpd_ctx {
     long long npieces = 0;
     rpd_stats stats{};
     cudaEvent_t ev[16] = {};
+    // clip stage: fork, end of each bin's clip kernel, end of each bin's work
+    cudaEvent_t evc[1 + 2 * RPD_NBINS] = {};
 
     template <typename T>
     T* alloc(size_t count) {
@@ -188,13 +191,14 @@ int bits_for(long long ns) {
         if (!(ptr)) return fail(c, RPD_E_OOM, "device allocation failed");    \
     } while (0)
 
-// Library-owned side streams (one per bin) and events, per device, used to
-// run the clip bins concurrently: the few heavy pairs of the high bins are
-// latency-bound and overlap with the throughput-bound low bins.
+// Library-owned side streams, per device: the clip bins run side by side (the
+// few heavy pairs of the high bins are latency-bound and overlap with the
+// throughput-bound low bins), as do the mesh combinatorics next to the kNN and
+// the four element kinds of the finalisation.  Each context orders its work on
+// them with its own events.
 struct BinStreams {
     bool ready = false;
     cudaStream_t s[RPD_NBINS];
-    cudaEvent_t fork, join[RPD_NBINS];
 };
 
 BinStreams* bin_streams() {
@@ -206,10 +210,7 @@ BinStreams* bin_streams() {
     BinStreams& b = per_dev[dev];
     if (!b.ready) {
         for (int k = 0; k < RPD_NBINS; k++)
-            if (cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming) != cudaSuccess)
-                return nullptr;
-        if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+            if (cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
         b.ready = true;
     }
     return &b;
@@ -223,19 +224,18 @@ rpd_status run_clip(rpd_ctx* c) {
     off[0] = 0;
     for (int b = 0; b < RPD_NBINS; b++) off[b + 1] = off[b] + c->hbin[b];
     BinStreams* bs = bin_streams();
-    if (bs) cudaEventRecord(bs->fork, s);
+    if (!bs) return fail(c, RPD_E_CUDA, "stream creation failed");
+    cudaEventRecord(c->evc[0], s);   // fork
     // heaviest bins first
     for (int b = RPD_NBINS - 1; b >= 0; b--) {
         const long long n = c->hbin[b];
         if (n == 0) continue;
-        cudaStream_t sb = s;
-        if (bs) {
-            sb = bs->s[b];
-            cudaStreamWaitEvent(sb, bs->fork, 0);
-        }
+        cudaStream_t sb = bs->s[b];
+        cudaStreamWaitEvent(sb, c->evc[0], 0);
         ClipArgs a = c->clip;
         if (b == 0) {
             launch_whole_tets(a, c->bins, c->bin_count, n, sb);
+            cudaEventRecord(c->evc[1 + b], sb);
         } else {
             a.qpair = c->qpair[b];
             a.qnv = c->qnv[b];
@@ -243,11 +243,11 @@ rpd_status run_clip(rpd_ctx* c) {
             a.qcap = n;
             a.qcount = c->qcount + b;
             launch_clip(a, b, c->opt.precision, c->bins + off[b], c->bin_count + b, n, sb);
+            cudaEventRecord(c->evc[1 + b], sb);
+            launch_volume(a, b, c->opt.precision, n, sb);
         }
-        if (bs) {
-            cudaEventRecord(bs->join[b], sb);
-            cudaStreamWaitEvent(s, bs->join[b], 0);
-        }
+        cudaEventRecord(c->evc[1 + RPD_NBINS + b], sb);
+        cudaStreamWaitEvent(s, c->evc[1 + RPD_NBINS + b], 0);
     }
     return cuda_check(c, "clip launch");
 }
@@ -290,6 +290,8 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     const long long nv = c->nv, nt = c->nt, ns = c->ns;
     for (int k = 0; k < 16; k++)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
+    for (int k = 0; k < 1 + 2 * RPD_NBINS; k++)
+        if (cudaEventCreate(&c->evc[k]) != cudaSuccess) return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
     // side streams: mesh combinatorics next to the sphere grid and kNN, the
     // clip bins, and the four element kinds of the finalisation
     BinStreams* bs = bin_streams();
@@ -469,6 +471,17 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->stats.ms_knn = elapsed(c, 1, 3);
     c->stats.ms_cand = elapsed(c, 3, 4);
     c->stats.ms_clip = elapsed(c, 4, 5);
+    for (int b = 0; b < RPD_NBINS; b++) {
+        if (c->hbin[b] == 0) continue;
+        float k = 0, w = 0;
+        if (cudaEventElapsedTime(&k, c->evc[0], c->evc[1 + b]) != cudaSuccess ||
+            cudaEventElapsedTime(&w, c->evc[0], c->evc[1 + RPD_NBINS + b]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        c->stats.ms_clip_kernels = std::max(c->stats.ms_clip_kernels, k);
+        c->stats.ms_clip_span = std::max(c->stats.ms_clip_span, w);
+    }
     for (int k = 0; k < 4; k++) c->stats.ms_finalize[k] = elapsed(c, 5, 6 + k);   // the kinds run side by side
     return RPD_OK;
 }
@@ -589,8 +602,10 @@ void rpd_destroy(rpd_ctx* ctx) {
     if (!ctx) return;
     ctx->release_all();
     cudaStreamSynchronize(ctx->stream);
-    for (int k = 0; k < 10; k++)
-        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    for (cudaEvent_t e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->evc)
+        if (e) cudaEventDestroy(e);
     cudaGetLastError();
     delete ctx;
 }

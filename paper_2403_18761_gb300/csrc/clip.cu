@@ -1141,7 +1141,6 @@ void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d
 
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,
                  cudaStream_t s) {
-    const int vw = bin <= 5 ? 4 : (bin == 6 ? 2 : 1);
     if (precision == RPD_FP32_FILTERED) {
         switch (bin) {
             case 1: launch_clip_t<float, 6, 4>(a, pairs, d_n, n, s); break;
@@ -1152,7 +1151,6 @@ void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs
             case 6: launch_clip_t<float, 34, 2>(a, pairs, d_n, n, s); break;
             case 7: launch_clip_t<float, 66, 1>(a, pairs, d_n, n, s); break;
         }
-        if (bin >= 1) launch_volume_t<float>(a, clip_vmax(bin), vw, n, s);
     } else {
         switch (bin) {
             case 1: launch_clip_t<double, 6, 4>(a, pairs, d_n, n, s); break;
@@ -1163,6 +1161,12 @@ void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs
             case 6: launch_clip_t<double, 34, 1>(a, pairs, d_n, n, s); break;
             case 7: launch_clip_t<double, 66, 1>(a, pairs, d_n, n, s); break;
         }
-        if (bin >= 1) launch_volume_t<double>(a, clip_vmax(bin), vw, n, s);
     }
+}
+
+void launch_volume(const ClipArgs& a, int bin, int precision, long long n, cudaStream_t s) {
+    if (bin < 1) return;
+    const int vw = bin <= 5 ? 4 : (bin == 6 ? 2 : 1);
+    if (precision == RPD_FP32_FILTERED) launch_volume_t<float>(a, clip_vmax(bin), vw, n, s);
+    else launch_volume_t<double>(a, clip_vmax(bin), vw, n, s);
 }

@@ -43,7 +43,8 @@ class rpd_stats(ctypes.Structure):
                 ("pred_exact", ctypes.c_int64), ("cand_fallback", ctypes.c_int64), ("whole_tets", ctypes.c_int64),
                 ("clip_vertices", ctypes.c_int64 * 3),
                 ("bin_pairs", ctypes.c_int64 * 8), ("bin_cut", ctypes.c_int64 * 8), ("ms_prep", ctypes.c_float), ("ms_knn", ctypes.c_float), ("ms_cand", ctypes.c_float),
-                ("ms_clip", ctypes.c_float), ("ms_finalize", ctypes.c_float * 4)]
+                ("ms_clip", ctypes.c_float), ("ms_finalize", ctypes.c_float * 4), ("ms_clip_kernels", ctypes.c_float),
+                ("ms_clip_span", ctypes.c_float)]
 
     def as_dict(self):
         out = {}
