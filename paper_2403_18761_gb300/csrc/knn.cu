@@ -591,29 +591,55 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
         }
         return;
     }
+    // Gather.  The lists ascend in power distance, so the entries within a
+    // corner's threshold are a prefix: lanes 8a..8a+7 test entries 0..7 of
+    // corner a's list at once; a corner whose 8th entry still passes goes on
+    // through the rest of its list below.  Each sphere is kept once.
     int sid = -1, nheld = 0;
-#pragma unroll
-    for (int a = 0; a < 4; a++) {
+    unsigned more;
+    {
+        const int a = lane >> 3, j = lane & 7;
+        const int va = a == 0 ? v[0] : (a == 1 ? v[1] : (a == 2 ? v[2] : v[3]));
+        const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
         const long long thr = __shfl_sync(0xffffffffu, Ml, a * 4 + bstar);
-        const int s = lane < K ? knn[(long long)v[a] * K + lane] : -1;
-        bool in = false;
-        if (s >= 0) in = pd_exact(X[a], ld_int3(Ci, s), W[s]) <= thr;
-        for (int h = 0; h < nheld; h++)
-            if (__shfl_sync(0xffffffffu, sid, h) == s) in = false;
-        const unsigned mask = __ballot_sync(0xffffffffu, in);
-        const int cnt = __popc(mask);
-        if (nheld + cnt > 32) {
-            if (lane == 0) {
-                fb_list[atomicAdd(fb_count, 1)] = (int32_t)t;
-                cand_cnt[t] = 0;
-            }
-            return;
-        }
-        const bool take = lane >= nheld && lane < nheld + cnt;
-        const int src = take ? __fns(mask, 0, lane - nheld + 1) : 0;
+        const int s = j < K ? knn[(long long)va * K + j] : -1;
+        const bool in = s >= 0 && pd_exact(xa, ld_int3(Ci, s), W[s]) <= thr;
+        const unsigned peers = __match_any_sync(0xffffffffu, in ? s : -1 - lane);
+        const bool first = in && (__ffs(peers) - 1 == lane);
+        const unsigned fm = __ballot_sync(0xffffffffu, first);
+        nheld = __popc(fm);
+        const int src = lane < nheld ? __fns(fm, 0, lane + 1) : 0;
         const int sn = __shfl_sync(0xffffffffu, s, src);
-        if (take) sid = sn;
-        nheld += cnt;
+        if (lane < nheld) sid = sn;
+        more = __ballot_sync(0xffffffffu, in && j == 7);
+    }
+    for (; more; more &= more - 1) {
+        const int a = (__ffs(more) - 1) >> 3;
+        const long long thr = __shfl_sync(0xffffffffu, Ml, a * 4 + bstar);
+        const int va = a == 0 ? v[0] : (a == 1 ? v[1] : (a == 2 ? v[2] : v[3]));
+        const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
+        for (int base = 8; base < K; base += 32) {
+            const int e = base + lane;
+            const int s = e < K ? knn[(long long)va * K + e] : -1;
+            bool in = false;
+            if (s >= 0) in = pd_exact(xa, ld_int3(Ci, s), W[s]) <= thr;
+            for (int h = 0; h < nheld; h++)
+                if (__shfl_sync(0xffffffffu, sid, h) == s) in = false;
+            const unsigned mask = __ballot_sync(0xffffffffu, in);
+            const int cnt = __popc(mask);
+            if (nheld + cnt > 32) {
+                if (lane == 0) {
+                    fb_list[atomicAdd(fb_count, 1)] = (int32_t)t;
+                    cand_cnt[t] = 0;
+                }
+                return;
+            }
+            const bool take = lane >= nheld && lane < nheld + cnt;
+            const int src = take ? __fns(mask, 0, lane - nheld + 1) : 0;
+            const int sn = __shfl_sync(0xffffffffu, s, src);
+            if (take) sid = sn;
+            nheld += cnt;
+        }
     }
     const bool held = lane < nheld;
     long long D[4] = {0, 0, 0, 0};
