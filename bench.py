@@ -321,6 +321,7 @@ def main():
                        "vertices_constructed": last["clip_vertices"]},
         "pairs": {"total": last["n_pairs"], "by_bin": last["bin_pairs"], "cut_by_bin": last["bin_cut"],
                   "whole_tets": last["whole_tets"], "cand_fallback": last["cand_fallback"], "k": kk},
+        "elements": {"records": last["n_records"], "keys": last["n_keys"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
         "gpu_launches": int(launches),

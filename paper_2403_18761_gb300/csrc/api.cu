@@ -406,6 +406,13 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     a.st = c->st;
     NEED(a.pflag && a.c_val && a.c_link && a.p_vol && a.p_mom && a.f_off && a.f_cnt && a.e_off && a.e_cnt);
     launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, s);
+    // finalisation buffers that do not depend on the record counts
+    long long* d_nseg = c->alloc<long long>(4);
+    c->piece_off = c->alloc<int64_t>(npairs + 1);
+    void* ptmp = c->alloc<char>(scan_tmp_bytes(npairs + 1));
+    NEED(d_nseg && c->piece_off && ptmp);
+    void* ftmp[4] = {nullptr, nullptr, nullptr, nullptr};
+    TRY(finalize_alloc(c, 1, d_nseg, &ftmp[0]));
     long long cap[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
     for (int attempt = 0; attempt < 2; attempt++) {
         for (int k = 0; k < 3; k++) {
@@ -416,7 +423,15 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             a.rlink[k] = c->alloc<uint8_t>(cap[k]);
             NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
         }
+        if (attempt == 1) cudaStreamWaitEvent(s, c->ev[6], 0);   // the first pass's cells are finalised
         TRY(run_clip(c));
+        record(c, 5);   // clip done: the finalisation forks here
+        // cells and piece offsets need only the pair count: they run while the
+        // host waits for the record counts
+        cudaStreamWaitEvent(bs->s[0], c->ev[5], 0);
+        launch_finalize(c->clip, 1, npairs, c->ns, c->key_bits, c->fout[0], ftmp[0], bs->s[0]);
+        cudaEventRecord(c->ev[6], bs->s[0]);
+        scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
         unsigned long long cnt[3], qc[RPD_NBINS];
         cudaMemcpyAsync(cnt, c->rcount, sizeof(cnt), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(qc, c->qcount, sizeof(qc), cudaMemcpyDeviceToHost, s);
@@ -434,17 +449,12 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         if (attempt == 1) return fail(c, RPD_E_OVERFLOW, "record buffers overflowed twice");
     }
     for (int k = 0; k < 3; k++) c->stats.n_records[k + 1] = c->nrec[k];
-    // ---- A5-A7 for every kind, the four kinds side by side
-    long long* d_nseg = c->alloc<long long>(4);
-    c->piece_off = c->alloc<int64_t>(npairs + 1);
-    void* ptmp = c->alloc<char>(scan_tmp_bytes(npairs + 1));
-    NEED(d_nseg && c->piece_off && ptmp);
-    void* ftmp[4];
-    for (int kind = 1; kind <= 4; kind++) TRY(finalize_alloc(c, kind, d_nseg + kind - 1, &ftmp[kind - 1]));
-    record(c, 5);
-    for (int kind = 1; kind <= 4; kind++) {
+    // ---- A5-A7 for faces, edges and vertices, side by side (cells started above)
+    for (int kind = 2; kind <= 4; kind++) TRY(finalize_alloc(c, kind, d_nseg + kind - 1, &ftmp[kind - 1]));
+    record(c, 10);   // their buffers are allocated
+    for (int kind = 2; kind <= 4; kind++) {
         cudaStream_t sk = bs->s[kind - 1];
-        cudaStreamWaitEvent(sk, c->ev[5], 0);
+        cudaStreamWaitEvent(sk, c->ev[10], 0);
         if (c->kind_ok[kind - 1]) {
             const long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
             launch_finalize(c->clip, kind, n, c->ns, c->key_bits, c->fout[kind - 1], ftmp[kind - 1], sk);
@@ -454,7 +464,6 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         cudaEventRecord(c->ev[6 + kind - 1], sk);
     }
     TRY(cuda_check(c, "finalize launch"));
-    scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
     for (int kind = 1; kind <= 4; kind++) cudaStreamWaitEvent(s, c->ev[6 + kind - 1], 0);
     long long h[5];
     cudaMemcpyAsync(h, d_nseg, sizeof(long long) * 4, cudaMemcpyDeviceToHost, s);
