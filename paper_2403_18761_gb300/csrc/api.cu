@@ -216,6 +216,15 @@ BinStreams* bin_streams() {
     return &b;
 }
 
+// Make the caller's stream wait for everything this context queued on the
+// side streams (an event never recorded is already complete).
+void join_side_streams(rpd_ctx* c) {
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaStreamWaitEvent(c->stream, e, 0);
+    for (cudaEvent_t e : c->evc)
+        if (e) cudaStreamWaitEvent(c->stream, e, 0);
+}
+
 rpd_status run_clip(rpd_ctx* c) {
     cudaStream_t s = c->stream;
     cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
@@ -247,7 +256,9 @@ rpd_status run_clip(rpd_ctx* c) {
             launch_volume(a, b, c->opt.precision, n, sb);
         }
         cudaEventRecord(c->evc[1 + RPD_NBINS + b], sb);
-        cudaStreamWaitEvent(s, c->evc[1 + RPD_NBINS + b], 0);
+        // the records (what the finalisation reads) are complete once the
+        // clip kernel is; the volume pass joins at the end of the build
+        cudaStreamWaitEvent(s, c->evc[1 + b], 0);
     }
     return cuda_check(c, "clip launch");
 }
@@ -423,7 +434,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             a.rlink[k] = c->alloc<uint8_t>(cap[k]);
             NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
         }
-        if (attempt == 1) cudaStreamWaitEvent(s, c->ev[6], 0);   // the first pass's cells are finalised
+        if (attempt == 1) join_side_streams(c);   // the first pass's cells and volumes are done
         TRY(run_clip(c));
         record(c, 5);   // clip done: the finalisation forks here
         // cells and piece offsets need only the pair count: they run while the
@@ -465,6 +476,8 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     }
     TRY(cuda_check(c, "finalize launch"));
     for (int kind = 1; kind <= 4; kind++) cudaStreamWaitEvent(s, c->ev[6 + kind - 1], 0);
+    for (int b = 0; b < RPD_NBINS; b++)   // volume passes
+        if (c->hbin[b]) cudaStreamWaitEvent(s, c->evc[1 + RPD_NBINS + b], 0);
     long long h[5];
     cudaMemcpyAsync(h, d_nseg, sizeof(long long) * 4, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h + 4, c->piece_off + npairs, sizeof(long long), cudaMemcpyDeviceToHost, s);
@@ -609,6 +622,7 @@ const char* rpd_build_error(void) { return g_build_error.c_str(); }
 
 void rpd_destroy(rpd_ctx* ctx) {
     if (!ctx) return;
+    join_side_streams(ctx);   // nothing queued on a side stream may outlive its memory
     ctx->release_all();
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev)
