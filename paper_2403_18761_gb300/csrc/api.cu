@@ -151,7 +151,10 @@ const char* dev_reason(int code, const unsigned long long* cnt) {
 }
 
 // Read the device status block; returns RPD_OK or the first device error.
-rpd_status check_device(rpd_ctx* c) {
+// Synchronise the stream and read the device status: counters into the
+// stats, and an error raised on the device as the return value (with
+// raise == false the error code is only left in *code).
+rpd_status check_device(rpd_ctx* c, bool raise = true, int* code = nullptr) {
     DevState h;
     if (cudaMemcpyAsync(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -164,7 +167,8 @@ rpd_status check_device(rpd_ctx* c) {
     c->stats.cand_fallback = (int64_t)h.cnt[CNT_CAND_FALLBACK];
     c->stats.whole_tets = (int64_t)h.cnt[CNT_WHOLE];
     for (int k = 0; k < 3; k++) c->stats.clip_vertices[k] = (int64_t)h.cnt[CNT_NEWVERT1 + k];
-    if (h.err != 0) return fail(c, (rpd_status)h.err, dev_reason(h.err, h.cnt));
+    if (code) *code = h.err;
+    if (raise && h.err != 0) return fail(c, (rpd_status)h.err, dev_reason(h.err, h.cnt));
     return RPD_OK;
 }
 
@@ -199,6 +203,8 @@ int bits_for(long long ns) {
 struct BinStreams {
     bool ready = false;
     cudaStream_t s[RPD_NBINS];
+    cudaStream_t util;     // high priority: clearing scratch next to the clip
+    cudaStream_t fin[4];   // high priority: the element kinds, ahead of the volume pass
 };
 
 BinStreams* bin_streams() {
@@ -211,6 +217,11 @@ BinStreams* bin_streams() {
     if (!b.ready) {
         for (int k = 0; k < RPD_NBINS; k++)
             if (cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&b.util, cudaStreamNonBlocking, hi) != cudaSuccess) return nullptr;
+        for (int k = 0; k < 4; k++)
+            if (cudaStreamCreateWithPriority(&b.fin[k], cudaStreamNonBlocking, hi) != cudaSuccess) return nullptr;
         b.ready = true;
     }
     return &b;
@@ -264,9 +275,10 @@ rpd_status run_clip(rpd_ctx* c) {
 }
 
 // Output and workspace buffers of one kind's finalisation.
-rpd_status finalize_alloc(rpd_ctx* c, int kind, long long* d_count, void** tmp) {
+// Output and scratch buffers of one kind's finalisation, for up to ncap
+// pieces (kind 1) or records.
+rpd_status finalize_alloc(rpd_ctx* c, int kind, long long* d_count, long long ncap, void** tmp) {
     const int b = c->key_bits;
-    const long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
     FinalOut& o = c->fout[kind - 1];
     o.count = d_count;
     *tmp = nullptr;
@@ -274,12 +286,12 @@ rpd_status finalize_alloc(rpd_ctx* c, int kind, long long* d_count, void** tmp) 
         c->kind_ok[3] = false;
         return RPD_OK;
     }
-    const long long rows = kind == 1 ? c->ns : n;
+    const long long rows = kind == 1 ? c->ns : ncap;
     o.keys = c->alloc<int32_t>(rows * kind);
     o.chi = c->alloc<int32_t>(rows);
     o.beta = c->alloc<int32_t>(rows);
     o.flag = c->alloc<uint8_t>(rows);
-    *tmp = c->alloc<char>(finalize_tmp_bytes(kind, n, c->ns));
+    *tmp = c->alloc<char>(finalize_tmp_bytes(kind, ncap, c->ns));
     NEED(o.keys && o.chi && o.beta && o.flag && *tmp);
     return RPD_OK;
 }
@@ -423,8 +435,15 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     void* ptmp = c->alloc<char>(scan_tmp_bytes(npairs + 1));
     NEED(d_nseg && c->piece_off && ptmp);
     void* ftmp[4] = {nullptr, nullptr, nullptr, nullptr};
-    TRY(finalize_alloc(c, 1, d_nseg, &ftmp[0]));
+    long long fcap[4] = {npairs, 0, 0, 0};
+    TRY(finalize_alloc(c, 1, d_nseg, npairs, &ftmp[0]));
     long long cap[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
+    if (const char* e = getenv("RPD_RECORD_CAP")) {   // test hook: small first capacities force a rebuild
+        const long long v = atoll(e);
+        if (v > 0)
+            for (long long& x : cap) x = v;
+    }
+    long long h[5];
     for (int attempt = 0; attempt < 2; attempt++) {
         for (int k = 0; k < 3; k++) {
             a.rcap[k] = cap[k];
@@ -433,55 +452,66 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             a.rval[k] = c->alloc<int16_t>(cap[k]);
             a.rlink[k] = c->alloc<uint8_t>(cap[k]);
             NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
+            fcap[k + 1] = cap[k];
+            TRY(finalize_alloc(c, k + 2, d_nseg + k + 1, cap[k], &ftmp[k + 1]));
         }
-        if (attempt == 1) join_side_streams(c);   // the first pass's cells and volumes are done
+        if (attempt == 1) join_side_streams(c);   // everything of the first pass is done
+        record(c, 11);   // buffers allocated
         TRY(run_clip(c));
-        record(c, 5);   // clip done: the finalisation forks here
-        // cells and piece offsets need only the pair count: they run while the
-        // host waits for the record counts
-        cudaStreamWaitEvent(bs->s[0], c->ev[5], 0);
-        launch_finalize(c->clip, 1, npairs, c->ns, c->key_bits, c->fout[0], ftmp[0], bs->s[0]);
-        cudaEventRecord(c->ev[6], bs->s[0]);
+        // the finalisation scratch is cleared on a high-priority side stream while the clip runs
+        cudaStreamWaitEvent(bs->util, c->ev[11], 0);
+        for (int kind = 1; kind <= 4; kind++)
+            if (ftmp[kind - 1]) launch_finalize_clear(kind, fcap[kind - 1], c->ns, ftmp[kind - 1], bs->util);
+        cudaEventRecord(c->ev[12], bs->util);
+        cudaStreamWaitEvent(s, c->ev[12], 0);
+        record(c, 5);   // clip kernels done, scratch clear: the four kinds fork here
+        // ---- A5-A7, the four kinds side by side on high-priority streams; the
+        // record counts stay on the device (grids sized by the capacities)
+        for (int kind = 1; kind <= 4; kind++) {
+            cudaStream_t sk = bs->fin[kind - 1];
+            cudaStreamWaitEvent(sk, c->ev[5], 0);
+            if (c->kind_ok[kind - 1]) {
+                launch_finalize(c->clip, kind, fcap[kind - 1], fcap[kind - 1], c->ns, c->key_bits,
+                                c->fout[kind - 1], ftmp[kind - 1], sk);
+            } else {
+                cudaMemsetAsync(d_nseg + kind - 1, 0, sizeof(long long), sk);
+            }
+            cudaEventRecord(c->ev[6 + kind - 1], sk);
+        }
         scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
+        TRY(cuda_check(c, "finalize launch"));
+        for (int kind = 1; kind <= 4; kind++) cudaStreamWaitEvent(s, c->ev[6 + kind - 1], 0);
+        for (int b = 0; b < RPD_NBINS; b++)   // volume passes
+            if (c->hbin[b]) cudaStreamWaitEvent(s, c->evc[1 + RPD_NBINS + b], 0);
         unsigned long long cnt[3], qc[RPD_NBINS];
         cudaMemcpyAsync(cnt, c->rcount, sizeof(cnt), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(qc, c->qcount, sizeof(qc), cudaMemcpyDeviceToHost, s);
-        TRY(check_device(c));
+        cudaMemcpyAsync(h, d_nseg, sizeof(long long) * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h + 4, c->piece_off + npairs, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        int dev_err = 0;
+        TRY(check_device(c, false, &dev_err));
         for (int b = 0; b < RPD_NBINS; b++) c->stats.bin_cut[b] = (int64_t)qc[b];
         bool fits = true;
         for (int k = 0; k < 3; k++) {
             c->nrec[k] = (long long)cnt[k];
-            if ((long long)cnt[k] > cap[k]) {
+            if ((long long)cnt[k] > cap[k]) {   // records were dropped: rebuild from the clip
                 fits = false;
                 cap[k] = (long long)cnt[k] + 1024;
             }
         }
-        if (fits) break;
+        if (fits) {
+            if (dev_err) TRY(check_device(c));   // raises what the device reported
+            break;
+        }
         if (attempt == 1) return fail(c, RPD_E_OVERFLOW, "record buffers overflowed twice");
+        // the finalisation ran on truncated records: its status is void; keep
+        // the counters of the stages before the clip and start over
+        const unsigned long long fb = (unsigned long long)c->stats.cand_fallback;
+        cudaMemsetAsync(c->st, 0, sizeof(DevState), s);
+        cudaMemcpyAsync(&c->st->cnt[CNT_CAND_FALLBACK], &fb, sizeof(fb), cudaMemcpyHostToDevice, s);
+        TRY(check_device(c));
     }
     for (int k = 0; k < 3; k++) c->stats.n_records[k + 1] = c->nrec[k];
-    // ---- A5-A7 for faces, edges and vertices, side by side (cells started above)
-    for (int kind = 2; kind <= 4; kind++) TRY(finalize_alloc(c, kind, d_nseg + kind - 1, &ftmp[kind - 1]));
-    record(c, 10);   // their buffers are allocated
-    for (int kind = 2; kind <= 4; kind++) {
-        cudaStream_t sk = bs->s[kind - 1];
-        cudaStreamWaitEvent(sk, c->ev[10], 0);
-        if (c->kind_ok[kind - 1]) {
-            const long long n = kind == 1 ? c->npairs : c->nrec[kind - 2];
-            launch_finalize(c->clip, kind, n, c->ns, c->key_bits, c->fout[kind - 1], ftmp[kind - 1], sk);
-        } else {
-            cudaMemsetAsync(d_nseg + kind - 1, 0, sizeof(long long), sk);
-        }
-        cudaEventRecord(c->ev[6 + kind - 1], sk);
-    }
-    TRY(cuda_check(c, "finalize launch"));
-    for (int kind = 1; kind <= 4; kind++) cudaStreamWaitEvent(s, c->ev[6 + kind - 1], 0);
-    for (int b = 0; b < RPD_NBINS; b++)   // volume passes
-        if (c->hbin[b]) cudaStreamWaitEvent(s, c->evc[1 + RPD_NBINS + b], 0);
-    long long h[5];
-    cudaMemcpyAsync(h, d_nseg, sizeof(long long) * 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 4, c->piece_off + npairs, sizeof(long long), cudaMemcpyDeviceToHost, s);
-    TRY(check_device(c));
     for (int k = 0; k < 4; k++) {
         c->nkeys[k] = h[k];
         c->stats.n_keys[k] = h[k];

@@ -119,8 +119,11 @@ struct FinalOut {
     uint8_t* flag;
     long long* count;
 };
-size_t finalize_tmp_bytes(int kind, long long n, long long ns);
-void launch_finalize(const ClipArgs& a, int kind, long long n, long long ns, int key_bits, const FinalOut& out,
-                     void* tmp, cudaStream_t s);
+// Scratch for up to ncap pieces (kind 1) or records (kinds 2..4); it must be
+// cleared by launch_finalize_clear before launch_finalize (n <= ncap) runs.
+size_t finalize_tmp_bytes(int kind, long long ncap, long long ns);
+void launch_finalize_clear(int kind, long long ncap, long long ns, void* tmp, cudaStream_t s);
+void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, long long ns, int key_bits,
+                     const FinalOut& out, void* tmp, cudaStream_t s);
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet,
                            int32_t* d_sphere, double* d_vol, double* d_mom, cudaStream_t s);

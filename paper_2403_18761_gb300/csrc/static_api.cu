@@ -256,7 +256,8 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
     fo.count = ar.take<long long>(1);
     void* ftmp = ar.take<char>(finalize_tmp_bytes(kind, n, ns));
     NEED_S(!ar.full);
-    launch_finalize(a, kind, n, ns, b, fo, ftmp, s);
+    launch_finalize_clear(kind, n, ns, ftmp, s);
+    launch_finalize(a, kind, n, n, ns, b, fo, ftmp, s);
     long long m = 0;
     cudaMemcpyAsync(&m, fo.count, sizeof(long long), cudaMemcpyDeviceToHost, s);
     TRY_S(read_status(st, s));

@@ -1,12 +1,19 @@
-// A5-A7 helpers: union-find over element pieces, key unpacking, flags.
+// A5-A7: union-find over element pieces, chi and roots summed per key,
+// sorted key rows, flags.
 //
 // Components (Sec. 4.1.1): the pieces of one restricted element in two
 // face-adjacent tets belong to the same component when the element crosses
 // their shared face (the piece has a face on it for an RPC, an edge on it for
 // an RPF, an end point on it for an RPE).  Union-find hooks the larger root
 // under the smaller with atomicCAS, so parent pointers only decrease and no
-// cycle can form; every loop is bounded and reports RPD_E_TIMEOUT if the bound
-// is hit.
+// cycle can form; a negative parent marks a root, so a memset initialises the
+// forest.  Every loop is bounded and reports RPD_E_TIMEOUT if the bound is hit.
+//
+// chi and beta0 per key (Sec. 4.1.2, Sec. 4.1.1): every piece or record adds
+// its contribution and, if it is a root, one component to its key's slot of a
+// hash table (per sphere for cells).  The keys are then put in order by a
+// bucket pass on their first sphere index (the keys of one sphere are few)
+// and a rank inside each bucket.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -21,10 +28,11 @@ constexpr int UF_LIMIT = 1 << 22;
 __device__ __forceinline__ int uf_find(int32_t* parent, int x) {
     volatile int32_t* P = parent;
     for (int it = 0; it < UF_LIMIT; it++) {
-        int px = P[x];
-        if (px == x) return x;
-        int gx = P[px];
-        if (gx != px) P[x] = gx;   // path halving (benign race: gx is an ancestor)
+        const int px = P[x];
+        if (px < 0) return x;
+        const int gx = P[px];
+        if (gx < 0) return px;
+        P[x] = gx;   // path halving (benign race: gx is an ancestor)
         x = gx;
     }
     return -1;
@@ -41,15 +49,9 @@ __device__ __forceinline__ void uf_union(int32_t* parent, int a, int b, DevState
             a = b;
             b = t;
         }
-        int old = atomicCAS(&parent[a], a, b);
-        if (old == a) return;
+        if (atomicCAS(&parent[a], -1, b) == -1) return;
     }
     dev_fail(st, RPD_E_TIMEOUT, CNT_UF_LIMIT);
-}
-
-__global__ void k_iota(int32_t* p, long long n) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = (int32_t)i;
 }
 
 // slot of sphere `sph` among the (sorted) candidates of tet t, or -1
@@ -88,9 +90,15 @@ __global__ void k_link_cells(ClipArgs A, long long npairs, int32_t* __restrict__
     }
 }
 
-__global__ void k_link_records(ClipArgs A, int which, long long nrec, int32_t* __restrict__ parent) {
+// Record count of one kind: read on the device (written by the clip), capped.
+__device__ __forceinline__ long long rec_count(const ClipArgs& A, int which, long long nmax) {
+    const long long n = (long long)A.rcount[which];
+    return n < nmax ? n : nmax;
+}
+
+__global__ void k_link_records(ClipArgs A, int which, long long nmax, int32_t* __restrict__ parent) {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrec) return;
+    if (r >= rec_count(A, which, nmax)) return;
     unsigned lk = A.rlink[which][r];
     if (!lk) return;
     long long t = A.rtet[which][r];
@@ -132,7 +140,7 @@ __global__ void k_cell_agg(ClipArgs A, long long npairs, int32_t* __restrict__ p
     if (p >= npairs || A.pflag[p] != 1) return;
     const long long t = A.pair_tet[p];
     const int i = A.cand[t * RPD_MAXC + (p - A.pair_off[t])];
-    const bool root = uf_find(parent, (int)p) == (int)p;
+    const bool root = parent[p] < 0;
     atomicAdd(&cchi[i], (int)A.c_val[p]);
     if (root) atomicAdd(&cbeta[i], 1);
     cpres[i] = 1;
@@ -155,13 +163,13 @@ __global__ void k_cell_emit(long long ns, const uint8_t* __restrict__ cpres, con
 
 // Faces, edges, vertices: records hashed by key; chi and root counts summed
 // into the key's slot.
-__global__ void k_rec_agg(ClipArgs A, int which, long long nrec, int32_t* __restrict__ parent, uint64_t* __restrict__ tk,
+__global__ void k_rec_agg(ClipArgs A, int which, long long nmax, int32_t* __restrict__ parent, uint64_t* __restrict__ tk,
                           int32_t* __restrict__ tchi, int32_t* __restrict__ tbeta, unsigned long long mask,
                           int shift) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrec) return;
+    if (r >= rec_count(A, which, nmax)) return;
     const uint64_t key = A.rkey[which][r];
-    const bool root = parent ? uf_find(parent, (int)r) == (int)r : true;
+    const bool root = parent ? parent[r] < 0 : true;
     const long long h = table_insert(tk, mask, shift, key);
     if (h < 0) {   // cannot happen: capacity >= 2 * records
         dev_fail(A.st, RPD_E_OVERFLOW, CNT_CAPACITY);
@@ -171,9 +179,11 @@ __global__ void k_rec_agg(ClipArgs A, int which, long long nrec, int32_t* __rest
     if (root) atomicAdd(&tbeta[h], 1);
 }
 
-// Occupied slots appended (warp-aggregated) to (key, slot) lists.
-__global__ void k_table_compact(const uint64_t* __restrict__ tk, long long cap, uint64_t* __restrict__ ck,
-                                uint32_t* __restrict__ cs, unsigned long long* __restrict__ count) {
+// Occupied slots appended (warp-aggregated) to (key, slot) lists; each key
+// counted in the bucket of its first sphere.
+__global__ void k_table_compact(const uint64_t* __restrict__ tk, long long cap, int shift, uint64_t* __restrict__ ck,
+                                uint32_t* __restrict__ cs, unsigned long long* __restrict__ count,
+                                int32_t* __restrict__ bcount) {
     const long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint64_t key = h < cap ? tk[h] : HEMPTY;
@@ -187,25 +197,44 @@ __global__ void k_table_compact(const uint64_t* __restrict__ tk, long long cap, 
         const unsigned long long q = base + __popc(m & ((1u << lane) - 1u));
         ck[q] = key;
         cs[q] = (uint32_t)h;
+        atomicAdd(&bcount[key >> shift], 1);
     }
 }
 
-__global__ void k_rec_emit(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ ss,
-                           const unsigned long long* __restrict__ count, long long nmax, int kind, int b,
-                           const int32_t* __restrict__ tchi, const int32_t* __restrict__ tbeta,
-                           int32_t* __restrict__ keys, int32_t* __restrict__ chi, int32_t* __restrict__ beta,
-                           uint8_t* __restrict__ flag) {
+// (key, slot) into the bucket of the key's first sphere (any order inside).
+__global__ void k_bucket_fill(const uint64_t* __restrict__ ck, const uint32_t* __restrict__ cs,
+                              const unsigned long long* __restrict__ count, long long nmax, int shift,
+                              const int64_t* __restrict__ bstart, int32_t* __restrict__ bfill,
+                              uint64_t* __restrict__ bk, uint32_t* __restrict__ bs) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = (long long)*count;
-    if (i >= n || i >= nmax) return;
-    const uint64_t k = sk[i];
-    const uint32_t h = ss[i];
+    if (i >= (long long)*count || i >= nmax) return;
+    const uint64_t key = ck[i];
+    const long long b = (long long)(key >> shift);
+    const long long q = bstart[b] + atomicAdd(&bfill[b], 1);
+    bk[q] = key;
+    bs[q] = cs[i];
+}
+
+// Rank inside the bucket, then the output row: sorted key, chi, beta0, flag.
+__global__ void k_bucket_emit(const uint64_t* __restrict__ bk, const uint32_t* __restrict__ bs,
+                              const unsigned long long* __restrict__ count, long long nmax, int kind, int b,
+                              const int64_t* __restrict__ bstart, const int32_t* __restrict__ tchi,
+                              const int32_t* __restrict__ tbeta, int32_t* __restrict__ keys,
+                              int32_t* __restrict__ chi, int32_t* __restrict__ beta, uint8_t* __restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)*count || i >= nmax) return;
+    const uint64_t k = bk[i];
+    const long long bu = (long long)(k >> ((kind - 1) * b));
+    const long long b0 = bstart[bu], b1 = bstart[bu + 1];
+    long long q = b0;
+    for (long long j = b0; j < b1; j++) q += bk[j] < k;
     const uint64_t mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
-    for (int j = 0; j < kind; j++) keys[i * kind + j] = (int32_t)((k >> (b * (kind - 1 - j))) & mask);
+    for (int j = 0; j < kind; j++) keys[q * kind + j] = (int32_t)((k >> (b * (kind - 1 - j))) & mask);
+    const uint32_t h = bs[i];
     const int c = tchi[h], bb = tbeta[h];
-    chi[i] = c;
-    beta[i] = bb;
-    flag[i] = (bb == 1 && c == 1) ? 1 : 0;
+    chi[q] = c;
+    beta[q] = bb;
+    flag[q] = (bb == 1 && c == 1) ? 1 : 0;
 }
 
 __global__ void k_compact_pieces(ClipArgs A, long long npairs, const int64_t* __restrict__ off, int32_t* d_tet,
@@ -227,88 +256,119 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static int table_bits(long long n) {
     int b = 4;
-    while ((1ll << b) < 2 * n) b++;
+    while ((1ll << b) < n + 1) b++;
     return b;
 }
 
-size_t finalize_tmp_bytes(int kind, long long n, long long ns) {
-    const size_t m = (size_t)(n > 0 ? n : 1);
-    if (kind == 1) {
-        return al256(sizeof(int32_t) * m) + al256(sizeof(int32_t) * 2 * ns) + al256((size_t)ns) +
-               al256(sizeof(int64_t) * (ns + 1)) + al256(scan_tmp_bytes(ns));
-    }
-    const size_t cap = (size_t)1 << table_bits(n);
-    return al256(sizeof(int32_t) * m) + al256(sizeof(uint64_t) * cap) + al256(sizeof(int32_t) * 2 * cap) +
-           al256(sizeof(unsigned long long)) + 2 * al256(sizeof(uint64_t) * m) + 2 * al256(sizeof(uint32_t) * m) +
-           al256(radix_tmp_bytes(n));
+// Scratch layout of one kind: the 0xff-filled part first (parents, table
+// keys), then the zero-filled part, then the rest.
+namespace {
+struct Layout {
+    size_t ff_bytes, zero_bytes, total;
+    size_t o_tk, o_tchi, o_cnt, o_bcount, o_bfill, o_cchi, o_cpres, o_ck, o_cs, o_bstart, o_bk, o_bs, o_scan;
+};
+Layout layout(int kind, long long ncap, long long ns) {
+    Layout L{};
+    const size_t m = (size_t)(ncap > 0 ? ncap : 1);
+    const size_t cap = kind == 1 ? 0 : ((size_t)1 << table_bits(ncap));
+    size_t p = al256(sizeof(int32_t) * m);   // parents
+    L.o_tk = p;
+    p += al256(sizeof(uint64_t) * cap);
+    L.ff_bytes = p;
+    L.o_tchi = p;                            // tchi, tbeta
+    p += al256(sizeof(int32_t) * 2 * cap);
+    L.o_cnt = p;
+    p += al256(sizeof(unsigned long long));
+    L.o_bcount = p;
+    p += al256(sizeof(int32_t) * (ns + 1));
+    L.o_bfill = p;
+    p += al256(sizeof(int32_t) * (ns + 1));
+    L.o_cchi = p;                            // cchi, cbeta
+    p += al256(kind == 1 ? sizeof(int32_t) * 2 * ns : 0);
+    L.o_cpres = p;
+    p += al256(kind == 1 ? (size_t)ns : 0);
+    L.zero_bytes = p - L.ff_bytes;
+    L.o_ck = p;
+    p += al256(kind == 1 ? 0 : sizeof(uint64_t) * m);
+    L.o_cs = p;
+    p += al256(kind == 1 ? 0 : sizeof(uint32_t) * m);
+    L.o_bk = p;
+    p += al256(kind == 1 ? 0 : sizeof(uint64_t) * m);
+    L.o_bs = p;
+    p += al256(kind == 1 ? 0 : sizeof(uint32_t) * m);
+    L.o_bstart = p;
+    p += al256(sizeof(int64_t) * (ns + 1));
+    L.o_scan = p;
+    p += al256(scan_tmp_bytes(ns + 1));
+    L.total = p;
+    return L;
+}
+}  // namespace
+
+size_t finalize_tmp_bytes(int kind, long long ncap, long long ns) { return layout(kind, ncap, ns).total; }
+
+void launch_finalize_clear(int kind, long long ncap, long long ns, void* tmp, cudaStream_t s) {
+    const Layout L = layout(kind, ncap, ns);
+    cudaMemsetAsync(tmp, 0xff, L.ff_bytes, s);
+    cudaMemsetAsync((char*)tmp + L.ff_bytes, 0, L.zero_bytes, s);
 }
 
-void launch_finalize(const ClipArgs& a, int kind, long long n, long long ns, int key_bits, const FinalOut& out,
-                     void* tmp, cudaStream_t s) {
-    char* p = (char*)tmp;
-    int32_t* parent = (int32_t*)p;
-    p += al256(sizeof(int32_t) * (n > 0 ? n : 1));
+void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, long long ns, int key_bits,
+                     const FinalOut& out, void* tmp, cudaStream_t s) {
+    // kind 1: n = the number of pairs; kinds 2..4: n = the record capacity,
+    // the record count itself is read on the device (a.rcount)
+    const Layout L = layout(kind, ncap, ns);
+    char* base = (char*)tmp;
+    int32_t* parent = (int32_t*)base;
+    int32_t* bcount = (int32_t*)(base + L.o_bcount);
+    int32_t* bfill = (int32_t*)(base + L.o_bfill);
+    int64_t* bstart = (int64_t*)(base + L.o_bstart);
+    void* stmp = base + L.o_scan;
     if (kind == 1) {
-        int32_t* cchi = (int32_t*)p;
+        int32_t* cchi = (int32_t*)(base + L.o_cchi);
         int32_t* cbeta = cchi + ns;
-        p += al256(sizeof(int32_t) * 2 * ns);
-        uint8_t* cpres = (uint8_t*)p;
-        p += al256((size_t)ns);
-        int64_t* pos = (int64_t*)p;
-        p += al256(sizeof(int64_t) * (ns + 1));
-        cudaMemsetAsync(cchi, 0, sizeof(int32_t) * 2 * ns, s);
-        cudaMemsetAsync(cpres, 0, (size_t)ns, s);
+        uint8_t* cpres = (uint8_t*)(base + L.o_cpres);
         if (n > 0) {
-            k_iota<<<nblk(n, 256), 256, 0, s>>>(parent, n);
-            note_launch();
             k_link_cells<<<nblk(n, 256), 256, 0, s>>>(a, n, parent);
             note_launch();
             k_cell_agg<<<nblk(n, 256), 256, 0, s>>>(a, n, parent, cchi, cbeta, cpres);
             note_launch();
         }
-        scan_excl(cpres, pos, ns, p, s);
-        k_cell_emit<<<nblk(ns, 256), 256, 0, s>>>(ns, cpres, pos, cchi, cbeta, out.keys, out.chi, out.beta, out.flag,
-                                                  out.count);
+        scan_excl(cpres, bstart, ns, stmp, s);
+        k_cell_emit<<<nblk(ns, 256), 256, 0, s>>>(ns, cpres, bstart, cchi, cbeta, out.keys, out.chi, out.beta,
+                                                  out.flag, out.count);
         note_launch();
         return;
     }
     const int which = kind - 2;
-    const int tb = table_bits(n);
+    const int tb = table_bits(ncap);
     const long long cap = 1ll << tb;
-    uint64_t* tk = (uint64_t*)p;
-    p += al256(sizeof(uint64_t) * cap);
-    int32_t* tchi = (int32_t*)p;
+    uint64_t* tk = (uint64_t*)(base + L.o_tk);
+    int32_t* tchi = (int32_t*)(base + L.o_tchi);
     int32_t* tbeta = tchi + cap;
-    p += al256(sizeof(int32_t) * 2 * cap);
-    unsigned long long* cnt = (unsigned long long*)p;
-    p += al256(sizeof(unsigned long long));
-    const size_t m = (size_t)(n > 0 ? n : 1);
-    uint64_t* ck = (uint64_t*)p; p += al256(sizeof(uint64_t) * m);
-    uint64_t* sk = (uint64_t*)p; p += al256(sizeof(uint64_t) * m);
-    uint32_t* cs = (uint32_t*)p; p += al256(sizeof(uint32_t) * m);
-    uint32_t* ss = (uint32_t*)p; p += al256(sizeof(uint32_t) * m);
-    cudaMemsetAsync(tk, 0xff, sizeof(uint64_t) * cap, s);
-    cudaMemsetAsync(tchi, 0, sizeof(int32_t) * 2 * cap, s);
-    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+    unsigned long long* cnt = (unsigned long long*)(base + L.o_cnt);
+    uint64_t* ck = (uint64_t*)(base + L.o_ck);
+    uint32_t* cs = (uint32_t*)(base + L.o_cs);
+    uint64_t* bk = (uint64_t*)(base + L.o_bk);
+    uint32_t* bs = (uint32_t*)(base + L.o_bs);
+    const int shift = (kind - 1) * key_bits;   // first sphere of a key
     if (n > 0) {
-        int32_t* par = nullptr;
         if (which < 2) {   // faces and edges have components across tets; vertices are points
-            k_iota<<<nblk(n, 256), 256, 0, s>>>(parent, n);
-            note_launch();
             k_link_records<<<nblk(n, 256), 256, 0, s>>>(a, which, n, parent);
             note_launch();
-            par = parent;
         }
-        k_rec_agg<<<nblk(n, 256), 256, 0, s>>>(a, which, n, par, tk, tchi, tbeta, (unsigned long long)(cap - 1),
-                                               64 - tb);
+        k_rec_agg<<<nblk(n, 256), 256, 0, s>>>(a, which, n, which < 2 ? parent : nullptr, tk, tchi, tbeta,
+                                               (unsigned long long)(cap - 1), 64 - tb);
         note_launch();
     }
-    k_table_compact<<<nblk(cap, 256), 256, 0, s>>>(tk, cap, ck, cs, cnt);
+    k_table_compact<<<nblk(cap, 256), 256, 0, s>>>(tk, cap, shift, ck, cs, cnt, bcount);
     note_launch();
-    radix_sort_pairs_dn(ck, cs, sk, ss, (const long long*)cnt, n, kind * key_bits, p, &a.st->err, s);
+    scan_excl(bcount, bstart, ns, stmp, s);
     if (n > 0) {
-        k_rec_emit<<<nblk(n, 256), 256, 0, s>>>(sk, ss, cnt, n, kind, key_bits, tchi, tbeta, out.keys, out.chi,
-                                                out.beta, out.flag);
+        k_bucket_fill<<<nblk(n, 256), 256, 0, s>>>(ck, cs, cnt, n, shift, bstart, bfill, bk, bs);
+        note_launch();
+        k_bucket_emit<<<nblk(n, 256), 256, 0, s>>>(bk, bs, cnt, n, kind, key_bits, bstart, tchi, tbeta, out.keys,
+                                                   out.chi, out.beta, out.flag);
         note_launch();
     }
     cudaMemcpyAsync(out.count, cnt, sizeof(long long), cudaMemcpyDeviceToDevice, s);

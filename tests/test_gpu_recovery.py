@@ -1,0 +1,79 @@
+"""Recovery paths of rpd_build on the GPU: a rebuild after the element-record
+buffers overflow, and a clean failure when a device allocation fails.
+
+Both are driven from the host through the library's test hooks
+(RPD_RECORD_CAP: capacity of the first record buffers; RPD_FAIL_ALLOC_AFTER:
+the allocation that fails); neither touches the device in an unsafe way.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_18761_gb300 import build_workload
+from paper_2403_18761_gb300.rpd import collect
+from rpd_inputs import torus_c1
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def _same(a, b):
+    for kind in (1, 2, 3, 4):
+        for f in ("keys", "chi", "beta0", "flag"):
+            assert np.array_equal(a["kinds"][kind][f], b["kinds"][kind][f]), (kind, f)
+    for f in ("tet", "sphere", "vol", "moment"):
+        assert np.array_equal(a[f], b[f]), f
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_record_overflow_rebuilds_identically(precision):
+    w = torus_c1()
+    ctx = build_workload(w, precision=precision)
+    want = collect(ctx)
+    ctx.rpd_destroy()
+    os.environ["RPD_RECORD_CAP"] = "64"   # far below the element records of this mesh
+    try:
+        ctx = build_workload(w, precision=precision)
+        got = collect(ctx)
+        ctx.rpd_destroy()
+    finally:
+        del os.environ["RPD_RECORD_CAP"]
+    assert all(got["stats"]["n_records"][k] > 64 for k in (1, 2)), got["stats"]["n_records"]
+    _same(got, want)
+
+
+_CHILD = r"""
+import sys
+sys.path.insert(0, {root!r})
+from paper_2403_18761_gb300 import build_workload, RpdError
+from paper_2403_18761_gb300.rpd import RPD_E_OOM
+from rpd_inputs import torus_c1
+w = torus_c1()
+fails = 0
+try:
+    build_workload(w)
+except RpdError as e:
+    fails = 1
+    assert e.status == RPD_E_OOM, e.status
+print("FAILED_CLEANLY" if fails else "NO_FAILURE")
+"""
+
+
+@pytest.mark.parametrize("after", [3, 25, 60])
+def test_allocation_failure_is_reported(after):
+    env = dict(os.environ, RPD_FAIL_ALLOC_AFTER=str(after))
+    out = subprocess.run([sys.executable, "-c", _CHILD.format(root=ROOT)], env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "FAILED_CLEANLY" in out.stdout, out.stdout
