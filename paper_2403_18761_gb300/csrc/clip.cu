@@ -759,6 +759,35 @@ struct VolAcc<float> {
         df be[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
         if (m == 0) {
             set4(be, 6 - a - b - c, df_make(1.0f));
+        } else if (m == 1) {
+            // on the tet edge between corners c0 and c1: the exact row entries
+            // F0, F1 of the one radical plane give beta_c0 = F1 / (F1 - F0)
+            const int s = L.cand[bis[0] - 4];
+            const int3 cs = ld_int3(A.Ci, s);
+            const long long ws = A.W[s];
+            const int c0 = fc[0], c1 = fc[1];
+            const int3 x0 = c0 == 0 ? L.X[0] : (c0 == 1 ? L.X[1] : (c0 == 2 ? L.X[2] : L.X[3]));
+            const int3 x1 = c1 == 0 ? L.X[0] : (c1 == 1 ? L.X[1] : (c1 == 2 ? L.X[2] : L.X[3]));
+            const long long F0 = get4(L.di, c0) - pd_exact(x0, cs, ws);
+            const long long F1 = get4(L.di, c1) - pd_exact(x1, cs, ws);
+            const df b0 = df_div(df_from_i64(F1), df_from_i64(F1 - F0));
+            set4(be, c0, b0);
+            set4(be, c1, df_sub(df_make(1.0f), b0));
+        } else if (m == 2) {
+            // on a tet face: the cofactors of two exact rows over the three
+            // free columns, in exact 128-bit integers (|entry| < 2^47)
+            long long F[4], G[4];
+            row_i64(L, A.Ci, A.W, bis[0] - 4, F);
+            row_i64(L, A.Ci, A.W, bis[1] - 4, G);
+            const long long f0 = get4(F, fc[0]), f1 = get4(F, fc[1]), f2 = get4(F, fc[2]);
+            const long long g0 = get4(G, fc[0]), g1 = get4(G, fc[1]), g2 = get4(G, fc[2]);
+            const __int128 k0 = (__int128)f1 * g2 - (__int128)f2 * g1;
+            const __int128 k1 = (__int128)f2 * g0 - (__int128)f0 * g2;
+            const __int128 k2 = (__int128)f0 * g1 - (__int128)f1 * g0;
+            const df inv = df_div(df_make(1.0f), df_from_i128(k0 + k1 + k2));
+            set4(be, fc[0], df_mul(df_from_i128(k0), inv));
+            set4(be, fc[1], df_mul(df_from_i128(k1), inv));
+            set4(be, fc[2], df_mul(df_from_i128(k2), inv));
         } else {
             df R[3][4];
 #pragma unroll
@@ -795,9 +824,9 @@ struct VolAcc<float> {
                     C[k] = (k & 1) ? df_neg(d) : d;
                 }
             }
-            const df sum = df_add(df_add(C[0], C[1]), df_add(C[2], C[3]));
+            const df inv = df_div(df_make(1.0f), df_add(df_add(C[0], C[1]), df_add(C[2], C[3])));
 #pragma unroll
-            for (int z = 1; z < 4; z++) be[z] = df_div(C[z], sum);
+            for (int z = 1; z < 4; z++) be[z] = df_mul(C[z], inv);
         }
         out[0] = be[1];
         out[1] = be[2];

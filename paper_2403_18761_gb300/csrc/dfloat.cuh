@@ -61,3 +61,17 @@ __device__ __forceinline__ df df_from_i64(long long v) {
 }
 
 __device__ __forceinline__ df df_scale(df x, float p2) { return {x.hi * p2, x.lo * p2}; }
+
+// |v| < 2^127 to double-float: the top 48 bits exactly, the rest truncated
+// (relative error below 2^-47).
+__device__ __forceinline__ df df_from_i128(__int128 v) {
+    const bool neg = v < 0;
+    unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const int len = hi ? 128 - __clzll((long long)hi) : 64 - (lo ? __clzll((long long)lo) : 64);
+    const int sh = len > 48 ? len - 48 : 0;
+    const long long top = (long long)(a >> sh);   // < 2^48
+    df r = df_from_i64(neg ? -top : top);
+    if (sh) r = df_scale(r, __int_as_float((127 + sh) << 23));
+    return r;
+}
