@@ -604,9 +604,8 @@ static rpd_status copy_rows(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, const 
     if (cap < m) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of elements");
     if (m == 0) return RPD_OK;
     const FinalOut& o = ctx->fout[kind - 1];
-    if (d_keys)
-        cudaMemcpyAsync(d_keys, o.keys, sizeof(int32_t) * m * kind, cudaMemcpyDeviceToDevice, ctx->stream);
-    if (d_dst) cudaMemcpyAsync(d_dst, src, elem * m, cudaMemcpyDeviceToDevice, ctx->stream);
+    launch_copy_rows(d_keys ? o.keys : nullptr, d_keys, m * kind, d_dst ? src : nullptr, d_dst, m, (int)elem,
+                     ctx->stream);
     return cuda_check(ctx, "output copy");
 }
 

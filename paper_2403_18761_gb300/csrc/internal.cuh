@@ -125,5 +125,9 @@ size_t finalize_tmp_bytes(int kind, long long ncap, long long ns);
 void launch_finalize_clear(int kind, long long ncap, long long ns, void* tmp, cudaStream_t s);
 void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, long long ns, int key_bits,
                      const FinalOut& out, void* tmp, cudaStream_t s);
+// One launch copying n_keys int32 key entries and n values of elem (1 or 4)
+// bytes; a NULL source skips that part.
+void launch_copy_rows(const int32_t* keys, int32_t* d_keys, long long n_keys, const void* vals, void* d_vals,
+                      long long n, int elem, cudaStream_t s);
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet,
                            int32_t* d_sphere, double* d_vol, double* d_mom, cudaStream_t s);

@@ -16,6 +16,8 @@
 // and a rank inside each bucket.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "prim.cuh"
 
@@ -98,7 +100,8 @@ __device__ __forceinline__ long long rec_count(const ClipArgs& A, int which, lon
 
 __global__ void k_link_records(ClipArgs A, int which, long long nmax, int32_t* __restrict__ parent) {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rec_count(A, which, nmax)) return;
+    const long long nrec = rec_count(A, which, nmax);   // records past it were never written
+    if (r >= nrec) return;
     unsigned lk = A.rlink[which][r];
     if (!lk) return;
     long long t = A.rtet[which][r];
@@ -116,7 +119,7 @@ __global__ void k_link_records(ClipArgs A, int which, long long nmax, int32_t* _
         if (s2 >= 0) {
             long long p2 = A.pair_off[t2] + s2;
             if (A.pflag[p2] == 1) {
-                long long b0 = off[p2], b1 = b0 + cnt[p2];
+                long long b0 = off[p2], b1 = min(b0 + (long long)cnt[p2], nrec);
                 for (long long z = b0; z < b1; z++)
                     if (A.rkey[which][z] == key) {
                         r2 = z;
@@ -235,6 +238,20 @@ __global__ void k_bucket_emit(const uint64_t* __restrict__ bk, const uint32_t* _
     chi[q] = c;
     beta[q] = bb;
     flag[q] = (bb == 1 && c == 1) ? 1 : 0;
+}
+
+__global__ void k_copy_rows(const int32_t* __restrict__ keys, int32_t* __restrict__ d_keys, long long nk,
+                            const void* __restrict__ vals, void* __restrict__ d_vals, long long n, int elem) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nk + n; i += stride) {
+        if (i < nk) {
+            if (keys) d_keys[i] = keys[i];
+        } else if (vals) {
+            const long long j = i - nk;
+            if (elem == 4) ((int32_t*)d_vals)[j] = ((const int32_t*)vals)[j];
+            else ((uint8_t*)d_vals)[j] = ((const uint8_t*)vals)[j];
+        }
+    }
 }
 
 __global__ void k_compact_pieces(ClipArgs A, long long npairs, const int64_t* __restrict__ off, int32_t* d_tet,
@@ -372,6 +389,15 @@ void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, l
         note_launch();
     }
     cudaMemcpyAsync(out.count, cnt, sizeof(long long), cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_copy_rows(const int32_t* keys, int32_t* d_keys, long long n_keys, const void* vals, void* d_vals,
+                      long long n, int elem, cudaStream_t s) {
+    const long long total = n_keys + n;
+    if (total <= 0 || (!keys && !vals)) return;
+    const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 16);
+    k_copy_rows<<<blocks, 256, 0, s>>>(keys, d_keys, n_keys, vals, d_vals, n, elem);
+    note_launch();
 }
 
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet, int32_t* d_sphere,

@@ -139,33 +139,25 @@ class Ctx:
         self._check(fn(self.handle, kind, None, None, 0, ctypes.byref(n)))
         return n.value
 
+    def _rows(self, fn, kind, vdtype):
+        """Keys int32[n, kind] and one value per key, in fresh device tensors."""
+        n = self._query(fn, kind)
+        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
+        vals = torch.empty(n, dtype=vdtype, device=self.device)
+        self._check(fn(self.handle, kind, keys.data_ptr(), vals.data_ptr(), n, None))
+        return keys, vals
+
     def rpd_euler(self, kind):
         """(keys int32[n, kind], chi int32[n]) on the device."""
-        lib = load()
-        n = self._query(lib.rpd_euler, kind)
-        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
-        chi = torch.empty(n, dtype=torch.int32, device=self.device)
-        out = ctypes.c_int64(0)
-        self._check(lib.rpd_euler(self.handle, kind, _ptr(keys), _ptr(chi), n, ctypes.byref(out)))
-        return keys, chi
+        return self._rows(load().rpd_euler, kind, torch.int32)
 
     def rpd_components(self, kind):
-        lib = load()
-        n = self._query(lib.rpd_components, kind)
-        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
-        beta = torch.empty(n, dtype=torch.int32, device=self.device)
-        out = ctypes.c_int64(0)
-        self._check(lib.rpd_components(self.handle, kind, _ptr(keys), _ptr(beta), n, ctypes.byref(out)))
-        return keys, beta
+        """(keys int32[n, kind], beta0 int32[n]) on the device."""
+        return self._rows(load().rpd_components, kind, torch.int32)
 
     def rpd_contractible(self, kind):
-        lib = load()
-        n = self._query(lib.rpd_contractible, kind)
-        keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
-        flag = torch.empty(n, dtype=torch.uint8, device=self.device)
-        out = ctypes.c_int64(0)
-        self._check(lib.rpd_contractible(self.handle, kind, _ptr(keys), _ptr(flag), n, ctypes.byref(out)))
-        return keys, flag
+        """(keys int32[n, kind], flag uint8[n]) on the device."""
+        return self._rows(load().rpd_contractible, kind, torch.uint8)
 
     def rpd_pieces(self):
         """(tet int32[n], sphere int32[n], vol f64[n], moment f64[n,3]) sorted by (tet, sphere)."""
