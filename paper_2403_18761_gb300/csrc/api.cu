@@ -33,6 +33,37 @@ long long alloc_budget() {
 
 std::atomic<long long> g_launches{0};
 
+// Timing events are recycled per device: a context takes its events from the
+// pool and returns them, all completed, when it is destroyed.
+struct EventPool {
+    std::mutex mu;
+    std::vector<cudaEvent_t> free_ev[64];
+};
+EventPool& event_pool() {
+    static EventPool p;
+    return p;
+}
+bool acquire_events(int dev, cudaEvent_t* out, int n) {
+    EventPool& P = event_pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    for (int k = 0; k < n; k++) {
+        if (!P.free_ev[dev].empty()) {
+            out[k] = P.free_ev[dev].back();
+            P.free_ev[dev].pop_back();
+        } else if (cudaEventCreate(&out[k]) != cudaSuccess) {
+            out[k] = nullptr;
+            return false;
+        }
+    }
+    return true;
+}
+void release_events(int dev, cudaEvent_t* ev, int n) {
+    EventPool& P = event_pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    for (int k = 0; k < n; k++)
+        if (ev[k]) P.free_ev[dev].push_back(ev[k]);
+}
+
 // One stream-ordered memory pool per device, owned by the library, that keeps
 // freed workspace cached (release threshold = max) so that repeated builds
 // reuse it instead of mapping fresh memory at every synchronisation.
@@ -101,9 +132,15 @@ struct rpd_ctx {
     int64_t* piece_off = nullptr;
     long long npieces = 0;
     rpd_stats stats{};
+    int device = 0;
     cudaEvent_t ev[16] = {};
     // clip stage: fork, end of each bin's clip kernel, end of each bin's work
     cudaEvent_t evc[1 + 2 * RPD_NBINS] = {};
+
+    // Optional chunk that alloc carves from before it asks the pool: one pool
+    // call instead of dozens after the pair count is known.
+    char* chunk = nullptr;
+    size_t chunk_size = 0, chunk_off = 0;
 
     template <typename T>
     T* alloc(size_t count) {
@@ -112,6 +149,13 @@ struct rpd_ctx {
         if (budget >= 0 && nalloc >= budget) {
             failed_alloc = true;
             return nullptr;
+        }
+        const size_t rounded = (bytes + 255) & ~(size_t)255;
+        if (chunk && chunk_off + rounded <= chunk_size) {
+            T* q = (T*)(chunk + chunk_off);
+            chunk_off += rounded;
+            nalloc++;
+            return q;
         }
         void* p = nullptr;
         cudaMemPool_t pool = library_pool();
@@ -124,9 +168,19 @@ struct rpd_ctx {
         allocs.push_back(p);
         return (T*)p;
     }
+    // Reserve one chunk of `bytes` for the allocations that follow.
+    bool reserve(size_t bytes) {
+        char* p = alloc<char>(bytes);
+        if (!p) return false;
+        chunk = p;
+        chunk_size = bytes;
+        chunk_off = 0;
+        return true;
+    }
     void release_all() {
         for (void* p : allocs) cudaFreeAsync(p, stream);
         allocs.clear();
+        chunk = nullptr;
     }
 };
 
@@ -311,10 +365,10 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
                  const double* d_radii) {
     cudaStream_t s = c->stream;
     const long long nv = c->nv, nt = c->nt, ns = c->ns;
-    for (int k = 0; k < 16; k++)
-        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
-    for (int k = 0; k < 1 + 2 * RPD_NBINS; k++)
-        if (cudaEventCreate(&c->evc[k]) != cudaSuccess) return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
+    if (cudaGetDevice(&c->device) != cudaSuccess || c->device < 0 || c->device >= 64)
+        return fail(c, RPD_E_CUDA, "no usable current device");
+    if (!acquire_events(c->device, c->ev, 16) || !acquire_events(c->device, c->evc, 1 + 2 * RPD_NBINS))
+        return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
     // side streams: mesh combinatorics next to the sphere grid and kNN, the
     // clip bins, and the four element kinds of the finalisation
     BinStreams* bs = bin_streams();
@@ -388,6 +442,14 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->stats.n_pairs = npairs;
     for (int b = 0; b < RPD_NBINS; b++) c->stats.bin_pairs[b] = c->hbin[b] = hb[b];
     // ---- A3-A4
+    {   // one chunk for the pair, queue, record and finalisation buffers
+        size_t est = (size_t)npairs * 760 + ((size_t)ns * 64 + (4 << 20));
+        for (int b = 1; b < RPD_NBINS; b++) est += (size_t)c->hbin[b] * (2 * clip_vmax(b) * 4 + 8);
+        const long long cap0[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
+        est += finalize_tmp_bytes(1, npairs, ns);
+        for (int k = 0; k < 3; k++) est += finalize_tmp_bytes(k + 2, cap0[k], ns) + (size_t)cap0[k] * 40;
+        NEED(c->reserve(est));
+    }
     c->pair_tet = c->alloc<int32_t>(npairs);
     c->bins = c->alloc<int32_t>(npairs);
     c->rcount = c->alloc<unsigned long long>(3);
@@ -654,10 +716,8 @@ void rpd_destroy(rpd_ctx* ctx) {
     join_side_streams(ctx);   // nothing queued on a side stream may outlive its memory
     ctx->release_all();
     cudaStreamSynchronize(ctx->stream);
-    for (cudaEvent_t e : ctx->ev)
-        if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : ctx->evc)
-        if (e) cudaEventDestroy(e);
+    release_events(ctx->device, ctx->ev, 16);
+    release_events(ctx->device, ctx->evc, 1 + 2 * RPD_NBINS);
     cudaGetLastError();
     delete ctx;
 }
