@@ -65,7 +65,9 @@ typedef struct {
     int32_t debug_checks; /* test switches (0 in production): value 1 sends every
                              non-corner clip predicate past the first-stage
                              filter to the FP64 stage, value 2 straight to the
-                             exact 256-bit stage.  Results must not change.     */
+                             exact 256-bit stage; bit 4 makes the neighbour
+                             search keep distance and id apart (the form used
+                             above 2^17 spheres).  Results must not change.     */
 } rpd_options;
 
 typedef struct {

@@ -410,8 +410,8 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     NEED(cell_sph && cell_w && ktmp);
     launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
                        gtmp, s);
-    launch_knn(c->Xi, nv, c->Ci, c->W, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp,
-               &c->st->err, s);
+    launch_knn(c->Xi, nv, ns, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp,
+               &c->st->err, (c->opt.debug_checks & 4) != 0, s);
     TRY(cuda_check(c, "knn launch"));
     record(c, 3);
     // ---- A2

@@ -38,9 +38,9 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
 // bound of the power distance of every sphere left out of the list.
 // tmp must hold knn_tmp_bytes(nv); ncap bounds the number of grid cells.
 size_t knn_tmp_bytes(long long nv);
-void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
-                const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, long long ncap, int K,
-                int32_t* knn, long long* dplus, void* tmp, int* d_err, cudaStream_t s);
+void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
+                const int4* cell_sph, const long long* cell_w, long long ncap, int K, int32_t* knn, long long* dplus,
+                void* tmp, int* d_err, bool two_word, cudaStream_t s);
 // Candidate spheres of every tet (superset of the spheres whose cell meets
 // the tet with positive volume), sorted by index, at most RPD_MAXC.
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,

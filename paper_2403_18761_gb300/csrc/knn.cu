@@ -227,48 +227,93 @@ __device__ __forceinline__ long long outside_box_lb2(int3 x, const GridParams& g
     return best == LLONG_MAX ? LLONG_MAX : best * best;
 }
 
-// Sift (d, id) down from the root of a max-heap of size m held in column
-// `lane` of hd/hi.
-template <int KMAX>
-__device__ __forceinline__ void heap_sift_down(long long (*hd)[32], int (*hi)[32], int lane, int m, long long d,
-                                               int id) {
+// Heap entries, ordered by (power distance, sphere id).  With ns <= 2^17 an
+// entry is one 64-bit key, (pd + 2^46) << 17 | id (|pd| < 2^46), whose integer
+// order is that order; otherwise the distance and the id are kept apart.
+struct PackedEntry {
+    typedef unsigned long long E;
+    static __device__ __forceinline__ E make(long long d, int id) {
+        return ((unsigned long long)(d + (1ll << 46)) << 17) | (unsigned)id;
+    }
+    static __device__ __forceinline__ long long dist(E e) { return (long long)(e >> 17) - (1ll << 46); }
+    static __device__ __forceinline__ int sid(E e) { return (int)(e & 0x1ffffu); }
+    static __device__ __forceinline__ bool less(E a, E b) { return a < b; }
+    static __device__ __forceinline__ E empty() { return ~0ull; }
+    template <int KMAX>
+    struct Storage {
+        E k[4][KMAX][32];
+    };
+    template <int KMAX>
+    struct Heap {   // column `lane` of one warp's heaps
+        E (*k)[32];
+        __device__ __forceinline__ Heap(Storage<KMAX>& s, int warp) : k(s.k[warp]) {}
+        __device__ __forceinline__ E get(int p, int l) const { return k[p][l]; }
+        __device__ __forceinline__ void set(int p, int l, E e) const { k[p][l] = e; }
+    };
+};
+
+struct PairEntry {
+    struct E {
+        long long d;
+        int i;
+    };
+    static __device__ __forceinline__ E make(long long d, int id) { return {d, id}; }
+    static __device__ __forceinline__ long long dist(E e) { return e.d; }
+    static __device__ __forceinline__ int sid(E e) { return e.i; }
+    static __device__ __forceinline__ bool less(E a, E b) { return pair_less(a.d, a.i, b.d, b.i); }
+    static __device__ __forceinline__ E empty() { return {LLONG_MAX, INT_MAX}; }
+    template <int KMAX>
+    struct Storage {
+        long long d[4][KMAX][32];
+        int i[4][KMAX][32];
+    };
+    template <int KMAX>
+    struct Heap {
+        long long (*d)[32];
+        int (*i)[32];
+        __device__ __forceinline__ Heap(Storage<KMAX>& s, int warp) : d(s.d[warp]), i(s.i[warp]) {}
+        __device__ __forceinline__ E get(int p, int l) const { return {d[p][l], i[p][l]}; }
+        __device__ __forceinline__ void set(int p, int l, E e) const {
+            d[p][l] = e.d;
+            i[p][l] = e.i;
+        }
+    };
+};
+
+// Sift e down from the root of a max-heap of size m held in column `lane`.
+template <typename P, typename H>
+__device__ __forceinline__ void heap_sift_down(const H& h, int lane, int m, typename P::E e) {
     int p = 0;
     while (true) {
         int ch = 2 * p + 1;
         if (ch >= m) break;
-        long long cd = hd[ch][lane];
-        int ci = hi[ch][lane];
+        typename P::E c = h.get(ch, lane);
         if (ch + 1 < m) {
-            const long long c2 = hd[ch + 1][lane];
-            const int i2 = hi[ch + 1][lane];
-            if (pair_less(cd, ci, c2, i2)) {
+            const typename P::E c2 = h.get(ch + 1, lane);
+            if (P::less(c, c2)) {
                 ch++;
-                cd = c2;
-                ci = i2;
+                c = c2;
             }
         }
-        if (!pair_less(d, id, cd, ci)) break;
-        hd[p][lane] = cd;
-        hi[p][lane] = ci;
+        if (!P::less(e, c)) break;
+        h.set(p, lane, c);
         p = ch;
     }
-    hd[p][lane] = d;
-    hi[p][lane] = id;
+    h.set(p, lane, e);
 }
 
-template <int KMAX>
+template <int KMAX, typename P>
 __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
                                                     long long nv, const GridParams* __restrict__ gp,
                                                     const int64_t* __restrict__ start, const int4* __restrict__ sph,
                                                     const long long* __restrict__ sw, int K,
                                                     int32_t* __restrict__ knn, long long* __restrict__ dplus) {
+    typedef typename P::E E;
     const unsigned FULL = 0xffffffffu;
-    __shared__ long long hd_all[4][KMAX][32];
-    __shared__ int hi_all[4][KMAX][32];
+    __shared__ typename P::template Storage<KMAX> store;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & 3;   // quarter of the stream this lane sees
-    long long(*hd)[32] = hd_all[warp];
-    int(*hi)[32] = hi_all[warp];
+    const typename P::template Heap<KMAX> heap(store, warp);
     const long long wbase = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 8;
     if (wbase >= nv) return;   // warp-uniform
     const long long idx = wbase + (lane >> 2);
@@ -285,8 +330,7 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
     hi3.y = __reduce_max_sync(FULL, c.y);
     hi3.z = __reduce_max_sync(FULL, c.z);
     int cnt = 0;                 // size of this lane's heap
-    long long kd = LLONG_MAX;    // its root once full
-    int ki = INT_MAX;
+    E kr = P::empty();           // its root once full
     long long gmin = LLONG_MAX;  // smallest full-heap root distance in the group
     long long dp = LLONG_MAX;
     bool done = !valid;
@@ -355,7 +399,7 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
                     const long long wj = __shfl_sync(FULL, ws, jj);
                     if (done || jj >= nb) continue;
                     const long long d = pd_exact(x, cj, wj);
-                    if (d <= gmin && (cnt < K || pair_less(d, idj, kd, ki))) mark |= 1u << t;
+                    if (d <= gmin && (cnt < K || P::less(P::make(d, idj), kr))) mark |= 1u << t;
                     else dp = min(dp, d);
                 }
                 // pass 2: insert the marked spheres, one per lane per round
@@ -369,34 +413,28 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
                     const long long wj = __shfl_sync(FULL, ws, jj);
                     if (!has) continue;
                     const long long d = pd_exact(x, cj, wj);
+                    const E e = P::make(d, id);
                     if (cnt < K) {   // push and sift up
                         int p = cnt++;
                         while (p > 0) {
                             const int q = (p - 1) >> 1;
-                            const long long qd = hd[q][lane];
-                            const int qi = hi[q][lane];
-                            if (!pair_less(qd, qi, d, id)) break;
-                            hd[p][lane] = qd;
-                            hi[p][lane] = qi;
+                            const E qe = heap.get(q, lane);
+                            if (!P::less(qe, e)) break;
+                            heap.set(p, lane, qe);
                             p = q;
                         }
-                        hd[p][lane] = d;
-                        hi[p][lane] = id;
-                        if (cnt == K) {
-                            kd = hd[0][lane];
-                            ki = hi[0][lane];
-                        }
-                    } else if (pair_less(d, id, kd, ki)) {   // replace the root
-                        dp = min(dp, kd);
-                        heap_sift_down<KMAX>(hd, hi, lane, K, d, id);
-                        kd = hd[0][lane];
-                        ki = hi[0][lane];
+                        heap.set(p, lane, e);
+                        if (cnt == K) kr = heap.get(0, lane);
+                    } else if (P::less(e, kr)) {   // replace the root
+                        dp = min(dp, P::dist(kr));
+                        heap_sift_down<P>(heap, lane, K, e);
+                        kr = heap.get(0, lane);
                     } else {
                         dp = min(dp, d);
                     }
                 }
                 // group bound: smallest root among the group's full heaps
-                long long gr = cnt == K ? kd : LLONG_MAX;
+                long long gr = cnt == K ? P::dist(kr) : LLONG_MAX;
                 gr = min(gr, __shfl_xor_sync(FULL, gr, 1));
                 gr = min(gr, __shfl_xor_sync(FULL, gr, 2));
                 gmin = min(gmin, gr);
@@ -421,11 +459,9 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
     }
     // heap sort each lane's column into ascending order
     for (int n = cnt; n > 1; n--) {
-        const long long rd = hd[0][lane];
-        const int ri = hi[0][lane];
-        heap_sift_down<KMAX>(hd, hi, lane, n - 1, hd[n - 1][lane], hi[n - 1][lane]);
-        hd[n - 1][lane] = rd;
-        hi[n - 1][lane] = ri;
+        const E r = heap.get(0, lane);
+        heap_sift_down<P>(heap, lane, n - 1, heap.get(n - 1, lane));
+        heap.set(n - 1, lane, r);
     }
     __syncwarp();
     // merge the four sorted columns of each vertex: the K smallest go to the
@@ -437,22 +473,22 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
         int p0 = 0, p1 = 0, p2 = 0, p3 = 0;
         const int l0 = lane;
         for (int j = 0; j < K; j++) {
-            long long bd = LLONG_MAX;
-            int bi = INT_MAX, bc = -1;
-            if (p0 < n0 && pair_less(hd[p0][l0], hi[p0][l0], bd, bi)) { bd = hd[p0][l0]; bi = hi[p0][l0]; bc = 0; }
-            if (p1 < n1 && pair_less(hd[p1][l0 + 1], hi[p1][l0 + 1], bd, bi)) { bd = hd[p1][l0 + 1]; bi = hi[p1][l0 + 1]; bc = 1; }
-            if (p2 < n2 && pair_less(hd[p2][l0 + 2], hi[p2][l0 + 2], bd, bi)) { bd = hd[p2][l0 + 2]; bi = hi[p2][l0 + 2]; bc = 2; }
-            if (p3 < n3 && pair_less(hd[p3][l0 + 3], hi[p3][l0 + 3], bd, bi)) { bd = hd[p3][l0 + 3]; bi = hi[p3][l0 + 3]; bc = 3; }
-            knn[v * K + j] = bc < 0 ? -1 : bi;
+            E be = P::empty();
+            int bc = -1;
+            if (p0 < n0 && P::less(heap.get(p0, l0), be)) { be = heap.get(p0, l0); bc = 0; }
+            if (p1 < n1 && P::less(heap.get(p1, l0 + 1), be)) { be = heap.get(p1, l0 + 1); bc = 1; }
+            if (p2 < n2 && P::less(heap.get(p2, l0 + 2), be)) { be = heap.get(p2, l0 + 2); bc = 2; }
+            if (p3 < n3 && P::less(heap.get(p3, l0 + 3), be)) { be = heap.get(p3, l0 + 3); bc = 3; }
+            knn[v * K + j] = bc < 0 ? -1 : P::sid(be);
             p0 += bc == 0;
             p1 += bc == 1;
             p2 += bc == 2;
             p3 += bc == 3;
         }
-        if (p0 < n0) dmin = min(dmin, hd[p0][l0]);
-        if (p1 < n1) dmin = min(dmin, hd[p1][l0 + 1]);
-        if (p2 < n2) dmin = min(dmin, hd[p2][l0 + 2]);
-        if (p3 < n3) dmin = min(dmin, hd[p3][l0 + 3]);
+        if (p0 < n0) dmin = min(dmin, P::dist(heap.get(p0, l0)));
+        if (p1 < n1) dmin = min(dmin, P::dist(heap.get(p1, l0 + 1)));
+        if (p2 < n2) dmin = min(dmin, P::dist(heap.get(p2, l0 + 2)));
+        if (p3 < n3) dmin = min(dmin, P::dist(heap.get(p3, l0 + 3)));
     }
     dmin = min(dmin, __shfl_xor_sync(FULL, dmin, 1));
     dmin = min(dmin, __shfl_xor_sync(FULL, dmin, 2));
@@ -788,9 +824,9 @@ size_t knn_tmp_bytes(long long nv) {
     return 2 * al(sizeof(uint64_t) * nv) + 2 * al(sizeof(uint32_t) * nv) + radix_tmp_bytes(nv);
 }
 
-void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long long* W, const GridParams* gp,
-                const int64_t* cell_start, const int4* cell_sph, const long long* cell_w, long long ncap, int K,
-                int32_t* knn, long long* dplus, void* tmp, int* d_err, cudaStream_t s) {
+void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
+                const int4* cell_sph, const long long* cell_w, long long ncap, int K, int32_t* knn, long long* dplus,
+                void* tmp, int* d_err, bool two_word, cudaStream_t s) {
     if (nv == 0) return;
     char* p = (char*)tmp;
     uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
@@ -802,7 +838,12 @@ void launch_knn(const int32_t* Xi, long long nv, const int32_t* Ci, const long l
     k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
     note_launch();
     radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, d_err, s);
-    k_knn_group<RPD_MAXK><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
+    if (ns <= (1 << 17) && !two_word)
+        k_knn_group<RPD_MAXK, PackedEntry><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K,
+                                                                         knn, dplus);
+    else
+        k_knn_group<RPD_MAXK, PairEntry><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K,
+                                                                       knn, dplus);
     note_launch();
 }
 

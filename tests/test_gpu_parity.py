@@ -153,6 +153,19 @@ def test_forced_slow_paths_agree(block_small, force):
     _check_kinds(g, _oracle_kinds(o))
 
 
+def test_two_word_neighbour_heap_agrees(block_small):
+    """The neighbour search's two-word heap entries (used above 2^17 spheres)
+    give the same lists as the packed keys, hence identical results."""
+    w, o = block_small
+    g = collect(build_workload(w, precision="fp32", debug=4))
+    _check_pieces(w, g, o["tet"], o["sphere"], o["vol"], o["moment"])
+    _check_kinds(g, _oracle_kinds(o))
+    h = collect(build_workload(w, precision="fp32"))
+    for f in ("tet", "sphere", "vol", "moment"):
+        assert np.array_equal(g[f], h[f]), f
+    assert g["stats"]["n_pairs"] == h["stats"]["n_pairs"]
+
+
 def test_k1_uses_candidate_fallback(torus):
     w, o = torus
     g = collect(build_workload(w, k=1))
