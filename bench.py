@@ -160,7 +160,30 @@ def oracle_baseline(w, frac, seed=20240318, nthreads=None):
     dt = time.perf_counter() - t0
     return dict(value=len(o["tet"]) / dt, unit=UNIT, cores=o["nthreads"], kind="oracle",
                 sample=f"{n} of {w.nt} tets ({100 * frac:.1f}%, seed {seed}), all {w.ns} spheres, "
-                       f"brute-force C oracle; {len(o['tet'])} pieces in {dt:.2f} s"), dt
+                       f"brute-force C oracle; {len(o['tet'])} pieces in {dt:.2f} s"), (sub, o)
+
+
+def volume_error(w, pieces, sub, o):
+    """Volume and first-moment error of the GPU pieces of the sampled tets
+    against the oracle, relative to the tet's volume (moments: volume x
+    diameter, about the tet centroid)."""
+    gt, gs, gv, gm = pieces
+    keep = np.isin(gt, sub)
+    gt, gs, gv, gm = gt[keep], gs[keep], gv[keep], gm[keep]
+    if not (np.array_equal(gt, o["tet"]) and np.array_equal(gs, o["sphere"])):
+        return {"pieces_match": False}
+    q, _, _ = w.ints()
+    sc = 1.0 / float(1 << w.grid_bits)
+    P = q[w.tets[gt].astype(np.int64)].astype(np.float64) * sc
+    a, b, c = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]
+    vt = np.einsum("ij,ij->i", a, np.cross(b, c)) / 6.0
+    cen = P.mean(axis=1)
+    diam = np.max(np.linalg.norm(P[:, :, None, :] - P[:, None, :, :], axis=-1), axis=(1, 2))
+    ev = np.abs(gv - o["vol"]) / vt
+    em = np.linalg.norm((gm - gv[:, None] * cen) - (o["moment"] - o["vol"][:, None] * cen), axis=1) / (vt * diam)
+    return {"pieces_match": True, "pieces": int(len(gv)), "volume_max": float(ev.max(initial=0)),
+            "volume_median": float(np.median(ev)) if len(ev) else 0.0, "moment_max": float(em.max(initial=0)),
+            "relative_to": "tet volume (moment: tet volume x diameter)"}
 
 
 def run_reference(args, w):
@@ -207,6 +230,7 @@ def main():
     ap.add_argument("--ref-frac", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling)")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -330,9 +354,36 @@ def main():
                                   precision),
         "step_ms_max": t_step,
     }
+    # ---- the other precision, same step (SURVEY: FP32-filtered vs FP64)
+    if not args.no_compare:
+        other = "fp64" if precision == "fp32" else "fp32"
+        oms = []
+        with torch.cuda.stream(stream):
+            for it in range(args.warmup + args.steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx = rpd_build(V, T, C, R, precision=other, k=kk, grid_bits=w.grid_bits, stream=stream)
+                for kind in (1, 2, 3, 4):
+                    ctx.rpd_euler(kind), ctx.rpd_components(kind), ctx.rpd_contractible(kind)
+                e1.record(stream)
+                e1.synchronize()
+                if it >= args.warmup:
+                    oms.append(e0.elapsed_time(e1))
+                npo = ctx.rpd_stats_get()["n_pieces"]
+                ctx.rpd_destroy()
+        ovalue = npo * len(oms) / (sum(oms) / 1e3)
+        v32, v64 = (value, ovalue) if precision == "fp32" else (ovalue, value)
+        line["precision_compare"] = {"fp32": v32, "fp64": v64, "fp32_over_fp64": v32 / v64, "unit": UNIT,
+                                     "pieces_equal": bool(npo == last["n_pieces"])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, _ = oracle_baseline(w, args.cpu_frac)
+        cb, (sub, o) = oracle_baseline(w, args.cpu_frac)
         line["cpu_baseline"] = cb
+        with torch.cuda.stream(stream):
+            ctx = rpd_build(V, T, C, R, precision=precision, k=kk, grid_bits=w.grid_bits, stream=stream)
+            pieces = [x.cpu().numpy() for x in ctx.rpd_pieces()]
+            ctx.rpd_destroy()
+        line["error_vs_oracle"] = volume_error(w, pieces, sub, o)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
