@@ -101,21 +101,24 @@ class EllipsoidBlob:
         self.lo = (self.centers - rad[:, None]).min(axis=0)
         self.hi = (self.centers + rad[:, None]).max(axis=0)
 
-    def sdf(self, x, chunk: int = 1 << 16):
+    def sdf(self, x, chunk: int = 4096):
+        """Approximate signed distance; batched over all ellipsoids with torch
+        (CPU, every host core) in float64."""
+        import torch
         x = np.asarray(x, dtype=np.float64)
         shp = x.shape[:-1]
-        x = x.reshape(-1, 3)
-        out = np.empty(len(x))
-        amin = self.axes.min(axis=1)
-        for s in range(0, len(x), chunk):
-            xs = x[s:s + chunk]
-            best = np.full(len(xs), np.inf)
-            for e in range(len(self.axes)):
-                y = (xs - self.centers[e]) @ self.rot[e]
-                g = (np.linalg.norm(y / self.axes[e], axis=1) - 1.0) * amin[e]
-                np.minimum(best, g, out=best)
-            out[s:s + chunk] = best
-        return out.reshape(shp)
+        xt = torch.from_numpy(np.ascontiguousarray(x.reshape(-1, 3)))
+        c = torch.from_numpy(self.centers)                    # (E, 3)
+        r = torch.from_numpy(np.ascontiguousarray(self.rot))  # (E, 3, 3)
+        inv_a = torch.from_numpy(1.0 / self.axes)              # (E, 3)
+        amin = torch.from_numpy(self.axes.min(axis=1))         # (E,)
+        out = torch.empty(xt.shape[0], dtype=torch.float64)
+        for s in range(0, xt.shape[0], chunk):
+            d = xt[s:s + chunk][None, :, :] - c[:, None, :]      # (E, n, 3)
+            y = torch.bmm(d, r) * inv_a[:, None, :]
+            g = (torch.linalg.vector_norm(y, dim=2) - 1.0) * amin[:, None]
+            out[s:s + chunk] = g.min(dim=0).values
+        return out.numpy().reshape(shp)
 
     def medial_spheres(self, n: int, rng: np.random.Generator, eps: float = 0.01, gmax: float = 0.6):
         """Interior points where the finite-difference gradient of the depth is
