@@ -317,6 +317,7 @@ rpd_status run_clip(rpd_ctx* c) {
             a.qcap = n;
             a.qcount = c->qcount + b;
             launch_clip(a, b, c->opt.precision, c->bins + off[b], c->bin_count + b, n, sb);
+            launch_records(a, b, n, sb);
             cudaEventRecord(c->evc[1 + b], sb);
             launch_volume(a, b, c->opt.precision, n, sb);
         }
@@ -490,7 +491,6 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     a.force_slow = c->opt.debug_checks & 3;
     a.st = c->st;
     NEED(a.pflag && a.c_val && a.c_link && a.p_vol && a.p_mom && a.f_off && a.f_cnt && a.e_off && a.e_cnt);
-    launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, s);
     // finalisation buffers that do not depend on the record counts
     long long* d_nseg = c->alloc<long long>(4);
     c->piece_off = c->alloc<int64_t>(npairs + 1);
@@ -518,15 +518,18 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             TRY(finalize_alloc(c, k + 2, d_nseg + k + 1, cap[k], &ftmp[k + 1]));
         }
         if (attempt == 1) join_side_streams(c);   // everything of the first pass is done
-        record(c, 11);   // buffers allocated
-        TRY(run_clip(c));
-        // the finalisation scratch is cleared on a high-priority side stream while the clip runs
+        // the finalisation scratch is cleared on a high-priority side stream,
+        // queued before any clip block can occupy the SMs
+        record(c, 11);
         cudaStreamWaitEvent(bs->util, c->ev[11], 0);
         for (int kind = 1; kind <= 4; kind++)
             if (ftmp[kind - 1]) launch_finalize_clear(kind, fcap[kind - 1], c->ns, ftmp[kind - 1], bs->util);
         cudaEventRecord(c->ev[12], bs->util);
+        if (attempt == 0)
+            launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, s);
+        TRY(run_clip(c));
         cudaStreamWaitEvent(s, c->ev[12], 0);
-        record(c, 5);   // clip kernels done, scratch clear: the four kinds fork here
+        record(c, 5);   // clip and record kernels done, scratch clear: the four kinds fork here
         // ---- A5-A7, the four kinds side by side on high-priority streams; the
         // record counts stay on the device (grids sized by the capacities)
         for (int kind = 1; kind <= 4; kind++) {

@@ -340,6 +340,145 @@ __device__ __forceinline__ bool bit(unsigned long long m0, unsigned long long m1
     return v < 64 ? ((m0 >> v) & 1) : ((m1 >> (v - 64)) & 1);
 }
 
+// Fractional Euler records of one cut piece (Sec. 4.1.2): the RPC contribution
+// V - E + F - 1 with carrier weights and its links through tet faces, one RPF
+// record per radical face of a sphere j > i (polygon V - E + 1), one RPE
+// record per edge on two radical planes of spheres > i, one RPV record per
+// vertex on three.  All lanes call it (warp-wide reservations); inactive
+// lanes emit nothing.
+template <int VMAX, typename S>
+__device__ __forceinline__ void emit_records(const ClipArgs& A, const Lane& L, const S& V, int nslot, long long p,
+                                             bool active) {
+    const int b = A.key_bits;
+    unsigned long long fmask = 0;   // planes present as faces
+    unsigned nF = 0, nE = 0, nV = 0;
+    if (active) {
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            const int x0 = tb(tw, 0), x1 = tb(tw, 1), x2 = tb(tw, 2);
+            fmask |= (1ull << x0) | (1ull << x1) | (1ull << x2);
+            if (x0 >= 4 && x1 >= 4 && x2 >= 4 && L.cand[x0 - 4] > L.i && L.cand[x1 - 4] > L.i && L.cand[x2 - 4] > L.i)
+                nV++;
+            const int ex[3] = {x0, x1, x2}, ey[3] = {x1, x2, x0};
+#pragma unroll
+            for (int e = 0; e < 3; e++)
+                if (ex[e] < ey[e] && ex[e] >= 4 && L.cand[ex[e] - 4] > L.i && L.cand[ey[e] - 4] > L.i) nE++;
+        }
+        for (int pl = 4; pl < 4 + L.n; pl++)
+            if (((fmask >> pl) & 1) && L.cand[pl - 4] > L.i) nF++;
+    }
+    const long long fb = warp_reserve(nF, &A.rcount[0]);
+    const long long eb = warp_reserve(nE, &A.rcount[1]);
+    const long long vb = warp_reserve(nV, &A.rcount[2]);
+    if (!active) return;
+    A.f_off[p] = (int32_t)fb;
+    A.f_cnt[p] = (uint8_t)nF;
+    A.e_off[p] = (int32_t)eb;
+    A.e_cnt[p] = (uint8_t)nE;
+    const int32_t* adj = A.adj + 4 * L.t;
+    // RPC contribution V - E + F - C and links through tet faces
+    {
+        int sv = 0, se = 0, sf = 0;
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            sv += carrier_weight(tfbits(tw), L.own);
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3);
+                if (x < y) se += carrier_weight(fbits(x) | fbits(y), L.own);
+            }
+        }
+        unsigned lk = 0;
+        for (int f = 0; f < 4; f++)
+            if ((fmask >> f) & 1) {
+                sf += carrier_weight(1u << f, L.own);
+                if (adj[f] >= 0) lk |= 1u << f;
+            }
+        sf += __popcll(fmask >> 4);   // radical faces are interior (weight 1)
+        A.c_val[p] = sv - se + sf - 1;
+        A.c_link[p] = (uint8_t)lk;
+    }
+    // RPF records: walk the polygon on the radical plane of each sphere j > i
+    {
+        long long wr = fb;
+        for (int pl = 4; pl < 4 + L.n; pl++) {
+            if (!((fmask >> pl) & 1)) continue;
+            const int j = L.cand[pl - 4];
+            if (j <= L.i) continue;
+            int v0 = 0;
+            while (is_dead(V.trip(v0)) || pos_of(V.trip(v0), pl) < 0) v0++;
+            int sv = 0, se = 0, v = v0;
+            unsigned lk = 0;
+            for (int guard = 0; guard < VMAX; guard++) {
+                const uint32_t tw = V.trip(v);
+                const int kp = pos_of(tw, pl);
+                const int r = tb(tw, (kp + 2) % 3);          // edge (r -> pl) leads to the next vertex
+                sv += carrier_weight(tfbits(tw), L.own);
+                se += carrier_weight(fbits(r), L.own);
+                if (r < 4 && adj[r] >= 0) lk |= 1u << r;
+                v = tb(V.nb(v), (kp + 2) % 3);
+                if (v == v0) break;
+            }
+            if (wr < A.rcap[0]) {
+                A.rkey[0][wr] = ((unsigned long long)L.i << b) | (unsigned long long)j;
+                A.rtet[0][wr] = (int32_t)L.t;
+                A.rval[0][wr] = (int16_t)(sv - se + 1);
+                A.rlink[0][wr] = (uint8_t)lk;
+            }
+            wr++;
+        }
+    }
+    // RPE records (edges on two radical planes) and RPV records
+    {
+        long long we = eb, wv = vb;
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.trip(v);
+            if (is_dead(tw)) continue;
+            const uint32_t nw = V.nb(v);
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3), z = tb(tw, (e + 2) % 3);
+                if (!(x < y && x >= 4)) continue;
+                const int j = L.cand[x - 4], k = L.cand[y - 4];
+                if (j <= L.i || k <= L.i) continue;
+                const uint32_t tw2 = V.trip(tb(nw, e));       // other end point (holds y -> x)
+                const int tz = tb(tw2, 0) + tb(tw2, 1) + tb(tw2, 2) - x - y;
+                const int sv = carrier_weight(fbits(z), L.own) + carrier_weight(fbits(tz), L.own);
+                unsigned lk = 0;
+                if (z < 4 && adj[z] >= 0) lk |= 1u << z;
+                if (tz < 4 && adj[tz] >= 0) lk |= 1u << tz;
+                const int lo = min(j, k), hi = max(j, k);
+                if (we < A.rcap[1]) {
+                    A.rkey[1][we] = ((unsigned long long)L.i << (2 * b)) | ((unsigned long long)lo << b) |
+                                    (unsigned long long)hi;
+                    A.rtet[1][we] = (int32_t)L.t;
+                    A.rval[1][we] = (int16_t)(sv - 1);
+                    A.rlink[1][we] = (uint8_t)lk;
+                }
+                we++;
+            }
+            const int x0 = tb(tw, 0), x1 = tb(tw, 1), x2 = tb(tw, 2);
+            if (x0 >= 4 && x1 >= 4 && x2 >= 4) {
+                const int j = L.cand[x0 - 4], k = L.cand[x1 - 4], m3 = L.cand[x2 - 4];
+                if (j > L.i && k > L.i && m3 > L.i) {
+                    const int s0 = min(j, min(k, m3)), s2 = max(j, max(k, m3)), s1 = j + k + m3 - s0 - s2;
+                    if (wv < A.rcap[2] && 4 * b <= 64) {
+                        A.rkey[2][wv] = ((unsigned long long)L.i << (3 * b)) |
+                                        ((unsigned long long)s0 << (2 * b)) | ((unsigned long long)s1 << b) |
+                                        (unsigned long long)s2;
+                        A.rtet[2][wv] = (int32_t)L.t;
+                        A.rval[2][wv] = 1;
+                        A.rlink[2][wv] = 0;
+                    }
+                    wv++;
+                }
+            }
+        }
+    }
+}
+
 // ----------------------------------------------------------- clip kernel
 template <typename Real, int VMAX>
 __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __restrict__ pairs, long long q, bool active,
@@ -560,30 +699,9 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     dev_count(A.st, CNT_NEWVERT2, (nvp >> 10) & 1023u);
     dev_count(A.st, CNT_NEWVERT3, nvp >> 20);
 
-    // --------------------------------------------- fractional Euler records
-    const int b = A.key_bits;
-    unsigned long long fmask = 0;   // planes present as faces
-    unsigned nF = 0, nE = 0, nV = 0;
-    if (alive) {
-        for (int v = 0; v < nslot; v++) {
-            const uint32_t tw = V.trip(v);
-            if (is_dead(tw)) continue;
-            const int x0 = tb(tw, 0), x1 = tb(tw, 1), x2 = tb(tw, 2);
-            fmask |= (1ull << x0) | (1ull << x1) | (1ull << x2);
-            if (x0 >= 4 && x1 >= 4 && x2 >= 4 && L.cand[x0 - 4] > L.i && L.cand[x1 - 4] > L.i && L.cand[x2 - 4] > L.i)
-                nV++;
-            const int ex[3] = {x0, x1, x2}, ey[3] = {x1, x2, x0};
-#pragma unroll
-            for (int e = 0; e < 3; e++)
-                if (ex[e] < ey[e] && ex[e] >= 4 && L.cand[ex[e] - 4] > L.i && L.cand[ey[e] - 4] > L.i) nE++;
-        }
-        for (int pl = 4; pl < 4 + L.n; pl++)
-            if (((fmask >> pl) & 1) && L.cand[pl - 4] > L.i) nF++;
-    }
-    const long long fb = warp_reserve(nF, &A.rcount[0]);
-    const long long eb = warp_reserve(nE, &A.rcount[1]);
-    const long long vb = warp_reserve(nV, &A.rcount[2]);
-    // cut pieces go to the volume queue of this bin
+    // ------------------------- whole pieces here; cut pieces to the queue
+    // (their fractional Euler records are emitted by k_records, their volume
+    // by k_volume)
     const bool queued = alive && !whole;
     const long long qb = warp_reserve(queued ? 1u : 0u, A.qcount);
     if (queued && qb < A.qcap) {
@@ -594,122 +712,27 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
             A.qtrip[(2LL * v + 1) * A.qcap + qb] = V.nb(v);
         }
     }
-    if (active) {
-        A.pflag[p] = alive ? 1 : 0;
-        A.f_off[p] = (int32_t)fb;
-        A.f_cnt[p] = (uint8_t)nF;
-        A.e_off[p] = (int32_t)eb;
-        A.e_cnt[p] = (uint8_t)nE;
-    }
+    if (!active) return;
+    A.pflag[p] = alive ? 1 : 0;
     if (!alive) {
-        if (active) {
-            A.c_val[p] = 0;
-            A.c_link[p] = 0;
-            A.p_vol[p] = 0.0;
-            A.p_mom[3 * p] = A.p_mom[3 * p + 1] = A.p_mom[3 * p + 2] = 0.0;
-        }
+        A.c_val[p] = 0;
+        A.c_link[p] = 0;
+        A.f_off[p] = A.e_off[p] = 0;
+        A.f_cnt[p] = A.e_cnt[p] = 0;
+        A.p_vol[p] = 0.0;
+        A.p_mom[3 * p] = A.p_mom[3 * p + 1] = A.p_mom[3 * p + 2] = 0.0;
         return;
     }
-    const int32_t* adj = A.adj + 4 * L.t;
-    // RPC contribution V - E + F - C and links through tet faces
-    {
-        int sv = 0, se = 0, sf = 0;
-        for (int v = 0; v < nslot; v++) {
-            const uint32_t tw = V.trip(v);
-            if (is_dead(tw)) continue;
-            sv += carrier_weight(tfbits(tw), L.own);
-#pragma unroll
-            for (int e = 0; e < 3; e++) {
-                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3);
-                if (x < y) se += carrier_weight(fbits(x) | fbits(y), L.own);
-            }
-        }
+    if (!whole) return;
+    {   // the whole tet: V - E + F - 1 from the ownership bits, links on every shared face
+        const int32_t* adj = A.adj + 4 * L.t;
         unsigned lk = 0;
         for (int f = 0; f < 4; f++)
-            if ((fmask >> f) & 1) {
-                sf += carrier_weight(1u << f, L.own);
-                if (adj[f] >= 0) lk |= 1u << f;
-            }
-        sf += __popcll(fmask >> 4);   // radical faces are interior (weight 1)
-        A.c_val[p] = sv - se + sf - 1;
+            if (adj[f] >= 0) lk |= 1u << f;
+        A.c_val[p] = __popc(L.own & 0xfu) - __popc(L.own & 0x3f0u) + __popc(L.own & 0x3c00u) - 1;
         A.c_link[p] = (uint8_t)lk;
-    }
-    // RPF records: walk the polygon on the radical plane of each sphere j > i
-    {
-        long long wr = fb;
-        for (int pl = 4; pl < 4 + L.n; pl++) {
-            if (!((fmask >> pl) & 1)) continue;
-            const int j = L.cand[pl - 4];
-            if (j <= L.i) continue;
-            int v0 = 0;
-            while (is_dead(V.trip(v0)) || pos_of(V.trip(v0), pl) < 0) v0++;
-            int sv = 0, se = 0, v = v0;
-            unsigned lk = 0;
-            for (int guard = 0; guard < VMAX; guard++) {
-                const uint32_t tw = V.trip(v);
-                const int kp = pos_of(tw, pl);
-                const int r = tb(tw, (kp + 2) % 3);          // edge (r -> pl) leads to the next vertex
-                sv += carrier_weight(tfbits(tw), L.own);
-                se += carrier_weight(fbits(r), L.own);
-                if (r < 4 && adj[r] >= 0) lk |= 1u << r;
-                v = tb(V.nb(v), (kp + 2) % 3);
-                if (v == v0) break;
-            }
-            if (wr < A.rcap[0]) {
-                A.rkey[0][wr] = ((unsigned long long)L.i << b) | (unsigned long long)j;
-                A.rtet[0][wr] = (int32_t)L.t;
-                A.rval[0][wr] = (int16_t)(sv - se + 1);
-                A.rlink[0][wr] = (uint8_t)lk;
-            }
-            wr++;
-        }
-    }
-    // RPE records (edges on two radical planes) and RPV records
-    {
-        long long we = eb, wv = vb;
-        for (int v = 0; v < nslot; v++) {
-            const uint32_t tw = V.trip(v);
-            if (is_dead(tw)) continue;
-            const uint32_t nw = V.nb(v);
-#pragma unroll
-            for (int e = 0; e < 3; e++) {
-                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3), z = tb(tw, (e + 2) % 3);
-                if (!(x < y && x >= 4)) continue;
-                const int j = L.cand[x - 4], k = L.cand[y - 4];
-                if (j <= L.i || k <= L.i) continue;
-                const uint32_t tw2 = V.trip(tb(nw, e));       // other end point (holds y -> x)
-                const int tz = tb(tw2, 0) + tb(tw2, 1) + tb(tw2, 2) - x - y;
-                const int sv = carrier_weight(fbits(z), L.own) + carrier_weight(fbits(tz), L.own);
-                unsigned lk = 0;
-                if (z < 4 && adj[z] >= 0) lk |= 1u << z;
-                if (tz < 4 && adj[tz] >= 0) lk |= 1u << tz;
-                const int lo = min(j, k), hi = max(j, k);
-                if (we < A.rcap[1]) {
-                    A.rkey[1][we] = ((unsigned long long)L.i << (2 * b)) | ((unsigned long long)lo << b) |
-                                    (unsigned long long)hi;
-                    A.rtet[1][we] = (int32_t)L.t;
-                    A.rval[1][we] = (int16_t)(sv - 1);
-                    A.rlink[1][we] = (uint8_t)lk;
-                }
-                we++;
-            }
-            const int x0 = tb(tw, 0), x1 = tb(tw, 1), x2 = tb(tw, 2);
-            if (x0 >= 4 && x1 >= 4 && x2 >= 4) {
-                const int j = L.cand[x0 - 4], k = L.cand[x1 - 4], m3 = L.cand[x2 - 4];
-                if (j > L.i && k > L.i && m3 > L.i) {
-                    const int s0 = min(j, min(k, m3)), s2 = max(j, max(k, m3)), s1 = j + k + m3 - s0 - s2;
-                    if (wv < A.rcap[2] && 4 * b <= 64) {
-                        A.rkey[2][wv] = ((unsigned long long)L.i << (3 * b)) |
-                                        ((unsigned long long)s0 << (2 * b)) | ((unsigned long long)s1 << b) |
-                                        (unsigned long long)s2;
-                        A.rtet[2][wv] = (int32_t)L.t;
-                        A.rval[2][wv] = 1;
-                        A.rlink[2][wv] = 0;
-                    }
-                    wv++;
-                }
-            }
-        }
+        A.f_off[p] = A.e_off[p] = 0;
+        A.f_cnt[p] = A.e_cnt[p] = 0;
     }
     // whole tets: volume and moment in closed form; cut pieces were queued
     if (whole) {
@@ -736,6 +759,48 @@ __global__ void __launch_bounds__(128) k_clip(ClipArgs A, const int32_t* __restr
         clip_one<Real, VMAX>(A, pairs, q, q < n, V);
         __syncwarp();
     }
+}
+
+// ------------------------------------------------------ fractional Euler records
+// One lane per cut piece of a bin's queue: the piece's slot words (triplet,
+// dual neighbours) are staged in shared memory, then emit_records runs on them.
+struct QStore {
+    uint32_t* base;
+    int lane;
+    __device__ __forceinline__ uint32_t& w(int v, int k) const { return base[(v * 2 + k) * 32 + lane]; }
+    __device__ __forceinline__ uint32_t trip(int v) const { return base[(v * 2) * 32 + lane]; }
+    __device__ __forceinline__ uint32_t nb(int v) const { return base[(v * 2 + 1) * 32 + lane]; }
+};
+
+template <int VMAX>
+__global__ void __launch_bounds__(128) k_records(ClipArgs A) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const QStore V{smem + (size_t)warp * VMAX * 2 * 32, lane};
+    const long long qn = (long long)*A.qcount;
+    const long long n = qn < A.qcap ? qn : A.qcap;
+    const long long q0 = (long long)blockIdx.x * blockDim.x + warp * 32;
+    if (q0 >= n) return;   // warp-uniform
+    const long long q = q0 + lane;
+    const bool active = q < n;
+    Lane L{};
+    long long p = 0;
+    int nslot = 0;
+    if (active) {
+        p = A.qpair[q];
+        nslot = A.qnv[q];
+        L.t = A.pair_tet[p];
+        L.si = (int)(p - A.pair_off[L.t]);
+        L.n = A.cand_cnt[L.t];
+        L.cand = A.cand + L.t * RPD_MAXC;
+        L.i = L.cand[L.si];
+        L.own = A.own[L.t];
+        for (int v = 0; v < nslot; v++) {
+            V.w(v, 0) = A.qtrip[(2LL * v) * A.qcap + q];
+            V.w(v, 1) = A.qtrip[(2LL * v + 1) * A.qcap + q];
+        }
+    }
+    emit_records<VMAX>(A, L, V, nslot, p, active);
 }
 
 // ------------------------------------------------------ volume and moment
@@ -1190,6 +1255,27 @@ void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs
             case 6: launch_clip_t<double, 34, 1>(a, pairs, d_n, n, s); break;
             case 7: launch_clip_t<double, 66, 1>(a, pairs, d_n, n, s); break;
         }
+    }
+}
+
+template <int VMAX, int WARPS>
+void launch_records_t(const ClipArgs& a, long long nmax, cudaStream_t s) {
+    if (nmax <= 0) return;
+    const size_t smem = (size_t)WARPS * VMAX * 2 * 32 * sizeof(uint32_t);
+    k_records<VMAX><<<nblk(nmax, 32 * WARPS), 32 * WARPS, smem, s>>>(a);
+    note_launch();
+}
+
+void launch_records(const ClipArgs& a, int bin, long long n, cudaStream_t s) {
+    switch (bin) {
+        case 1: launch_records_t<6, 4>(a, n, s); break;
+        case 2: launch_records_t<8, 4>(a, n, s); break;
+        case 3: launch_records_t<10, 4>(a, n, s); break;
+        case 4: launch_records_t<14, 4>(a, n, s); break;
+        case 5: launch_records_t<18, 4>(a, n, s); break;
+        case 6: launch_records_t<34, 4>(a, n, s); break;
+        case 7: launch_records_t<66, 2>(a, n, s); break;
+        default: break;
     }
 }
 

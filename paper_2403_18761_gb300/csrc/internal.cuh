@@ -102,6 +102,8 @@ void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long lon
 void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s);
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,
                  cudaStream_t s);
+// Fractional Euler records of the cut pieces queued by bin `bin` (at most n).
+void launch_records(const ClipArgs& a, int bin, long long n, cudaStream_t s);
 // Volume and first moment of the cut pieces queued by bin `bin` (at most n).
 void launch_volume(const ClipArgs& a, int bin, int precision, long long n, cudaStream_t s);
 

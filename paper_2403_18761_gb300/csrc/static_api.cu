@@ -237,6 +237,7 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
             ab.qcap = nb;
             ab.qcount = qcount + bb;
             launch_clip(ab, bb, o.precision, bins + off, bin_count + bb, nb, s);
+            launch_records(ab, bb, nb, s);
             launch_volume(ab, bb, o.precision, nb, s);
         }
         off += nb;
