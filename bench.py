@@ -49,6 +49,21 @@ FP32_LANES_PER_SM = 128
 CLIP_TRAFFIC_BYTES = {("block_c2", "fp32"): 81.66e6}
 
 
+def job_throughput(local_ms, local_units, world, device="cpu"):
+    """Whole-job throughput of N replicas: the timed region is the slowest
+    rank's (max over ranks of its summed step times) and every rank processed
+    local_units (weak scaling: the same workload per rank).  Returns
+    (max time in ms, units per second over all ranks)."""
+    import torch
+    import torch.distributed as dist
+    total_ms = float(local_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return total_ms, local_units * world / (total_ms / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -296,13 +311,7 @@ def main():
     launches = rpd_launch_count() - launches0
     clocks = clk.summary()
     t_step = max(ms)
-    if world > 1:
-        tt = torch.tensor([sum(ms)], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    else:
-        total_ms = sum(ms)
-    value = pieces * world / (total_ms / 1e3)
+    total_ms, value = job_throughput(sum(ms), pieces, world, dev)
 
     # ---- end to end through the C-ABI from pinned host buffers
     hV = torch.as_tensor(w.verts, dtype=torch.float64).pin_memory()
