@@ -811,6 +811,29 @@ __global__ void __launch_bounds__(128) k_records(ClipArgs A) {
 // face's first vertex; faces are walked through the dual adjacency.
 //   vol(P) = vol(t) |sum d|,  d = det(P_R, P_v, P_v')
 //   int_P x = vol(P) X0 + vol(t) sum_c (X_c - X0) (beta_a,c |sum d| + sign * sum d (P_R+P_v+P_v')_c / 4)
+// Exact rows F_s[c] = pd(X_c, i) - pd(X_c, s) of every candidate plane of a
+// piece, built once per piece (all loads issued together) and read by the
+// vertex coordinates.  Shared memory, [slot][corner][lane].
+struct RowCache {
+    long long* base;
+    int lane;
+    __device__ __forceinline__ long long get(int slot, int c) const { return base[(slot * 4 + c) * 32 + lane]; }
+    __device__ __forceinline__ void row(int slot, long long F[4]) const {
+#pragma unroll
+        for (int c = 0; c < 4; c++) F[c] = get(slot, c);
+    }
+    __device__ __forceinline__ void fill(const Lane& L, const int32_t* __restrict__ Ci,
+                                         const long long* __restrict__ W) const {
+        for (int s2 = 0; s2 < L.n; s2++) {
+            if (s2 == L.si) continue;
+            long long F[4];
+            row_i64(L, Ci, W, s2, F);
+#pragma unroll
+            for (int c = 0; c < 4; c++) base[(s2 * 4 + c) * 32 + lane] = F[c];
+        }
+    }
+};
+
 template <typename Real>
 struct VolAcc;
 
@@ -818,7 +841,7 @@ struct VolAcc;
 template <>
 struct VolAcc<float> {
     df s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-    static __device__ __forceinline__ void beta(const Lane& L, const ClipArgs& A, int a, int b, int c, df out[3]) {
+    static __device__ __forceinline__ void beta(const Lane& L, const RowCache& RC, int a, int b, int c, df out[3]) {
         int fc[4], bis[3];
         const int m = split_planes(a, b, c, fc, bis);
         df be[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
@@ -827,14 +850,9 @@ struct VolAcc<float> {
         } else if (m == 1) {
             // on the tet edge between corners c0 and c1: the exact row entries
             // F0, F1 of the one radical plane give beta_c0 = F1 / (F1 - F0)
-            const int s = L.cand[bis[0] - 4];
-            const int3 cs = ld_int3(A.Ci, s);
-            const long long ws = A.W[s];
             const int c0 = fc[0], c1 = fc[1];
-            const int3 x0 = c0 == 0 ? L.X[0] : (c0 == 1 ? L.X[1] : (c0 == 2 ? L.X[2] : L.X[3]));
-            const int3 x1 = c1 == 0 ? L.X[0] : (c1 == 1 ? L.X[1] : (c1 == 2 ? L.X[2] : L.X[3]));
-            const long long F0 = get4(L.di, c0) - pd_exact(x0, cs, ws);
-            const long long F1 = get4(L.di, c1) - pd_exact(x1, cs, ws);
+            const long long F0 = RC.get(bis[0] - 4, c0);
+            const long long F1 = RC.get(bis[0] - 4, c1);
             const df b0 = df_div(df_from_i64(F1), df_from_i64(F1 - F0));
             set4(be, c0, b0);
             set4(be, c1, df_sub(df_make(1.0f), b0));
@@ -842,8 +860,8 @@ struct VolAcc<float> {
             // on a tet face: the cofactors of two exact rows over the three
             // free columns, in exact 128-bit integers (|entry| < 2^47)
             long long F[4], G[4];
-            row_i64(L, A.Ci, A.W, bis[0] - 4, F);
-            row_i64(L, A.Ci, A.W, bis[1] - 4, G);
+            RC.row(bis[0] - 4, F);
+            RC.row(bis[1] - 4, G);
             const long long f0 = get4(F, fc[0]), f1 = get4(F, fc[1]), f2 = get4(F, fc[2]);
             const long long g0 = get4(G, fc[0]), g1 = get4(G, fc[1]), g2 = get4(G, fc[2]);
             const __int128 k0 = (__int128)f1 * g2 - (__int128)f2 * g1;
@@ -859,7 +877,7 @@ struct VolAcc<float> {
             for (int k = 0; k < 3; k++) {
                 if (k >= m) break;
                 long long F[4];
-                row_i64(L, A.Ci, A.W, bis[k] - 4, F);
+                RC.row(bis[k] - 4, F);
                 unsigned long long mx = 0;
 #pragma unroll
                 for (int z = 0; z < 4; z++) mx = max(mx, (unsigned long long)(F[z] < 0 ? -F[z] : F[z]));
@@ -919,7 +937,7 @@ struct VolAcc<float> {
 template <>
 struct VolAcc<double> {
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    static __device__ __forceinline__ void beta(const Lane& L, const ClipArgs& A, int a, int b, int c, double out[3]) {
+    static __device__ __forceinline__ void beta(const Lane& L, const RowCache& RC, int a, int b, int c, double out[3]) {
         int fc[4], bis[3];
         const int m = split_planes(a, b, c, fc, bis);
         double be[4] = {0, 0, 0, 0};
@@ -931,7 +949,7 @@ struct VolAcc<double> {
             for (int k = 0; k < 3; k++) {
                 if (k >= m) break;
                 long long Fk[4];
-                row_i64(L, A.Ci, A.W, bis[k] - 4, Fk);
+                RC.row(bis[k] - 4, Fk);
                 scale_row<double>(Fk, Rd[k]);
             }
             cof_real<double>(m, Rd, fc, Cd);
@@ -985,11 +1003,13 @@ struct VStore {
 };
 
 template <typename Real>
-__global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax) {
+__global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) {
     typedef typename std::conditional<sizeof(Real) == 4, df, double>::type T;
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const VStore<T> V{smem + (size_t)warp * vmax * 8 * 32, lane};
+    const RowCache RC{(long long*)(smem + (size_t)nwarps * vmax * 8 * 32) + (size_t)warp * rmax * 4 * 32, lane};
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)*A.qcount;
     if (q >= n || q >= A.qcap) return;
@@ -1007,6 +1027,7 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax) {
         L.X[k] = ld_int3(A.Xi, A.tets[4 * L.t + k]);
         L.di[k] = pd_exact(L.X[k], ci, wi);
     }
+    RC.fill(L, A.Ci, A.W);
     int apex = -1;
     for (int v = 0; v < nslot; v++) {
         V.w(v, 0) = A.qtrip[(2LL * v) * A.qcap + q];
@@ -1016,14 +1037,14 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax) {
     // chart coordinates relative to the apex vertex
     T O[3];
     const uint32_t ta = V.w(apex, 0);
-    VolAcc<Real>::beta(L, A, tb(ta, 0), tb(ta, 1), tb(ta, 2), O);
+    VolAcc<Real>::beta(L, RC, tb(ta, 0), tb(ta, 1), tb(ta, 2), O);
     unsigned long long fm = 0;
     for (int v = 0; v < nslot; v++) {
         const uint32_t tw = V.w(v, 0);
         if (is_dead(tw) || v == apex) continue;
         fm |= (1ull << tb(tw, 0)) | (1ull << tb(tw, 1)) | (1ull << tb(tw, 2));
         T be[3];
-        VolAcc<Real>::beta(L, A, tb(tw, 0), tb(tw, 1), tb(tw, 2), be);
+        VolAcc<Real>::beta(L, RC, tb(tw, 0), tb(tw, 1), tb(tw, 2), be);
         for (int k = 0; k < 3; k++) {
             if constexpr (sizeof(Real) == 4) V.put(v, k, df_sub(be[k], O[k]));
             else V.put(v, k, be[k] - O[k]);
@@ -1189,15 +1210,15 @@ void launch_clip_t(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, 
 }
 
 template <typename Real>
-void launch_volume_t(const ClipArgs& a, int vmax, int warps, long long nmax, cudaStream_t s) {
+void launch_volume_t(const ClipArgs& a, int vmax, int rmax, int warps, long long nmax, cudaStream_t s) {
     if (nmax <= 0) return;
-    const size_t smem = (size_t)warps * vmax * 8 * 32 * sizeof(uint32_t);
+    const size_t smem = (size_t)warps * vmax * 8 * 32 * sizeof(uint32_t) + (size_t)warps * rmax * 4 * 32 * 8;
     static size_t configured = 0;
     if (smem > configured) {
         cudaFuncSetAttribute(k_volume<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = smem;
     }
-    k_volume<Real><<<nblk(nmax, 32 * warps), 32 * warps, smem, s>>>(a, vmax);
+    k_volume<Real><<<nblk(nmax, 32 * warps), 32 * warps, smem, s>>>(a, vmax, rmax);
     note_launch();
 }
 
@@ -1281,7 +1302,8 @@ void launch_records(const ClipArgs& a, int bin, long long n, cudaStream_t s) {
 
 void launch_volume(const ClipArgs& a, int bin, int precision, long long n, cudaStream_t s) {
     if (bin < 1) return;
+    static const int rmax[RPD_NBINS] = {1, 2, 3, 4, 6, 8, 16, 32};   // most candidates of a bin's tets
     const int vw = bin <= 5 ? 4 : (bin == 6 ? 2 : 1);
-    if (precision == RPD_FP32_FILTERED) launch_volume_t<float>(a, clip_vmax(bin), vw, n, s);
-    else launch_volume_t<double>(a, clip_vmax(bin), vw, n, s);
+    if (precision == RPD_FP32_FILTERED) launch_volume_t<float>(a, clip_vmax(bin), rmax[bin], vw, n, s);
+    else launch_volume_t<double>(a, clip_vmax(bin), rmax[bin], vw, n, s);
 }

@@ -56,19 +56,21 @@ __device__ __forceinline__ void uf_union(int32_t* parent, int a, int b, DevState
     dev_fail(st, RPD_E_TIMEOUT, CNT_UF_LIMIT);
 }
 
-// slot of sphere `sph` among the (sorted) candidates of tet t, or -1
+// Slot of sphere `sph` among the candidates of tet t, or -1.  A candidate row
+// is 32 ints (128-byte aligned): its used part is read with independent
+// 16-byte loads and searched in registers (one memory round trip).
 __device__ __forceinline__ int find_slot(const ClipArgs& A, long long t, int sph) {
-    int n = A.cand_cnt[t];
-    const int32_t* c = A.cand + t * RPD_MAXC;
-    int lo = 0, hi = n - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int v = c[mid];
-        if (v == sph) return mid;
-        if (v < sph) lo = mid + 1;
-        else hi = mid - 1;
+    const int n = A.cand_cnt[t];
+    const int4* c4 = reinterpret_cast<const int4*>(A.cand + t * RPD_MAXC);
+    int found = -1;
+    for (int k = 0; 4 * k < n; k++) {
+        const int4 v = c4[k];
+        if (v.x == sph && 4 * k < n) found = 4 * k;
+        if (v.y == sph && 4 * k + 1 < n) found = 4 * k + 1;
+        if (v.z == sph && 4 * k + 2 < n) found = 4 * k + 2;
+        if (v.w == sph && 4 * k + 3 < n) found = 4 * k + 3;
     }
-    return -1;
+    return found;
 }
 
 __global__ void k_link_cells(ClipArgs A, long long npairs, int32_t* __restrict__ parent) {
