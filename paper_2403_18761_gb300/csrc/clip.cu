@@ -853,7 +853,7 @@ struct VolAcc<float> {
             const int c0 = fc[0], c1 = fc[1];
             const long long F0 = RC.get(bis[0] - 4, c0);
             const long long F1 = RC.get(bis[0] - 4, c1);
-            const df b0 = df_div(df_from_i64(F1), df_from_i64(F1 - F0));
+            const df b0 = df_div_fast(df_from_i64(F1), df_from_i64(F1 - F0));
             set4(be, c0, b0);
             set4(be, c1, df_sub(df_make(1.0f), b0));
         } else if (m == 2) {
@@ -867,7 +867,7 @@ struct VolAcc<float> {
             const __int128 k0 = (__int128)f1 * g2 - (__int128)f2 * g1;
             const __int128 k1 = (__int128)f2 * g0 - (__int128)f0 * g2;
             const __int128 k2 = (__int128)f0 * g1 - (__int128)f1 * g0;
-            const df inv = df_div(df_make(1.0f), df_from_i128(k0 + k1 + k2));
+            const df inv = df_div_fast(df_make(1.0f), df_from_i128(k0 + k1 + k2));
             set4(be, fc[0], df_mul(df_from_i128(k0), inv));
             set4(be, fc[1], df_mul(df_from_i128(k1), inv));
             set4(be, fc[2], df_mul(df_from_i128(k2), inv));
@@ -907,7 +907,7 @@ struct VolAcc<float> {
                     C[k] = (k & 1) ? df_neg(d) : d;
                 }
             }
-            const df inv = df_div(df_make(1.0f), df_add(df_add(C[0], C[1]), df_add(C[2], C[3])));
+            const df inv = df_div_fast(df_make(1.0f), df_add(df_add(C[0], C[1]), df_add(C[2], C[3])));
 #pragma unroll
             for (int z = 1; z < 4; z++) be[z] = df_mul(C[z], inv);
         }
@@ -1039,17 +1039,38 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     const uint32_t ta = V.w(apex, 0);
     VolAcc<Real>::beta(L, RC, tb(ta, 0), tb(ta, 1), tb(ta, 2), O);
     unsigned long long fm = 0;
-    for (int v = 0; v < nslot; v++) {
-        const uint32_t tw = V.w(v, 0);
-        if (is_dead(tw) || v == apex) continue;
-        fm |= (1ull << tb(tw, 0)) | (1ull << tb(tw, 1)) | (1ull << tb(tw, 2));
+    // Coordinates by class of vertex (radical planes through it: 0-1, 2, 3):
+    // the cheap class in one pass, the others in passes of their own, so a
+    // lane on an expensive vertex holds up its warp only for that class.
+    unsigned long long h2lo = 0, h2hi = 0, h3lo = 0, h3hi = 0;   // slots of the m = 2 and m = 3 vertices
+    auto coords = [&](int v, uint32_t tw) {
         T be[3];
         VolAcc<Real>::beta(L, RC, tb(tw, 0), tb(tw, 1), tb(tw, 2), be);
         for (int k = 0; k < 3; k++) {
             if constexpr (sizeof(Real) == 4) V.put(v, k, df_sub(be[k], O[k]));
             else V.put(v, k, be[k] - O[k]);
         }
+    };
+    for (int v = 0; v < nslot; v++) {
+        const uint32_t tw = V.w(v, 0);
+        if (is_dead(tw) || v == apex) continue;
+        fm |= (1ull << tb(tw, 0)) | (1ull << tb(tw, 1)) | (1ull << tb(tw, 2));
+        const int m = (tb(tw, 0) >= 4) + (tb(tw, 1) >= 4) + (tb(tw, 2) >= 4);
+        const unsigned long long bit = 1ull << (v & 63);
+        if (m <= 1) coords(v, tw);
+        else if (m == 2) (v < 64 ? h2lo : h2hi) |= bit;
+        else (v < 64 ? h3lo : h3hi) |= bit;
     }
+    auto pass = [&](unsigned long long bits, int base) {
+        for (; bits; bits &= bits - 1) {
+            const int v = base + __ffsll((long long)bits) - 1;
+            coords(v, V.w(v, 0));
+        }
+    };
+    pass(h2lo, 0);
+    pass(h2hi, 64);
+    pass(h3lo, 0);
+    pass(h3hi, 64);
     fm &= ~((1ull << tb(ta, 0)) | (1ull << tb(ta, 1)) | (1ull << tb(ta, 2)));   // faces through the apex
     VolAcc<Real> acc;
     while (fm) {

@@ -51,6 +51,16 @@ __device__ __forceinline__ df df_div(df a, df b) {
     return fast_two_sum(q1, q2);
 }
 
+// a / b from approximate FP32 quotients (about 2^-22 each) and one exact
+// residual correction: relative error about 2^-44, the double-float level.
+// Needs |b.hi| within the normal FP32 range.
+__device__ __forceinline__ df df_div_fast(df a, df b) {
+    const float q1 = __fdividef(a.hi, b.hi);
+    const df r = df_sub(a, df_mul(df_make(q1), b));
+    const float q2 = __fdividef(r.hi, b.hi);
+    return fast_two_sum(q1, q2);
+}
+
 __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
 
 // Exact conversion of |v| < 2^48 (two exactly representable parts).
