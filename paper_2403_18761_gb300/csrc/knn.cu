@@ -185,7 +185,8 @@ __global__ void k_cell_fill(const int32_t* __restrict__ Ci, const long long* __r
 }
 
 // ---------------------------------------------------------------- kNN
-// Tiled form: eight mesh vertices per warp, four lanes per vertex.  Vertices
+// Tiled form (any number of spheres; with up to 2^17 the warp form below is
+// used unless a test asks for this one): eight mesh vertices per warp, four lanes per vertex.  Vertices
 // are processed in the order of their sphere-grid cell (a stable sort by cell
 // index), so the vertices of a warp lie in a few neighbouring cells.  The
 // warp walks box shells around the bounding box of its vertices' cells; each
@@ -227,31 +228,8 @@ __device__ __forceinline__ long long outside_box_lb2(int3 x, const GridParams& g
     return best == LLONG_MAX ? LLONG_MAX : best * best;
 }
 
-// Heap entries, ordered by (power distance, sphere id).  With ns <= 2^17 an
-// entry is one 64-bit key, (pd + 2^46) << 17 | id (|pd| < 2^46), whose integer
-// order is that order; otherwise the distance and the id are kept apart.
-struct PackedEntry {
-    typedef unsigned long long E;
-    static __device__ __forceinline__ E make(long long d, int id) {
-        return ((unsigned long long)(d + (1ll << 46)) << 17) | (unsigned)id;
-    }
-    static __device__ __forceinline__ long long dist(E e) { return (long long)(e >> 17) - (1ll << 46); }
-    static __device__ __forceinline__ int sid(E e) { return (int)(e & 0x1ffffu); }
-    static __device__ __forceinline__ bool less(E a, E b) { return a < b; }
-    static __device__ __forceinline__ E empty() { return ~0ull; }
-    template <int KMAX>
-    struct Storage {
-        E k[4][KMAX][32];
-    };
-    template <int KMAX>
-    struct Heap {   // column `lane` of one warp's heaps
-        E (*k)[32];
-        __device__ __forceinline__ Heap(Storage<KMAX>& s, int warp) : k(s.k[warp]) {}
-        __device__ __forceinline__ E get(int p, int l) const { return k[p][l]; }
-        __device__ __forceinline__ void set(int p, int l, E e) const { k[p][l] = e; }
-    };
-};
-
+// Heap entries, ordered by (power distance, sphere id), the distance and the
+// id kept apart (any number of spheres).
 struct PairEntry {
     struct E {
         long long d;
@@ -493,6 +471,154 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
     dmin = min(dmin, __shfl_xor_sync(FULL, dmin, 1));
     dmin = min(dmin, __shfl_xor_sync(FULL, dmin, 2));
     if (valid && sub == 0) dplus[v] = dmin;
+}
+
+// Warp form, for up to 2^17 spheres: one mesh vertex per warp.  A list
+// entry is one 64-bit key, (pd + 2^46) << 17 | id (|pd| < 2^46), whose
+// integer order is the (power distance, id) order.  The warp keeps the K
+// smallest keys seen so far sorted across its lanes (lane j holds the j-th,
+// lanes >= K hold nothing), walks box shells around the vertex's grid cell
+// and evaluates the spheres of each shell 32 at a time, one per lane.  A
+// chunk key enters only if it is below the K-th key; when a few enter they
+// are inserted one by one (a ballot finds the position, a shuffle shifts the
+// tail), when many enter the chunk is sorted by a bitonic network and merged
+// with the list (the elementwise minimum of the list and the reversed chunk
+// holds the 32 smallest of both as a bitonic sequence).  Everything rejected,
+// pushed out or left unexplored lowers D+.  The walk stops as in the tiled
+// form: once the distance to the next shell minus max r^2 exceeds the K-th
+// distance.
+__device__ __forceinline__ unsigned long long knn_key(long long d, int id) {
+    return ((unsigned long long)(d + (1ll << 46)) << 17) | (unsigned)id;
+}
+__device__ __forceinline__ long long knn_key_dist(unsigned long long e) { return (long long)(e >> 17) - (1ll << 46); }
+
+__global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
+                                                  long long nv, const GridParams* __restrict__ gp,
+                                                  const int64_t* __restrict__ start, const int4* __restrict__ sph,
+                                                  const long long* __restrict__ sw, int K, int32_t* __restrict__ knn,
+                                                  long long* __restrict__ dplus) {
+    typedef unsigned long long U;
+    const unsigned FULL = 0xffffffffu;
+    const U EMPTY = ~0ull;
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nv) return;   // warp-uniform
+    const long long v = vorder[w];
+    const GridParams g = *gp;
+    const int3 x = ld_int3(Xi, v);
+    const int3 c = cell_of(x, g);
+    U L = EMPTY;               // lane j: the j-th smallest key so far
+    long long dp = LLONG_MAX;  // smallest distance known to be outside the list
+    int3 plo = make_int3(1, 1, 1), phi = make_int3(0, 0, 0);   // processed box (empty)
+    long long lb2 = LLONG_MAX;
+    for (int r = 0; r < (1 << 22); r++) {
+        const int3 blo = make_int3(max(c.x - r, 0), max(c.y - r, 0), max(c.z - r, 0));
+        const int3 bhi = make_int3(min(c.x + r, g.dim.x - 1), min(c.y + r, g.dim.y - 1), min(c.z + r, g.dim.z - 1));
+        // rows (y, z) of the new shell, one per lane: the whole row outside
+        // the processed box's (y, z) range, else the parts left and right of
+        // it; their spheres are concatenated and evaluated 32 at a time
+        const int ny = bhi.y - blo.y + 1, nrow = ny * (bhi.z - blo.z + 1);
+        for (int rb = 0; rb < nrow; rb += 32) {
+            long long a0 = 0, b0 = 0;
+            int na = 0, nbb = 0;
+            if (rb + lane < nrow) {
+                const int yy = blo.y + (rb + lane) % ny, zz = blo.z + (rb + lane) / ny;
+                const int qrow = (zz * g.dim.y + yy) * g.dim.x;
+                a0 = start[qrow + blo.x];
+                if (zz >= plo.z && zz <= phi.z && yy >= plo.y && yy <= phi.y) {
+                    na = (int)(start[qrow + plo.x] - a0);
+                    b0 = start[qrow + phi.x + 1];
+                    nbb = (int)(start[qrow + bhi.x + 1] - b0);
+                } else {
+                    na = (int)(start[qrow + bhi.x + 1] - a0);
+                }
+            }
+            const int m = na + nbb;
+            int incl = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int ntot = __shfl_sync(FULL, incl, 31);
+            for (int pb = 0; pb < ntot; pb += 32) {
+                const int item = pb + lane;
+                int j = 0;   // first lane whose inclusive count exceeds item
+#pragma unroll
+                for (int step = 16; step; step >>= 1) {
+                    const int probe = __shfl_sync(FULL, incl, j + step - 1);
+                    if (probe <= item) j += step;
+                }
+                j = min(j, 31);
+                const int oj = item - __shfl_sync(FULL, incl - m, j);
+                const int naj = __shfl_sync(FULL, na, j);
+                const long long a0j = __shfl_sync(FULL, a0, j), b0j = __shfl_sync(FULL, b0, j);
+                U key = EMPTY;
+                if (item < ntot) {
+                    const long long e = oj < naj ? a0j + oj : b0j + (oj - naj);
+                    const int4 cs = sph[e];
+                    key = knn_key(pd_exact(x, make_int3(cs.x, cs.y, cs.z), sw[e]), cs.w);
+                }
+                const U tau = __shfl_sync(FULL, L, K - 1);
+                const bool pass = key < tau;
+                if (!pass && key != EMPTY) dp = min(dp, knn_key_dist(key));
+                unsigned bal = __ballot_sync(FULL, pass);
+                if (__popc(bal) <= 6) {
+                    while (bal) {   // one by one
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const U k = __shfl_sync(FULL, key, src);
+                        const int pos = __popc(__ballot_sync(FULL, L < k));
+                        if (pos >= K) {   // an earlier insertion raised the bar
+                            dp = min(dp, knn_key_dist(k));
+                            continue;
+                        }
+                        const U ev = __shfl_sync(FULL, L, K - 1);
+                        if (ev != EMPTY) dp = min(dp, knn_key_dist(ev));
+                        const U up = __shfl_up_sync(FULL, L, 1);
+                        if (lane > pos) L = up;
+                        if (lane == pos) L = k;
+                        if (lane >= K) L = EMPTY;
+                    }
+                } else {   // bitonic sort of the entering keys, then merge
+                    U s = pass ? key : EMPTY;
+#pragma unroll
+                    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                            const U o = __shfl_xor_sync(FULL, s, jj);
+                            const bool lower = (lane & jj) == 0, up = (lane & kk) == 0;
+                            s = (lower == up) ? min(s, o) : max(s, o);
+                        }
+                    }
+                    const U rv = __shfl_sync(FULL, s, 31 - lane);
+                    U lo = min(L, rv);
+                    const U hi = max(L, rv);
+                    if (hi != EMPTY) dp = min(dp, knn_key_dist(hi));
+#pragma unroll
+                    for (int jj = 16; jj > 0; jj >>= 1) {
+                        const U o = __shfl_xor_sync(FULL, lo, jj);
+                        lo = (lane & jj) ? max(lo, o) : min(lo, o);
+                    }
+                    L = lo;
+                    if (lane >= K) {
+                        if (L != EMPTY) dp = min(dp, knn_key_dist(L));
+                        L = EMPTY;
+                    }
+                }
+            }
+        }
+        plo = blo;
+        phi = bhi;
+        lb2 = outside_box_lb2(x, g, blo, bhi);   // uniform over the warp
+        const U tau = __shfl_sync(FULL, L, K - 1);
+        if (lb2 == LLONG_MAX || (tau != EMPTY && lb2 - g.wmax > knn_key_dist(tau))) break;
+    }
+    if (lb2 != LLONG_MAX) dp = min(dp, lb2 - g.wmax);   // whatever was not explored
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dp = min(dp, __shfl_xor_sync(FULL, dp, o));
+    if (lane < K) knn[v * K + lane] = L == EMPTY ? -1 : (int)(L & 0x1ffffu);
+    if (lane == 0) dplus[v] = dp;
 }
 
 // Sort key of a vertex: the index of its sphere-grid cell.
@@ -839,8 +965,7 @@ void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams*
     note_launch();
     radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, d_err, s);
     if (ns <= (1 << 17) && !two_word)
-        k_knn_group<RPD_MAXK, PackedEntry><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K,
-                                                                         knn, dplus);
+        k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
     else
         k_knn_group<RPD_MAXK, PairEntry><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K,
                                                                        knn, dplus);

@@ -142,12 +142,28 @@ __global__ void k_link_records(ClipArgs A, int which, long long nmax, int32_t* _
 __global__ void k_cell_agg(ClipArgs A, long long npairs, int32_t* __restrict__ parent, int32_t* __restrict__ cchi,
                            int32_t* __restrict__ cbeta, uint8_t* __restrict__ cpres) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npairs || A.pflag[p] != 1) return;
-    const long long t = A.pair_tet[p];
-    const int i = A.cand[t * RPD_MAXC + (p - A.pair_off[t])];
-    const bool root = parent[p] < 0;
-    atomicAdd(&cchi[i], (int)A.c_val[p]);
-    if (root) atomicAdd(&cbeta[i], 1);
+    const bool live = p < npairs && A.pflag[p] == 1;
+    int i = -1, c = 0, r = 0;
+    if (live) {
+        const long long t = A.pair_tet[p];
+        i = A.cand[t * RPD_MAXC + (p - A.pair_off[t])];
+        c = (int)A.c_val[p];
+        r = parent[p] < 0;
+    }
+    // the pairs of a warp come from a few neighbouring tets and share spheres:
+    // one atomic per distinct sphere of the warp
+    const unsigned peers = __match_any_sync(0xffffffffu, i);
+    const int leader = __ffs(peers) - 1;
+    const int lane = threadIdx.x & 31;
+    int sc = 0, sr = 0;
+    for (unsigned m = peers; m; m &= m - 1) {
+        const int k = __ffs(m) - 1;
+        sc += __shfl_sync(peers, c, k);
+        sr += __shfl_sync(peers, r, k);
+    }
+    if (!live || lane != leader) return;
+    if (sc) atomicAdd(&cchi[i], sc);
+    if (sr) atomicAdd(&cbeta[i], sr);
     cpres[i] = 1;
 }
 
