@@ -400,7 +400,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->gp = c->alloc<GridParams>(1);
     c->cell_start = c->alloc<int64_t>(ncap + 1);
     c->cell_ids = c->alloc<int32_t>(ns);
-    c->cell_wmax = c->alloc<long long>(ncap);
+    c->cell_wmax = c->alloc<long long>(2 * ncap);
     void* gtmp = c->alloc<char>(grid_tmp_bytes(ns, ncap));
     c->knn = c->alloc<int32_t>(nv * c->K);
     c->dplus = c->alloc<long long>(nv);
@@ -411,7 +411,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     NEED(cell_sph && cell_w && ktmp);
     launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
                        gtmp, s);
-    launch_knn(c->Xi, nv, ns, c->gp, c->cell_start, cell_sph, cell_w, ncap, c->K, c->knn, c->dplus, ktmp,
+    launch_knn(c->Xi, nv, ns, c->gp, c->cell_start, cell_sph, cell_w, c->cell_wmax, ncap, c->K, c->knn, c->dplus, ktmp,
                &c->st->err, (c->opt.debug_checks & 4) != 0, s);
     TRY(cuda_check(c, "knn launch"));
     record(c, 3);

@@ -30,7 +30,9 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
 // ----------------------------------------------------------------- knn.cu
 size_t grid_tmp_bytes(long long ns, long long ncap);
 // Counting sort of the spheres into grid cells: cell_start (ncap + 1
-// offsets), and per sorted slot the sphere id, (centre, id) and weight.
+// offsets), and per sorted slot the sphere id, (centre, id) and weight;
+// cell_wmax (2 ncap entries) gets the largest weight r^2 of each cell, then
+// of each row of cells along x (index z * dim.y + y).
 void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
                         int64_t* cell_start, int32_t* cell_ids, int4* cell_sph, long long* cell_w,
                         long long* cell_wmax, void* tmp, cudaStream_t s);
@@ -39,8 +41,8 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
 // tmp must hold knn_tmp_bytes(nv); ncap bounds the number of grid cells.
 size_t knn_tmp_bytes(long long nv);
 void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
-                const int4* cell_sph, const long long* cell_w, long long ncap, int K, int32_t* knn, long long* dplus,
-                void* tmp, int* d_err, bool two_word, cudaStream_t s);
+                const int4* cell_sph, const long long* cell_w, const long long* cell_wmax, long long ncap, int K,
+                int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s);
 // Candidate spheres of every tet (superset of the spheres whose cell meets
 // the tet with positive volume), sorted by index, at most RPD_MAXC.
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,

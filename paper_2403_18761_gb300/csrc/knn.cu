@@ -101,8 +101,34 @@ __device__ __forceinline__ void for_shell(const GridParams& g, int3 c, int r, F&
     }
 }
 
-__global__ void k_bbox(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns, long long ncap,
-                       GridParams* gp) {
+// Grid over the sphere centres' bounding box with about one sphere per cell
+// and at most ncap cells.
+__device__ GridParams grid_params(const int* mn, const int* mx, long long wm, long long ns, long long ncap) {
+    long long ext[3];
+    for (int a = 0; a < 3; a++) ext[a] = (long long)mx[a] - mn[a] + 1;
+    double vol = (double)ext[0] * (double)ext[1] * (double)ext[2];
+    double target = (double)(ns < 1 ? 1 : ns);
+    long long cell = (long long)ceil(cbrt(vol / target));
+    if (cell < 1) cell = 1;
+    long long d[3];
+    for (int it = 0; it < 200; it++) {
+        for (int a = 0; a < 3; a++) d[a] = (ext[a] - 1) / cell + 1;
+        if (d[0] * d[1] * d[2] <= ncap) break;
+        cell = cell + cell / 4 + 1;
+    }
+    GridParams g;
+    g.org = make_int3(mn[0], mn[1], mn[2]);
+    g.cell = (int)cell;
+    g.dim = make_int3((int)d[0], (int)d[1], (int)d[2]);
+    g.ncell = (int)(d[0] * d[1] * d[2]);
+    g.wmax = wm;
+    return g;
+}
+
+// Bounding box of the sphere centres and the largest weight, reduced over
+// the block; thread 0 returns the grid parameters in *out (shared memory).
+__device__ void block_grid_params(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns,
+                                  long long ncap, GridParams* out) {
     __shared__ int smin[3][32], smax[3][32];
     __shared__ long long swm[32];
     int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
@@ -132,31 +158,99 @@ __global__ void k_bbox(const int32_t* __restrict__ Ci, const long long* __restri
             for (int a = 0; a < 3; a++) { mn[a] = min(mn[a], smin[a][q]); mx[a] = max(mx[a], smax[a][q]); }
             wm = max(wm, swm[q]);
         }
-        long long ext[3];
-        for (int a = 0; a < 3; a++) ext[a] = (long long)mx[a] - mn[a] + 1;
-        double vol = (double)ext[0] * (double)ext[1] * (double)ext[2];
-        double target = (double)(ns < 1 ? 1 : ns);
-        long long cell = (long long)ceil(cbrt(vol / target));
-        if (cell < 1) cell = 1;
-        long long d[3];
-        for (int it = 0; it < 200; it++) {
-            for (int a = 0; a < 3; a++) d[a] = (ext[a] - 1) / cell + 1;
-            if (d[0] * d[1] * d[2] <= ncap) break;
-            cell = cell + cell / 4 + 1;
+        *out = grid_params(mn, mx, wm, ns, ncap);
+    }
+}
+
+__global__ void k_bbox(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns, long long ncap,
+                       GridParams* gp) {
+    __shared__ GridParams sg;
+    block_grid_params(Ci, W, ns, ncap, &sg);
+    if (threadIdx.x == 0) *gp = sg;
+}
+
+// The whole sphere grid in one block, for up to GRID_SMALL_CAP cells: the
+// grid parameters, per-cell counts in shared memory, their exclusive scan
+// (cell_start) and the fill, with no launches in between.
+constexpr int GRID_SMALL_CAP = 11264;   // counts within 44 KB of shared memory
+
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
         }
-        GridParams g;
-        g.org = make_int3(mn[0], mn[1], mn[2]);
-        g.cell = (int)cell;
-        g.dim = make_int3((int)d[0], (int)d[1], (int)d[2]);
-        g.ncell = (int)(d[0] * d[1] * d[2]);
-        g.wmax = wm;
-        *gp = g;
+        wsum[lane] = t;   // inclusive prefix of the warp totals
+    }
+    __syncthreads();
+    *total = wsum[nw - 1];
+    return incl - v + (w > 0 ? wsum[w - 1] : 0);
+}
+
+__global__ void __launch_bounds__(1024) k_grid_small(const int32_t* __restrict__ Ci, const long long* __restrict__ W,
+                                                     long long ns, long long ncap, GridParams* gp,
+                                                     int64_t* __restrict__ start, int32_t* __restrict__ ids,
+                                                     int4* __restrict__ sph, long long* __restrict__ sw,
+                                                     long long* __restrict__ cwmax, long long* __restrict__ rwmax) {
+    extern __shared__ int scount[];
+    __shared__ GridParams sg;
+    block_grid_params(Ci, W, ns, ncap, &sg);
+    for (long long q = threadIdx.x; q < ncap; q += blockDim.x) {
+        scount[q] = 0;
+        cwmax[q] = 0;
+        rwmax[q] = 0;
+    }
+    __syncthreads();
+    const GridParams g = sg;
+    if (threadIdx.x == 0) *gp = g;
+    for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int3 c = cell_of(ld_int3(Ci, i), g);
+        const int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
+        atomicAdd(&scount[q], 1);
+        atomicMax((unsigned long long*)&cwmax[q], (unsigned long long)W[i]);
+        atomicMax((unsigned long long*)&rwmax[c.z * g.dim.y + c.y], (unsigned long long)W[i]);
+    }
+    __syncthreads();
+    const int per = (int)((ncap + blockDim.x - 1) / blockDim.x);
+    const int lo = min((long long)threadIdx.x * per, ncap), hi = min((long long)lo + per, ncap);
+    int sum = 0;
+    for (int q = lo; q < hi; q++) sum += scount[q];
+    int total;
+    int run = block_excl_scan(sum, &total);
+    for (int q = lo; q < hi; q++) {
+        const int n = scount[q];
+        start[q] = run;
+        scount[q] = run;   // becomes the fill cursor
+        run += n;
+    }
+    if (threadIdx.x == 0) start[ncap] = total;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int3 ci = ld_int3(Ci, i);
+        const int3 c = cell_of(ci, g);
+        const int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
+        const int pos = atomicAdd(&scount[q], 1);
+        ids[pos] = (int32_t)i;
+        sph[pos] = make_int4(ci.x, ci.y, ci.z, (int)i);
+        sw[pos] = W[i];
     }
 }
 
 __global__ void k_cell_count(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns,
                              const GridParams* __restrict__ gp, int32_t* __restrict__ count,
-                             long long* __restrict__ cwmax) {
+                             long long* __restrict__ cwmax, long long* __restrict__ rwmax) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     GridParams g = *gp;
@@ -164,6 +258,7 @@ __global__ void k_cell_count(const int32_t* __restrict__ Ci, const long long* __
     int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
     atomicAdd(&count[q], 1);
     atomicMax((unsigned long long*)&cwmax[q], (unsigned long long)W[i]);
+    atomicMax((unsigned long long*)&rwmax[c.z * g.dim.y + c.y], (unsigned long long)W[i]);
 }
 
 // Cell-sorted copy of the spheres: ids, (centre, id) and weight per slot.
@@ -495,15 +590,16 @@ __device__ __forceinline__ long long knn_key_dist(unsigned long long e) { return
 __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
                                                   long long nv, const GridParams* __restrict__ gp,
                                                   const int64_t* __restrict__ start, const int4* __restrict__ sph,
-                                                  const long long* __restrict__ sw, int K, int32_t* __restrict__ knn,
-                                                  long long* __restrict__ dplus) {
+                                                  const long long* __restrict__ sw,
+                                                  const long long* __restrict__ rwmax, int K,
+                                                  int32_t* __restrict__ knn, long long* __restrict__ dplus) {
     typedef unsigned long long U;
     const unsigned FULL = 0xffffffffu;
     const U EMPTY = ~0ull;
     const int lane = threadIdx.x & 31;
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nv) return;   // warp-uniform
-    const long long v = vorder[w];
+    const long long v = vorder ? (long long)vorder[w] : w;
     const GridParams g = *gp;
     const int3 x = ld_int3(Xi, v);
     const int3 c = cell_of(x, g);
@@ -521,16 +617,34 @@ __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi
         for (int rb = 0; rb < nrow; rb += 32) {
             long long a0 = 0, b0 = 0;
             int na = 0, nbb = 0;
+            // a run whose lower bound |x - box|^2 - (max r^2 of its row)
+            // exceeds the K-th distance cannot enter; the bound goes to D+
+            const U tau = __shfl_sync(FULL, L, K - 1);
+            const long long td = tau == EMPTY ? LLONG_MAX : knn_key_dist(tau);
             if (rb + lane < nrow) {
                 const int yy = blo.y + (rb + lane) % ny, zz = blo.z + (rb + lane) / ny;
                 const int qrow = (zz * g.dim.y + yy) * g.dim.x;
+                const long long gy = axis_gap(x.y, g.org.y, yy, g.cell), gz = axis_gap(x.z, g.org.z, zz, g.cell);
+                const long long base = gy * gy + gz * gz - rwmax[zz * g.dim.y + yy];
+                // spheres of cells q0..q1 of the row, or 0 when the run is culled
+                auto run = [&](int q0, int q1, long long first) -> int {
+                    const int n = (int)(start[qrow + q1 + 1] - first);
+                    if (n == 0) return 0;
+                    const long long lo = (long long)g.org.x + (long long)q0 * g.cell;
+                    const long long hi = (long long)g.org.x + (long long)(q1 + 1) * g.cell - 1;
+                    const long long gx = x.x < lo ? lo - x.x : (x.x > hi ? x.x - hi : 0);
+                    const long long lb = base + gx * gx;
+                    if (lb <= td) return n;
+                    dp = min(dp, lb);
+                    return 0;
+                };
                 a0 = start[qrow + blo.x];
                 if (zz >= plo.z && zz <= phi.z && yy >= plo.y && yy <= phi.y) {
-                    na = (int)(start[qrow + plo.x] - a0);
+                    if (blo.x < plo.x) na = run(blo.x, plo.x - 1, a0);
                     b0 = start[qrow + phi.x + 1];
-                    nbb = (int)(start[qrow + bhi.x + 1] - b0);
+                    if (phi.x < bhi.x) nbb = run(phi.x + 1, bhi.x, b0);
                 } else {
-                    na = (int)(start[qrow + bhi.x + 1] - a0);
+                    na = run(blo.x, bhi.x, a0);
                 }
             }
             const int m = na + nbb;
@@ -720,29 +834,32 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
         o[a] = knn[(long long)v[a] * K];
         dp[a] = dplus[v[a]];
     }
-    // M(a, b) = pd(X_a, owner of corner b), one entry per lane 0..15
+    // M(a, b) = pd(X_a, owner of corner b), one entry per lane 0..15.  Lane
+    // (a, b) also holds whether corner a's list is complete up to M(a, b) and
+    // M(a, b) - M(a, a); the lanes of one b then combine over a.
     long long Ml = 0;
-    if (lane < 16) {
-        const int a = lane >> 2, b = lane & 3;
+    bool comp = true;
+    long long score = 0;
+    {
+        const int a = (lane >> 2) & 3, b = lane & 3;
         const int ob = b == 0 ? o[0] : (b == 1 ? o[1] : (b == 2 ? o[2] : o[3]));
         const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
-        Ml = pd_exact(xa, ld_int3(Ci, ob), W[ob]);
+        const long long dpa = a == 0 ? dp[0] : (a == 1 ? dp[1] : (a == 2 ? dp[2] : dp[3]));
+        if (lane < 16) Ml = pd_exact(xa, ld_int3(Ci, ob), W[ob]);
+        const long long maa = __shfl_sync(0xffffffffu, Ml, a * 5);
+        comp = dpa > Ml;
+        score = Ml - maa;
     }
+    score = max(score, __shfl_xor_sync(0xffffffffu, score, 4));
+    score = max(score, __shfl_xor_sync(0xffffffffu, score, 8));
+    const unsigned cbits = __ballot_sync(0xffffffffu, comp);
     int bstar = -1;
     long long best = LLONG_MAX;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
-        bool complete = true;
-        long long score = 0;
-#pragma unroll
-        for (int a = 0; a < 4; a++) {
-            const long long mab = __shfl_sync(0xffffffffu, Ml, a * 4 + b);
-            const long long maa = __shfl_sync(0xffffffffu, Ml, a * 4 + a);
-            complete &= dp[a] > mab;
-            score = max(score, mab - maa);
-        }
-        if (complete && score < best) {
-            best = score;
+        const long long sb = __shfl_sync(0xffffffffu, score, b);
+        if (((cbits >> b) & 0x1111u) == 0x1111u && sb < best) {
+            best = sb;
             bstar = b;
         }
     }
@@ -811,21 +928,33 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
 #pragma unroll
         for (int c = 0; c < 4; c++) D[c] = pd_exact(X[c], cs, ws);
     }
-    // exact corner filter against every other gathered sphere
+    // exact corner filter against every other gathered sphere; the corner
+    // distances of the warp's spheres are read back from shared memory
+    // (broadcast loads)
+    struct alignas(32) D4 {
+        long long x, y, z, w;
+    };
+    __shared__ D4 sD[8][32];
+    __shared__ long long sKey[8][32];
+    __shared__ int sSid[8][32];
+    const int wib = threadIdx.x >> 5;
+    const long long key = D[0] + D[1] + D[2] + D[3];
+    sD[wib][lane] = D4{D[0], D[1], D[2], D[3]};
+    sKey[wib][lane] = key;
+    sSid[wib][lane] = sid;
+    __syncwarp();
     bool ok = held;
     for (int j = 0; j < nheld; j++) {
-        bool some = false;
-#pragma unroll
-        for (int c = 0; c < 4; c++) some |= D[c] <= __shfl_sync(0xffffffffu, D[c], j);
+        const D4 dj = sD[wib][j];
+        const bool some = D[0] <= dj.x || D[1] <= dj.y || D[2] <= dj.z || D[3] <= dj.w;
         if (j != lane) ok = ok && some;
     }
     const unsigned kmask = __ballot_sync(0xffffffffu, ok);
-    const long long key = D[0] + D[1] + D[2] + D[3];
     int rank = 0, rank2 = 0;
     for (unsigned m = kmask; m; m &= m - 1) {
         const int j = __ffs(m) - 1;
-        const int sj = __shfl_sync(0xffffffffu, sid, j);
-        const long long kj = __shfl_sync(0xffffffffu, key, j);
+        const int sj = sSid[wib][j];
+        const long long kj = sKey[wib][j];
         rank += sj < sid;
         rank2 += (kj < key) || (kj == key && sj < sid);
     }
@@ -930,6 +1059,12 @@ size_t grid_tmp_bytes(long long ns, long long ncap) {
 void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
                         int64_t* cell_start, int32_t* cell_ids, int4* cell_sph, long long* cell_w,
                         long long* cell_wmax, void* tmp, cudaStream_t s) {
+    if (ncap <= GRID_SMALL_CAP) {
+        k_grid_small<<<1, 1024, sizeof(int) * ncap, s>>>(Ci, W, ns, ncap, gp, cell_start, cell_ids, cell_sph, cell_w,
+                                                         cell_wmax, cell_wmax + ncap);
+        note_launch();
+        return;
+    }
     char* p = (char*)tmp;
     int32_t* count = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
     int32_t* fill = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
@@ -938,8 +1073,8 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
     note_launch();
     cudaMemsetAsync(count, 0, sizeof(int32_t) * ncap, s);
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncap, s);
-    cudaMemsetAsync(cell_wmax, 0, sizeof(long long) * ncap, s);
-    k_cell_count<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, count, cell_wmax);
+    cudaMemsetAsync(cell_wmax, 0, sizeof(long long) * 2 * ncap, s);
+    k_cell_count<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, count, cell_wmax, cell_wmax + ncap);
     note_launch();
     scan_excl(count, cell_start, ncap, stmp, s);
     k_cell_fill<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, cell_start, fill, cell_ids, cell_sph, cell_w);
@@ -951,8 +1086,8 @@ size_t knn_tmp_bytes(long long nv) {
 }
 
 void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
-                const int4* cell_sph, const long long* cell_w, long long ncap, int K, int32_t* knn, long long* dplus,
-                void* tmp, int* d_err, bool two_word, cudaStream_t s) {
+                const int4* cell_sph, const long long* cell_w, const long long* cell_wmax, long long ncap, int K,
+                int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s) {
     if (nv == 0) return;
     char* p = (char*)tmp;
     uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
@@ -961,14 +1096,17 @@ void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams*
     uint32_t* v1 = (uint32_t*)p; p += al(sizeof(uint32_t) * nv);
     int bits = 1;
     while ((1ll << bits) < ncap) bits++;
-    k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
-    note_launch();
-    radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, d_err, s);
-    if (ns <= (1 << 17) && !two_word)
-        k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K, knn, dplus);
-    else
+    if (ns <= (1 << 17) && !two_word) {
+        // one vertex per warp in input order: the sphere grid stays in cache
+        k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nullptr, nv, gp, cell_start, cell_sph, cell_w,
+                                                       cell_wmax + ncap, K, knn, dplus);
+    } else {
+        k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
+        note_launch();
+        radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, d_err, s);
         k_knn_group<RPD_MAXK, PairEntry><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K,
                                                                        knn, dplus);
+    }
     note_launch();
 }
 

@@ -141,7 +141,7 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
     int32_t* cell_ids = ar.take<int32_t>(ns);
     int4* cell_sph = ar.take<int4>(ns);
     long long* cell_w = ar.take<long long>(ns);
-    long long* cell_wmax = ar.take<long long>(ncap);
+    long long* cell_wmax = ar.take<long long>(2 * ncap);
     void* gtmp = ar.take<char>(grid_tmp_bytes(ns, ncap));
     int32_t* knn = ar.take<int32_t>(nv * K);
     long long* dplus = ar.take<long long>(nv);
@@ -161,7 +161,7 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
     launch_snap(d_verts, nv, d_centers, d_radii, ns, o.grid_bits, Xi, Ci, W, st, s);
     launch_prep_mesh(tets, nt, nv, Xi, adj, own, ptmp, st, s);
     launch_sphere_grid(Ci, W, ns, ncap, gp, cell_start, cell_ids, cell_sph, cell_w, cell_wmax, gtmp, s);
-    launch_knn(Xi, nv, ns, gp, cell_start, cell_sph, cell_w, ncap, K, knn, dplus, ktmp, &st->err,
+    launch_knn(Xi, nv, ns, gp, cell_start, cell_sph, cell_w, cell_wmax, ncap, K, knn, dplus, ktmp, &st->err,
                (o.debug_checks & 4) != 0, s);
     launch_candidates(tets, nt, nv, Xi, Ci, W, knn, dplus, K, gp, cell_start, cell_ids, cell_wmax, cand_cnt, cand,
                       cand_ord, fb_list, fb_count, st, s);

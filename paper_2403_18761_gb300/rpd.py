@@ -108,8 +108,16 @@ def _ptr(t):
 
 
 def _dev_f64(x, dev):
+    if isinstance(x, torch.Tensor) and x.dtype == torch.float64 and x.device == dev and x.is_contiguous():
+        return x
     t = torch.as_tensor(x, dtype=torch.float64)
     return t.to(dev).contiguous()
+
+
+def _dev_i32(x, dev):
+    if isinstance(x, torch.Tensor) and x.dtype == torch.int32 and x.device == dev and x.is_contiguous():
+        return x
+    return torch.as_tensor(x, dtype=torch.int32).to(dev).contiguous()
 
 
 def _stream_handle(stream):
@@ -126,7 +134,9 @@ class Ctx:
         self.stream = stream
         self.device = device
         self._keep = keep
-        self._nkeys = list(self.rpd_stats_get()["n_keys"])   # element counts per kind (fixed after the build)
+        st = rpd_stats()   # element counts per kind (fixed after the build)
+        self._check(load().rpd_stats_get(self.handle, ctypes.byref(st)))
+        self._nkeys = list(st.n_keys)
 
     def _check(self, st):
         if st != RPD_OK:
@@ -197,8 +207,10 @@ def rpd_build(verts, tets, centers, radii, precision="fp32", k=16, grid_bits=20,
         raise RuntimeError("librpd needs a CUDA device; there is no CPU fallback")
     lib = load()
     dev = torch.device(device)
+    if dev.index is None:
+        dev = torch.device(dev.type, torch.cuda.current_device())
     V = _dev_f64(verts, dev)
-    T = torch.as_tensor(tets, dtype=torch.int32).to(dev).contiguous()
+    T = _dev_i32(tets, dev)
     C = _dev_f64(centers, dev)
     R = _dev_f64(radii, dev)
     opt = rpd_options()
