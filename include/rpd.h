@@ -133,6 +133,16 @@ rpd_status rpd_components(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, int32_t*
 rpd_status rpd_contractible(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, uint8_t* d_flag, int64_t cap,
                             int64_t* n);
 
+/* Every element table of rpd_euler, rpd_components and rpd_contractible, for
+ * all four kinds, in one launch into one caller-owned device buffer (for
+ * bindings that serve many queries).  Layout, in bytes from d_out, every part
+ * starting on a multiple of 16 bytes: for kind = 1..4 in order, keys
+ * i32[n_k*kind], chi i32[n_k], beta0 i32[n_k]; then for kind = 1..4, flag
+ * u8[n_k]; n_k = rpd_stats.n_keys[kind-1].  Two-phase: with d_out == NULL
+ * only *bytes is set; otherwise cap_bytes >= *bytes and a 16-byte aligned
+ * d_out are required (RPD_E_INVALID).  Written on the build's stream. */
+rpd_status rpd_export(rpd_ctx* ctx, void* d_out, int64_t cap_bytes, int64_t* bytes);
+
 /* Nonempty pieces P(t,i) = t cap cell_i (Tet-Cell, Sec. 5.2) sorted by (t, i):
  * d_tet i32[n], d_sphere i32[n], d_vol f64[n], d_moment3 f64[n*3] (integral
  * of x over the piece).  Any output pointer may be NULL.  Same two-phase

@@ -1,6 +1,7 @@
 // C-ABI of librpd: context lifecycle, orchestration of the stages, outputs.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -690,6 +691,35 @@ rpd_status rpd_contractible(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, uint8_
     if (!ctx) return RPD_E_INVALID;
     TRY(check_kind(ctx, kind));
     return copy_rows(ctx, kind, d_keys, ctx->fout[kind - 1].flag, d_flag, sizeof(uint8_t), cap, n);
+}
+
+rpd_status rpd_export(rpd_ctx* ctx, void* d_out, int64_t cap_bytes, int64_t* bytes) {
+    if (!ctx) return RPD_E_INVALID;
+    ExportArgs a{};
+    const auto al16 = [](long long x) { return (x + 15) & ~15ll; };
+    long long off = 0;
+    char* base = (char*)d_out;
+    for (int k = 1; k <= 4; k++) {
+        const long long m = ctx->nkeys[k - 1];
+        const FinalOut& o = ctx->fout[k - 1];
+        const void* src[3] = {o.keys, o.chi, o.beta};
+        const long long n[3] = {m * k, m, m};
+        for (int j = 0; j < 3; j++) {
+            if (n[j] > 0) a.seg[a.nseg++] = ExportSeg{src[j], base + off, n[j], 4};
+            off = al16(off + 4 * n[j]);
+        }
+    }
+    for (int k = 1; k <= 4; k++) {
+        const long long m = ctx->nkeys[k - 1];
+        if (m > 0) a.seg[a.nseg++] = ExportSeg{ctx->fout[k - 1].flag, base + off, m, 1};
+        off = al16(off + m);
+    }
+    if (bytes) *bytes = off;
+    if (!d_out) return RPD_OK;
+    if (cap_bytes < off) return fail(ctx, RPD_E_INVALID, "cap_bytes is smaller than the export size");
+    if (((uintptr_t)d_out & 15) != 0) return fail(ctx, RPD_E_INVALID, "d_out must be 16-byte aligned");
+    launch_export(a, ctx->stream);
+    return cuda_check(ctx, "export launch");
 }
 
 rpd_status rpd_pieces(rpd_ctx* ctx, int32_t* d_tet, int32_t* d_sphere, double* d_vol, double* d_moment3, int64_t cap,

@@ -133,5 +133,18 @@ void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, l
 // bytes; a NULL source skips that part.
 void launch_copy_rows(const int32_t* keys, int32_t* d_keys, long long n_keys, const void* vals, void* d_vals,
                       long long n, int elem, cudaStream_t s);
+// One launch copying up to 16 segments (n elements of elem = 1 or 4 bytes
+// each, source to destination).
+struct ExportSeg {
+    const void* src;
+    void* dst;
+    long long n;
+    int elem;
+};
+struct ExportArgs {
+    ExportSeg seg[16];
+    int nseg;
+};
+void launch_export(const ExportArgs& a, cudaStream_t s);
 void launch_compact_pieces(const ClipArgs& a, long long npairs, const int64_t* off, int32_t* d_tet,
                            int32_t* d_sphere, double* d_vol, double* d_mom, cudaStream_t s);

@@ -272,6 +272,16 @@ __global__ void k_copy_rows(const int32_t* __restrict__ keys, int32_t* __restric
     }
 }
 
+// blockIdx.y selects the segment
+__global__ void k_export(ExportArgs a) {
+    const ExportSeg g = a.seg[blockIdx.y];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += stride) {
+        if (g.elem == 4) ((int32_t*)g.dst)[i] = ((const int32_t*)g.src)[i];
+        else ((uint8_t*)g.dst)[i] = ((const uint8_t*)g.src)[i];
+    }
+}
+
 __global__ void k_compact_pieces(ClipArgs A, long long npairs, const int64_t* __restrict__ off, int32_t* d_tet,
                                  int32_t* d_sphere, double* d_vol, double* d_mom) {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -415,6 +425,15 @@ void launch_copy_rows(const int32_t* keys, int32_t* d_keys, long long n_keys, co
     if (total <= 0 || (!keys && !vals)) return;
     const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 16);
     k_copy_rows<<<blocks, 256, 0, s>>>(keys, d_keys, n_keys, vals, d_vals, n, elem);
+    note_launch();
+}
+
+void launch_export(const ExportArgs& a, cudaStream_t s) {
+    long long nmax = 0;
+    for (int i = 0; i < a.nseg; i++) nmax = std::max(nmax, a.seg[i].n);
+    if (a.nseg == 0 || nmax == 0) return;
+    const unsigned bx = (unsigned)std::min<long long>((nmax + 255) / 256, 152LL * 4);
+    k_export<<<dim3(bx, (unsigned)a.nseg), 256, 0, s>>>(a);
     note_launch();
 }
 

@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = [P, ctypes.c_int, P, P, I64, ctypes.POINTER(I64)]
         f.restype = ctypes.c_int
+    lib.rpd_export.argtypes = [P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_export.restype = ctypes.c_int
     lib.rpd_pieces.argtypes = [P, P, P, P, P, I64, ctypes.POINTER(I64)]
     lib.rpd_pieces.restype = ctypes.c_int
     lib.rpd_stats_get.argtypes = [P, ctypes.POINTER(rpd_stats)]
@@ -134,6 +136,7 @@ class Ctx:
         self.stream = stream
         self.device = device
         self._keep = keep
+        self._tabs = None
         st = rpd_stats()   # element counts per kind (fixed after the build)
         self._check(load().rpd_stats_get(self.handle, ctypes.byref(st)))
         self._nkeys = list(st.n_keys)
@@ -149,25 +152,84 @@ class Ctx:
         self._check(fn(self.handle, kind, None, None, 0, ctypes.byref(n)))
         return n.value
 
-    def _rows(self, fn, kind, vdtype):
-        """Keys int32[n, kind] and one value per key, in fresh device tensors."""
+    def rows_direct(self, name, kind):
+        """Keys int32[n, kind] and one value per key in fresh device tensors,
+        through the per-kind C entry point `name` (rpd_euler, rpd_components
+        or rpd_contractible)."""
+        fn = getattr(load(), name)
         n = self._query(fn, kind)
         keys = torch.empty((n, kind), dtype=torch.int32, device=self.device)
-        vals = torch.empty(n, dtype=vdtype, device=self.device)
+        vals = torch.empty(n, dtype=torch.uint8 if name == "rpd_contractible" else torch.int32, device=self.device)
         self._check(fn(self.handle, kind, keys.data_ptr(), vals.data_ptr(), n, None))
         return keys, vals
 
+    def _export_all(self):
+        """All element tables through one rpd_export call, as views of one
+        device buffer: {kind: [keys, chi, beta0, flag]}, or the RpdError the
+        per-kind entry points report for that kind."""
+        lib = load()
+        tabs, n = {}, ctypes.c_int64(0)
+        for kind in (1, 2, 3, 4):
+            st = lib.rpd_euler(self.handle, kind, None, None, 0, ctypes.byref(n))
+            if st != RPD_OK:
+                tabs[kind] = RpdError(st, lib.rpd_last_error(self.handle).decode())
+        nb = ctypes.c_int64(0)
+        self._check(lib.rpd_export(self.handle, None, 0, ctypes.byref(nb)))
+        buf = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=self.device)
+        self._check(lib.rpd_export(self.handle, buf.data_ptr(), nb.value, None))
+        # the layout documented with rpd_export: int32 parts (each padded to
+        # 16 bytes) for kinds 1..4, then the uint8 flags; split in one call
+        # per region
+        al = lambda x: (x + 15) & ~15
+        sizes, off = [], 0
+        for kind in (1, 2, 3, 4):
+            m = self._nkeys[kind - 1]
+            for cnt in (m * kind, m, m):
+                sizes += [cnt, al(4 * cnt) // 4 - cnt]
+                off += al(4 * cnt)
+        foff = off
+        fsizes = []
+        for kind in (1, 2, 3, 4):
+            m = self._nkeys[kind - 1]
+            fsizes += [m, al(m) - m]
+            off += al(m)
+        parts = buf[:foff].view(torch.int32).split(sizes)
+        flags = buf[foff:off].split(fsizes)
+        for kind in (1, 2, 3, 4):
+            if kind not in tabs:
+                j = 6 * (kind - 1)
+                tabs[kind] = [parts[j].view(-1, kind), parts[j + 2], parts[j + 4], flags[2 * (kind - 1)]]
+        if off != nb.value:
+            raise RuntimeError("rpd_export layout mismatch")
+        return tabs
+
+    def _table(self, kind):
+        if not 1 <= kind <= 4:
+            self._query(load().rpd_euler, kind)   # the C entry point reports it
+        if self._tabs is None:
+            self._tabs = self._export_all()
+        t = self._tabs[kind]
+        if isinstance(t, RpdError):
+            raise t
+        return t
+
+    # The three queries return views of one buffer filled by rpd_export (the
+    # keys tensor of a kind is shared by the three); rows_direct goes through
+    # the per-kind entry points instead.
     def rpd_euler(self, kind):
         """(keys int32[n, kind], chi int32[n]) on the device."""
-        return self._rows(load().rpd_euler, kind, torch.int32)
+        t = self._table(kind)
+        return t[0], t[1]
 
     def rpd_components(self, kind):
         """(keys int32[n, kind], beta0 int32[n]) on the device."""
-        return self._rows(load().rpd_components, kind, torch.int32)
+        t = self._table(kind)
+        return t[0], t[2]
 
     def rpd_contractible(self, kind):
         """(keys int32[n, kind], flag uint8[n]) on the device."""
-        return self._rows(load().rpd_contractible, kind, torch.uint8)
+        t = self._table(kind)
+        return t[0], t[3]
 
     def rpd_pieces(self):
         """(tet int32[n], sphere int32[n], vol f64[n], moment f64[n,3]) sorted by (tet, sphere)."""

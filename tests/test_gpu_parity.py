@@ -154,8 +154,9 @@ def test_forced_slow_paths_agree(block_small, force):
 
 
 def test_two_word_neighbour_heap_agrees(block_small):
-    """The neighbour search's two-word heap entries (used above 2^17 spheres)
-    give the same lists as the packed keys, hence identical results."""
+    """The tiled neighbour search with two-word heap entries (the form used
+    above 2^17 spheres) gives the same lists as the warp form with packed
+    keys, hence identical results."""
     w, o = block_small
     g = collect(build_workload(w, precision="fp32", debug=4))
     _check_pieces(w, g, o["tet"], o["sphere"], o["vol"], o["moment"])
@@ -164,6 +165,23 @@ def test_two_word_neighbour_heap_agrees(block_small):
     for f in ("tet", "sphere", "vol", "moment"):
         assert np.array_equal(g[f], h[f]), f
     assert g["stats"]["n_pairs"] == h["stats"]["n_pairs"]
+
+
+def test_export_views_match_per_kind_entry_points(block_small):
+    """The binding's queries (views of one rpd_export buffer) hold exactly
+    what rpd_euler / rpd_components / rpd_contractible copy out one by one."""
+    w, _ = block_small
+    ctx = build_workload(w, precision="fp32")
+    for kind in (1, 2, 3, 4):
+        for name, view in (("rpd_euler", ctx.rpd_euler), ("rpd_components", ctx.rpd_components),
+                           ("rpd_contractible", ctx.rpd_contractible)):
+            k1, v1 = view(kind)
+            k2, v2 = ctx.rows_direct(name, kind)
+            assert k1.shape == k2.shape and k1.shape[0] > 0
+            assert torch.equal(k1, k2) and torch.equal(v1, v2) and v1.dtype == v2.dtype, (name, kind)
+    with pytest.raises(RpdError) as e:
+        ctx.rpd_euler(5)
+    assert e.value.status == RPD_E_INVALID
 
 
 def test_k1_uses_candidate_fallback(torus):
