@@ -320,17 +320,15 @@ rpd_status run_clip(rpd_ctx* c) {
             launch_clip(a, b, c->opt.precision, c->bins + off[b], c->bin_count + b, n, sb);
             launch_records(a, b, n, sb);
             cudaEventRecord(c->evc[1 + b], sb);
-            launch_volume(a, b, c->opt.precision, n, sb);
         }
-        cudaEventRecord(c->evc[1 + RPD_NBINS + b], sb);
         // the records (what the finalisation reads) are complete once the
-        // clip kernel is; the volume pass joins at the end of the build
+        // record kernel is; the bin's volume pass is launched with the
+        // finalisation and joins at the end of the build
         cudaStreamWaitEvent(s, c->evc[1 + b], 0);
     }
     return cuda_check(c, "clip launch");
 }
 
-// Output and workspace buffers of one kind's finalisation.
 // Output and scratch buffers of one kind's finalisation, for up to ncap
 // pieces (kind 1) or records.
 rpd_status finalize_alloc(rpd_ctx* c, int kind, long long* d_count, long long ncap, void** tmp) {
@@ -543,6 +541,23 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
                 cudaMemsetAsync(d_nseg + kind - 1, 0, sizeof(long long), sk);
             }
             cudaEventRecord(c->ev[6 + kind - 1], sk);
+        }
+        // the volume passes start with the finalisation (high-priority
+        // streams first), so they do not compete with the clip kernels
+        for (int b = RPD_NBINS - 1; b >= 0; b--) {
+            if (c->hbin[b] == 0) continue;
+            cudaStream_t sb = bs->s[b];
+            if (b > 0) {
+                cudaStreamWaitEvent(sb, c->ev[5], 0);
+                ClipArgs va = c->clip;
+                va.qpair = c->qpair[b];
+                va.qnv = c->qnv[b];
+                va.qtrip = c->qtrip[b];
+                va.qcap = c->hbin[b];
+                va.qcount = c->qcount + b;
+                launch_volume(va, b, c->opt.precision, c->hbin[b], sb);
+            }
+            cudaEventRecord(c->evc[1 + RPD_NBINS + b], sb);
         }
         scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
         TRY(cuda_check(c, "finalize launch"));
