@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of the clip kernels of one step (k_clip over all
 # bins + k_whole) on block_c2, from one ncu capture of the current kernels
 # (profiles/clip_block_c2.md); None once the kernels change.
-CLIP_TRAFFIC_BYTES = {("block_c2", "fp32"): 81.66e6}
+CLIP_TRAFFIC_BYTES = {("block_c2", "fp32"): 67.86e6}
 
 
 def job_throughput(local_ms, local_units, world, device="cpu"):
