@@ -291,10 +291,14 @@ void join_side_streams(rpd_ctx* c) {
         if (e) cudaStreamWaitEvent(c->stream, e, 0);
 }
 
-rpd_status run_clip(rpd_ctx* c) {
+// zero_counts: the record and queue counters are zeroed here (the binning
+// zeroes them before the first pass).
+rpd_status run_clip(rpd_ctx* c, bool zero_counts) {
     cudaStream_t s = c->stream;
-    cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
-    cudaMemsetAsync(c->qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
+    if (zero_counts) {
+        cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
+        cudaMemsetAsync(c->qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
+    }
     long long off[RPD_NBINS + 1];
     off[0] = 0;
     for (int b = 0; b < RPD_NBINS; b++) off[b + 1] = off[b] + c->hbin[b];
@@ -432,6 +436,16 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     launch_bin_count(c->cand_cnt, nt, c->bin_count, s);
     TRY(cuda_check(c, "candidate launch"));
     record(c, 4);
+    // the pairs are put in bin order before the pair count is read, with room
+    // for 4 pairs per tet (binned again below if there are more)
+    const long long pcap = 4 * nt + 1024;
+    c->pair_tet = c->alloc<int32_t>(pcap);
+    c->bins = c->alloc<int32_t>(pcap);
+    c->rcount = c->alloc<unsigned long long>(3);
+    c->qcount = c->alloc<unsigned long long>(RPD_NBINS);
+    NEED(c->pair_tet && c->bins && c->rcount && c->qcount);
+    launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, pcap, c->rcount,
+                     c->qcount, s);
     cudaStreamWaitEvent(s, c->ev[2], 0);   // mesh combinatorics done
     long long npairs = 0;
     int32_t hb[RPD_NBINS];
@@ -450,11 +464,13 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         for (int k = 0; k < 3; k++) est += finalize_tmp_bytes(k + 2, cap0[k], ns) + (size_t)cap0[k] * 40;
         NEED(c->reserve(est));
     }
-    c->pair_tet = c->alloc<int32_t>(npairs);
-    c->bins = c->alloc<int32_t>(npairs);
-    c->rcount = c->alloc<unsigned long long>(3);
-    c->qcount = c->alloc<unsigned long long>(RPD_NBINS);
-    NEED(c->pair_tet && c->bins && c->rcount && c->qcount);
+    if (npairs > pcap) {
+        c->pair_tet = c->alloc<int32_t>(npairs);
+        c->bins = c->alloc<int32_t>(npairs);
+        NEED(c->pair_tet && c->bins);
+        launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, npairs,
+                         c->rcount, c->qcount, s);
+    }
     for (int b = 1; b < RPD_NBINS; b++) {
         long long n = c->hbin[b];
         if (n == 0) continue;
@@ -521,12 +537,12 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         // queued before any clip block can occupy the SMs
         record(c, 11);
         cudaStreamWaitEvent(bs->util, c->ev[11], 0);
+        ClearList clr{};
         for (int kind = 1; kind <= 4; kind++)
-            if (ftmp[kind - 1]) launch_finalize_clear(kind, fcap[kind - 1], c->ns, ftmp[kind - 1], bs->util);
+            if (ftmp[kind - 1]) finalize_clear_list(kind, fcap[kind - 1], c->ns, ftmp[kind - 1], clr);
+        launch_clear(clr, bs->util);
         cudaEventRecord(c->ev[12], bs->util);
-        if (attempt == 0)
-            launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, s);
-        TRY(run_clip(c));
+        TRY(run_clip(c, attempt > 0));
         cudaStreamWaitEvent(s, c->ev[12], 0);
         record(c, 5);   // clip and record kernels done, scratch clear: the four kinds fork here
         // ---- A5-A7, the four kinds side by side on high-priority streams; the

@@ -1189,24 +1189,30 @@ __global__ void k_bin_count(const int32_t* __restrict__ cand_cnt, long long nt, 
     warp_bin_add(n, n > 0 ? bin_of(n) : 0, bin_count);
 }
 
-__global__ void k_bin_prefix(const int32_t* __restrict__ bin_count, int32_t* __restrict__ bin_fill) {
+__global__ void k_bin_prefix(const int32_t* __restrict__ bin_count, int32_t* __restrict__ bin_fill,
+                             unsigned long long* __restrict__ rcount, unsigned long long* __restrict__ qcount) {
     int run = 0;
     for (int b = 0; b < RPD_NBINS; b++) {
         bin_fill[b] = run;
         run += bin_count[b];
+        if (qcount) qcount[b] = 0;
     }
+    if (rcount)
+        for (int k = 0; k < 3; k++) rcount[k] = 0;
 }
 
+// Writes past cap are dropped (the caller bins again with room for all pairs).
 __global__ void k_bin_pairs(const int32_t* __restrict__ cand_cnt, const int64_t* __restrict__ pair_off, long long nt,
-                            int32_t* __restrict__ pair_tet, int32_t* __restrict__ bins, int32_t* __restrict__ bin_fill) {
+                            int32_t* __restrict__ pair_tet, int32_t* __restrict__ bins, int32_t* __restrict__ bin_fill,
+                            long long cap) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = t < nt ? cand_cnt[t] : 0;
     const int base = warp_bin_add(n, n > 0 ? bin_of(n) : 0, bin_fill);
     if (n <= 0) return;
     const long long off = pair_off[t];
     for (int k = 0; k < n; k++) {
-        pair_tet[off + k] = (int32_t)t;
-        bins[base + k] = (int32_t)(off + k);
+        if (off + k < cap) pair_tet[off + k] = (int32_t)t;
+        if (base + k < cap) bins[base + k] = (int32_t)(off + k);
     }
 }
 
@@ -1261,11 +1267,12 @@ void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count,
 }
 
 void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet, int32_t* bins,
-                      const int32_t* bin_count, int32_t* bin_fill, cudaStream_t s) {
-    if (nt == 0) return;
-    k_bin_prefix<<<1, 1, 0, s>>>(bin_count, bin_fill);
+                      const int32_t* bin_count, int32_t* bin_fill, long long cap, unsigned long long* rcount,
+                      unsigned long long* qcount, cudaStream_t s) {
+    k_bin_prefix<<<1, 1, 0, s>>>(bin_count, bin_fill, rcount, qcount);
     note_launch();
-    k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_fill);
+    if (nt == 0) return;
+    k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_fill, cap);
     note_launch();
 }
 

@@ -98,8 +98,11 @@ struct ClipArgs {
 int clip_vmax(int bin);
 void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s);
 // bins: one array of npairs pair ids, bin b starting at sum of earlier counts.
+// Pairs grouped by bin (pair_tet and bins hold cap entries; writes past cap
+// are dropped); also zeroes the record and queue counters when given.
 void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet,
-                      int32_t* bins, const int32_t* bin_count, int32_t* bin_fill, cudaStream_t s);
+                      int32_t* bins, const int32_t* bin_count, int32_t* bin_fill, long long cap,
+                      unsigned long long* rcount, unsigned long long* qcount, cudaStream_t s);
 // Pair counts are read on the device (d_n); n/nmax only size the grid.
 void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s);
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,
@@ -127,6 +130,15 @@ struct FinalOut {
 // cleared by launch_finalize_clear before launch_finalize (n <= ncap) runs.
 size_t finalize_tmp_bytes(int kind, long long ncap, long long ns);
 void launch_finalize_clear(int kind, long long ncap, long long ns, void* tmp, cudaStream_t s);
+// Byte ranges to fill, cleared by one launch.
+struct ClearList {
+    void* p[16];
+    long long bytes[16];
+    int value[16];
+    int n;
+};
+void finalize_clear_list(int kind, long long ncap, long long ns, void* tmp, ClearList& L);
+void launch_clear(const ClearList& L, cudaStream_t s);
 void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, long long ns, int key_bits,
                      const FinalOut& out, void* tmp, cudaStream_t s);
 // One launch copying n_keys int32 key entries and n values of elem (1 or 4)

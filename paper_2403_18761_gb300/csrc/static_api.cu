@@ -221,9 +221,7 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
         qtrip[bb] = ar.take<uint32_t>(2LL * hb[bb] * clip_vmax(bb));
     }
     NEED_S(!ar.full);
-    launch_bin_pairs(cand_cnt, pair_off, nt, pair_tet, bins, bin_count, bin_fill, s);
-    cudaMemsetAsync(rcount, 0, sizeof(unsigned long long) * 3, s);
-    cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
+    launch_bin_pairs(cand_cnt, pair_off, nt, pair_tet, bins, bin_count, bin_fill, npairs, rcount, qcount, s);
     long long off = 0;
     for (int bb = 0; bb < RPD_NBINS; bb++) {
         const long long nb = hb[bb];

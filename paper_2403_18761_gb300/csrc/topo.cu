@@ -15,6 +15,7 @@
 // bucket pass on their first sphere index (the keys of one sphere are few)
 // and a rank inside each bucket.
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <algorithm>
 
@@ -272,6 +273,25 @@ __global__ void k_copy_rows(const int32_t* __restrict__ keys, int32_t* __restric
     }
 }
 
+// Fill byte ranges (blockIdx.y selects the range): 16-byte stores over the
+// aligned middle, single bytes at the ends.
+__global__ void k_clear(ClearList C) {
+    char* p = (char*)C.p[blockIdx.y];
+    const long long n = C.bytes[blockIdx.y];
+    const unsigned char v = (unsigned char)C.value[blockIdx.y];
+    const long long a = (long long)((16 - ((uintptr_t)p & 15)) & 15);
+    const long long head = n < a ? n : a;
+    const long long n16 = (n - head) / 16;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned w = 0x01010101u * v;
+    uint4* q = (uint4*)(p + head);
+    for (long long i = tid; i < n16; i += stride) q[i] = make_uint4(w, w, w, w);
+    const long long tail0 = head + 16 * n16;
+    if (tid < head) p[tid] = (char)v;
+    if (tid < n - tail0) p[tail0 + tid] = (char)v;
+}
+
 // blockIdx.y selects the segment
 __global__ void k_export(ExportArgs a) {
     const ExportSeg g = a.seg[blockIdx.y];
@@ -352,10 +372,30 @@ Layout layout(int kind, long long ncap, long long ns) {
 
 size_t finalize_tmp_bytes(int kind, long long ncap, long long ns) { return layout(kind, ncap, ns).total; }
 
-void launch_finalize_clear(int kind, long long ncap, long long ns, void* tmp, cudaStream_t s) {
+void finalize_clear_list(int kind, long long ncap, long long ns, void* tmp, ClearList& C) {
     const Layout L = layout(kind, ncap, ns);
-    cudaMemsetAsync(tmp, 0xff, L.ff_bytes, s);
-    cudaMemsetAsync((char*)tmp + L.ff_bytes, 0, L.zero_bytes, s);
+    if (C.n + 2 > 16) return;
+    C.p[C.n] = tmp;
+    C.bytes[C.n] = (long long)L.ff_bytes;
+    C.value[C.n++] = 0xff;
+    C.p[C.n] = (char*)tmp + L.ff_bytes;
+    C.bytes[C.n] = (long long)L.zero_bytes;
+    C.value[C.n++] = 0;
+}
+
+void launch_clear(const ClearList& C, cudaStream_t s) {
+    long long nmax = 0;
+    for (int i = 0; i < C.n; i++) nmax = std::max(nmax, C.bytes[i]);
+    if (C.n == 0 || nmax == 0) return;
+    const unsigned bx = (unsigned)std::min<long long>((nmax + 16 * 256 - 1) / (16 * 256), 152LL * 8);
+    k_clear<<<dim3(bx, (unsigned)C.n), 256, 0, s>>>(C);
+    note_launch();
+}
+
+void launch_finalize_clear(int kind, long long ncap, long long ns, void* tmp, cudaStream_t s) {
+    ClearList C{};
+    finalize_clear_list(kind, ncap, ns, tmp, C);
+    launch_clear(C, s);
 }
 
 void launch_finalize(const ClipArgs& a, int kind, long long n, long long ncap, long long ns, int key_bits,
