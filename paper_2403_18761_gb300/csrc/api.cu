@@ -438,7 +438,11 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     record(c, 4);
     // the pairs are put in bin order before the pair count is read, with room
     // for 4 pairs per tet (binned again below if there are more)
-    const long long pcap = 4 * nt + 1024;
+    long long pcap = 4 * nt + 1024;
+    if (const char* e = getenv("RPD_PAIR_CAP")) {   // test hook: a small first capacity forces the second binning
+        const long long v = atoll(e);
+        if (v > 0) pcap = v;
+    }
     c->pair_tet = c->alloc<int32_t>(pcap);
     c->bins = c->alloc<int32_t>(pcap);
     c->rcount = c->alloc<unsigned long long>(3);

@@ -62,45 +62,6 @@ __device__ __forceinline__ long long box_dist2(int3 x, const GridParams& g, int 
     return dx * dx + dy * dy + dz * dz;
 }
 
-// Lower bound of |x - y|^2 over points y in grid cells at Chebyshev index
-// distance >= r from cell c (LLONG_MAX when there is no such cell).
-__device__ __forceinline__ long long ring_lb2(int3 x, const GridParams& g, int3 c, int r) {
-    long long best = LLONG_MAX;
-    const int xs[3] = {x.x, x.y, x.z}, cs[3] = {c.x, c.y, c.z}, ds[3] = {g.dim.x, g.dim.y, g.dim.z},
-              os[3] = {g.org.x, g.org.y, g.org.z};
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        if (cs[a] + r <= ds[a] - 1) {
-            long long start = (long long)os[a] + (long long)(cs[a] + r) * g.cell;
-            best = min(best, max(0LL, start - xs[a]));
-        }
-        if (cs[a] - r >= 0) {
-            long long end = (long long)os[a] + (long long)(cs[a] - r + 1) * g.cell - 1;
-            best = min(best, max(0LL, (long long)xs[a] - end));
-        }
-    }
-    return best == LLONG_MAX ? LLONG_MAX : best * best;
-}
-
-// Visit the cells of the Chebyshev shell of radius r around c.
-template <typename F>
-__device__ __forceinline__ void for_shell(const GridParams& g, int3 c, int r, F&& f) {
-    const int z0 = max(-r, -c.z), z1 = min(r, g.dim.z - 1 - c.z);
-    const int y0 = max(-r, -c.y), y1 = min(r, g.dim.y - 1 - c.y);
-    for (int dz = z0; dz <= z1; dz++) {
-        for (int dy = y0; dy <= y1; dy++) {
-            bool full = (dz == -r || dz == r || dy == -r || dy == r);
-            if (full) {
-                const int x0 = max(-r, -c.x), x1 = min(r, g.dim.x - 1 - c.x);
-                for (int dx = x0; dx <= x1; dx++) f(c.x + dx, c.y + dy, c.z + dz);
-            } else {
-                if (c.x - r >= 0) f(c.x - r, c.y + dy, c.z + dz);
-                if (r > 0 && c.x + r <= g.dim.x - 1) f(c.x + r, c.y + dy, c.z + dz);
-            }
-        }
-    }
-}
-
 // Grid over the sphere centres' bounding box with about one sphere per cell
 // and at most ncap cells.
 __device__ GridParams grid_params(const int* mn, const int* mx, long long wm, long long ns, long long ncap) {
@@ -747,61 +708,6 @@ __global__ void k_vertex_cells(const int32_t* __restrict__ Xi, long long nv, con
 }
 
 // ---------------------------------------------------------- candidates
-struct Gathered {
-    int id;
-    long long D[4];
-};
-
-// Keep the gathered spheres that pass the exact corner test against every
-// other gathered sphere; write them sorted by index.
-// Also writes the clip order: slots sorted by power distance at the tet
-// centroid (sum_a pd(X_a, s) = 4 pd(centroid, s) + a sphere-independent term).
-template <int CAP>
-__device__ void finish_candidates(Gathered* G, int n, long long t, int32_t* __restrict__ cand_cnt,
-                                  int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st) {
-    int kept[RPD_MAXC];   // indices into G, sorted by sphere index
-    int nk = 0;
-    for (int s = 0; s < n; s++) {
-        bool ok = true;
-        for (int j = 0; j < n && ok; j++) {
-            if (j == s) continue;
-            bool some = false;
-#pragma unroll
-            for (int a = 0; a < 4; a++) some |= (G[s].D[a] <= G[j].D[a]);
-            ok = some;
-        }
-        if (!ok) continue;
-        if (nk == RPD_MAXC) {
-            dev_fail(st, RPD_E_OVERFLOW, CNT_OVERFLOW);
-            cand_cnt[t] = 0;
-            return;
-        }
-        int p = nk++;
-        while (p > 0 && G[kept[p - 1]].id > G[s].id) {
-            kept[p] = kept[p - 1];
-            p--;
-        }
-        kept[p] = s;
-    }
-    uint8_t ord[RPD_MAXC];
-    for (int j = 0; j < nk; j++) {
-        cand[t * RPD_MAXC + j] = G[kept[j]].id;
-        const Gathered& g = G[kept[j]];
-        long long key = g.D[0] + g.D[1] + g.D[2] + g.D[3];
-        int p = j;
-        while (p > 0) {
-            const Gathered& h = G[kept[ord[p - 1]]];
-            long long hk = h.D[0] + h.D[1] + h.D[2] + h.D[3];
-            if (hk <= key) break;
-            ord[p] = ord[p - 1];
-            p--;
-        }
-        ord[p] = (uint8_t)j;
-    }
-    for (int j = 0; j < nk; j++) cand_ord[t * RPD_MAXC + j] = ord[j];
-    cand_cnt[t] = nk;
-}
-
 __device__ __forceinline__ bool load_tet(const int32_t* __restrict__ T, long long t, long long nv,
                                          const int32_t* __restrict__ Xi, int* v, int3* X) {
     for (int a = 0; a < 4; a++) {
@@ -965,89 +871,151 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
     if (lane == 0) cand_cnt[t] = __popc(kmask);
 }
 
-#define RPD_FB_GATHER 128
+// Fallback for a tet whose corner lists are not complete enough: one block
+// per tet collects every sphere m with pd(X_a, m) <= pd(X_a, o_b*) for some
+// corner a (b* as in the warp form), then applies the same exact corner
+// filter and orders.  The threads split all grid cells (each cell and each
+// sphere seen once, so the list needs no duplicate check; cells pruned by
+// their largest weight) and append through a shared counter.  A bounded scan
+// replaces a ring search, whose stop test with the largest weight of all
+// spheres can keep it going over most of the grid.
+constexpr int FB_GATHER = 128;   // spheres gathered per tet at most
+constexpr int FB_THREADS = 256;
 
-__device__ void fallback_one(const int32_t* __restrict__ T, long long nv, const int32_t* __restrict__ Xi,
-                             const int32_t* __restrict__ Ci, const long long* __restrict__ W,
-                             const int32_t* __restrict__ knn, int K, const GridParams* __restrict__ gp,
-                             const int64_t* __restrict__ start, const int32_t* __restrict__ ids,
-                             const long long* __restrict__ cwmax, long long t, int32_t* __restrict__ cand_cnt,
-                             int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st);
-
-__global__ void __launch_bounds__(64) k_candidates_fallback(const int32_t* __restrict__ T, long long nv,
-                                      const int32_t* __restrict__ Xi, const int32_t* __restrict__ Ci,
-                                      const long long* __restrict__ W, const int32_t* __restrict__ knn, int K,
-                                      const GridParams* __restrict__ gp, const int64_t* __restrict__ start,
-                                      const int32_t* __restrict__ ids, const long long* __restrict__ cwmax,
-                                      const int32_t* __restrict__ fb_list, const int32_t* __restrict__ fb_count,
-                                      int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand,
-                                      uint8_t* __restrict__ cand_ord, DevState* st) {
+__global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
+    const int32_t* __restrict__ T, long long nv, const int32_t* __restrict__ Xi, const int32_t* __restrict__ Ci,
+    const long long* __restrict__ W, const int32_t* __restrict__ knn, int K, const GridParams* __restrict__ gp,
+    const int64_t* __restrict__ start, const int32_t* __restrict__ ids, const long long* __restrict__ cwmax,
+    const int32_t* __restrict__ fb_list, const int32_t* __restrict__ fb_count, int32_t* __restrict__ cand_cnt,
+    int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st) {
+    const unsigned FULL = 0xffffffffu;
+    __shared__ int sid[FB_GATHER];
+    __shared__ long long sD[FB_GATHER][4];
+    __shared__ uint8_t skeep[FB_GATHER];
+    __shared__ int sn;
+    const int tid = threadIdx.x, lane = tid & 31;
     const long long nfb = *fb_count;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nfb;
-         q += (long long)gridDim.x * blockDim.x)
-        fallback_one(T, nv, Xi, Ci, W, knn, K, gp, start, ids, cwmax, fb_list[q], cand_cnt, cand, cand_ord, st);
-}
-
-__device__ void fallback_one(const int32_t* __restrict__ T, long long nv, const int32_t* __restrict__ Xi,
-                             const int32_t* __restrict__ Ci, const long long* __restrict__ W,
-                             const int32_t* __restrict__ knn, int K, const GridParams* __restrict__ gp,
-                             const int64_t* __restrict__ start, const int32_t* __restrict__ ids,
-                             const long long* __restrict__ cwmax, long long t, int32_t* __restrict__ cand_cnt,
-                             int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st) {
-    int v[4];
-    int3 X[4];
-    if (!load_tet(T, t, nv, Xi, v, X)) return;
     const GridParams g = *gp;
-    int o[4];
-    long long M[4][4];
-    for (int a = 0; a < 4; a++) o[a] = knn[(long long)v[a] * K];
-    for (int b = 0; b < 4; b++)
-        for (int a = 0; a < 4; a++) M[a][b] = pd_exact(X[a], ld_int3(Ci, o[b]), W[o[b]]);
-    int bstar = 0;
-    long long best = LLONG_MAX;
-    for (int b = 0; b < 4; b++) {
-        long long score = 0;
-        for (int a = 0; a < 4; a++) score = max(score, M[a][b] - M[a][a]);
-        if (score < best) { best = score; bstar = b; }
-    }
-    Gathered G[RPD_FB_GATHER];
-    int n = 0;
-    bool over = false;
-    for (int a = 0; a < 4 && !over; a++) {
-        long long thr = M[a][bstar];
-        int3 x = X[a];
-        int3 c = cell_of(x, g);
-        for (int r = 0; !over; r++) {
-            if (r > 0) {
-                long long lb2 = ring_lb2(x, g, c, r);
-                if (lb2 == LLONG_MAX || lb2 - g.wmax > thr) break;
-            }
-            for_shell(g, c, r, [&](int qx, int qy, int qz) {
-                int cq = (qz * g.dim.y + qy) * g.dim.x + qx;
-                if (over || box_dist2(x, g, qx, qy, qz) - cwmax[cq] > thr) return;
-                for (long long e = start[cq]; e < start[cq + 1]; e++) {
-                    int s = ids[e];
-                    int3 cs = ld_int3(Ci, s);
-                    long long ws = W[s];
-                    if (pd_exact(x, cs, ws) > thr) continue;
-                    bool dup = false;
-                    for (int z = 0; z < n && !dup; z++) dup = (G[z].id == s);
-                    if (dup) continue;
-                    if (n == RPD_FB_GATHER) { over = true; return; }
-                    G[n].id = s;
-                    for (int cc = 0; cc < 4; cc++) G[n].D[cc] = pd_exact(X[cc], cs, ws);
-                    n++;
-                }
-            });
+    const int ncell = g.dim.x * g.dim.y * g.dim.z, nxy = g.dim.x * g.dim.y;
+    for (long long q = blockIdx.x; q < nfb; q += gridDim.x) {
+        const long long t = fb_list[q];   // uniform over the block
+        int v[4];
+        int3 X[4];
+        if (!load_tet(T, t, nv, Xi, v, X)) {
+            if (tid == 0) cand_cnt[t] = 0;
+            continue;
         }
+        int o[4];
+        for (int a = 0; a < 4; a++) o[a] = knn[(long long)v[a] * K];
+        long long M[4][4];
+        for (int b = 0; b < 4; b++)
+            for (int a = 0; a < 4; a++) M[a][b] = pd_exact(X[a], ld_int3(Ci, o[b]), W[o[b]]);
+        int bstar = 0;
+        long long best = LLONG_MAX;
+        for (int b = 0; b < 4; b++) {
+            long long score = 0;
+            for (int a = 0; a < 4; a++) score = max(score, M[a][b] - M[a][a]);
+            if (score < best) {
+                best = score;
+                bstar = b;
+            }
+        }
+        long long thr[4];
+        for (int a = 0; a < 4; a++) thr[a] = M[a][bstar];
+        if (tid == 0) sn = 0;
+        __syncthreads();
+        // every grid cell once: opened when some corner a may have a sphere
+        // of it within thr_a (|X_a - cell|^2 - max r^2 of the cell <= thr_a)
+        for (int ci = tid; ci < ncell; ci += FB_THREADS) {
+            const int qz = ci / nxy, rxy = ci - qz * nxy, qy = rxy / g.dim.x, qx = rxy - qy * g.dim.x;
+            const long long cw = cwmax[ci];
+            bool open = false;
+            for (int a = 0; a < 4; a++) open |= box_dist2(X[a], g, qx, qy, qz) - cw <= thr[a];
+            if (!open) continue;
+            for (long long e = start[ci]; e < start[ci + 1]; e++) {
+                const int sph = ids[e];
+                const int3 cs = ld_int3(Ci, sph);
+                const long long ws = W[sph];
+                bool in = false;
+                for (int a = 0; a < 4; a++) in |= pd_exact(X[a], cs, ws) <= thr[a];
+                if (!in) continue;
+                const int pos = atomicAdd(&sn, 1);
+                if (pos < FB_GATHER) sid[pos] = sph;
+            }
+        }
+        __syncthreads();
+        const int n = sn;
+        if (n > FB_GATHER) {
+            if (tid == 0) {
+                dev_fail(st, RPD_E_OVERFLOW, CNT_OVERFLOW);
+                cand_cnt[t] = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+        // corner distances of the gathered spheres, then the exact corner
+        // filter: keep i when, against every other j, some corner is at least
+        // as close to i as to j
+        if (tid < n) {
+            const int3 cs = ld_int3(Ci, sid[tid]);
+            const long long ws = W[sid[tid]];
+            for (int cc = 0; cc < 4; cc++) sD[tid][cc] = pd_exact(X[cc], cs, ws);
+        }
+        __syncthreads();
+        if (tid < n) {
+            const long long d0 = sD[tid][0], d1 = sD[tid][1], d2 = sD[tid][2], d3 = sD[tid][3];
+            bool ok = true;
+            for (int j = 0; j < n && ok; j++)
+                if (j != tid) ok = d0 <= sD[j][0] || d1 <= sD[j][1] || d2 <= sD[j][2] || d3 <= sD[j][3];
+            skeep[tid] = ok;
+        }
+        __syncthreads();
+        if (tid < 32) {   // the kept spheres, one per lane: rank by id and by (sum of corner distances, id)
+            unsigned keep[FB_GATHER / 32];
+            int nk = 0;
+            for (int k = 0; k < FB_GATHER / 32; k++) {
+                const int i = 32 * k + lane;
+                keep[k] = __ballot_sync(FULL, i < n && skeep[i]);
+                nk += __popc(keep[k]);
+            }
+            if (nk > RPD_MAXC) {
+                if (lane == 0) {
+                    dev_fail(st, RPD_E_OVERFLOW, CNT_OVERFLOW);
+                    cand_cnt[t] = 0;
+                }
+            } else {
+                int mine = -1, k0 = 0;
+                for (int k = 0; k < FB_GATHER / 32; k++) {
+                    const unsigned m = keep[k];
+                    const int c = __popc(m);
+                    if (lane >= k0 && lane < k0 + c) mine = 32 * k + (int)__fns(m, 0, lane - k0 + 1);
+                    k0 += c;
+                }
+                int my = -1;
+                long long key = 0;
+                if (mine >= 0) {
+                    my = sid[mine];
+                    key = sD[mine][0] + sD[mine][1] + sD[mine][2] + sD[mine][3];
+                }
+                int rank = 0, rank2 = 0;
+                for (int j = 0; j < nk; j++) {
+                    const int sj = __shfl_sync(FULL, my, j);
+                    const long long kj = __shfl_sync(FULL, key, j);
+                    rank += sj < my;
+                    rank2 += (kj < key) || (kj == key && sj < my);
+                }
+                if (mine >= 0) {
+                    cand[t * RPD_MAXC + rank] = my;
+                    cand_ord[t * RPD_MAXC + rank2] = (uint8_t)rank;
+                }
+                if (lane == 0) {
+                    cand_cnt[t] = nk;
+                    atomicAdd(&st->cnt[CNT_CAND_FALLBACK], 1ull);
+                }
+            }
+        }
+        __syncthreads();
     }
-    if (over) {
-        dev_fail(st, RPD_E_OVERFLOW, CNT_OVERFLOW);
-        cand_cnt[t] = 0;
-        return;
-    }
-    atomicAdd(&st->cnt[CNT_CAND_FALLBACK], 1ull);
-    finish_candidates<RPD_FB_GATHER>(G, n, t, cand_cnt, cand, cand_ord, st);
 }
 
 }  // namespace
@@ -1121,7 +1089,7 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
                                                           cand_ord,
                                                fb_list, fb_count, st);
     note_launch();
-    k_candidates_fallback<<<152, 64, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids, cell_wmax,
-                                             fb_list, fb_count, cand_cnt, cand, cand_ord, st);
+    k_candidates_fallback<<<152 * 4, FB_THREADS, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids,
+                                                         cell_wmax, fb_list, fb_count, cand_cnt, cand, cand_ord, st);
     note_launch();
 }

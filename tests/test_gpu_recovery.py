@@ -2,8 +2,9 @@
 buffers overflow, and a clean failure when a device allocation fails.
 
 Both are driven from the host through the library's test hooks
-(RPD_RECORD_CAP: capacity of the first record buffers; RPD_FAIL_ALLOC_AFTER:
-the allocation that fails); neither touches the device in an unsafe way.
+(RPD_RECORD_CAP: capacity of the first record buffers; RPD_PAIR_CAP: room of
+the binning done before the pair count is known; RPD_FAIL_ALLOC_AFTER: the
+allocation that fails); none touches the device in an unsafe way.
 """
 import os
 import subprocess
@@ -50,6 +51,25 @@ def test_record_overflow_rebuilds_identically(precision):
     finally:
         del os.environ["RPD_RECORD_CAP"]
     assert all(got["stats"]["n_records"][k] > 64 for k in (1, 2)), got["stats"]["n_records"]
+    _same(got, want)
+
+
+def test_pair_binning_overflow_bins_again():
+    """With room for far fewer pairs than there are, the binning done before
+    the pair count is read drops its excess writes and is redone with room for
+    all pairs; results are identical."""
+    w = torus_c1()
+    ctx = build_workload(w, precision="fp32")
+    want = collect(ctx)
+    ctx.rpd_destroy()
+    os.environ["RPD_PAIR_CAP"] = "100"
+    try:
+        ctx = build_workload(w, precision="fp32")
+        got = collect(ctx)
+        ctx.rpd_destroy()
+    finally:
+        del os.environ["RPD_PAIR_CAP"]
+    assert got["stats"]["n_pairs"] > 100
     _same(got, want)
 
 
