@@ -733,13 +733,24 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
         if (lane == 0) cand_cnt[t] = 0;
         return;
     }
-    int o[4];
+    // Entries 0..7 of every corner's list (lanes 8a..8a+7), with their
+    // centres and weights, are loaded first: entry 0 is the corner's owner,
+    // so everything up to the gather needs only these and shuffles.
+    const unsigned FULL = 0xffffffffu;
+    const int a8 = lane >> 3, j8 = lane & 7;
+    const int va = a8 == 0 ? v[0] : (a8 == 1 ? v[1] : (a8 == 2 ? v[2] : v[3]));
+    const int3 xa8 = a8 == 0 ? X[0] : (a8 == 1 ? X[1] : (a8 == 2 ? X[2] : X[3]));
+    const int s8 = j8 < K ? knn[(long long)va * K + j8] : -1;
+    int3 c8 = make_int3(0, 0, 0);
+    long long w8 = 0;
+    if (s8 >= 0) {
+        c8 = ld_int3(Ci, s8);
+        w8 = W[s8];
+    }
+    const long long pd8 = s8 >= 0 ? pd_exact(xa8, c8, w8) : LLONG_MAX;
     long long dp[4];
 #pragma unroll
-    for (int a = 0; a < 4; a++) {
-        o[a] = knn[(long long)v[a] * K];
-        dp[a] = dplus[v[a]];
-    }
+    for (int a = 0; a < 4; a++) dp[a] = dplus[v[a]];
     // M(a, b) = pd(X_a, owner of corner b), one entry per lane 0..15.  Lane
     // (a, b) also holds whether corner a's list is complete up to M(a, b) and
     // M(a, b) - M(a, a); the lanes of one b then combine over a.
@@ -748,22 +759,24 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
     long long score = 0;
     {
         const int a = (lane >> 2) & 3, b = lane & 3;
-        const int ob = b == 0 ? o[0] : (b == 1 ? o[1] : (b == 2 ? o[2] : o[3]));
+        const int3 cb = make_int3(__shfl_sync(FULL, c8.x, 8 * b), __shfl_sync(FULL, c8.y, 8 * b),
+                                  __shfl_sync(FULL, c8.z, 8 * b));
+        const long long wb = __shfl_sync(FULL, w8, 8 * b);
         const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
         const long long dpa = a == 0 ? dp[0] : (a == 1 ? dp[1] : (a == 2 ? dp[2] : dp[3]));
-        if (lane < 16) Ml = pd_exact(xa, ld_int3(Ci, ob), W[ob]);
-        const long long maa = __shfl_sync(0xffffffffu, Ml, a * 5);
+        if (lane < 16) Ml = pd_exact(xa, cb, wb);
+        const long long maa = __shfl_sync(FULL, Ml, a * 5);
         comp = dpa > Ml;
         score = Ml - maa;
     }
-    score = max(score, __shfl_xor_sync(0xffffffffu, score, 4));
-    score = max(score, __shfl_xor_sync(0xffffffffu, score, 8));
-    const unsigned cbits = __ballot_sync(0xffffffffu, comp);
+    score = max(score, __shfl_xor_sync(FULL, score, 4));
+    score = max(score, __shfl_xor_sync(FULL, score, 8));
+    const unsigned cbits = __ballot_sync(FULL, comp);
     int bstar = -1;
     long long best = LLONG_MAX;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
-        const long long sb = __shfl_sync(0xffffffffu, score, b);
+        const long long sb = __shfl_sync(FULL, score, b);
         if (((cbits >> b) & 0x1111u) == 0x1111u && sb < best) {
             best = sb;
             bstar = b;
@@ -779,38 +792,50 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
     // Gather.  The lists ascend in power distance, so the entries within a
     // corner's threshold are a prefix: lanes 8a..8a+7 test entries 0..7 of
     // corner a's list at once; a corner whose 8th entry still passes goes on
-    // through the rest of its list below.  Each sphere is kept once.
+    // through the rest of its list below.  Each sphere is kept once, with its
+    // centre and weight.
     int sid = -1, nheld = 0;
+    int3 hc = make_int3(0, 0, 0);
+    long long hw = 0;
     unsigned more;
     {
-        const int a = lane >> 3, j = lane & 7;
-        const int va = a == 0 ? v[0] : (a == 1 ? v[1] : (a == 2 ? v[2] : v[3]));
-        const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
-        const long long thr = __shfl_sync(0xffffffffu, Ml, a * 4 + bstar);
-        const int s = j < K ? knn[(long long)va * K + j] : -1;
-        const bool in = s >= 0 && pd_exact(xa, ld_int3(Ci, s), W[s]) <= thr;
-        const unsigned peers = __match_any_sync(0xffffffffu, in ? s : -1 - lane);
+        const long long thr = __shfl_sync(FULL, Ml, a8 * 4 + bstar);
+        const bool in = s8 >= 0 && pd8 <= thr;
+        const unsigned peers = __match_any_sync(FULL, in ? s8 : -1 - lane);
         const bool first = in && (__ffs(peers) - 1 == lane);
-        const unsigned fm = __ballot_sync(0xffffffffu, first);
+        const unsigned fm = __ballot_sync(FULL, first);
         nheld = __popc(fm);
         const int src = lane < nheld ? __fns(fm, 0, lane + 1) : 0;
-        const int sn = __shfl_sync(0xffffffffu, s, src);
-        if (lane < nheld) sid = sn;
-        more = __ballot_sync(0xffffffffu, in && j == 7);
+        const int sn = __shfl_sync(FULL, s8, src);
+        const int3 cn = make_int3(__shfl_sync(FULL, c8.x, src), __shfl_sync(FULL, c8.y, src),
+                                  __shfl_sync(FULL, c8.z, src));
+        const long long wn = __shfl_sync(FULL, w8, src);
+        if (lane < nheld) {
+            sid = sn;
+            hc = cn;
+            hw = wn;
+        }
+        more = __ballot_sync(FULL, in && j8 == 7);
     }
     for (; more; more &= more - 1) {
         const int a = (__ffs(more) - 1) >> 3;
-        const long long thr = __shfl_sync(0xffffffffu, Ml, a * 4 + bstar);
-        const int va = a == 0 ? v[0] : (a == 1 ? v[1] : (a == 2 ? v[2] : v[3]));
+        const long long thr = __shfl_sync(FULL, Ml, a * 4 + bstar);
+        const int vb = a == 0 ? v[0] : (a == 1 ? v[1] : (a == 2 ? v[2] : v[3]));
         const int3 xa = a == 0 ? X[0] : (a == 1 ? X[1] : (a == 2 ? X[2] : X[3]));
         for (int base = 8; base < K; base += 32) {
             const int e = base + lane;
-            const int s = e < K ? knn[(long long)va * K + e] : -1;
+            const int s = e < K ? knn[(long long)vb * K + e] : -1;
             bool in = false;
-            if (s >= 0) in = pd_exact(xa, ld_int3(Ci, s), W[s]) <= thr;
+            int3 cs = make_int3(0, 0, 0);
+            long long ws = 0;
+            if (s >= 0) {
+                cs = ld_int3(Ci, s);
+                ws = W[s];
+                in = pd_exact(xa, cs, ws) <= thr;
+            }
             for (int h = 0; h < nheld; h++)
-                if (__shfl_sync(0xffffffffu, sid, h) == s) in = false;
-            const unsigned mask = __ballot_sync(0xffffffffu, in);
+                if (__shfl_sync(FULL, sid, h) == s) in = false;
+            const unsigned mask = __ballot_sync(FULL, in);
             const int cnt = __popc(mask);
             if (nheld + cnt > 32) {
                 if (lane == 0) {
@@ -821,18 +846,23 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
             }
             const bool take = lane >= nheld && lane < nheld + cnt;
             const int src = take ? __fns(mask, 0, lane - nheld + 1) : 0;
-            const int sn = __shfl_sync(0xffffffffu, s, src);
-            if (take) sid = sn;
+            const int sn = __shfl_sync(FULL, s, src);
+            const int3 cn = make_int3(__shfl_sync(FULL, cs.x, src), __shfl_sync(FULL, cs.y, src),
+                                      __shfl_sync(FULL, cs.z, src));
+            const long long wn = __shfl_sync(FULL, ws, src);
+            if (take) {
+                sid = sn;
+                hc = cn;
+                hw = wn;
+            }
             nheld += cnt;
         }
     }
     const bool held = lane < nheld;
     long long D[4] = {0, 0, 0, 0};
     if (held) {
-        const int3 cs = ld_int3(Ci, sid);
-        const long long ws = W[sid];
 #pragma unroll
-        for (int c = 0; c < 4; c++) D[c] = pd_exact(X[c], cs, ws);
+        for (int c = 0; c < 4; c++) D[c] = pd_exact(X[c], hc, hw);
     }
     // exact corner filter against every other gathered sphere; the corner
     // distances of the warp's spheres are read back from shared memory
