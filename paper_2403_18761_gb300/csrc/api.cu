@@ -133,6 +133,7 @@ struct rpd_ctx {
     int64_t* piece_off = nullptr;
     long long npieces = 0;
     rpd_stats stats{};
+    bool timed = false;   // stats' stage times filled in
     int device = 0;
     cudaEvent_t ev[16] = {};
     // clip stage: fork, end of each bin's clip kernel, end of each bin's work
@@ -620,6 +621,13 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->npieces = h[4];
     c->stats.n_pieces = h[4];
     c->stats.n_records[0] = h[4];
+    c->timed = false;   // stage times are read from the events when the stats are asked for
+    return RPD_OK;
+}
+
+// Stage times of the build from its events (all complete once it returned).
+void stage_times(rpd_ctx* c) {
+    if (c->timed) return;
     c->stats.ms_prep = elapsed(c, 0, 2);   // snapping + mesh combinatorics (beside the kNN)
     c->stats.ms_knn = elapsed(c, 1, 3);
     c->stats.ms_cand = elapsed(c, 3, 4);
@@ -636,7 +644,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         c->stats.ms_clip_span = std::max(c->stats.ms_clip_span, w);
     }
     for (int k = 0; k < 4; k++) c->stats.ms_finalize[k] = elapsed(c, 5, 6 + k);   // the kinds run side by side
-    return RPD_OK;
+    c->timed = true;
 }
 
 rpd_status check_kind(rpd_ctx* c, int kind) {
@@ -771,6 +779,7 @@ int64_t rpd_launch_count(void) { return g_launches.load(std::memory_order_relaxe
 
 rpd_status rpd_stats_get(const rpd_ctx* ctx, rpd_stats* out) {
     if (!ctx || !out) return RPD_E_INVALID;
+    stage_times(const_cast<rpd_ctx*>(ctx));
     *out = ctx->stats;
     return RPD_OK;
 }

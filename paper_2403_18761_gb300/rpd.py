@@ -137,16 +137,14 @@ class Ctx:
         self.device = device
         self._keep = keep
         self._tabs = None
-        st = rpd_stats()   # element counts per kind (fixed after the build)
-        self._check(load().rpd_stats_get(self.handle, ctypes.byref(st)))
-        self._nkeys = list(st.n_keys)
+        self._nkeys = None   # element counts per kind, read with the first query
 
     def _check(self, st):
         if st != RPD_OK:
             raise RpdError(st, load().rpd_last_error(self.handle).decode())
 
     def _query(self, fn, kind):
-        if 1 <= kind <= 4:
+        if 1 <= kind <= 4 and self._nkeys is not None:
             return self._nkeys[kind - 1]
         n = ctypes.c_int64(0)
         self._check(fn(self.handle, kind, None, None, 0, ctypes.byref(n)))
@@ -168,11 +166,14 @@ class Ctx:
         device buffer: {kind: [keys, chi, beta0, flag]}, or the RpdError the
         per-kind entry points report for that kind."""
         lib = load()
-        tabs, n = {}, ctypes.c_int64(0)
+        tabs, nk = {}, []
         for kind in (1, 2, 3, 4):
+            n = ctypes.c_int64(0)
             st = lib.rpd_euler(self.handle, kind, None, None, 0, ctypes.byref(n))
             if st != RPD_OK:
                 tabs[kind] = RpdError(st, lib.rpd_last_error(self.handle).decode())
+            nk.append(n.value)
+        self._nkeys = nk
         nb = ctypes.c_int64(0)
         self._check(lib.rpd_export(self.handle, None, 0, ctypes.byref(nb)))
         buf = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=self.device)
