@@ -379,6 +379,15 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     BinStreams* bs = bin_streams();
     if (!bs) return fail(c, RPD_E_CUDA, "stream creation failed");
     record(c, 0);
+    {   // one chunk for every buffer sized before the pair count is known
+        const long long ncap = 2 * ns + 64, pcap = 4 * nt + 1024;
+        const size_t est = sizeof(DevState) + 4 * 3 * (nv + ns) + 8 * ns + 4 * 4 * nt + 4 * nt + 4 * 4 * nt +
+                           prep_tmp_bytes(nt, nv) + sizeof(GridParams) + 8 * (ncap + 1) + 4 * ns + 8 * 2 * ncap +
+                           grid_tmp_bytes(ns, ncap) + 4 * nv * c->K + 8 * nv + 16 * ns + 8 * ns + knn_tmp_bytes(nv) +
+                           4 * nt + (4 + 1) * nt * RPD_MAXC + 4 * nt + 4 + 8 * (nt + 1) + scan_tmp_bytes(nt + 1) +
+                           8 * RPD_NBINS + 8 * pcap + 8 * (3 + RPD_NBINS) + 40 * 256;
+        NEED(c->reserve(est));
+    }
     c->st = c->alloc<DevState>(1);
     c->Xi = c->alloc<int32_t>(3 * nv);
     c->Ci = c->alloc<int32_t>(3 * ns);
