@@ -11,6 +11,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -137,6 +138,7 @@ class Ctx:
         self.device = device
         self._keep = keep
         self._tabs = None
+        self._buf = None     # the rpd_export buffer behind the query views
         self._nkeys = None   # element counts per kind, read with the first query
 
     def _check(self, st):
@@ -178,6 +180,7 @@ class Ctx:
         self._check(lib.rpd_export(self.handle, None, 0, ctypes.byref(nb)))
         buf = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=self.device)
         self._check(lib.rpd_export(self.handle, buf.data_ptr(), nb.value, None))
+        self._buf = buf
         # the layout documented with rpd_export: int32 parts (each padded to
         # 16 bytes) for kinds 1..4, then the uint8 flags; split in one call
         # per region
@@ -213,6 +216,32 @@ class Ctx:
         if isinstance(t, RpdError):
             raise t
         return t
+
+    def tables_host(self):
+        """Every element table on the host in one device-to-host copy of the
+        rpd_export buffer: ({kind: (keys, chi, beta0, flag)} as numpy views of
+        one pinned host buffer, bytes copied).  Kinds the build cannot report
+        are left out."""
+        if self._tabs is None:
+            self._tabs = self._export_all()
+        host = torch.empty(self._buf.numel(), dtype=torch.uint8, pin_memory=True)
+        with torch.cuda.stream(self.stream):   # ordered after the export on the build's stream
+            host.copy_(self._buf, non_blocking=True)
+        self.stream.synchronize()
+        base = self._buf.data_ptr()
+        h = host.numpy()
+        out = {}
+        for kind, t in self._tabs.items():
+            if isinstance(t, RpdError):
+                continue
+            views = []
+            for x in t:   # the same byte ranges as the device views
+                off = x.data_ptr() - base
+                nbytes = x.numel() * x.element_size()
+                views.append(h[off:off + nbytes].view(np.int32 if x.dtype == torch.int32 else np.uint8)
+                             .reshape(tuple(x.shape)))
+            out[kind] = tuple(views)
+        return out, self._buf.numel()
 
     # The three queries return views of one buffer filled by rpd_export (the
     # keys tensor of a kind is shared by the three); rows_direct goes through

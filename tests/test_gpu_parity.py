@@ -179,6 +179,14 @@ def test_export_views_match_per_kind_entry_points(block_small):
             k2, v2 = ctx.rows_direct(name, kind)
             assert k1.shape == k2.shape and k1.shape[0] > 0
             assert torch.equal(k1, k2) and torch.equal(v1, v2) and v1.dtype == v2.dtype, (name, kind)
+    host, nbytes = ctx.tables_host()   # one copy of the export buffer
+    assert nbytes > 0 and sorted(host) == [1, 2, 3, 4]
+    for kind in (1, 2, 3, 4):
+        keys, chi = ctx.rpd_euler(kind)
+        _, beta = ctx.rpd_components(kind)
+        _, flag = ctx.rpd_contractible(kind)
+        for got, want in zip(host[kind], (keys, chi, beta, flag)):
+            assert np.array_equal(got, want.cpu().numpy()), kind
     with pytest.raises(RpdError) as e:
         ctx.rpd_euler(5)
     assert e.value.status == RPD_E_INVALID
@@ -187,6 +195,17 @@ def test_export_views_match_per_kind_entry_points(block_small):
 def test_k1_uses_candidate_fallback(torus):
     w, o = torus
     g = collect(build_workload(w, k=1))
+    assert g["stats"]["cand_fallback"] > 0
+    _check_pieces(w, g, o["tet"], o["sphere"], o["vol"], o["moment"])
+    _check_kinds(g, _oracle_kinds(o))
+
+
+def test_k1_fallback_on_block_matches_oracle(block_small):
+    """k = 1 sends the 13k-tet block's tets that straddle cells through the candidate
+    fallback (one block per tet scanning the whole sphere grid); the results
+    still match the oracle exactly."""
+    w, o = block_small
+    g = collect(build_workload(w, precision="fp32", k=1))
     assert g["stats"]["cand_fallback"] > 0
     _check_pieces(w, g, o["tet"], o["sphere"], o["vol"], o["moment"])
     _check_kinds(g, _oracle_kinds(o))
