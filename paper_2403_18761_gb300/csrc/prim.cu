@@ -10,8 +10,6 @@
 
 namespace {
 
-inline unsigned div_up_ll(long long a, int b) { return (unsigned)((a + b - 1) / b); }
-
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -343,9 +341,4 @@ static void radix_sort_impl(const uint64_t* keys_in, const uint32_t* vals_in, ui
 void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                       long long n, int bits, void* tmp, int* d_err, cudaStream_t s) {
     radix_sort_impl(keys_in, vals_in, keys_out, vals_out, nullptr, n, bits, tmp, d_err, s);
-}
-
-void radix_sort_pairs_dn(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                         const long long* d_n, long long nmax, int bits, void* tmp, int* d_err, cudaStream_t s) {
-    radix_sort_impl(keys_in, vals_in, keys_out, vals_out, d_n, nmax, bits, tmp, d_err, s);
 }

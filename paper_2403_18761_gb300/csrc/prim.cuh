@@ -22,9 +22,3 @@ void scan_excl(const int64_t* in, int64_t* out, long long n, void* tmp, cudaStre
 size_t radix_tmp_bytes(long long n);
 void radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                       uint32_t* vals_out, long long n, int bits, void* tmp, int* d_err, cudaStream_t s);
-// Same with the element count read on the device from *d_n (<= nmax); tmp
-// must hold radix_tmp_bytes(nmax).
-void radix_sort_pairs_dn(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
-                         uint32_t* vals_out, const long long* d_n, long long nmax, int bits, void* tmp, int* d_err,
-                         cudaStream_t s);
-
