@@ -22,14 +22,12 @@ thread_local std::string g_build_error;
 
 // Optional host-side allocation-failure injection for tests:
 // RPD_FAIL_ALLOC_AFTER=N makes the (N+1)-th device allocation of a build fail.
-long long g_alloc_budget = -2;
-
 long long alloc_budget() {
-    if (g_alloc_budget == -2) {
+    static const long long budget = [] {
         const char* e = getenv("RPD_FAIL_ALLOC_AFTER");
-        g_alloc_budget = e ? atoll(e) : -1;
-    }
-    return g_alloc_budget;
+        return e ? atoll(e) : -1ll;
+    }();
+    return budget;
 }
 
 std::atomic<long long> g_launches{0};
@@ -70,10 +68,13 @@ void release_events(int dev, cudaEvent_t* ev, int n) {
 // reuse it instead of mapping fresh memory at every synchronisation.
 cudaMemPool_t library_pool() {
     static cudaMemPool_t pools[64];
-    static bool ready[64];
+    static std::atomic<bool> ready[64];
+    static std::mutex mu;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!ready[dev]) {
+    if (ready[dev].load(std::memory_order_acquire)) return pools[dev];
+    std::lock_guard<std::mutex> lock(mu);   // first use on this device: create it once
+    if (!ready[dev].load(std::memory_order_relaxed)) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
         props.location.type = cudaMemLocationTypeDevice;
@@ -81,7 +82,7 @@ cudaMemPool_t library_pool() {
         if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) return nullptr;
         unsigned long long thr = ~0ull;
         cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &thr);
-        ready[dev] = true;
+        ready[dev].store(true, std::memory_order_release);
     }
     return pools[dev];
 }

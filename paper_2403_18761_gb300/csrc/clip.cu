@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -1223,15 +1224,30 @@ inline unsigned grid_for(long long n, int tpb) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// Dynamic shared memory above 48 KB needs the kernel's limit raised; the
+// attribute belongs to the current device, so it is raised once per device
+// (thread-safe).
+struct SmemLimit {
+    std::mutex mu;
+    size_t set[64] = {};
+};
+
+inline void raise_smem_limit(const void* fn, size_t bytes, SmemLimit& L) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(L.mu);
+    if (bytes > L.set[dev]) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        L.set[dev] = bytes;
+    }
+}
+
 template <typename Real, int VMAX, int WARPS>
 void launch_clip_t(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long n, cudaStream_t s) {
     if (n <= 0) return;
     const size_t smem = (size_t)WARPS * VMAX * (PrecTraits<Real>::VW + 1) * 32 * sizeof(uint32_t);
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_clip<Real, VMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
-    }
+    static SmemLimit lim;
+    raise_smem_limit((const void*)k_clip<Real, VMAX>, smem, lim);
     k_clip<Real, VMAX><<<grid_for(n, 32 * WARPS), 32 * WARPS, smem, s>>>(a, pairs, d_n);
     note_launch();
 }
@@ -1240,11 +1256,8 @@ template <typename Real>
 void launch_volume_t(const ClipArgs& a, int vmax, int rmax, int warps, long long nmax, cudaStream_t s) {
     if (nmax <= 0) return;
     const size_t smem = (size_t)warps * vmax * 8 * 32 * sizeof(uint32_t) + (size_t)warps * rmax * 4 * 32 * 8;
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaFuncSetAttribute(k_volume<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = smem;
-    }
+    static SmemLimit lim;
+    raise_smem_limit((const void*)k_volume<Real>, smem, lim);
     k_volume<Real><<<nblk(nmax, 32 * warps), 32 * warps, smem, s>>>(a, vmax, rmax);
     note_launch();
 }
