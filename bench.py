@@ -362,7 +362,7 @@ def main():
                                   precision),
         "step_ms_max": t_step,
     }
-    # ---- the other precision, same step (SURVEY: FP32-filtered vs FP64)
+    # ---- the other precision, same step (FP32-filtered vs FP64 throughput)
     if not args.no_compare:
         other = "fp64" if precision == "fp32" else "fp32"
         oms = []
