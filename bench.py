@@ -86,7 +86,8 @@ def clip_roofline(stage, n_sm, workload, precision):
         flop.append(FLOP_SIGN_TEST * max(tests - sum(nv), 0) + sum(f * n for f, n in zip(FLOP_NEW_VERTEX, nv)))
         ms.append(s["ms_clip_kernels"])
     achieved = float(np.mean(flop)) / (float(np.mean(ms)) * 1e-3) / 1e12
-    return {"kernel": "k_clip over all candidate-count bins (side by side on the bin streams) + k_whole",
+    return {"kernel": "k_clip over all candidate-count bins + k_whole (side by side on the bin streams; "
+                      "timed to the end of the record kernels that follow them there)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": CLIP_TRAFFIC_BYTES.get((workload, precision)), "flop_per_launch": float(np.mean(flop)),
             "ms_per_launch": float(np.mean(ms)),
