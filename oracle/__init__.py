@@ -13,6 +13,11 @@ Two tiers, sharing no code with the CUDA library:
                        clipped against every other sphere; aggregated here with
                        numpy and scipy.
 
+``run(w, k=K)`` runs the same C clipping on per-tet candidate sets found by
+the library's neighbour + candidate algorithm (restated in C in the same file,
+no code shared with the library).  It is the benchmark's same-algorithm CPU
+baseline, not a parity reference; a CPU test checks it against the brute force.
+
 Per-key aggregation (this file):
   chi(key)   = sum of the per-piece fractional contributions (Sec. 4.1.2);
   beta0(key) = connected components of the key's pieces linked across shared
@@ -57,6 +62,8 @@ def _load():
         I64 = ctypes.c_int64
         lib.orc_run.restype = P
         lib.orc_run.argtypes = [I64, P, I64, P, I64, P, P, P, I64, ctypes.c_int]
+        lib.orc_run_knn.restype = P
+        lib.orc_run_knn.argtypes = [I64, P, I64, P, I64, P, P, P, I64, ctypes.c_int, ctypes.c_int]
         lib.orc_status.restype = ctypes.c_int
         lib.orc_status.argtypes = [P]
         lib.orc_npieces.restype = I64
@@ -81,8 +88,9 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
-def clip_all(verts_i, tets, centers_i, radii_i, subset=None, nthreads=None):
-    """Run the C brute force.  Integer grid inputs.  Returns raw pieces and
+def clip_all(verts_i, tets, centers_i, radii_i, subset=None, nthreads=None, k=0):
+    """Run the C brute force (k = 0) or the same-algorithm baseline with k
+    power neighbours per vertex.  Integer grid inputs.  Returns raw pieces and
     element nodes (unsorted) and the face adjacency."""
     lib = _load()
     X = np.ascontiguousarray(verts_i, dtype=np.int64)
@@ -91,8 +99,8 @@ def clip_all(verts_i, tets, centers_i, radii_i, subset=None, nthreads=None):
     R = np.ascontiguousarray(radii_i, dtype=np.int64)
     sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int32)
     nth = nthreads or os.cpu_count() or 1
-    h = lib.orc_run(len(X), _ptr(X), len(T), _ptr(T), len(R), _ptr(C), _ptr(R), _ptr(sub),
-                    0 if sub is None else len(sub), nth)
+    args = (len(X), _ptr(X), len(T), _ptr(T), len(R), _ptr(C), _ptr(R), _ptr(sub), 0 if sub is None else len(sub), nth)
+    h = lib.orc_run_knn(*args, int(k)) if k else lib.orc_run(*args)
     try:
         st = lib.orc_status(h)
         if st != 0:
@@ -152,12 +160,13 @@ def aggregate(raw, nt):
     return res
 
 
-def run(w, subset=None, nthreads=None):
+def run(w, subset=None, nthreads=None, k=0):
     """Oracle RPD of a seeded workload: pieces (sorted by (tet, sphere)) in
-    world units and, unless ``subset`` is given, per-key chi / beta0 / flags."""
+    world units and, unless ``subset`` is given, per-key chi / beta0 / flags.
+    k > 0 selects the same-algorithm CPU baseline (k power neighbours)."""
     q, c, r = w.ints()
     t0 = time.perf_counter()
-    raw = clip_all(q, w.tets, c, r, subset=subset, nthreads=nthreads)
+    raw = clip_all(q, w.tets, c, r, subset=subset, nthreads=nthreads, k=k)
     elapsed = time.perf_counter() - t0
     s = 1.0 / float(1 << w.grid_bits)
     order = np.lexsort((raw["p_i"], raw["p_t"]))

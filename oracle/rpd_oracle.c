@@ -191,6 +191,11 @@ typedef struct {
     const int32_t *subset;
     int64_t nsub;
     int nthreads;
+    /* same-algorithm baseline only (K > 0): per mesh vertex the K nearest
+     * spheres in power distance, their distances and the bound D+ */
+    int K;
+    int32_t *knn;
+    int64_t *knd, *dplus;
 } mesh_t;
 
 typedef struct {
@@ -314,7 +319,10 @@ static int cmp_sk(const void *a, const void *b) {
     return x->k < y->k ? -1 : (x->k > y->k);
 }
 
-static void process_tet(out_t *o, int64_t t, sortkey_t *order, vtx_t *V, vtx_t *V2, plane_t *bis) {
+/* Clip tet t against the spheres of `cand` (ncand ids, ascending), or against
+ * every sphere when cand is NULL (the brute force). */
+static void process_tet(out_t *o, int64_t t, sortkey_t *order, vtx_t *V, vtx_t *V2, plane_t *bis,
+                        const int32_t *cand, int64_t ncand) {
     const mesh_t *m = o->m;
     int64_t X[4][3];
     for (int a = 0; a < 4; a++)
@@ -343,16 +351,18 @@ static void process_tet(out_t *o, int64_t t, sortkey_t *order, vtx_t *V, vtx_t *
     /* spheres by power distance at the centroid (order only affects speed) */
     double cen[3];
     for (int k = 0; k < 3; k++) cen[k] = 0.25 * (double)(X[0][k] + X[1][k] + X[2][k] + X[3][k]);
-    int64_t ns = m->ns;
-    for (int64_t s = 0; s < ns; s++) {
+    int64_t ns = cand ? ncand : m->ns;
+    for (int64_t q0 = 0; q0 < ns; q0++) {
+        int64_t s = cand ? cand[q0] : q0;
         double d = 0;
         for (int k = 0; k < 3; k++) { double q = cen[k] - (double)m->C[s * 3 + k]; d += q * q; }
-        order[s].d = (int64_t)llround(d - (double)m->W[s]);
-        order[s].k = (int32_t)s;
+        order[q0].d = (int64_t)llround(d - (double)m->W[s]);
+        order[q0].k = (int32_t)s;
     }
     qsort(order, ns, sizeof(sortkey_t), cmp_sk);
     /* exact power distances of the corners */
-    for (int64_t i = 0; i < ns; i++) {
+    for (int64_t ii = 0; ii < ns; ii++) {
+        const int64_t i = cand ? cand[ii] : ii;
         int nvx = 4;
         for (int a = 0; a < 4; a++) {
             int n = 0;
@@ -553,19 +563,266 @@ static void process_tet(out_t *o, int64_t t, sortkey_t *order, vtx_t *V, vtx_t *
     }
 }
 
+/* ------------------------------------------- same-algorithm CPU baseline
+ * Timed baseline of the benchmark, not a parity reference (a CPU test checks
+ * that its pieces and elements equal the brute force's).  It follows the
+ * neighbour and candidate algorithm of the GPU library, written here in plain
+ * C from the same argument, with no code in common:
+ *   - per mesh vertex x: the K spheres of smallest power distance pd(x, m)
+ *     (exact 64-bit integers), found by a ring search over a uniform grid of
+ *     sphere centres, and D+(x), a lower bound on pd(x, m) of every sphere m
+ *     left out of the list;
+ *   - per tet with corners x_a: if sphere i owns part of the tet then, for
+ *     every sphere j, some corner has pd(x_a, i) <= pd(x_a, j), because
+ *     pd(., i) - pd(., j) is affine.  With j = o_b, the nearest sphere of
+ *     corner b, i lies in G = union over a of {m : pd(x_a, m) <= pd(x_a, o_b)},
+ *     read from the lists when every list covers its threshold (D+(x_a) >
+ *     pd(x_a, o_b)), else from a scan of all spheres;
+ *   - G is filtered by the same corner test against every other member, and
+ *     each remaining candidate is clipped by the other candidates' radical
+ *     planes (process_tet), which gives the same pieces as clipping against
+ *     every sphere. */
+typedef struct {
+    int64_t org[3], cell;
+    int64_t dim[3];
+    int64_t *start;   /* ncell + 1 */
+    int32_t *ids;     /* sphere ids sorted by cell */
+    int64_t wmax;
+} sgrid_t;
+
+static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static int64_t cell_coord(const sgrid_t *g, int a, int64_t x) {
+    int64_t d = x - g->org[a];
+    int64_t q = d >= 0 ? d / g->cell : -((-d + g->cell - 1) / g->cell);
+    return clampi(q, 0, g->dim[a] - 1);
+}
+
+static int build_sgrid(const mesh_t *m, sgrid_t *g) {
+    int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
+    g->wmax = 0;
+    for (int64_t s = 0; s < m->ns; s++) {
+        for (int a = 0; a < 3; a++) {
+            int64_t v = m->C[s * 3 + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+        if (m->W[s] > g->wmax) g->wmax = m->W[s];
+    }
+    double vol = 1;
+    for (int a = 0; a < 3; a++) vol *= (double)(hi[a] - lo[a] + 1);
+    int64_t cell = (int64_t)ceil(cbrt(vol / (double)m->ns));
+    if (cell < 1) cell = 1;
+    g->cell = cell;
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; a++) {
+        g->org[a] = lo[a];
+        g->dim[a] = (hi[a] - lo[a]) / cell + 1;
+        ncell *= g->dim[a];
+    }
+    g->start = calloc(ncell + 1, sizeof(int64_t));
+    g->ids = malloc(sizeof(int32_t) * (m->ns > 0 ? m->ns : 1));
+    int64_t *fill = malloc(sizeof(int64_t) * ncell);
+    int64_t *cid = malloc(sizeof(int64_t) * (m->ns > 0 ? m->ns : 1));
+    if (!g->start || !g->ids || !fill || !cid) { free(fill); free(cid); return ORC_OOM; }
+    for (int64_t s = 0; s < m->ns; s++) {
+        int64_t c = 0;
+        for (int a = 2; a >= 0; a--) c = c * g->dim[a] + cell_coord(g, a, m->C[s * 3 + a]);
+        cid[s] = c;
+        g->start[c + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; c++) g->start[c + 1] += g->start[c];
+    for (int64_t c = 0; c < ncell; c++) fill[c] = g->start[c];
+    for (int64_t s = 0; s < m->ns; s++) g->ids[fill[cid[s]]++] = (int32_t)s;
+    free(fill); free(cid);
+    return ORC_OK;
+}
+
+/* K nearest spheres of point x (sorted by (distance, id)) and D+(x). */
+static void knn_point(const mesh_t *m, const sgrid_t *g, const int64_t *x, int K, int32_t *ids, int64_t *dist,
+                      int64_t *dplus) {
+    int cnt = 0;
+    int64_t c0[3];
+    for (int a = 0; a < 3; a++) c0[a] = cell_coord(g, a, x[a]);
+    for (int64_t r = 0;; r++) {
+        int64_t lo[3], hi[3];
+        for (int a = 0; a < 3; a++) { lo[a] = c0[a] - r; hi[a] = c0[a] + r; }
+        for (int64_t cz = clampi(lo[2], 0, g->dim[2] - 1); cz <= clampi(hi[2], 0, g->dim[2] - 1); cz++)
+            for (int64_t cy = clampi(lo[1], 0, g->dim[1] - 1); cy <= clampi(hi[1], 0, g->dim[1] - 1); cy++)
+                for (int64_t cx = clampi(lo[0], 0, g->dim[0] - 1); cx <= clampi(hi[0], 0, g->dim[0] - 1); cx++) {
+                    /* only the cells of ring r (Chebyshev distance r from c0) */
+                    int64_t dx = cx - c0[0], dy = cy - c0[1], dz = cz - c0[2];
+                    int64_t cheb = llabs(dx);
+                    if (llabs(dy) > cheb) cheb = llabs(dy);
+                    if (llabs(dz) > cheb) cheb = llabs(dz);
+                    if (cheb != r) continue;
+                    int64_t c = (cz * g->dim[1] + cy) * g->dim[0] + cx;
+                    for (int64_t q = g->start[c]; q < g->start[c + 1]; q++) {
+                        int32_t sid = g->ids[q];
+                        int64_t d = pd64(x, m->C + (int64_t)sid * 3, m->W[sid]);
+                        if (cnt == K && (d > dist[K - 1] || (d == dist[K - 1] && sid > ids[K - 1]))) continue;
+                        int pos = cnt < K ? cnt++ : K - 1;
+                        while (pos > 0 && (dist[pos - 1] > d || (dist[pos - 1] == d && ids[pos - 1] > sid))) {
+                            dist[pos] = dist[pos - 1];
+                            ids[pos] = ids[pos - 1];
+                            pos--;
+                        }
+                        dist[pos] = d;
+                        ids[pos] = sid;
+                    }
+                }
+        /* spheres outside the box of rings <= r lie beyond one of its
+         * unclamped faces: their centre is at least `gap` away from x */
+        int64_t gap = INT64_MAX;
+        for (int a = 0; a < 3; a++) {
+            if (lo[a] > 0) {
+                int64_t gl = x[a] - (g->org[a] + lo[a] * g->cell);
+                if (gl < 0) gl = 0;
+                if (gl < gap) gap = gl;
+            }
+            if (hi[a] < g->dim[a] - 1) {
+                int64_t gh = g->org[a] + (hi[a] + 1) * g->cell - x[a];
+                if (gh < 0) gh = 0;
+                if (gh < gap) gap = gh;
+            }
+        }
+        const int64_t kth = cnt == K ? dist[K - 1] : INT64_MAX;
+        if (gap == INT64_MAX) {   /* every cell visited */
+            *dplus = kth;
+            break;
+        }
+        const int64_t lb = gap * gap - g->wmax;
+        if (cnt == K && lb > kth) {
+            *dplus = kth;   /* evicted spheres are >= the K-th; the rest >= lb > kth */
+            break;
+        }
+    }
+    for (int k = cnt; k < K; k++) { ids[k] = -1; dist[k] = INT64_MAX; }
+}
+
+typedef struct {
+    const mesh_t *m;
+    const sgrid_t *g;
+    const uint8_t *need;
+    int64_t v_begin, v_end;
+} knn_job_t;
+
+static void *knn_worker(void *arg) {
+    knn_job_t *j = arg;
+    const mesh_t *m = j->m;
+    for (int64_t v = j->v_begin; v < j->v_end; v++)
+        if (j->need[v])
+            knn_point(m, j->g, m->X + v * 3, m->K, m->knn + v * m->K, m->knd + v * m->K, m->dplus + v);
+    return NULL;
+}
+
+static int compute_knn(mesh_t *m) {
+    sgrid_t g = {0};
+    int st = build_sgrid(m, &g);
+    uint8_t *need = calloc(m->nv, 1);
+    m->knn = malloc(sizeof(int32_t) * m->nv * m->K);
+    m->knd = malloc(sizeof(int64_t) * m->nv * m->K);
+    m->dplus = malloc(sizeof(int64_t) * m->nv);
+    if (st != ORC_OK || !need || !m->knn || !m->knd || !m->dplus) { free(g.start); free(g.ids); free(need); return ORC_OOM; }
+    int64_t count = m->subset ? m->nsub : m->nt;
+    for (int64_t q = 0; q < count; q++) {
+        int64_t t = m->subset ? m->subset[q] : q;
+        for (int a = 0; a < 4; a++) need[m->T[t * 4 + a]] = 1;
+    }
+    int nth = m->nthreads;
+    knn_job_t *jobs = malloc(sizeof(knn_job_t) * nth);
+    pthread_t *th = malloc(sizeof(pthread_t) * nth);
+    for (int k = 0; k < nth; k++) {
+        jobs[k].m = m; jobs[k].g = &g; jobs[k].need = need;
+        jobs[k].v_begin = m->nv * k / nth;
+        jobs[k].v_end = m->nv * (k + 1) / nth;
+        pthread_create(&th[k], NULL, knn_worker, &jobs[k]);
+    }
+    for (int k = 0; k < nth; k++) pthread_join(th[k], NULL);
+    free(jobs); free(th); free(need); free(g.start); free(g.ids);
+    return ORC_OK;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Candidate spheres of tet t (ascending ids) into cand; returns their count. */
+static int64_t tet_candidates(const mesh_t *m, int64_t t, int32_t *cand, int64_t *gath_pd) {
+    const int K = m->K;
+    const int64_t *X[4];
+    int32_t v[4];
+    for (int a = 0; a < 4; a++) { v[a] = m->T[t * 4 + a]; X[a] = m->X + (int64_t)v[a] * 3; }
+    int64_t n = 0;
+    int bsel = -1;
+    int64_t tau[4];
+    for (int b = 0; b < 4 && bsel < 0; b++) {
+        const int32_t ob = m->knn[(int64_t)v[b] * K];
+        int ok = 1;
+        for (int a = 0; a < 4; a++) {
+            tau[a] = pd64(X[a], m->C + (int64_t)ob * 3, m->W[ob]);
+            if (!(tau[a] < m->dplus[v[a]])) ok = 0;
+        }
+        if (ok) bsel = b;
+    }
+    if (bsel >= 0) {
+        for (int a = 0; a < 4; a++)
+            for (int k = 0; k < K; k++) {
+                const int32_t sid = m->knn[(int64_t)v[a] * K + k];
+                if (sid < 0 || m->knd[(int64_t)v[a] * K + k] > tau[a]) break;
+                int dup = 0;
+                for (int64_t z = 0; z < n && !dup; z++) dup = cand[z] == sid;
+                if (!dup) cand[n++] = sid;
+            }
+    } else {   /* lists do not cover the thresholds of any corner: scan every sphere */
+        const int32_t o0 = m->knn[(int64_t)v[0] * K];
+        for (int a = 0; a < 4; a++) tau[a] = pd64(X[a], m->C + (int64_t)o0 * 3, m->W[o0]);
+        for (int64_t s = 0; s < m->ns; s++) {
+            int in = 0;
+            for (int a = 0; a < 4 && !in; a++) in = pd64(X[a], m->C + s * 3, m->W[s]) <= tau[a];
+            if (in) cand[n++] = (int32_t)s;
+        }
+    }
+    /* exact corner filter: i survives iff for every other j some corner has
+     * pd(x_a, i) <= pd(x_a, j) */
+    for (int64_t q = 0; q < n; q++)
+        for (int a = 0; a < 4; a++) gath_pd[q * 4 + a] = pd64(X[a], m->C + (int64_t)cand[q] * 3, m->W[cand[q]]);
+    int64_t keep = 0;
+    for (int64_t q = 0; q < n; q++) {
+        int ok = 1;
+        for (int64_t r = 0; r < n && ok; r++) {
+            if (r == q) continue;
+            int some = 0;
+            for (int a = 0; a < 4 && !some; a++) some = gath_pd[q * 4 + a] <= gath_pd[r * 4 + a];
+            ok = some;
+        }
+        if (ok) cand[keep++] = cand[q];
+    }
+    qsort(cand, keep, sizeof(int32_t), cmp_i32);
+    return keep;
+}
+
 static void *worker(void *arg) {
     out_t *o = arg;
     const mesh_t *m = o->m;
     sortkey_t *order = malloc(sizeof(sortkey_t) * (m->ns > 0 ? m->ns : 1));
     vtx_t *V = malloc(sizeof(vtx_t) * MAXV), *V2 = malloc(sizeof(vtx_t) * MAXV);
     plane_t *bis = malloc(sizeof(plane_t) * (m->ns > 0 ? m->ns : 1));
-    if (!order || !V || !V2 || !bis) { o->status = ORC_OOM; goto done; }
+    int32_t *cand = m->K > 0 ? malloc(sizeof(int32_t) * (m->ns > 0 ? m->ns : 1)) : NULL;
+    int64_t *gpd = m->K > 0 ? malloc(sizeof(int64_t) * 4 * (m->ns > 0 ? m->ns : 1)) : NULL;
+    if (!order || !V || !V2 || !bis || (m->K > 0 && (!cand || !gpd))) { o->status = ORC_OOM; goto done; }
     for (int64_t s = o->t_begin; s < o->t_end && o->status == ORC_OK; s += o->t_stride) {
         int64_t t = m->subset ? m->subset[s] : s;
-        process_tet(o, t, order, V, V2, bis);
+        if (m->K > 0) {
+            const int64_t nc = tet_candidates(m, t, cand, gpd);
+            process_tet(o, t, order, V, V2, bis, cand, nc);
+        } else {
+            process_tet(o, t, order, V, V2, bis, NULL, 0);
+        }
     }
 done:
-    free(order); free(V); free(V2); free(bis);
+    free(order); free(V); free(V2); free(bis); free(cand); free(gpd);
     return NULL;
 }
 
@@ -673,13 +930,15 @@ static int check_orient(const mesh_t *m) {
     return ORC_OK;
 }
 
-orc_result *orc_run(int64_t nv, const int64_t *X, int64_t nt, const int32_t *T, int64_t ns,
-                    const int64_t *C, const int64_t *R, const int32_t *subset, int64_t nsub, int nthreads) {
+static orc_result *run_common(int64_t nv, const int64_t *X, int64_t nt, const int32_t *T, int64_t ns,
+                              const int64_t *C, const int64_t *R, const int32_t *subset, int64_t nsub, int nthreads,
+                              int K) {
     orc_result *res = calloc(1, sizeof(orc_result));
     if (!res) return NULL;
     mesh_t m = {0};
     m.X = X; m.T = T; m.C = C; m.nv = nv; m.nt = nt; m.ns = ns;
     m.subset = subset; m.nsub = nsub; m.nthreads = nthreads > 0 ? nthreads : 1;
+    m.K = K;
     int64_t *W = malloc(sizeof(int64_t) * (ns > 0 ? ns : 1));
     for (int64_t s = 0; s < ns; s++) W[s] = R[s] * R[s];
     m.W = W;
@@ -689,7 +948,8 @@ orc_result *orc_run(int64_t nv, const int64_t *X, int64_t nt, const int32_t *T, 
         if (C[s] > (1 << 21) || C[s] < -(1 << 21)) { res->status = ORC_INVALID; free(W); return res; }
     int st = check_orient(&m);
     if (st == ORC_OK) st = build_tables(&m);
-    if (st != ORC_OK) { res->status = st; free(W); return res; }
+    if (st == ORC_OK && K > 0) st = compute_knn(&m);
+    if (st != ORC_OK) { res->status = st; free(W); free(m.knn); free(m.knd); free(m.dplus); return res; }
     int nth = m.nthreads;
     int64_t count = subset ? nsub : nt;
     out_t *outs = calloc(nth, sizeof(out_t));
@@ -728,7 +988,23 @@ orc_result *orc_run(int64_t nv, const int64_t *X, int64_t nt, const int32_t *T, 
     }
     res->adj = m.adj;
     free(outs); free(th); free(W); free(m.own); free(m.nshare);
+    free(m.knn); free(m.knd); free(m.dplus);
     return res;
+}
+
+/* Brute force: every tet clipped against every other sphere. */
+orc_result *orc_run(int64_t nv, const int64_t *X, int64_t nt, const int32_t *T, int64_t ns,
+                    const int64_t *C, const int64_t *R, const int32_t *subset, int64_t nsub, int nthreads) {
+    return run_common(nv, X, nt, T, ns, C, R, subset, nsub, nthreads, 0);
+}
+
+/* Same-algorithm CPU baseline: K power neighbours per vertex, candidates per
+ * tet, each candidate clipped by the other candidates (bench only). */
+orc_result *orc_run_knn(int64_t nv, const int64_t *X, int64_t nt, const int32_t *T, int64_t ns,
+                        const int64_t *C, const int64_t *R, const int32_t *subset, int64_t nsub, int nthreads,
+                        int K) {
+    if (K < 1) K = 1;
+    return run_common(nv, X, nt, T, ns, C, R, subset, nsub, nthreads, K);
 }
 
 int orc_status(const orc_result *r) { return r ? r->status : ORC_OOM; }
