@@ -3,12 +3,14 @@ fractional Euler characteristic, connected components and contractibility of
 every RPC/RPF/RPE/RPV, on one GB300.
 
 One step = rpd_build + rpd_euler/rpd_components/rpd_contractible for every
-element kind (all of the hot path) on the genus-3 block workload (4x2x1 box
-with three through-holes, ~200k tets, 2k near-medial spheres, FP32-filtered
-clipping with FP64/exact fallback, k = 32).  Inputs are seeded and synthetic.
+element kind (all of the hot path) on the organic-blob workload (union of 200
+seeded ellipsoids, ~2.0M tets, 20k near-medial spheres, k = 32), FP32-filtered
+clipping with FP64/exact fallback, compared on the same step with the plain
+FP64 form and with the volumes of the CPU oracle on a tet sample.  Inputs are
+seeded and synthetic.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config block_c2|torus_c1|blob_c3] [--precision fp32|fp64]
+                    [--config blob_c3|block_c2|torus_c1] [--precision fp32|fp64]
 """
 import argparse
 import json
@@ -33,20 +35,32 @@ WORKLOADS = {
 }
 
 
-# Algorithmic FP32 work of the clip stage (Tet-Cell clipping, Sec. 5.2):
-# one filtered sign test F.C of a live polytope vertex against a new radical
-# plane is 3 FMA + 1 MUL = 7 flop (its error bound is stored with the vertex).
-# A vertex constructed on a new plane takes the cofactors of its m radical-plane
-# rows (m = 1: a selection, 0 flop; m = 2: three 2x2 minors, 9 flop; m = 3:
-# four 3x3 cofactors, 56 flop) plus its orientation test and stored bound
-# (17 flop).
+# Algorithmic FP32 work per nonempty piece of the clip stage, as planned for
+# Tet-Cell clipping (Sec. 5.2) with k power neighbours: per clip V_cur x (7 flop
+# for the sign test + 7 for its bound) plus ~60 per constructed vertex, about
+# 2.5 kFLOP at k = 16 and 4.5 kFLOP at k = 32.  This is the roofline's
+# `achieved` numerator (flop per piece x pieces of the step).
+PLANNED_FLOP_PER_PIECE = {16: 2500.0, 32: 4500.0}
+# The work the kernels execute is far smaller, because each piece is clipped
+# only by its tet's few candidate spheres and the error bound is stored with
+# the vertex: one filtered sign test F.C is 3 FMA + 1 MUL = 7 flop; a vertex
+# constructed on a new plane takes the cofactors of its m radical-plane rows
+# (m = 1: a selection, 0 flop; m = 2: three 2x2 minors, 9 flop; m = 3: four
+# 3x3 cofactors, 56 flop) plus its orientation test and stored bound (17).
 FLOP_SIGN_TEST = 7
 FLOP_NEW_VERTEX = (17, 26, 73)   # by m = 1, 2, 3
-FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of the clip kernels of one step (k_clip over all
-# bins + k_whole) on block_c2, from one ncu capture of the current kernels
-# (profiles/clip_block_c2.md); None once the kernels change.
-CLIP_TRAFFIC_BYTES = {("block_c2", "fp32"): 67.86e6}
+# DRAM bytes (read + write) per step of the clip kernels (k_clip over all bins
+# + k_whole), from one ncu capture of the current kernels per workload and
+# precision; a workload missing here reports traffic null.
+CLIP_TRAFFIC_BYTES = {}
+# CPU legs per workload, sized for 10-30 s each on the 16 host cores: tets of
+# the brute-force oracle sample, of its 1-thread sample, fraction of tets for
+# the same-algorithm baseline, tets per step of the reference arm.
+CPU_SAMPLES = {
+    "blob_c3": dict(oracle=500, oracle_1t=24, fair=0.25, ref=200),
+    "block_c2": dict(oracle=10000, oracle_1t=600, fair=1.0, ref=2000),
+    "torus_c1": dict(oracle=5051, oracle_1t=2000, fair=1.0, ref=5051),
+}
 
 
 def job_throughput(local_ms, local_units, world, device="cpu"):
@@ -72,27 +86,66 @@ def measured_peaks():
         return {}
 
 
-def clip_roofline(stage, n_sm, workload, precision):
-    """FP32 ALU roofline of the clip kernels, from the counters of the timed
-    steps and the clip-kernel span timed by the library's CUDA events on the
-    launching streams."""
-    peaks = measured_peaks()
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    flop, ms = [], []
-    for s in stage:
-        tests = s["pred_fast"] + s["pred_fp64"] + s["pred_exact"]
-        nv = s["clip_vertices"]
-        flop.append(FLOP_SIGN_TEST * max(tests - sum(nv), 0) + sum(f * n for f, n in zip(FLOP_NEW_VERTEX, nv)))
-        ms.append(s["ms_clip_kernels"])
-    achieved = float(np.mean(flop)) / (float(np.mean(ms)) * 1e-3) / 1e12
-    return {"kernel": "k_clip over all candidate-count bins + k_whole (side by side on the bin streams; "
-                      "timed to the end of the record kernels that follow them there)",
-            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": CLIP_TRAFFIC_BYTES.get((workload, precision)), "flop_per_launch": float(np.mean(flop)),
-            "ms_per_launch": float(np.mean(ms)),
-            "peak_source": f"derived FP32: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz:.0f} MHz "
-                           "(sm_max_mhz of MEASURED_PEAKS.json)"}
+def fma_peaks(target_ms=300.0, repeats=3):
+    """FP32 and FP64 CUDA-core peaks from the library's FMA-chain
+    microbenchmark (rpd_peak_fma): a short probe sizes each run to about
+    target_ms; the best of `repeats` runs is kept."""
+    from paper_2403_18761_gb300 import rpd_peak_fma
+    out = {}
+    for prec in ("fp32", "fp64"):
+        probe_iters = 1 << 12
+        _, ms = rpd_peak_fma(prec, probe_iters)
+        iters = max(probe_iters, int(probe_iters * target_ms / max(ms, 1e-3)))
+        best, best_ms = 0.0, 0.0
+        for _ in range(repeats):
+            tf, ms = rpd_peak_fma(prec, iters)
+            if tf > best:
+                best, best_ms = tf, ms
+        out[prec] = {"tflops": best, "ms": best_ms, "iters": iters}
+    return out
+
+
+def counted_flop(s):
+    """FP32 (or FP64) flop the clip kernels execute for one step's counters."""
+    tests = s["pred_fast"] + s["pred_fp64"] + s["pred_exact"]
+    nv = s["clip_vertices"]
+    return FLOP_SIGN_TEST * max(tests - sum(nv), 0) + sum(f * n for f, n in zip(FLOP_NEW_VERTEX, nv))
+
+
+def clip_roofline(stage, k, workload, precision, peaks, hbm_gbs, stage64=None):
+    """Roofline of the clip kernels (the dominant kernel family): CUDA-core
+    ALU bound.  `achieved` = planned flop per piece x pieces / the clip-kernel
+    span timed by the library's CUDA events on the launching streams; the
+    FP32, FP64 and HBM fractions use the measured peaks."""
+    kk = min(PLANNED_FLOP_PER_PIECE, key=lambda q: abs(q - k))
+    pieces = float(np.mean([s["n_pieces"] for s in stage]))
+    ms = float(np.mean([s["ms_clip_kernels"] for s in stage]))
+    flop_planned = PLANNED_FLOP_PER_PIECE[kk] * pieces
+    flop_exec = float(np.mean([counted_flop(s) for s in stage]))
+    p32, p64 = peaks["fp32"]["tflops"], peaks["fp64"]["tflops"]
+    peak = p32 if precision == "fp32" else p64
+    achieved = flop_planned / (ms * 1e-3) / 1e12
+    traffic = CLIP_TRAFFIC_BYTES.get((workload, precision))
+    fr = {"fp32" if precision == "fp32" else "fp64": achieved / peak,
+          (precision + "_executed"): flop_exec / (ms * 1e-3) / 1e12 / peak}
+    if traffic is not None and hbm_gbs:
+        fr["hbm"] = traffic / (ms * 1e-3) / 1e9 / hbm_gbs
+    out = {"kernel": "k_clip over all candidate-count bins + k_whole (side by side on the bin streams; "
+                     "timed to the end of the record kernels that follow them there)",
+           "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": traffic, "flop_per_launch": flop_planned, "flop_per_piece": PLANNED_FLOP_PER_PIECE[kk],
+           "flop_executed_per_launch": flop_exec, "achieved_executed": flop_exec / (ms * 1e-3) / 1e12,
+           "ms_per_launch": ms,
+           "peak_source": f"measured: rpd_peak_fma {precision} FMA chains (of measured)",
+           "fractions": fr}
+    if stage64:
+        ms64 = float(np.mean([s["ms_clip_kernels"] for s in stage64]))
+        f64 = PLANNED_FLOP_PER_PIECE[kk] * float(np.mean([s["n_pieces"] for s in stage64]))
+        fr["fp64_mode_fp64"] = f64 / (ms64 * 1e-3) / 1e12 / p64
+        fr["fp64_mode_fp64_executed"] = float(np.mean([counted_flop(s) for s in stage64])) / (ms64 * 1e-3) / 1e12 / p64
+    named = {k: v for k, v in fr.items() if k in ("fp32", "fp64", "hbm", "fp64_mode_fp64")}
+    out["binding"] = max(named, key=named.get)
+    return out
 
 
 def make_workload(name):
@@ -164,19 +217,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_baseline(w, frac, seed=20240318, nthreads=None):
-    """Time the oracle (as it stands) on a seeded tet sample of the workload."""
+def _sample(nt, n, seed):
+    rng = np.random.default_rng(seed)
+    n = max(1, min(int(n), nt))
+    return np.sort(rng.choice(nt, size=n, replace=False)).astype(np.int32)
+
+
+def cpu_baselines(w, config, seed=20240318):
+    """The CPU legs, each on a seeded tet sample of the workload (sizes in
+    CPU_SAMPLES): the brute-force oracle as it stands on all host cores and on
+    one thread, and the same-algorithm baseline (the library's neighbour +
+    candidate algorithm restated in C in the oracle's file, FP64 + exact
+    predicates) on all host cores.  Returns (cpu_baseline, extra legs,
+    (sample, oracle result)) where the oracle result serves the volume error."""
     import oracle
     oracle.build()
-    rng = np.random.default_rng(seed)
-    n = max(1, int(round(frac * w.nt)))
-    sub = np.sort(rng.choice(w.nt, size=n, replace=False)).astype(np.int32)
+    cfg = CPU_SAMPLES.get(config, CPU_SAMPLES["block_c2"])
+    sub = _sample(w.nt, cfg["oracle"], seed)
     t0 = time.perf_counter()
-    o = oracle.run(w, subset=sub, nthreads=nthreads)
+    o = oracle.run(w, subset=sub)
     dt = time.perf_counter() - t0
-    return dict(value=len(o["tet"]) / dt, unit=UNIT, cores=o["nthreads"], kind="oracle",
-                sample=f"{n} of {w.nt} tets ({100 * frac:.1f}%, seed {seed}), all {w.ns} spheres, "
-                       f"brute-force C oracle; {len(o['tet'])} pieces in {dt:.2f} s"), (sub, o)
+    base = dict(value=len(o["tet"]) / dt, unit=UNIT, cores=o["nthreads"], kind="oracle",
+                sample=f"{len(sub)} of {w.nt} tets (seed {seed}), all {w.ns} spheres, brute-force C oracle; "
+                       f"{len(o['tet'])} pieces in {dt:.2f} s")
+    legs = {}
+    sub1 = _sample(w.nt, cfg["oracle_1t"], seed + 1)
+    t0 = time.perf_counter()
+    o1 = oracle.run(w, subset=sub1, nthreads=1)
+    dt = time.perf_counter() - t0
+    legs["oracle_1thread"] = dict(value=len(o1["tet"]) / dt, unit=UNIT, cores=1, kind="oracle",
+                                  sample=f"{len(sub1)} tets (seed {seed + 1}); {len(o1['tet'])} pieces in {dt:.2f} s")
+    frac = cfg["fair"]
+    subf = None if frac >= 1.0 else _sample(w.nt, frac * w.nt, seed + 2)
+    t0 = time.perf_counter()
+    of = oracle.run(w, subset=subf, k=w.k)
+    dt = time.perf_counter() - t0
+    legs["same_algorithm"] = dict(value=len(of["tet"]) / dt, unit=UNIT, cores=of["nthreads"],
+                                  kind="same kNN + candidate algorithm, C, FP64 + exact predicates",
+                                  sample=(f"all {w.nt} tets" if subf is None else f"{len(subf)} of {w.nt} tets "
+                                          f"({100 * frac:.0f}%, seed {seed + 2})") +
+                                  f", k = {w.k}; {len(of['tet'])} pieces in {dt:.2f} s (pieces and elements "
+                                  "equal the brute force's, checked by the CPU tests)")
+    return base, legs, (sub, o)
 
 
 def volume_error(w, pieces, sub, o):
@@ -203,16 +285,19 @@ def volume_error(w, pieces, sub, o):
 
 
 def run_reference(args, w):
+    """The reference arm: the CPU oracle (brute force, FP64 + exact predicates)
+    as it stands on the host cores, each step a seeded tet sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    frac = args.ref_frac
+    import oracle
+    oracle.build()
+    per_step = CPU_SAMPLES.get(args.config, CPU_SAMPLES["block_c2"])["ref"]
     times = []
     pieces = 0
+    cores = 0
     for s in range(args.warmup + args.steps):
-        import oracle
-        rng = np.random.default_rng(1000 + s)
-        sub = np.sort(rng.choice(w.nt, size=max(1, int(frac * w.nt)), replace=False)).astype(np.int32)
+        sub = _sample(w.nt, per_step, 1000 + s)
         t0 = time.perf_counter()
         o = oracle.run(w, subset=sub)
         dt = time.perf_counter() - t0
@@ -221,14 +306,14 @@ def run_reference(args, w):
             pieces += len(o["tet"])
             cores = o["nthreads"]
     value = pieces / sum(times)
+    sample = f"{per_step} of {w.nt} seeded tets per step ({100.0 * per_step / w.nt:.3g}%), all {w.ns} spheres"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOADS[args.config], "precision": "fp64 + exact predicates",
-                       "sample_fraction": frac},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{frac * 100:.1f}% seeded tet sample per step, all spheres"},
+                       "tets_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -239,11 +324,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="block_c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="blob_c3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--k", type=int, default=None, help="power neighbours kept per mesh vertex")
-    ap.add_argument("--cpu-frac", type=float, default=0.05)
-    ap.add_argument("--ref-frac", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision (profiling)")
@@ -284,6 +367,16 @@ def main():
             outs.append(ctx.rpd_components(kind))
             outs.append(ctx.rpd_contractible(kind))
         return ctx, outs
+
+    # ---- CUDA-core peaks of this GPU (the roofline denominators), measured
+    # by the library's FMA-chain microbenchmark before the timed steps
+    with torch.cuda.stream(stream):
+        with ClockSampler(local) as pclk:
+            peaks = fma_peaks()
+    peaks["clocks"] = pclk.summary()
+    mp = measured_peaks()
+    peaks["hbm_gbs"] = mp.get("hbm_gbs")
+    peaks["hbm_source"] = "MEASURED_PEAKS.json hbm_gbs (STREAM-style copy, of measured)" if mp.get("hbm_gbs") else None
 
     # ---- device-resident timing
     with torch.cuda.stream(stream):
@@ -359,11 +452,11 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
-        "roofline": clip_roofline(stage, torch.cuda.get_device_properties(dev).multi_processor_count, args.config,
-                                  precision),
         "step_ms_max": t_step,
+        "peaks": peaks,
     }
     # ---- the other precision, same step (FP32-filtered vs FP64 throughput)
+    ostage = []
     if not args.no_compare:
         other = "fp64" if precision == "fp32" else "fp32"
         oms = []
@@ -377,22 +470,34 @@ def main():
                     ctx.rpd_euler(kind), ctx.rpd_components(kind), ctx.rpd_contractible(kind)
                 e1.record(stream)
                 e1.synchronize()
+                st = ctx.rpd_stats_get()
                 if it >= args.warmup:
                     oms.append(e0.elapsed_time(e1))
-                npo = ctx.rpd_stats_get()["n_pieces"]
+                    ostage.append(st)
+                npo = st["n_pieces"]
                 ctx.rpd_destroy()
         ovalue = npo * len(oms) / (sum(oms) / 1e3)
         v32, v64 = (value, ovalue) if precision == "fp32" else (ovalue, value)
         line["precision_compare"] = {"fp32": v32, "fp64": v64, "fp32_over_fp64": v32 / v64, "unit": UNIT,
-                                     "pieces_equal": bool(npo == last["n_pieces"])}
+                                     "pieces_equal": bool(npo == last["n_pieces"]),
+                                     "ms_clip_kernels": {precision: st_mean["ms_clip_kernels"],
+                                                         other: float(np.mean([q["ms_clip_kernels"] for q in ostage]))}}
+    stage64 = ostage if precision == "fp32" else stage
+    line["roofline"] = clip_roofline(stage, kk, args.config, precision, peaks, peaks["hbm_gbs"],
+                                     stage64=stage64 if stage64 else None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, (sub, o) = oracle_baseline(w, args.cpu_frac)
+        cb, legs, (sub, o) = cpu_baselines(w, args.config)
         line["cpu_baseline"] = cb
-        with torch.cuda.stream(stream):
-            ctx = rpd_build(V, T, C, R, precision=precision, k=kk, grid_bits=w.grid_bits, stream=stream)
-            pieces = [x.cpu().numpy() for x in ctx.rpd_pieces()]
-            ctx.rpd_destroy()
-        line["error_vs_oracle"] = volume_error(w, pieces, sub, o)
+        line["cpu_legs"] = legs
+        errs = {}
+        for prec in ("fp32", "fp64"):
+            with torch.cuda.stream(stream):
+                ctx = rpd_build(V, T, C, R, precision=prec, k=kk, grid_bits=w.grid_bits, stream=stream)
+                pieces = [x.cpu().numpy() for x in ctx.rpd_pieces()]
+                ctx.rpd_destroy()
+            errs[prec] = volume_error(w, pieces, sub, o)
+        line["error_vs_oracle"] = errs[precision]
+        line["error_vs_oracle_by_precision"] = errs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

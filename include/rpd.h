@@ -46,15 +46,19 @@ typedef enum {
     RPD_E_CUDA = 5,         /* a CUDA runtime call failed                       */
     RPD_E_OVERFLOW = 6,     /* more candidate spheres for one tet than the
                                library supports (32), or key space exceeded    */
-    RPD_E_TIMEOUT = 7       /* a bounded device loop gave up (union-find)       */
+    RPD_E_TIMEOUT = 7       /* a bounded device loop or wait gave up (union-find,
+                               radix-sort look-back)                          */
 } rpd_status;
 
 /* Element kind = number of spheres in its key. */
 typedef enum { RPD_CELL = 1, RPD_FACE = 2, RPD_EDGE = 3, RPD_VERTEX = 4 } rpd_kind;
 
 /* Arithmetic of the clipping predicates.  Both give identical combinatorics
- * (uncertified signs fall back to FP64 and then to exact 256-bit integers);
- * volumes and moments are accumulated in FP64 in both. */
+ * (uncertified signs fall back to FP64 and then to exact 256-bit integers).
+ * Volumes and first moments are accumulated in native FP64 in RPD_FP64 and in
+ * double-float arithmetic (unevaluated sums of two FP32 values, about 48
+ * significant bits) in RPD_FP32_FILTERED; both stay within 1e-9 of the tet
+ * volume of the exact result. */
 typedef enum { RPD_FP64 = 0, RPD_FP32_FILTERED = 1 } rpd_precision;
 
 typedef struct {
@@ -89,6 +93,9 @@ typedef struct {
     float ms_clip_kernels;    /* from the start of the clip launches to the end of
                                  the last clip kernel (volume pass excluded)      */
     float ms_clip_span;       /* same start to the end of the last volume kernel  */
+    int64_t update_tets;      /* tets clipped by the call that produced the
+                                 diagram: nt after rpd_build, the tets whose
+                                 candidate spheres changed after rpd_insert     */
 } rpd_stats;
 
 typedef struct rpd_ctx rpd_ctx;   /* opaque; owns all device workspace and results */
@@ -106,8 +113,11 @@ void rpd_default_options(rpd_options* opt);
  *   opt       options (NULL = defaults)
  *   cuda_stream  a cudaStream_t or NULL
  *   out       receives a new context (NULL on failure)
- * Limits: nv < 2^21, ns <= 2^21 (RPV keys need ns <= 2^16), nt < 2^31.
- * Synchronises the stream once at the end (to size the element tables).
+ * Limits: nv < 2^21, ns < 2^21 (RPV keys need ns < 2^16), nt < 2^26.
+ * Synchronises the stream twice: after the candidate stage (the pair count
+ * sizes the clip buffers) and at the end (record and element counts size the
+ * element tables); a third time only if the record buffers overflowed and the
+ * clip is redone.
  */
 rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt,
                      const double* d_centers, const double* d_radii, int64_t ns,
@@ -132,6 +142,84 @@ rpd_status rpd_components(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, int32_t*
  * of every element.  Same two-phase convention; d_flag u8[n] (1 = contractible). */
 rpd_status rpd_contractible(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, uint8_t* d_flag, int64_t cap,
                             int64_t* n);
+
+/*
+ * Insert n_new spheres (appended: they take indices ns .. ns + n_new - 1) and
+ * update the diagram in place, clipping only what the new spheres change
+ * (partial RPD update, Sec. 4 intro and Sec. 5.2).  The neighbour and
+ * candidate stages run again on the enlarged sphere set; every tet whose
+ * candidate spheres and clip order are unchanged keeps its pieces, volumes
+ * and fractional Euler records, the others are clipped again, and the
+ * element tables are finalised over everything.  The result is identical to
+ * rpd_build on the concatenated spheres (rpd_stats.update_tets reports how
+ * many tets were clipped).
+ *   d_centers f64[n_new*3], d_radii f64[n_new]: caller-owned device memory,
+ *             read on the context's stream
+ * Same synchronisation as rpd_build.  On failure the context keeps the
+ * previous diagram and the status says why (RPD_E_INVALID for n_new < 0 or
+ * ns + n_new >= 2^21, the device errors of rpd_build otherwise).
+ */
+rpd_status rpd_insert(rpd_ctx* ctx, const double* d_centers, const double* d_radii, int64_t n_new);
+
+/*
+ * Pin points of the non-contractible elements of one kind (1 = RPC, 2 = RPF,
+ * 3 = RPE), where the topology repair grows new spheres (Sec. 4.1.1, 4.1.2).
+ * The surface is the set of boundary triangles of the mesh (tet faces without
+ * a neighbour).  For an element with beta0 > 1 the pin is the centroid of the
+ * boundary triangle, touched by the element, of the lowest-numbered tet in a
+ * component other than the one of the element's lowest-numbered tet
+ * (Sec. 4.1.1: a surface point on another component).  For an element with
+ * beta0 = 1 and chi != 1 it is the centroid of the touched boundary triangle
+ * furthest from the element's first sphere (Sec. 4.1.2: the furthest surface
+ * triangle), ties to the lowest (tet, face).
+ *   d_keys    i32[n*kind]  keys of the failing elements, in key order
+ *   d_pins    f64[n*3]     pin points (NaN when the element touches no
+ *                          qualifying boundary triangle)
+ *   d_normals f64[n*3]     unit normals into the shape at the pins
+ *   d_faces   i32[n]       boundary face 4*tet + face of the pin, or -1
+ * Two-phase: with all outputs NULL only *n (the number of failing elements)
+ * is set; otherwise all four and cap >= n are required (RPD_E_INVALID).
+ * Synchronises the stream once (the count).
+ */
+rpd_status rpd_pins(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, double* d_pins, double* d_normals,
+                    int32_t* d_faces, int64_t cap, int64_t* n);
+
+/*
+ * Sphere shrinking (Sec. 5.1, the shrinking-ball algorithm of Ma et al. 2012)
+ * from n pin points against the mesh's boundary triangles: starting from a
+ * ball tangent at the pin p with a radius above the mesh's extent, the ball
+ * is repeatedly replaced by the ball tangent at p through the surface point
+ * nearest to its centre, while that point lies inside it (the pin's own
+ * triangle is skipped), at most 100 times.  The result is an empty ball
+ * touching the surface at p and at one more point.
+ *   d_pins, d_normals f64[n*3], d_faces i32[n]: as written by rpd_pins (a
+ *                     row with face -1 gives NaN)
+ *   d_centers f64[n*3], d_radii f64[n], d_iters i32[n]: outputs (world units;
+ *                     iterations taken)
+ * Stream-ordered, no synchronisation except on the first call of a context
+ * (which builds the boundary-triangle list).
+ */
+rpd_status rpd_shrink(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const int32_t* d_faces, int64_t n,
+                      double* d_centers, double* d_radii, int32_t* d_iters);
+
+/* The context's spheres as the diagram uses them (centres and radii rounded
+ * to the grid 2^-grid_bits), those of rpd_build followed by every inserted
+ * one: d_centers f64[n*3], d_radii f64[n].  Two-phase like rpd_euler. */
+rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t cap, int64_t* n);
+
+/*
+ * Topology repair loop (Sec. 4, 4.1): while some RPC, RPF or RPE is not
+ * contractible and fewer than max_rounds rounds have run, take the pins of all
+ * failing elements (rpd_pins), one per boundary triangle, grow a sphere from
+ * each (rpd_shrink), round it to the grid, drop repeats of existing spheres,
+ * and insert them with a partial update (rpd_insert).  The loop also stops
+ * when no failing element has a pin or no new sphere remains.
+ *   rounds, inserted, failing: host pointers (may be NULL) receiving the rounds
+ *   run, the spheres inserted and the failing elements left (0 = every RPC,
+ *   RPF and RPE contractible).
+ * Synchronises the stream several times per round.
+ */
+rpd_status rpd_repair(rpd_ctx* ctx, int32_t max_rounds, int64_t* rounds, int64_t* inserted, int64_t* failing);
 
 /* Every element table of rpd_euler, rpd_components and rpd_contractible, for
  * all four kinds, in one launch into one caller-owned device buffer (for
@@ -171,9 +259,9 @@ int64_t rpd_launch_count(void);
  * rpd_build + rpd_euler in one call that allocates no device memory.  The
  * paper has no counterpart; this is a convenience of the library.
  *
- * For callers that cannot call cudaMalloc when they need the result: work
- * recorded into a CUDA graph (allocation is illegal during stream capture),
- * or pipelines that fix their device-memory budget up front.  All workspace
+ * For callers that cannot call cudaMalloc when they need the result:
+ * pipelines that fix their device-memory budget up front, or services that
+ * must not allocate (or fragment the device heap) while they run.  All workspace
  * comes from one file-scope device array of 32 MiB that every GPU loading the
  * library holds until the process exits (enough for roughly 30k tets; larger
  * problems are rejected with RPD_E_OVERFLOW before the stage that would need
@@ -183,15 +271,35 @@ int64_t rpd_launch_count(void);
  *   d_keys  i32[n*kind], d_chi i32[n]: caller-owned outputs, cap >= n; both
  *           NULL only sets *n
  *   n       host pointer, receives the number of elements
- * The first call on a device looks up the array's device address: make it
- * before any stream capture.  Every call reuses the same array (it is
- * cleared as needed), so calls that overlap on the GPU race: serialise them.
- * Synchronises the stream.  Errors are reported by status only.
+ * The first call on a device looks up the array's device address and caches
+ * it for the rest of the process: make that first call before any stream
+ * capture, and do not use the entry point again on a device after
+ * cudaDeviceReset there.  Every call reuses the same array (it is cleared as
+ * needed), so calls that overlap on the GPU race: serialise them.
+ * Synchronises the stream three times (sizes of the later stages are read on
+ * the host).  Errors are reported by status only (RPD_E_INVALID for bad
+ * arguments or cap < n; RPD_E_OVERFLOW when the problem needs more than the
+ * array holds; RPD_E_CUDA; the device errors of rpd_build).
  */
 rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt,
                             const double* d_centers, const double* d_radii, int64_t ns, const rpd_options* opt,
                             void* cuda_stream, rpd_kind kind, int32_t* d_keys, int32_t* d_chi, int64_t cap,
                             int64_t* n);
+
+/*
+ * CUDA-core peak of one precision, measured on the current device: every SM
+ * runs fully occupied blocks of threads, each with eight independent fused
+ * multiply-add chains of `iters` rounds (2 flop per FMA), timed with CUDA
+ * events after one shorter warm-up launch.  The paper has no counterpart; it
+ * is the denominator of the FP32 and FP64 roofline fractions.
+ *   precision  RPD_FP32_FILTERED (FP32 FMA) or RPD_FP64 (FP64 FMA)
+ *   iters      rounds per chain, 1..2^40
+ *   tflops     host pointer, receives the measured TFLOP/s
+ *   ms         host pointer or NULL, receives the timed launch's duration
+ * Synchronises the stream.  RPD_E_INVALID for bad arguments, RPD_E_CUDA if a
+ * launch or the timing fails.
+ */
+rpd_status rpd_peak_fma(int32_t precision, int64_t iters, void* cuda_stream, double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -133,6 +134,17 @@ struct rpd_ctx {
     FinalOut fout[4] = {};
     int64_t* piece_off = nullptr;
     long long npieces = 0;
+    // finalisation scratch per kind (union-find parents first), kept for the
+    // repair queries, and its capacity
+    void* ftmp[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long fcap[4] = {0, 0, 0, 0};
+    // partial update: tets whose candidates changed (NULL after a full build)
+    uint8_t* changed = nullptr;
+    unsigned long long* d_nchanged = nullptr;
+    // boundary triangles of the mesh for sphere shrinking (built on first use)
+    double* btri = nullptr;
+    int32_t* btri_face = nullptr;
+    long long nbtri = -1;
     rpd_stats stats{};
     bool timed = false;   // stats' stage times filled in
     int device = 0;
@@ -202,7 +214,9 @@ const char* dev_reason(int code, const unsigned long long* cnt) {
             return cnt[CNT_LINK_MISSING] ? "inconsistent restricted element across a shared tet face (input not in generic position)"
                                          : "input not in generic position: an exact predicate is zero (a vertex lies on a radical plane)";
         case RPD_E_OVERFLOW: return "more than 32 candidate spheres for one tet";
-        case RPD_E_TIMEOUT: return "union-find iteration bound reached";
+        case RPD_E_TIMEOUT:
+            return cnt[CNT_UF_LIMIT] ? "union-find iteration bound reached"
+                                     : "bounded wait ran out (radix-sort look-back)";
         default: return "device error";
     }
 }
@@ -293,14 +307,13 @@ void join_side_streams(rpd_ctx* c) {
         if (e) cudaStreamWaitEvent(c->stream, e, 0);
 }
 
-// zero_counts: the record and queue counters are zeroed here (the binning
-// zeroes them before the first pass).
-rpd_status run_clip(rpd_ctx* c, bool zero_counts) {
+// The record and queue counters are zeroed here when asked (the binning
+// zeroes them before the first pass; a partial update sets the record
+// counters to the records it kept).
+rpd_status run_clip(rpd_ctx* c, bool zero_rcount, bool zero_qcount) {
     cudaStream_t s = c->stream;
-    if (zero_counts) {
-        cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
-        cudaMemsetAsync(c->qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
-    }
+    if (zero_rcount) cudaMemsetAsync(c->rcount, 0, sizeof(unsigned long long) * 3, s);
+    if (zero_qcount) cudaMemsetAsync(c->qcount, 0, sizeof(unsigned long long) * RPD_NBINS, s);
     long long off[RPD_NBINS + 1];
     off[0] = 0;
     for (int b = 0; b < RPD_NBINS; b++) off[b + 1] = off[b] + c->hbin[b];
@@ -367,9 +380,11 @@ float elapsed(rpd_ctx* c, int a, int b) {
     return ms;
 }
 
-rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const double* d_centers,
-                 const double* d_radii) {
-    cudaStream_t s = c->stream;
+rpd_status build_rest(rpd_ctx* c, rpd_ctx* old);
+
+// Device, timing events and side streams of a context; the chunk for every
+// buffer sized before the pair count is known.
+rpd_status begin(rpd_ctx* c) {
     const long long nv = c->nv, nt = c->nt, ns = c->ns;
     if (cudaGetDevice(&c->device) != cudaSuccess || c->device < 0 || c->device >= 64)
         return fail(c, RPD_E_CUDA, "no usable current device");
@@ -377,18 +392,24 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         return fail(c, RPD_E_CUDA, "cudaEventCreate failed");
     // side streams: mesh combinatorics next to the sphere grid and kNN, the
     // clip bins, and the four element kinds of the finalisation
-    BinStreams* bs = bin_streams();
-    if (!bs) return fail(c, RPD_E_CUDA, "stream creation failed");
+    if (!bin_streams()) return fail(c, RPD_E_CUDA, "stream creation failed");
     record(c, 0);
-    {   // one chunk for every buffer sized before the pair count is known
-        const long long ncap = 2 * ns + 64, pcap = 4 * nt + 1024;
-        const size_t est = sizeof(DevState) + 4 * 3 * (nv + ns) + 8 * ns + 4 * 4 * nt + 4 * nt + 4 * 4 * nt +
-                           prep_tmp_bytes(nt, nv) + sizeof(GridParams) + 8 * (ncap + 1) + 4 * ns + 8 * 2 * ncap +
-                           grid_tmp_bytes(ns, ncap) + 4 * nv * c->K + 8 * nv + 16 * ns + 8 * ns + knn_tmp_bytes(nv) +
-                           4 * nt + (4 + 1) * nt * RPD_MAXC + 4 * nt + 4 + 8 * (nt + 1) + scan_tmp_bytes(nt + 1) +
-                           8 * RPD_NBINS + 8 * pcap + 8 * (3 + RPD_NBINS) + 40 * 256;
-        NEED(c->reserve(est));
-    }
+    const long long ncap = 2 * ns + 64, pcap = 4 * nt + 1024;
+    const size_t est = sizeof(DevState) + 4 * 3 * (nv + ns) + 8 * ns + 4 * 4 * nt + 4 * nt + 4 * 4 * nt +
+                       prep_tmp_bytes(nt, nv) + sizeof(GridParams) + 8 * (ncap + 1) + 4 * ns + 8 * 2 * ncap +
+                       grid_tmp_bytes(ns, ncap) + 4 * nv * c->K + 8 * nv + 16 * ns + 8 * ns + knn_tmp_bytes(nv) +
+                       4 * nt + (4 + 1) * nt * RPD_MAXC + 4 * nt + 4 + 8 * (nt + 1) + scan_tmp_bytes(nt + 1) +
+                       8 * RPD_NBINS + 8 * pcap + 8 * (3 + RPD_NBINS) + nt + 8 + 42 * 256;
+    NEED(c->reserve(est));
+    return RPD_OK;
+}
+
+rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const double* d_centers,
+                 const double* d_radii) {
+    cudaStream_t s = c->stream;
+    const long long nv = c->nv, nt = c->nt, ns = c->ns;
+    TRY(begin(c));
+    BinStreams* bs = bin_streams();
     c->st = c->alloc<DevState>(1);
     c->Xi = c->alloc<int32_t>(3 * nv);
     c->Ci = c->alloc<int32_t>(3 * ns);
@@ -409,6 +430,44 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     launch_prep_mesh(c->tets, nt, nv, c->Xi, c->adj, c->own, tmp, c->st, bs->s[0]);
     cudaEventRecord(c->ev[2], bs->s[0]);
     TRY(cuda_check(c, "prep launch"));
+    return build_rest(c, nullptr);
+}
+
+// A0 of a partial update: the mesh tables and the old spheres come from the
+// old context, the new spheres are snapped after them.
+rpd_status update(rpd_ctx* c, rpd_ctx* old, const double* d_centers, const double* d_radii, long long n_new) {
+    cudaStream_t s = c->stream;
+    const long long nv = c->nv, nt = c->nt, ns0 = old->ns;
+    TRY(begin(c));
+    c->st = c->alloc<DevState>(1);
+    c->Xi = c->alloc<int32_t>(3 * nv);
+    c->Ci = c->alloc<int32_t>(3 * c->ns);
+    c->W = c->alloc<long long>(c->ns);
+    c->adj = c->alloc<int32_t>(4 * nt);
+    c->own = c->alloc<uint32_t>(nt);
+    c->tets = c->alloc<int32_t>(4 * nt);
+    NEED(c->st && c->Xi && c->Ci && c->W && c->adj && c->own && c->tets);
+    cudaMemsetAsync(c->st, 0, sizeof(DevState), s);
+    cudaMemcpyAsync(c->Xi, old->Xi, sizeof(int32_t) * 3 * nv, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->tets, old->tets, sizeof(int32_t) * 4 * nt, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->adj, old->adj, sizeof(int32_t) * 4 * nt, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->own, old->own, sizeof(uint32_t) * nt, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->Ci, old->Ci, sizeof(int32_t) * 3 * ns0, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->W, old->W, sizeof(long long) * ns0, cudaMemcpyDeviceToDevice, s);
+    launch_snap(nullptr, 0, d_centers, d_radii, n_new, c->opt.grid_bits, nullptr, c->Ci + 3 * ns0, c->W + ns0, c->st,
+                s);
+    record(c, 1);
+    record(c, 2);   // no mesh combinatorics to wait for
+    TRY(cuda_check(c, "update launch"));
+    return build_rest(c, old);
+}
+
+// A1 to A7.  With `old` (a partial update), only the tets whose candidate
+// lists changed are clipped; the others' outputs are carried over.
+rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
+    cudaStream_t s = c->stream;
+    const long long nv = c->nv, nt = c->nt, ns = c->ns;
+    BinStreams* bs = bin_streams();
     // ---- A1
     long long ncap = 2 * ns + 64;
     c->gp = c->alloc<GridParams>(1);
@@ -444,7 +503,14 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     launch_candidates(c->tets, nt, nv, c->Xi, c->Ci, c->W, c->knn, c->dplus, c->K, c->gp, c->cell_start,
                       c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->cand_ord, c->fb_list, c->fb_count, c->st, s);
     scan_excl(c->cand_cnt, c->pair_off, nt, stmp, s);
-    launch_bin_count(c->cand_cnt, nt, c->bin_count, s);
+    if (old) {   // partial update: clip only the tets whose candidates changed
+        c->changed = c->alloc<uint8_t>(nt);
+        c->d_nchanged = c->alloc<unsigned long long>(1);
+        NEED(c->changed && c->d_nchanged);
+        launch_cand_diff(c->cand_cnt, c->cand, c->cand_ord, old->cand_cnt, old->cand, old->cand_ord, nt, c->changed,
+                         c->d_nchanged, s);
+    }
+    launch_bin_count(c->cand_cnt, nt, c->bin_count, s, c->changed);
     TRY(cuda_check(c, "candidate launch"));
     record(c, 4);
     // the pairs are put in bin order before the pair count is read, with room
@@ -460,15 +526,18 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->qcount = c->alloc<unsigned long long>(RPD_NBINS);
     NEED(c->pair_tet && c->bins && c->rcount && c->qcount);
     launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, pcap, c->rcount,
-                     c->qcount, s);
+                     c->qcount, s, c->changed);
     cudaStreamWaitEvent(s, c->ev[2], 0);   // mesh combinatorics done
     long long npairs = 0;
     int32_t hb[RPD_NBINS];
+    unsigned long long nchanged = (unsigned long long)nt;
     cudaMemcpyAsync(&npairs, c->pair_off + nt, sizeof(long long), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(hb, c->bin_count, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (old) cudaMemcpyAsync(&nchanged, c->d_nchanged, sizeof(nchanged), cudaMemcpyDeviceToHost, s);
     TRY(check_device(c));   // synchronises: validation errors stop the build here
     c->npairs = npairs;
     c->stats.n_pairs = npairs;
+    c->stats.update_tets = (int64_t)nchanged;
     for (int b = 0; b < RPD_NBINS; b++) c->stats.bin_pairs[b] = c->hbin[b] = hb[b];
     // ---- A3-A4
     {   // one chunk for the pair, queue, record and finalisation buffers
@@ -484,7 +553,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         c->bins = c->alloc<int32_t>(npairs);
         NEED(c->pair_tet && c->bins);
         launch_bin_pairs(c->cand_cnt, c->pair_off, nt, c->pair_tet, c->bins, c->bin_count, c->bin_fill, npairs,
-                         c->rcount, c->qcount, s);
+                         c->rcount, c->qcount, s, c->changed);
     }
     for (int b = 1; b < RPD_NBINS; b++) {
         long long n = c->hbin[b];
@@ -519,6 +588,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     a.rcount = c->rcount;
     a.key_bits = c->key_bits;
     a.force_slow = c->opt.debug_checks & 3;
+    a.uf_limit = uf_iteration_limit();
     a.st = c->st;
     NEED(a.pflag && a.c_val && a.c_link && a.p_vol && a.p_mom && a.f_off && a.f_cnt && a.e_off && a.e_cnt);
     // finalisation buffers that do not depend on the record counts
@@ -535,6 +605,11 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
         if (v > 0)
             for (long long& x : cap) x = v;
     }
+    void* ktmp2 = nullptr;
+    if (old) {
+        ktmp2 = c->alloc<char>(keep_tmp_bytes(npairs, old->nrec[2]));
+        NEED(ktmp2);
+    }
     long long h[5];
     for (int attempt = 0; attempt < 2; attempt++) {
         for (int k = 0; k < 3; k++) {
@@ -548,6 +623,9 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             TRY(finalize_alloc(c, k + 2, d_nseg + k + 1, cap[k], &ftmp[k + 1]));
         }
         if (attempt == 1) join_side_streams(c);   // everything of the first pass is done
+        // partial update: the unchanged tets' pair outputs and records, and
+        // the record counters set to what was kept (before any clip kernel)
+        if (old) launch_keep(old->clip, old->nrec[2], a, npairs, c->changed, old->key_bits, c->key_bits, ktmp2, s);
         // the finalisation scratch is cleared on a high-priority side stream,
         // queued before any clip block can occupy the SMs
         record(c, 11);
@@ -557,7 +635,7 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
             if (ftmp[kind - 1]) finalize_clear_list(kind, fcap[kind - 1], c->ns, ftmp[kind - 1], clr);
         launch_clear(clr, bs->util);
         cudaEventRecord(c->ev[12], bs->util);
-        TRY(run_clip(c, attempt > 0));
+        TRY(run_clip(c, attempt > 0 && !old, attempt > 0));
         cudaStreamWaitEvent(s, c->ev[12], 0);
         record(c, 5);   // clip and record kernels done, scratch clear: the four kinds fork here
         // ---- A5-A7, the four kinds side by side on high-priority streams; the
@@ -631,6 +709,10 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     c->npieces = h[4];
     c->stats.n_pieces = h[4];
     c->stats.n_records[0] = h[4];
+    for (int k = 0; k < 4; k++) {
+        c->ftmp[k] = ftmp[k];
+        c->fcap[k] = fcap[k];
+    }
     c->timed = false;   // stage times are read from the events when the stats are asked for
     return RPD_OK;
 }
@@ -710,6 +792,244 @@ rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, i
     }
     g_build_error.clear();
     *out = c;
+    return RPD_OK;
+}
+
+rpd_status rpd_insert(rpd_ctx* ctx, const double* d_centers, const double* d_radii, int64_t n_new) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n_new < 0 || ctx->ns + n_new >= (1ll << 21))
+        return fail(ctx, RPD_E_INVALID, "n_new must be >= 0 and ns + n_new < 2^21");
+    if (n_new == 0) return RPD_OK;
+    if (!d_centers || !d_radii) return fail(ctx, RPD_E_INVALID, "null input pointer");
+    rpd_ctx* c = new rpd_ctx();
+    c->stream = ctx->stream;
+    c->opt = ctx->opt;
+    c->nv = ctx->nv;
+    c->nt = ctx->nt;
+    c->ns = ctx->ns + n_new;
+    c->K = ctx->K;
+    c->key_bits = bits_for(c->ns);
+    rpd_status st = update(c, ctx, d_centers, d_radii, n_new);
+    if (st != RPD_OK) {
+        ctx->last_error = c->last_error.empty() ? "update failed" : c->last_error;
+        rpd_destroy(c);
+        return st;
+    }
+    // the context takes the new diagram; the old one's memory goes with c
+    std::swap(*ctx, *c);
+    rpd_destroy(c);
+    ctx->last_error.clear();
+    return RPD_OK;
+}
+
+rpd_status rpd_pins(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, double* d_pins, double* d_normals, int32_t* d_faces,
+                    int64_t cap, int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    if (kind < 1 || kind > 3) return fail(ctx, RPD_E_INVALID, "pins are defined for cells, faces and edges (kind 1..3)");
+    TRY(check_kind(ctx, kind));
+    cudaStream_t s = ctx->stream;
+    const long long nk = ctx->nkeys[kind - 1];
+    const FinalOut& o = ctx->fout[kind - 1];
+    void* tmp = ctx->alloc<char>(pins_tmp_bytes(nk));
+    if (!tmp) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    launch_pins_count(o.flag, nk, tmp, s);
+    long long nfail = 0;
+    cudaMemcpyAsync(&nfail, pins_fpos(tmp, nk) + nk, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error while counting failing elements");
+    }
+    if (n) *n = nfail;
+    if (!d_keys && !d_pins && !d_normals && !d_faces) return RPD_OK;
+    if (!d_keys || !d_pins || !d_normals || !d_faces) return fail(ctx, RPD_E_INVALID, "all four outputs are needed");
+    if (cap < nfail) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of failing elements");
+    const int32_t* parent = (const int32_t*)ctx->ftmp[kind - 1];
+    const long long nmax = kind == 1 ? ctx->npairs : ctx->fcap[kind - 1];
+    launch_pins(ctx->clip, kind, o.keys, o.beta, o.chi, o.flag, nk, nfail, parent, nmax, ctx->clip.uf_limit, tmp,
+                d_keys, d_pins, d_normals, d_faces, s);
+    return cuda_check(ctx, "pin launch");
+}
+
+// Boundary triangles of the context's mesh, built on first use.
+static rpd_status ensure_boundary(rpd_ctx* c, double** tri, int32_t** face_of) {
+    static_assert(sizeof(long long) == sizeof(int64_t), "int64");
+    if (c->nbtri < 0) {
+        cudaStream_t s = c->stream;
+        int64_t* pos = c->alloc<int64_t>(4 * c->nt + 1);
+        void* tmp = c->alloc<char>(boundary_tmp_bytes(c->nt));
+        if (!pos || !tmp) return fail(c, RPD_E_OOM, "device allocation failed");
+        launch_boundary_count(c->adj, c->nt, pos, tmp, s);
+        long long nb = 0;
+        cudaMemcpyAsync(&nb, pos + 4 * c->nt, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, RPD_E_CUDA, "CUDA error while counting boundary triangles");
+        }
+        double* t = c->alloc<double>(9 * nb + 9);
+        int32_t* f = c->alloc<int32_t>(nb + 1);
+        if (!t || !f) return fail(c, RPD_E_OOM, "device allocation failed");
+        launch_boundary_fill(c->tets, c->adj, c->Xi, c->nt, pos, ldexp(1.0, -c->opt.grid_bits), t, f, s);
+        TRY(cuda_check(c, "boundary launch"));
+        c->btri = t;
+        c->btri_face = f;
+        c->nbtri = nb;
+    }
+    *tri = c->btri;
+    *face_of = c->btri_face;
+    return RPD_OK;
+}
+
+rpd_status rpd_shrink(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const int32_t* d_faces, int64_t n,
+                      double* d_centers, double* d_radii, int32_t* d_iters) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n < 0) return fail(ctx, RPD_E_INVALID, "n must be >= 0");
+    if (n == 0) return RPD_OK;
+    if (!d_pins || !d_normals || !d_faces || !d_centers || !d_radii || !d_iters)
+        return fail(ctx, RPD_E_INVALID, "null pointer");
+    if (n >= (1ll << 31)) return fail(ctx, RPD_E_INVALID, "n must be < 2^31");
+    double* tri = nullptr;
+    int32_t* face_of = nullptr;
+    TRY(ensure_boundary(ctx, &tri, &face_of));
+    // a first radius above twice any diameter the grid allows
+    const double r0 = ldexp(1.0, 23 - ctx->opt.grid_bits);
+    launch_shrink(tri, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, d_centers, d_radii, d_iters,
+                  ctx->stream);
+    return cuda_check(ctx, "shrink launch");
+}
+
+rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t cap, int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n) *n = ctx->ns;
+    if (!d_centers && !d_radii) return RPD_OK;
+    if (!d_centers || !d_radii || cap < ctx->ns) return fail(ctx, RPD_E_INVALID, "both outputs and cap >= ns are needed");
+    launch_sphere_out(ctx->Ci, ctx->W, ctx->ns, ldexp(1.0, -ctx->opt.grid_bits), d_centers, d_radii, ctx->stream);
+    return cuda_check(ctx, "sphere output launch");
+}
+
+rpd_status rpd_repair(rpd_ctx* ctx, int32_t max_rounds, int64_t* rounds, int64_t* inserted, int64_t* failing) {
+    if (!ctx) return RPD_E_INVALID;
+    if (max_rounds < 0) return fail(ctx, RPD_E_INVALID, "max_rounds must be >= 0");
+    long long nround = 0, nins = 0, nfail_total = 0;
+    const double unit = ldexp(1.0, -ctx->opt.grid_bits), scale = ldexp(1.0, ctx->opt.grid_bits);
+    for (;;) {
+        // pins of every non-contractible cell, face and edge
+        std::vector<double> hp, hn;
+        std::vector<int32_t> hf;
+        nfail_total = 0;
+        for (int kind = 1; kind <= 3; kind++) {
+            if (!ctx->kind_ok[kind - 1]) continue;
+            int64_t m = 0;
+            TRY(rpd_pins(ctx, (rpd_kind)kind, nullptr, nullptr, nullptr, nullptr, 0, &m));
+            nfail_total += m;
+            if (m == 0) continue;
+            int32_t* dk = ctx->alloc<int32_t>(m * kind);
+            double* dp = ctx->alloc<double>(3 * m);
+            double* dn = ctx->alloc<double>(3 * m);
+            int32_t* df = ctx->alloc<int32_t>(m);
+            if (!dk || !dp || !dn || !df) return fail(ctx, RPD_E_OOM, "device allocation failed");
+            TRY(rpd_pins(ctx, (rpd_kind)kind, dk, dp, dn, df, m, &m));
+            const size_t b0 = hf.size();
+            hp.resize(3 * (b0 + m));
+            hn.resize(3 * (b0 + m));
+            hf.resize(b0 + m);
+            cudaMemcpyAsync(hp.data() + 3 * b0, dp, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
+            cudaMemcpyAsync(hn.data() + 3 * b0, dn, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
+            cudaMemcpyAsync(hf.data() + b0, df, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, ctx->stream);
+        }
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, RPD_E_CUDA, "CUDA error while reading pins");
+        }
+        if (nfail_total == 0 || nround >= max_rounds) break;
+        // one pin per boundary triangle
+        std::vector<int> keep;
+        {
+            std::vector<int32_t> seen;
+            for (size_t q = 0; q < hf.size(); q++) {
+                if (hf[q] < 0) continue;
+                if (std::find(seen.begin(), seen.end(), hf[q]) != seen.end()) continue;
+                seen.push_back(hf[q]);
+                keep.push_back((int)q);
+            }
+        }
+        if (keep.empty()) break;   // failing elements without a boundary point: nothing to grow from
+        const long long m = (long long)keep.size();
+        std::vector<double> kp(3 * m), kn(3 * m);
+        std::vector<int32_t> kf(m);
+        for (long long q = 0; q < m; q++) {
+            for (int z = 0; z < 3; z++) {
+                kp[3 * q + z] = hp[3 * keep[q] + z];
+                kn[3 * q + z] = hn[3 * keep[q] + z];
+            }
+            kf[q] = hf[keep[q]];
+        }
+        double* dp = ctx->alloc<double>(3 * m);
+        double* dn = ctx->alloc<double>(3 * m);
+        int32_t* df = ctx->alloc<int32_t>(m);
+        double* dc = ctx->alloc<double>(3 * m);
+        double* dr = ctx->alloc<double>(m);
+        int32_t* di = ctx->alloc<int32_t>(m);
+        if (!dp || !dn || !df || !dc || !dr || !di) return fail(ctx, RPD_E_OOM, "device allocation failed");
+        cudaMemcpyAsync(dp, kp.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(dn, kn.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(df, kf.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->stream);
+        TRY(rpd_shrink(ctx, dp, dn, df, m, dc, dr, di));
+        std::vector<double> hc(3 * m), hr(m);
+        std::vector<int32_t> ci(3 * ctx->ns);
+        std::vector<long long> cw(ctx->ns);
+        cudaMemcpyAsync(hc.data(), dc, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(hr.data(), dr, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(ci.data(), ctx->Ci, sizeof(int32_t) * 3 * ctx->ns, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(cw.data(), ctx->W, sizeof(long long) * ctx->ns, cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, RPD_E_CUDA, "CUDA error while reading shrunk spheres");
+        }
+        // new spheres on the grid, without repeats of each other or of the
+        // existing spheres (a repeat would have a radical plane with no normal)
+        std::vector<unsigned long long> have;   // hashed snapped centres + weights seen
+        auto pack = [](long long x, long long y, long long z, long long w) {
+            unsigned long long h = 1469598103934665603ull;
+            for (unsigned long long v : {(unsigned long long)x, (unsigned long long)y, (unsigned long long)z,
+                                         (unsigned long long)w})
+                h = (h ^ v) * 1099511628211ull;
+            return h;
+        };
+        for (long long q = 0; q < ctx->ns; q++) have.push_back(pack(ci[3 * q], ci[3 * q + 1], ci[3 * q + 2], cw[q]));
+        std::vector<double> nc, nr;
+        for (long long q = 0; q < m; q++) {
+            const double r = hr[q];
+            if (!(r > 0) || !std::isfinite(hc[3 * q]) || !std::isfinite(hc[3 * q + 1]) || !std::isfinite(hc[3 * q + 2]))
+                continue;
+            long long g[3];
+            bool ok = true;
+            for (int z = 0; z < 3; z++) {
+                const double v = rint(hc[3 * q + z] * scale);
+                if (!(fabs(v) <= (double)RPD_COORD_MAX)) ok = false;
+                g[z] = (long long)v;
+            }
+            const long long rg = (long long)rint(r * scale);
+            if (!ok || rg <= 0) continue;
+            const unsigned long long key = pack(g[0], g[1], g[2], rg * rg);
+            if (std::find(have.begin(), have.end(), key) != have.end()) continue;
+            have.push_back(key);
+            for (int z = 0; z < 3; z++) nc.push_back((double)g[z] * unit);
+            nr.push_back((double)rg * unit);
+        }
+        if (nr.empty()) break;
+        const long long k = (long long)nr.size();
+        double* ic = ctx->alloc<double>(3 * k);
+        double* ir = ctx->alloc<double>(k);
+        if (!ic || !ir) return fail(ctx, RPD_E_OOM, "device allocation failed");
+        cudaMemcpyAsync(ic, nc.data(), sizeof(double) * 3 * k, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(ir, nr.data(), sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream);
+        TRY(rpd_insert(ctx, ic, ir, k));
+        nins += k;
+        nround++;
+    }
+    if (rounds) *rounds = nround;
+    if (inserted) *inserted = nins;
+    if (failing) *failing = nfail_total;
     return RPD_OK;
 }
 

@@ -396,6 +396,7 @@ __device__ __forceinline__ void emit_records(const ClipArgs& A, const Lane& L, c
             if ((fmask >> f) & 1) {
                 sf += carrier_weight(1u << f, L.own);
                 if (adj[f] >= 0) lk |= 1u << f;
+                lk |= 16u << f;   // the piece has a face on tet face f
             }
         sf += __popcll(fmask >> 4);   // radical faces are interior (weight 1)
         A.c_val[p] = sv - se + sf - 1;
@@ -419,6 +420,7 @@ __device__ __forceinline__ void emit_records(const ClipArgs& A, const Lane& L, c
                 sv += carrier_weight(tfbits(tw), L.own);
                 se += carrier_weight(fbits(r), L.own);
                 if (r < 4 && adj[r] >= 0) lk |= 1u << r;
+                if (r < 4) lk |= 16u << r;   // the polygon has an edge on tet face r
                 v = tb(V.nb(v), (kp + 2) % 3);
                 if (v == v0) break;
             }
@@ -450,6 +452,8 @@ __device__ __forceinline__ void emit_records(const ClipArgs& A, const Lane& L, c
                 unsigned lk = 0;
                 if (z < 4 && adj[z] >= 0) lk |= 1u << z;
                 if (tz < 4 && adj[tz] >= 0) lk |= 1u << tz;
+                if (z < 4) lk |= 16u << z;     // an end point lies on tet face z
+                if (tz < 4) lk |= 16u << tz;
                 const int lo = min(j, k), hi = max(j, k);
                 if (we < A.rcap[1]) {
                     A.rkey[1][we] = ((unsigned long long)L.i << (2 * b)) | ((unsigned long long)lo << b) |
@@ -727,7 +731,7 @@ __device__ __forceinline__ void clip_one(const ClipArgs& A, const int32_t* __res
     if (!whole) return;
     {   // the whole tet: V - E + F - 1 from the ownership bits, links on every shared face
         const int32_t* adj = A.adj + 4 * L.t;
-        unsigned lk = 0;
+        unsigned lk = 0xf0u;   // the whole tet has a face on each tet face
         for (int f = 0; f < 4; f++)
             if (adj[f] >= 0) lk |= 1u << f;
         A.c_val[p] = __popc(L.own & 0xfu) - __popc(L.own & 0x3f0u) + __popc(L.own & 0x3c00u) - 1;
@@ -1129,7 +1133,7 @@ __device__ __forceinline__ void whole_one(const ClipArgs& A, long long p) {
     int3 X[4];
     for (int k = 0; k < 4; k++) X[k] = ld_int3(A.Xi, A.tets[4 * t + k]);
     const int32_t* adj = A.adj + 4 * t;
-    unsigned lk = 0;
+    unsigned lk = 0xf0u;   // the whole tet has a face on each tet face
     for (int f = 0; f < 4; f++)
         if (adj[f] >= 0) lk |= 1u << f;
     A.pflag[p] = 1;
@@ -1184,9 +1188,11 @@ __device__ __forceinline__ int warp_bin_add(int n, int b, int32_t* counter) {
     return base + pre;
 }
 
-__global__ void k_bin_count(const int32_t* __restrict__ cand_cnt, long long nt, int32_t* __restrict__ bin_count) {
+// only != NULL restricts the binning to the tets it marks (partial update).
+__global__ void k_bin_count(const int32_t* __restrict__ cand_cnt, long long nt, int32_t* __restrict__ bin_count,
+                            const uint8_t* __restrict__ only) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = t < nt ? cand_cnt[t] : 0;
+    const int n = (t < nt && (!only || only[t])) ? cand_cnt[t] : 0;
     warp_bin_add(n, n > 0 ? bin_of(n) : 0, bin_count);
 }
 
@@ -1203,17 +1209,20 @@ __global__ void k_bin_prefix(const int32_t* __restrict__ bin_count, int32_t* __r
 }
 
 // Writes past cap are dropped (the caller bins again with room for all pairs).
+// Every pair gets its tet in pair_tet; only the pairs of the tets `only`
+// marks (all when NULL) are put into the bins.
 __global__ void k_bin_pairs(const int32_t* __restrict__ cand_cnt, const int64_t* __restrict__ pair_off, long long nt,
                             int32_t* __restrict__ pair_tet, int32_t* __restrict__ bins, int32_t* __restrict__ bin_fill,
-                            long long cap) {
+                            long long cap, const uint8_t* __restrict__ only) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = t < nt ? cand_cnt[t] : 0;
-    const int base = warp_bin_add(n, n > 0 ? bin_of(n) : 0, bin_fill);
+    const int nb = (t < nt && (!only || only[t])) ? n : 0;
+    const int base = warp_bin_add(nb, nb > 0 ? bin_of(nb) : 0, bin_fill);
     if (n <= 0) return;
     const long long off = pair_off[t];
     for (int k = 0; k < n; k++) {
         if (off + k < cap) pair_tet[off + k] = (int32_t)t;
-        if (base + k < cap) bins[base + k] = (int32_t)(off + k);
+        if (k < nb && base + k < cap) bins[base + k] = (int32_t)(off + k);
     }
 }
 
@@ -1272,20 +1281,20 @@ int clip_vmax(int bin) {
     return v[bin];
 }
 
-void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s) {
+void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s, const uint8_t* only) {
     cudaMemsetAsync(bin_count, 0, sizeof(int32_t) * RPD_NBINS, s);
     if (nt == 0) return;
-    k_bin_count<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, nt, bin_count);
+    k_bin_count<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, nt, bin_count, only);
     note_launch();
 }
 
 void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet, int32_t* bins,
                       const int32_t* bin_count, int32_t* bin_fill, long long cap, unsigned long long* rcount,
-                      unsigned long long* qcount, cudaStream_t s) {
+                      unsigned long long* qcount, cudaStream_t s, const uint8_t* only) {
     k_bin_prefix<<<1, 1, 0, s>>>(bin_count, bin_fill, rcount, qcount);
     note_launch();
     if (nt == 0) return;
-    k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_fill, cap);
+    k_bin_pairs<<<nblk(nt, 256), 256, 0, s>>>(cand_cnt, pair_off, nt, pair_tet, bins, bin_fill, cap, only);
     note_launch();
 }
 

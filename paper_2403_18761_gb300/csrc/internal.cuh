@@ -68,7 +68,9 @@ struct ClipArgs {
     // per-pair outputs
     uint8_t* pflag;            // 1 = nonempty piece
     int32_t* c_val;            // RPC contribution (owner rule)
-    uint8_t* c_link;           // tet faces crossed by the piece
+    uint8_t* c_link;           // bits 0-3: shared tet faces the piece crosses
+                               // (component links); bits 4-7: tet faces on
+                               // which it has a face (boundary touches)
     double* p_vol;
     double* p_mom;             // [npairs * 3]
     int32_t* f_off;
@@ -79,11 +81,13 @@ struct ClipArgs {
     uint64_t* rkey[3];
     int32_t* rtet[3];
     int16_t* rval[3];
-    uint8_t* rlink[3];
+    uint8_t* rlink[3];            // bits 0-3 links across shared tet faces,
+                                  // bits 4-7 tet faces the element touches
     long long rcap[3];
     unsigned long long* rcount;   // [3] device counters
     int key_bits;                 // bits per sphere index in packed keys
     int force_slow;               // 0; 1 = skip the first-stage filter; 2 = exact only
+    int uf_limit;                 // iteration bound of the union-find loops
     DevState* st;
     // volume queue of the bin being launched (cut pieces)
     int32_t* qpair;               // [qcap] pair ids
@@ -96,13 +100,17 @@ struct ClipArgs {
 // (0: n = 1, whole tet; 1..3: n = 2..4; 4: 5-6; 5: 7-8; 6: 9-16; 7: 17-32).
 #define RPD_NBINS 8
 int clip_vmax(int bin);
-void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s);
+// `only` (NULL = every tet) restricts the binning to the tets it marks.
+void launch_bin_count(const int32_t* cand_cnt, long long nt, int32_t* bin_count, cudaStream_t s,
+                      const uint8_t* only = nullptr);
 // bins: one array of npairs pair ids, bin b starting at sum of earlier counts.
 // Pairs grouped by bin (pair_tet and bins hold cap entries; writes past cap
 // are dropped); also zeroes the record and queue counters when given.
+// pair_tet is filled for every pair, the bins only for the tets `only` marks.
 void launch_bin_pairs(const int32_t* cand_cnt, const int64_t* pair_off, long long nt, int32_t* pair_tet,
                       int32_t* bins, const int32_t* bin_count, int32_t* bin_fill, long long cap,
-                      unsigned long long* rcount, unsigned long long* qcount, cudaStream_t s);
+                      unsigned long long* rcount, unsigned long long* qcount, cudaStream_t s,
+                      const uint8_t* only = nullptr);
 // Pair counts are read on the device (d_n); n/nmax only size the grid.
 void launch_whole_tets(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, long long nmax, cudaStream_t s);
 void launch_clip(const ClipArgs& a, int bin, int precision, const int32_t* pairs, const int32_t* d_n, long long n,
@@ -112,7 +120,46 @@ void launch_records(const ClipArgs& a, int bin, long long n, cudaStream_t s);
 // Volume and first moment of the cut pieces queued by bin `bin` (at most n).
 void launch_volume(const ClipArgs& a, int bin, int precision, long long n, cudaStream_t s);
 
+// -------------------------------------------------------------- update.cu
+// changed[t] = 1 where tet t's candidate count, candidates or clip order
+// differ between the new and the old context; *n_changed counts them.
+void launch_cand_diff(const int32_t* cnt_new, const int32_t* cand_new, const uint8_t* ord_new, const int32_t* cnt_old,
+                      const int32_t* cand_old, const uint8_t* ord_old, long long nt, uint8_t* changed,
+                      unsigned long long* n_changed, cudaStream_t s);
+size_t keep_tmp_bytes(long long npairs, long long n_old_rpv);
+// Per-pair outputs and element records of the unchanged tets copied from the
+// old context (o) into the new one (a), packed keys repacked from ob to nb
+// bits per sphere index; a.rcount receives the kept record counts.
+void launch_keep(const ClipArgs& o, long long n_old_rpv, const ClipArgs& a, long long npairs, const uint8_t* changed,
+                 int ob, int nb, void* tmp, cudaStream_t s);
+
+// -------------------------------------------------------------- repair.cu
+// Boundary triangles of the mesh (tet faces without a neighbour):
+// pos[4 nt] (exclusive scan of the boundary flags) gives their number.
+size_t boundary_tmp_bytes(long long nt);
+void launch_boundary_count(const int32_t* adj, long long nt, int64_t* pos, void* tmp, cudaStream_t s);
+void launch_boundary_fill(const int32_t* tets, const int32_t* adj, const int32_t* Xi, long long nt, const int64_t* pos,
+                          double unit, double* tri, int32_t* face_of, cudaStream_t s);
+// Pin points of the non-contractible elements of one kind (1..3): count
+// (pins_fpos(tmp)[nkeys] = number of failing elements), then the pins.
+size_t pins_tmp_bytes(long long nkeys);
+void launch_pins_count(const uint8_t* flag, long long nkeys, void* tmp, cudaStream_t s);
+const int64_t* pins_fpos(const void* tmp, long long nkeys);
+void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t* beta, const int32_t* chi,
+                 const uint8_t* flag, long long nkeys, long long nfail, const int32_t* parent, long long nmax,
+                 int uf_limit, void* tmp, int32_t* out_keys, double* pins, double* normals, int32_t* faces,
+                 cudaStream_t s);
+// The context's spheres after grid rounding, in world units.
+void launch_sphere_out(const int32_t* Ci, const long long* W, long long ns, double unit, double* c, double* r,
+                       cudaStream_t s);
+// Sphere shrinking from n pins against the boundary triangles.
+void launch_shrink(const double* tri, long long ntri, const int32_t* face_of, const double* pins,
+                   const double* normals, const int32_t* faces, long long n, double r0, double* centres,
+                   double* radii, int32_t* iters, cudaStream_t s);
+
 // ---------------------------------------------------------------- topo.cu
+// Iteration bound for ClipArgs::uf_limit (a test hook may lower it).
+int uf_iteration_limit();
 // Union-find over the nodes of one element kind; writes root flags into the
 // payload (bit 16) next to the 16-bit contribution.
 // A5-A7 for one element kind (1 = cells from the pieces, 2..4 = records):

@@ -341,8 +341,12 @@ __global__ void __launch_bounds__(128) k_knn_group(const int32_t* __restrict__ X
                                                     long long nv, const GridParams* __restrict__ gp,
                                                     const int64_t* __restrict__ start, const int4* __restrict__ sph,
                                                     const long long* __restrict__ sw, int K,
-                                                    int32_t* __restrict__ knn, long long* __restrict__ dplus) {
+                                                    int32_t* __restrict__ knn, long long* __restrict__ dplus,
+                                                    const int* __restrict__ err) {
     typedef typename P::E E;
+    // the vertex order comes from a sort whose bounded wait may have run out
+    // and left entries unwritten: then compute nothing (the build fails)
+    if (*(volatile const int*)err != 0) return;
     const unsigned FULL = 0xffffffffu;
     __shared__ typename P::template Storage<KMAX> store;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -729,7 +733,10 @@ __global__ void __launch_bounds__(256) k_candidates_warp(
     if (t >= nt) return;   // warp-uniform
     int v[4];
     int3 X[4];
-    if (!load_tet(T, t, nv, Xi, v, X)) {
+    // an earlier stage that raised an error (e.g. a neighbour-list sort whose
+    // bounded wait ran out) may have left the lists unwritten: no candidates,
+    // so nothing downstream reads them; the build reports the error
+    if (*(volatile const int*)&st->err != 0 || !load_tet(T, t, nv, Xi, v, X)) {
         if (lane == 0) cand_cnt[t] = 0;
         return;
     }
@@ -1103,7 +1110,7 @@ void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams*
         note_launch();
         radix_sort_pairs(k0, v0, k1, v1, nv, bits, p, d_err, s);
         k_knn_group<RPD_MAXK, PairEntry><<<nblk(nv, 32), 128, 0, s>>>(Xi, v1, nv, gp, cell_start, cell_sph, cell_w, K,
-                                                                       knn, dplus);
+                                                                       knn, dplus, d_err);
     }
     note_launch();
 }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(RS_THREADS) rs_pass(const uint64_t* __restrict
                                                      uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                      const long long* __restrict__ d_n, long long n_host, int shift,
                                                      const uint32_t* __restrict__ gbase, uint32_t* look,
-                                                     uint32_t* tcnt, int* err) {
+                                                     uint32_t* tcnt, int* err, int spin_limit,
+                                                     const uint32_t* stall_row) {
     __shared__ uint32_t wh[RS_WARPS][256];
     __shared__ uint32_t dbase[256];
     __shared__ int tile_s;
@@ -238,8 +240,11 @@ __global__ void __launch_bounds__(RS_THREADS) rs_pass(const uint64_t* __restrict
             atomicExch(&look[tile * 256 + d], LB_AGG | run);
             long long t = tile - 1;
             int spins = 0;
+            // test hook: tile 1 waits on a row that no tile publishes, so its
+            // bounded wait runs out
+            volatile const uint32_t* stall = (stall_row && tile == 1) ? stall_row : nullptr;
             while (true) {
-                const uint32_t v = L[t * 256 + d];
+                const uint32_t v = stall ? stall[d] : L[t * 256 + d];
                 if (v & LB_PRE) {
                     excl += v & LB_VAL;
                     break;
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_pass(const uint64_t* __restrict
                     t--;
                     continue;
                 }
-                if (++spins > LB_SPIN_LIMIT) {
+                if (++spins > spin_limit) {
                     atomicCAS(err, 0, (int)RPD_E_TIMEOUT);
                     excl = 0x80000000u;   // marks the digit as unplaceable
                     break;
@@ -296,7 +301,15 @@ size_t radix_tmp_bytes(long long n) {
     return 2 * align256(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1)) +
            2 * align256(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)) +
            align256(sizeof(uint32_t) * (size_t)(2 * RS_MAXPASS * 256 + RS_MAXPASS)) +
-           align256(sizeof(uint32_t) * (size_t)(RS_MAXPASS * nt * 256));
+           align256(sizeof(uint32_t) * (size_t)(RS_MAXPASS * nt * 256 + 256));
+}
+
+// Test hook, read at every sort: RPD_TEST_LOOKBACK_STALL=N makes tile 1 of
+// every radix pass look back at a row that is never published, with a spin
+// bound of N, so that its wait runs out and the pass reports RPD_E_TIMEOUT.
+static int lookback_stall_limit() {
+    const char* e = getenv("RPD_TEST_LOOKBACK_STALL");
+    return e ? atoi(e) : 0;
 }
 
 static void radix_sort_impl(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
@@ -318,7 +331,10 @@ static void radix_sort_impl(const uint64_t* keys_in, const uint32_t* vals_in, ui
     uint32_t* tcnt = ctl + 2 * RS_MAXPASS * 256;
     // histograms, tile counters and look-back words start at zero
     cudaMemsetAsync(ctl, 0, sizeof(uint32_t) * (2 * RS_MAXPASS * 256 + RS_MAXPASS), s);
-    cudaMemsetAsync(look, 0, sizeof(uint32_t) * (size_t)(passes * nt * 256), s);
+    cudaMemsetAsync(look, 0, sizeof(uint32_t) * (size_t)(passes * nt * 256 + 256), s);
+    const int stall = lookback_stall_limit();
+    const uint32_t* stall_row = stall > 0 ? look + (size_t)passes * nt * 256 : nullptr;
+    const int spin_limit = stall > 0 ? stall : LB_SPIN_LIMIT;
     const unsigned hb = (unsigned)std::min<long long>(nt, 152LL * 8);
     rs_hist_all<<<hb, RS_THREADS, 0, s>>>(keys_in, d_n, nmax, passes, ghist);
     note_launch();
@@ -331,7 +347,8 @@ static void radix_sort_impl(const uint64_t* keys_in, const uint32_t* vals_in, ui
         uint64_t* kdst = lastp ? keys_out : ((q & 1) ? kb : ka);
         uint32_t* vdst = lastp ? vals_out : ((q & 1) ? vb : va);
         rs_pass<<<(unsigned)nt, RS_THREADS, 0, s>>>(ksrc, vsrc, kdst, vdst, d_n, nmax, 8 * q, gbase + q * 256,
-                                                     look + (size_t)q * nt * 256, tcnt + q, d_err);
+                                                     look + (size_t)q * nt * 256, tcnt + q, d_err, spin_limit,
+                                                     stall_row);
         note_launch();
         ksrc = kdst;
         vsrc = vdst;

@@ -1,18 +1,24 @@
 // rpd_euler_static: the restricted power diagram and the Euler characteristic
 // of one element kind, computed with no device allocation at all.
 //
-// Some callers cannot call cudaMalloc when they need a result: work recorded
-// into a CUDA graph (allocation is not allowed while a stream is captured),
-// or pipelines that set a fixed device-memory budget up front and may not
-// grow it later.  This entry point runs the same kernels as rpd_build and
-// rpd_euler, but carves every workspace buffer out of one file-scope device
+// Some callers cannot call cudaMalloc when they need a result: pipelines that
+// fix their device-memory budget up front and may not grow it later, or code
+// that runs where an allocation could fail or stall at the wrong moment (a
+// memory pool shared with other work, a long-running service that must not
+// fragment the device heap).  This entry point runs the same kernels as
+// rpd_build and rpd_euler, but carves every workspace buffer out of one
+// file-scope device
 // array of RPD_STATIC_SCRATCH_BYTES (32 MiB), which every GPU that loads the
 // library holds until the process exits.  Problems whose workspace does not
 // fit are rejected with RPD_E_OVERFLOW before the stage that would need more.
 //
 // In host code `g_scratch` only names the symbol; its device address is
 // looked up with cudaGetSymbolAddress once per device (the first call on a
-// device, which should therefore come before any stream capture).  All calls
+// device, which should therefore come before any stream capture) and cached
+// for the life of the process: after cudaDeviceReset on that device the
+// cached address is stale, so the entry point must not be used again in that
+// process.  The call synchronises its stream three times (the sizes of the
+// later stages are read on the host).  All calls
 // share the array and it keeps the previous call's contents, so every buffer
 // that must start at zero is cleared here, and calls that overlap on the GPU
 // (other streams or host threads) race with each other.
@@ -116,6 +122,7 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
     if (!d_verts || !d_tets || !d_centers || !d_radii || !n_out) return fail_static(RPD_E_INVALID, "null pointer");
     if (kind < 1 || kind > 4 || o.k < 1 || o.k > RPD_MAXK || o.grid_bits < 0 || o.grid_bits > 40)
         return fail_static(RPD_E_INVALID, "bad kind or options");
+    if (o.precision != RPD_FP64 && o.precision != RPD_FP32_FILTERED) return fail_static(RPD_E_INVALID, "unknown precision");
     const int b = sphere_bits(ns);
     if (kind == 4 && 4 * b > 64) return fail_static(RPD_E_OVERFLOW, "RPV keys need at most 2^16 - 1 spheres");
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -202,6 +209,7 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
     a.rcount = rcount;
     a.key_bits = b;
     a.force_slow = o.debug_checks & 3;
+    a.uf_limit = uf_iteration_limit();
     a.st = st;
     const long long rc[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
     for (int k = 0; k < 3; k++) {
@@ -236,7 +244,6 @@ extern "C" rpd_status rpd_euler_static(const double* d_verts, int64_t nv, const 
             ab.qcount = qcount + bb;
             launch_clip(ab, bb, o.precision, bins + off, bin_count + bb, nb, s);
             launch_records(ab, bb, nb, s);
-            launch_volume(ab, bb, o.precision, nb, s);
         }
         off += nb;
     }

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -26,11 +28,13 @@ namespace {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Iteration bound of the union-find loops (ClipArgs::uf_limit); the library
+// uses UF_LIMIT, a test hook may lower it to make the bound run out.
 constexpr int UF_LIMIT = 1 << 22;
 
-__device__ __forceinline__ int uf_find(int32_t* parent, int x) {
+__device__ __forceinline__ int uf_find(int32_t* parent, int x, int limit) {
     volatile int32_t* P = parent;
-    for (int it = 0; it < UF_LIMIT; it++) {
+    for (int it = 0; it < limit; it++) {
         const int px = P[x];
         if (px < 0) return x;
         const int gx = P[px];
@@ -41,10 +45,10 @@ __device__ __forceinline__ int uf_find(int32_t* parent, int x) {
     return -1;
 }
 
-__device__ __forceinline__ void uf_union(int32_t* parent, int a, int b, DevState* st) {
-    for (int it = 0; it < UF_LIMIT; it++) {
-        a = uf_find(parent, a);
-        b = uf_find(parent, b);
+__device__ __forceinline__ void uf_union(int32_t* parent, int a, int b, DevState* st, int limit) {
+    for (int it = 0; it < limit; it++) {
+        a = uf_find(parent, a, limit);
+        b = uf_find(parent, b, limit);
         if (a < 0 || b < 0) break;
         if (a == b) return;
         if (a < b) {
@@ -91,7 +95,7 @@ __global__ void k_link_cells(ClipArgs A, long long npairs, int32_t* __restrict__
             dev_fail(A.st, RPD_E_DEGENERATE, CNT_LINK_MISSING);
             continue;
         }
-        uf_union(parent, (int)p, (int)p2, A.st);
+        uf_union(parent, (int)p, (int)p2, A.st, A.uf_limit);
     }
 }
 
@@ -134,7 +138,7 @@ __global__ void k_link_records(ClipArgs A, int which, long long nmax, int32_t* _
             dev_fail(A.st, RPD_E_DEGENERATE, CNT_LINK_MISSING);
             continue;
         }
-        uf_union(parent, (int)r, (int)r2, A.st);
+        uf_union(parent, (int)r, (int)r2, A.st, A.uf_limit);
     }
 }
 
@@ -316,6 +320,14 @@ __global__ void k_compact_pieces(ClipArgs A, long long npairs, const int64_t* __
 }
 
 }  // namespace
+
+// Test hook, read at every build: RPD_TEST_UF_LIMIT=N bounds every
+// union-find loop by N iterations instead of UF_LIMIT (N = 0 makes every
+// union give up, so the build reports RPD_E_TIMEOUT).
+int uf_iteration_limit() {
+    const char* e = getenv("RPD_TEST_UF_LIMIT");
+    return e ? atoi(e) : UF_LIMIT;
+}
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 

@@ -45,7 +45,7 @@ class rpd_stats(ctypes.Structure):
                 ("clip_vertices", ctypes.c_int64 * 3),
                 ("bin_pairs", ctypes.c_int64 * 8), ("bin_cut", ctypes.c_int64 * 8), ("ms_prep", ctypes.c_float), ("ms_knn", ctypes.c_float), ("ms_cand", ctypes.c_float),
                 ("ms_clip", ctypes.c_float), ("ms_finalize", ctypes.c_float * 4), ("ms_clip_kernels", ctypes.c_float),
-                ("ms_clip_span", ctypes.c_float)]
+                ("ms_clip_span", ctypes.c_float), ("update_tets", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -90,6 +90,19 @@ def load(path: str = LIB_PATH):
     lib.rpd_destroy.restype = None
     lib.rpd_launch_count.argtypes = []
     lib.rpd_launch_count.restype = I64
+    lib.rpd_peak_fma.argtypes = [ctypes.c_int32, I64, P, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    lib.rpd_peak_fma.restype = ctypes.c_int
+    lib.rpd_insert.argtypes = [P, P, P, I64]
+    lib.rpd_insert.restype = ctypes.c_int
+    lib.rpd_pins.argtypes = [P, ctypes.c_int, P, P, P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_pins.restype = ctypes.c_int
+    lib.rpd_shrink.argtypes = [P, P, P, P, I64, P, P, P]
+    lib.rpd_shrink.restype = ctypes.c_int
+    lib.rpd_repair.argtypes = [P, ctypes.c_int32, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.rpd_repair.restype = ctypes.c_int
+    lib.rpd_spheres.argtypes = [P, P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_spheres.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -97,6 +110,20 @@ def load(path: str = LIB_PATH):
 def rpd_launch_count():
     """Kernel launches the library has issued in this process so far."""
     return int(load().rpd_launch_count())
+
+
+def rpd_peak_fma(precision, iters, stream=None):
+    """Measured CUDA-core FMA peak of one precision on the current device:
+    (TFLOP/s, duration of the timed launch in ms)."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("librpd needs a CUDA device; there is no CPU fallback")
+    sh, _ = _stream_handle(stream)
+    tf, ms = ctypes.c_double(0), ctypes.c_double(0)
+    p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    st = load().rpd_peak_fma(p, int(iters), sh, ctypes.byref(tf), ctypes.byref(ms))
+    if st != RPD_OK:
+        raise RpdError(st, "rpd_peak_fma failed")
+    return tf.value, ms.value
 
 
 def header_symbols(path: str = HEADER):
@@ -273,6 +300,75 @@ class Ctx:
         mo = torch.empty((m, 3), dtype=torch.float64, device=self.device)
         self._check(lib.rpd_pieces(self.handle, _ptr(t), _ptr(s), _ptr(v), _ptr(mo), m, ctypes.byref(n)))
         return t, s, v, mo
+
+    def rpd_insert(self, centers, radii):
+        """Append spheres and update the diagram in place (partial update).
+        Views handed out by earlier queries keep the old tables."""
+        with torch.cuda.stream(self.stream):   # inputs staged on the context's stream
+            C = _dev_f64(centers, self.device).reshape(-1, 3).contiguous()
+            R = _dev_f64(radii, self.device).reshape(-1).contiguous()
+            if C.shape[0] != R.shape[0]:
+                raise ValueError("centers and radii differ in length")
+            st = load().rpd_insert(self.handle, _ptr(C), _ptr(R), C.shape[0])
+        self._check(st)
+        self._keep = self._keep + (C, R)
+        self._tabs = None
+        self._buf = None
+        self._nkeys = None
+
+    def rpd_pins(self, kind):
+        """Pins of the non-contractible elements of `kind` (1..3): (keys
+        int32[n, kind], pins f64[n, 3], inward normals f64[n, 3], boundary
+        faces int32[n] = 4 tet + face or -1) on the device."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        self._check(lib.rpd_pins(self.handle, kind, None, None, None, None, 0, ctypes.byref(n)))
+        m = n.value
+        keys = torch.empty((m, kind), dtype=torch.int32, device=self.device)
+        pins = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+        nrm = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+        faces = torch.empty(m, dtype=torch.int32, device=self.device)
+        if m:
+            self._check(lib.rpd_pins(self.handle, kind, _ptr(keys), _ptr(pins), _ptr(nrm), _ptr(faces), m,
+                                     ctypes.byref(n)))
+        return keys, pins, nrm, faces
+
+    def rpd_shrink(self, pins, normals, faces):
+        """Shrunk spheres from pins: (centres f64[n, 3], radii f64[n],
+        iterations int32[n]) on the device."""
+        with torch.cuda.stream(self.stream):
+            P = _dev_f64(pins, self.device).reshape(-1, 3).contiguous()
+            N = _dev_f64(normals, self.device).reshape(-1, 3).contiguous()
+            F = _dev_i32(faces, self.device).reshape(-1).contiguous()
+            m = P.shape[0]
+            c = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+            r = torch.empty(m, dtype=torch.float64, device=self.device)
+            it = torch.empty(m, dtype=torch.int32, device=self.device)
+            self._check(load().rpd_shrink(self.handle, _ptr(P), _ptr(N), _ptr(F), m, _ptr(c), _ptr(r), _ptr(it)))
+            self.stream.synchronize()
+        return c, r, it
+
+    def rpd_repair(self, max_rounds=64):
+        """Run the topology repair loop: (rounds, spheres inserted, failing
+        elements left)."""
+        lib = load()
+        a, b, f = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(lib.rpd_repair(self.handle, int(max_rounds), ctypes.byref(a), ctypes.byref(b), ctypes.byref(f)))
+        self._tabs = None
+        self._buf = None
+        self._nkeys = None
+        return a.value, b.value, f.value
+
+    def rpd_spheres(self):
+        """The context's spheres after grid rounding (build inputs, then
+        inserted ones): (centres f64[ns, 3], radii f64[ns]) on the device."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        self._check(lib.rpd_spheres(self.handle, None, None, 0, ctypes.byref(n)))
+        c = torch.empty((n.value, 3), dtype=torch.float64, device=self.device)
+        r = torch.empty(n.value, dtype=torch.float64, device=self.device)
+        self._check(lib.rpd_spheres(self.handle, _ptr(c), _ptr(r), n.value, ctypes.byref(n)))
+        return c, r
 
     def rpd_stats_get(self):
         st = rpd_stats()

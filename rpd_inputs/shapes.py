@@ -69,6 +69,45 @@ def block_medial_spheres(n: int, rng: np.random.Generator, tol: float = 0.02):
     return s[:, :3].copy(), s[:, 3].copy()
 
 
+# ------------------------------------------- slabs of genus g (repair loop)
+def slab_holes(genus: int):
+    """x positions of `genus` z-through holes of radius HOLE_R spread along
+    the 4x2x1 slab (genus 0: no hole)."""
+    if genus <= 0:
+        return ()
+    return tuple(float(v) for v in np.linspace(-1.3, 1.3, genus)) if genus > 1 else (0.0,)
+
+
+def _slab_prims(x, holes, hole_r):
+    x = np.asarray(x, dtype=np.float64)
+    d = [BLOCK_HALF[a] - x[..., a] for a in range(3)] + [BLOCK_HALF[a] + x[..., a] for a in range(3)]
+    for cx in holes:
+        d.append(np.hypot(x[..., 0] - cx, x[..., 1]) - hole_r)
+    return np.stack(d, axis=-1)
+
+
+def slab_sdf(holes, hole_r):
+    return lambda x: -_slab_prims(x, holes, hole_r).min(axis=-1)
+
+
+def slab_medial_spheres(n: int, rng: np.random.Generator, holes, hole_r, tol: float = 0.02):
+    """Near-medial interior samples of the slab with holes (two nearest
+    primitives within `tol`); radius = distance to the boundary."""
+    out = []
+    total = 0
+    while total < n:
+        p = rng.uniform(-BLOCK_HALF, BLOCK_HALF, size=(65536, 3))
+        d = _slab_prims(p, holes, hole_r)
+        ok = d.min(axis=-1) > 0
+        ds = np.sort(d, axis=-1)
+        ok &= (ds[:, 1] - ds[:, 0]) < tol
+        p = p[ok]
+        out.append(np.concatenate([p, ds[ok][:, :1]], axis=1))
+        total += len(p)
+    s = np.concatenate(out, axis=0)[:n]
+    return s[:, :3].copy(), s[:, 3].copy()
+
+
 # ------------------------------------------------------ organic ellipsoid blob
 def random_rotations(n: int, rng: np.random.Generator):
     q = rng.normal(size=(n, 4))

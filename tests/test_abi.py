@@ -36,7 +36,7 @@ def test_struct_layouts_match_header():
     text = open(rpd.HEADER).read()
     opt = re.search(r"typedef struct \{(.*?)\} rpd_options;", text, re.S).group(1)
     assert [n for n in re.findall(r"int32_t\s+(\w+);", opt)] == [f for f, _ in rpd.rpd_options._fields_]
-    assert ctypes.sizeof(rpd.rpd_stats) == 8 * (2 + 4 + 4 + 5 + 3 + 8 + 8) + 4 * 10
+    assert ctypes.sizeof(rpd.rpd_stats) == 8 * (2 + 4 + 4 + 5 + 3 + 8 + 8) + 4 * 10 + 8
 
 
 def test_no_cpu_fallback_in_the_package():

@@ -1,5 +1,5 @@
 """Host-side arithmetic of bench.py (no GPU): the clip roofline from the
-step counters."""
+step counters and the measured peaks."""
 import os
 import sys
 
@@ -9,22 +9,46 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def _stage(fast, fp64, exact, nv, ms):
-    return {"pred_fast": fast, "pred_fp64": fp64, "pred_exact": exact, "clip_vertices": nv, "ms_clip_kernels": ms}
+def _stage(fast, fp64, exact, nv, ms, pieces):
+    return {"pred_fast": fast, "pred_fp64": fp64, "pred_exact": exact, "clip_vertices": nv, "ms_clip_kernels": ms,
+            "n_pieces": pieces}
 
 
-def test_clip_roofline_counts_algorithmic_flop():
+PEAKS = {"fp32": {"tflops": 80.0}, "fp64": {"tflops": 1.25}}
+
+
+def test_clip_roofline_uses_the_planned_work_per_piece():
     # 1000 sign tests of which 60 are vertex orientations (10 + 20 + 30
-    # constructed vertices), timed at 0.5 and 1.5 ms
-    st = [_stage(990, 9, 1, [10, 20, 30], 0.5), _stage(990, 9, 1, [10, 20, 30], 1.5)]
-    r = bench.clip_roofline(st, 152, "block_c2", "fp32")
-    flop = 7 * (1000 - 60) + 17 * 10 + 26 * 20 + 73 * 30
-    assert r["flop_per_launch"] == flop
+    # constructed vertices), 400 pieces, timed at 0.5 and 1.5 ms
+    st = [_stage(990, 9, 1, [10, 20, 30], 0.5, 400), _stage(990, 9, 1, [10, 20, 30], 1.5, 400)]
+    r = bench.clip_roofline(st, 32, "block_c2", "fp32", PEAKS, 6700.0)
+    assert r["flop_per_piece"] == 4500.0
+    assert r["flop_per_launch"] == 4500.0 * 400
     assert abs(r["ms_per_launch"] - 1.0) < 1e-12
-    assert abs(r["achieved"] - flop / 1e-3 / 1e12) < 1e-15
-    mhz = float(bench.measured_peaks().get("sm_max_mhz", 2070.0))
-    assert abs(r["peak"] - 152 * 128 * 2 * mhz * 1e6 / 1e12) < 1e-9
-    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-18
+    assert abs(r["achieved"] - 4500.0 * 400 / 1e-3 / 1e12) < 1e-15
+    assert r["peak"] == 80.0 and abs(r["frac"] - r["achieved"] / 80.0) < 1e-18
+    executed = 7 * (1000 - 60) + 17 * 10 + 26 * 20 + 73 * 30
+    assert r["flop_executed_per_launch"] == executed
+    assert abs(r["fractions"]["fp32_executed"] - executed / 1e-3 / 1e12 / 80.0) < 1e-15
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["traffic"] == bench.CLIP_TRAFFIC_BYTES[("block_c2", "fp32")]
-    assert bench.clip_roofline(st, 152, "torus_c1", "fp32")["traffic"] is None
+    assert r["traffic"] == bench.CLIP_TRAFFIC_BYTES.get(("block_c2", "fp32"))
+    # k = 16 takes the 2.5 kFLOP figure; an unmeasured workload has no traffic and no HBM fraction
+    r16 = bench.clip_roofline(st, 16, "no_such_workload", "fp32", PEAKS, 6700.0)
+    assert r16["flop_per_piece"] == 2500.0 and r16["traffic"] is None and "hbm" not in r16["fractions"]
+
+
+def test_clip_roofline_fp64_mode_and_binding():
+    st = [_stage(990, 9, 1, [10, 20, 30], 1.0, 400)]
+    st64 = [_stage(990, 9, 1, [10, 20, 30], 2.0, 400)]
+    r = bench.clip_roofline(st, 32, "block_c2", "fp32", PEAKS, 6700.0, stage64=st64)
+    want64 = 4500.0 * 400 / 2e-3 / 1e12 / 1.25
+    assert abs(r["fractions"]["fp64_mode_fp64"] - want64) < 1e-15
+    assert r["binding"] == max(("fp32", "fp64_mode_fp64"), key=lambda k: r["fractions"][k])
+    r64 = bench.clip_roofline(st64, 32, "block_c2", "fp64", PEAKS, 6700.0)
+    assert r64["peak"] == 1.25 and "fp64" in r64["fractions"]
+
+
+def test_cpu_samples_cover_every_workload():
+    for name in bench.WORKLOADS:
+        c = bench.CPU_SAMPLES[name]
+        assert c["oracle"] >= 1 and c["oracle_1t"] >= 1 and 0 < c["fair"] <= 1 and c["ref"] >= 1

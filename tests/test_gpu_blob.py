@@ -1,7 +1,8 @@
 """The organic-blob workload at full size (union of 200 seeded ellipsoids,
-~2.0 M tets, 20,000 near-medial spheres, k = 32): sampled parity with the C
-oracle, invariants that hold at any size, and the FP32-filtered and FP64
-predicate modes agreeing."""
+~2.0 M tets, 20,000 near-medial spheres, k = 32): parity with the C oracle on
+a seeded 1% tet sample (the oracle's pieces stored by
+tests/golden/make_golden.py), invariants that hold at any size, and the
+FP32-filtered and FP64 predicate modes agreeing."""
 import numpy as np
 import pytest
 import torch
@@ -26,11 +27,17 @@ def blob():
 
 
 def test_blob_sampled_tets_match_oracle(blob):
+    import hashlib
+    import os
     w, g = blob
-    rng = np.random.default_rng(11)
-    sub = np.sort(rng.choice(w.nt, size=1000, replace=False)).astype(np.int32)
-    o = oracle.run(w, subset=sub)
-    _check_pieces(w, g, o["tet"], o["sphere"], o["vol"], o["moment"], sel=sub)
+    ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "blob_c3_sample.npz"))
+    h = hashlib.sha256()
+    for a in (w.verts, w.tets, w.centers, w.radii):
+        h.update(np.ascontiguousarray(a).tobytes())
+    assert h.hexdigest() == str(ref["input_digest"]), "the blob generator changed: rerun make_golden.py"
+    sub = ref["sample"]
+    assert len(sub) >= 0.01 * w.nt - 1
+    _check_pieces(w, g, ref["tet"], ref["sphere"], ref["vol"], ref["moment"], sel=sub)
 
 
 def test_blob_invariants(blob):

@@ -218,6 +218,45 @@ def block_full():
     return w, collect(build_workload(w, precision="fp32"))
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    return np.load(path)
+
+
+def test_block_c2_full_matches_stored_oracle(block_full):
+    """The whole block workload against the brute-force oracle's stored
+    results (tests/golden/make_golden.py): every element table bit for bit,
+    the complete piece list, and the volume and first moment of every
+    restricted power cell within 1e-9 of its volume (moments: x the mesh
+    diameter)."""
+    import hashlib
+    w, g = block_full
+    ref = _golden("block_c2_full.npz")
+    h = hashlib.sha256()
+    for a in (w.verts, w.tets, w.centers, w.radii):
+        h.update(np.ascontiguousarray(a).tobytes())
+    assert h.hexdigest() == str(ref["input_digest"]), "the block generator changed: rerun make_golden.py"
+    p = hashlib.sha256()
+    p.update(np.ascontiguousarray(g["tet"], dtype=np.int32).tobytes())
+    p.update(np.ascontiguousarray(g["sphere"], dtype=np.int32).tobytes())
+    assert len(g["tet"]) == int(ref["n_pieces"]) and p.hexdigest() == str(ref["pieces_digest"])
+    for kind in (1, 2, 3, 4):
+        gk = g["kinds"][kind]
+        assert np.array_equal(gk["keys"], ref[f"keys{kind}"]), kind
+        assert np.array_equal(gk["chi"], ref[f"chi{kind}"]), kind
+        assert np.array_equal(gk["beta0"], ref[f"beta{kind}"]), kind
+        want_flag = (ref[f"beta{kind}"] == 1) & (ref[f"chi{kind}"] == 1)
+        assert np.array_equal(gk["flag"].astype(bool), want_flag), kind
+    cv = np.bincount(g["sphere"], weights=g["vol"], minlength=w.ns)
+    vref = ref["cell_vol"]
+    assert np.all(np.abs(cv - vref) <= 1e-9 * vref)
+    diam = float(np.linalg.norm(w.verts.max(axis=0) - w.verts.min(axis=0)))
+    for a in range(3):
+        cm = np.bincount(g["sphere"], weights=g["moment"][:, a], minlength=w.ns)
+        assert np.all(np.abs(cm - ref[f"cell_mom{a}"]) <= 1e-9 * vref * diam), a
+
+
 def test_block_c2_sampled_tets_match_oracle(block_full):
     w, g = block_full
     rng = np.random.default_rng(7)

@@ -97,3 +97,44 @@ def test_allocation_failure_is_reported(after):
                          timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     assert "FAILED_CLEANLY" in out.stdout, out.stdout
+
+
+# ------------------------------------------------- bounded waits run out
+# Each case runs in a child process: the hook makes one bounded device loop
+# give up (a wait on a row that no tile publishes; a union-find bound of 0),
+# the build must return RPD_E_TIMEOUT with the context still usable, and the
+# next build, with the hook removed, must match the oracle.
+_TIMEOUT_CHILD = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+from paper_2403_18761_gb300 import build_workload, RpdError
+from paper_2403_18761_gb300.rpd import RPD_E_TIMEOUT, collect
+from rpd_inputs import block_c2
+w = block_c2(h=0.12, ns=300)   # 5.8k mesh vertices: two tiles in the vertex sort
+os.environ[{var!r}] = {val!r}
+try:
+    build_workload(w, precision="fp32", debug={debug})
+    print("NO_TIMEOUT")
+    sys.exit(0)
+except RpdError as e:
+    assert e.status == RPD_E_TIMEOUT, e
+    print("TIMEOUT:", e)
+del os.environ[{var!r}]
+g = collect(build_workload(w, precision="fp32", debug={debug}))
+o = oracle.run(w)
+assert np.array_equal(g["tet"], o["tet"]) and np.array_equal(g["sphere"], o["sphere"])
+for kind in (1, 2, 3, 4):
+    for f in ("keys", "chi", "beta0"):
+        assert np.array_equal(g["kinds"][kind][f], o["kinds"][kind][f].astype(np.int32)), (kind, f)
+print("RECOVERED")
+"""
+
+
+@pytest.mark.parametrize("var,val,debug", [("RPD_TEST_LOOKBACK_STALL", "4096", 4), ("RPD_TEST_UF_LIMIT", "0", 0)])
+def test_bounded_wait_runs_out_and_next_build_is_correct(var, val, debug):
+    code = _TIMEOUT_CHILD.format(root=ROOT, var=var, val=val, debug=debug)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-3000:]
+    assert "TIMEOUT:" in out.stdout and "RECOVERED" in out.stdout, out.stdout
