@@ -52,7 +52,7 @@ FLOP_NEW_VERTEX = (17, 26, 73)   # by m = 1, 2, 3
 # DRAM bytes (read + write) per step of the clip kernels (k_clip over all bins
 # + k_whole), from one ncu capture of the current kernels per workload and
 # precision; a workload missing here reports traffic null.
-CLIP_TRAFFIC_BYTES = {}
+CLIP_TRAFFIC_BYTES = {("blob_c3", "fp32"): 894.12e6}
 # CPU legs per workload, sized for 10-30 s each on the 16 host cores: tets of
 # the brute-force oracle sample, of its 1-thread sample, fraction of tets for
 # the same-algorithm baseline, tets per step of the reference arm.

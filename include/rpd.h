@@ -171,7 +171,9 @@ rpd_status rpd_insert(rpd_ctx* ctx, const double* d_centers, const double* d_rad
  * (Sec. 4.1.1: a surface point on another component).  For an element with
  * beta0 = 1 and chi != 1 it is the centroid of the touched boundary triangle
  * furthest from the element's first sphere (Sec. 4.1.2: the furthest surface
- * triangle), ties to the lowest (tet, face).
+ * triangle), ties to the lowest (tet, face).  Boundary triangles that the
+ * repair loop (rpd_repair) of this context has already grown a sphere from are
+ * skipped, so that a failing element gets a new place to grow from.
  *   d_keys    i32[n*kind]  keys of the failing elements, in key order
  *   d_pins    f64[n*3]     pin points (NaN when the element touches no
  *                          qualifying boundary triangle)
@@ -202,6 +204,66 @@ rpd_status rpd_pins(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, double* d_pins
 rpd_status rpd_shrink(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const int32_t* d_faces, int64_t n,
                       double* d_centers, double* d_radii, int32_t* d_iters);
 
+/*
+ * Sphere shrinking from a proposed first radius (the learned proposer below;
+ * not in the paper).  d_r_start f64[n]: the first ball's radius per pin, 0 for
+ * the plain start.  The balls tangent at p are nested, so a first ball that
+ * holds a surface point lies above the fixed point and the shrinking reaches
+ * the same sphere as from the plain start; a first ball that holds none may
+ * lie below it, and that pin starts over from the plain radius (d_restarted
+ * i32[n], may be NULL, gets 1 there).  d_iters counts the rejected test too.
+ * Otherwise as rpd_shrink.
+ */
+rpd_status rpd_shrink_warm(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const int32_t* d_faces,
+                           int64_t n, const double* d_r_start, double* d_centers, double* d_radii, int32_t* d_iters,
+                           int32_t* d_restarted);
+
+/*
+ * Proposer inputs (not in the paper): for each pin p with inward normal n,
+ * RPD_PIN_FEATURES floats: u = (p - box centre) / (half the box's longest
+ * side) (3), n (3), and sin(pi 2^o u_a), cos(pi 2^o u_a) for o = 0..3 and
+ * a = x, y, z in that order (24); the box is the mesh's bounding box.
+ * d_x f32[n * RPD_PIN_FEATURES]; with d_radii f64[n] (may be NULL) also the
+ * regression targets d_t f32[n] = log2(r / box diagonal).  Stream-ordered
+ * (the first call of a context synchronises once to measure the box).
+ */
+#define RPD_PIN_FEATURES 30
+rpd_status rpd_pin_features(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const double* d_radii,
+                            int64_t n, float* d_x, float* d_t);
+
+/* Length of every restricted power edge RPE_ijk (the total length of its
+ * segments), with its key; the dual triangle's importance in the thinning
+ * (Sec. 5.3).  d_keys i32[n*3], d_len f64[n] (world units); two-phase like
+ * rpd_euler.  Lengths are summed per key in 64-bit fixed point (2^-24 grid
+ * units), so they do not depend on the order of the segments. */
+rpd_status rpd_edge_lengths(rpd_ctx* ctx, int32_t* d_keys, double* d_len, int64_t cap, int64_t* n);
+
+typedef struct {
+    int64_t vertices, edges, faces, tets;    /* medial mesh: RPC, RPF, RPE, RPV keys */
+    int64_t edges_thin, faces_thin, tets_thin; /* after thinning (vertices stay)     */
+    int64_t chi, chi_thin;                   /* V - E + F - T before and after       */
+} rpd_medial_info;
+
+/*
+ * Dual medial mesh (Sec. 3.2: a vertex per RPC, an edge per RPF, a triangle
+ * per RPE, a tetrahedron per RPV) and its geometry-guided thinning (Sec. 5.3):
+ * tet-triangle simple pairs are removed in ascending importance
+ * alpha_ijk = |RPE_ijk| / mean(2 r_i, 2 r_j, 2 r_k) until no tetrahedron is
+ * left, then triangle-edge simple pairs whose triangle belonged to an original
+ * tetrahedron while alpha < sigma (0.3 for CAD-like, 0.1 for organic shapes in
+ * the paper).  Ties go to the smaller triangle key, and a triangle with several
+ * free edges gives up the edge with the smallest key.  The pruning runs on the
+ * host (a sequential priority process); the tables and lengths come from the
+ * device.
+ *   info     host pointer, receives the counts and Euler characteristics
+ *   h_edges  HOST i32[cap_e*2] or NULL: the thinned mesh's edges, sorted keys
+ *   h_faces  HOST i32[cap_f*3] or NULL: its triangles
+ * Synchronises the stream.  RPD_E_INVALID for sigma < 0 or a cap below the
+ * thinned count (info is filled first).
+ */
+rpd_status rpd_medial(rpd_ctx* ctx, double sigma, rpd_medial_info* info, int32_t* h_edges, int64_t cap_e,
+                      int32_t* h_faces, int64_t cap_f);
+
 /* The context's spheres as the diagram uses them (centres and radii rounded
  * to the grid 2^-grid_bits), those of rpd_build followed by every inserted
  * one: d_centers f64[n*3], d_radii f64[n].  Two-phase like rpd_euler. */
@@ -220,6 +282,104 @@ rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t
  * Synchronises the stream several times per round.
  */
 rpd_status rpd_repair(rpd_ctx* ctx, int32_t max_rounds, int64_t* rounds, int64_t* inserted, int64_t* failing);
+
+/* Surface samples of the shape: the centroid of every boundary triangle of
+ * the mesh (tet faces without a neighbour), its unit normal into the shape
+ * and its face id 4*tet + face.  d_points, d_normals f64[n*3], d_faces i32[n];
+ * two-phase like rpd_euler.  Synchronises the stream on its first call. */
+rpd_status rpd_surface_samples(rpd_ctx* ctx, double* d_points, double* d_normals, int32_t* d_faces, int64_t cap,
+                               int64_t* n);
+
+/*
+ * Geometric preservation (Sec. 4.3): signed distance from each sample point to
+ * the enveloping volume of the medial mesh, the union of its spheres (RPC
+ * vertices), medial cones (RPF edges: spheres interpolated linearly between
+ * two) and medial slabs (RPE triangles: between three); negative inside.
+ * Each primitive's distance min |s - c(l)| - r(l) over its interpolated
+ * spheres is taken from its interior stationary point in closed form (the
+ * primitive's boundary is made of the lower primitives), in FP32 on
+ * coordinates relative to mesh vertex 0; the primitives are sorted by the
+ * Morton code of their centre and tiles farther than a sample's best distance
+ * are skipped.
+ *   d_samples f64[n*3]  points (world units), caller-owned device memory
+ *   d_dist    f32[n]    distances (world units)
+ *   d_prim    i32[n]    nearest primitive: row of the RPC table, then n_RPC +
+ *                       row of the RPF table, then n_RPC + n_RPF + row of the
+ *                       RPE table; -1 when there is none
+ * Synchronises the stream once (the mesh origin).
+ */
+rpd_status rpd_envelope_distance(rpd_ctx* ctx, const double* d_samples, int64_t n, float* d_dist, int32_t* d_prim);
+
+typedef struct {
+    int64_t rounds;       /* rounds that inserted spheres                             */
+    int64_t inserted;     /* spheres inserted                                         */
+    int64_t failing;      /* non-contractible RPC/RPF/RPE left                        */
+    int64_t far_samples;  /* surface samples farther than delta x diagonal left       */
+    double max_ratio;     /* largest sample distance / bounding-box diagonal left     */
+} rpd_repair_report;
+
+/*
+ * The repair loop with geometric preservation (Sec. 4.1, 4.3): each round
+ * grows spheres from the pins of the failing elements (as rpd_repair) or, once
+ * every RPC, RPF and RPE is contractible, from the surface samples whose
+ * distance to the envelope exceeds delta times the samples' bounding-box
+ * diagonal (Sec. 4.3's threshold), and inserts them with a partial update.
+ * Far samples are taken farthest first, skipping any within three times its
+ * own distance of a sample already taken in the round (a reading: the paper
+ * inserts a sphere per far sample without saying how many per round).  It
+ * stops when both are satisfied, when max_rounds rounds have run, or when a
+ * round has nothing new to insert.
+ *   rep  host pointer, receives the report (always filled on RPD_OK)
+ */
+rpd_status rpd_repair_geometry(rpd_ctx* ctx, double delta, int32_t max_rounds, rpd_repair_report* rep);
+
+/*
+ * Learned sphere proposer (the paper has no counterpart: it grows every sphere
+ * by sphere shrinking, Sec. 5.1).  A multilayer perceptron with n_in <= 32
+ * inputs, three hidden layers of 128 ReLU units and one linear output,
+ * trained on pairs (features of a pin -> radius the plain sphere shrinking
+ * grows from it); its prediction only sets where the shrinking starts
+ * (rpd_shrink_warm), so the grown sphere stays the plain method's and the
+ * exact RPD check stays the judge.  Hidden layers run on the tensor cores
+ * (tcgen05, BF16 operands, FP32 accumulation in tensor memory) in the
+ * library's own forward and backward kernels; weights are kept in FP32 and
+ * cast to BF16 for each step; Adam (beta 0.9 / 0.999, eps 1e-8).
+ * The network's buffers are its own device allocations (cudaMalloc).
+ * Parameter vector layout (FP32, 37377 values): W0[128][32], b0[128],
+ * W1[128][128], b1[128], W2[128][128], b2[128], w3[128], b3; W0's columns
+ * past n_in are zero.  Inputs: d_x f32[n][n_in] row-major, d_t f32[n].
+ * Every call synchronises the network's stream and returns RPD_E_TIMEOUT if
+ * a tensor-core completion wait ran out, RPD_E_CUDA / RPD_E_OOM otherwise.
+ */
+typedef struct rpd_mlp rpd_mlp;
+rpd_status rpd_mlp_create(int32_t n_in, uint64_t seed, void* cuda_stream, rpd_mlp** out);
+/* Copy the parameters out (d_out f32[cap], cap >= 37377) or in. */
+rpd_status rpd_mlp_params(rpd_mlp* mlp, float* d_out, int64_t cap, int64_t* n);
+rpd_status rpd_mlp_set_params(rpd_mlp* mlp, const float* d_in, int64_t n);
+/* Predictions d_y f32[n]. */
+rpd_status rpd_mlp_forward(rpd_mlp* mlp, const float* d_x, int64_t n, float* d_y);
+/* Gradient (d_grad f32[37377], may be NULL) of the mean squared error
+ * mean((y - t)^2) over the n rows, and the loss on the host; no update. */
+rpd_status rpd_mlp_grad(rpd_mlp* mlp, const float* d_x, const float* d_t, int64_t n, float* d_grad, float* h_loss);
+/* `steps` Adam steps with learning rate lr on consecutive slices of `batch`
+ * rows (wrapping around; shuffle the rows beforehand); *h_loss = the last
+ * step's loss. */
+rpd_status rpd_mlp_train(rpd_mlp* mlp, const float* d_x, const float* d_t, int64_t n, int32_t steps, int32_t batch,
+                         float lr, float* h_loss);
+void rpd_mlp_destroy(rpd_mlp* mlp);
+
+/* First radii proposed by a network for n pins: d_r_start f64[n] =
+ * margin * diag * 2^y with y the network's output on rpd_pin_features
+ * (margin >= 1 aims above the fixed point).  Synchronises both streams. */
+rpd_status rpd_propose(rpd_ctx* ctx, rpd_mlp* mlp, const double* d_pins, const double* d_normals, int64_t n,
+                       double margin, double* d_r_start);
+/* Make rpd_repair and rpd_repair_geometry start each shrinking from the
+ * network's proposal (rpd_propose + rpd_shrink_warm); NULL restores the
+ * plain start.  The context does not own the network. */
+rpd_status rpd_set_proposer(rpd_ctx* ctx, rpd_mlp* mlp, double margin);
+/* Sphere-shrinking work of the context's repair loops so far: pins shrunk,
+ * iterations summed over them, proposals rejected. */
+rpd_status rpd_shrink_counters(rpd_ctx* ctx, int64_t* pins, int64_t* iters, int64_t* restarts);
 
 /* Every element table of rpd_euler, rpd_components and rpd_contractible, for
  * all four kinds, in one launch into one caller-owned device buffer (for

@@ -20,6 +20,8 @@ baseline, not a parity reference; a CPU test checks it against the brute force.
 
 Per-key aggregation (this file):
   chi(key)   = sum of the per-piece fractional contributions (Sec. 4.1.2);
+  length     = summed segment lengths of an edge element (grid units), the
+               RPE length in the thinning's importance (Sec. 5.3);
   beta0(key) = connected components of the key's pieces linked across shared
                tet faces (Sec. 4.1.1);
   flag(key)  = beta0 == 1 and chi == 1 (Sec. 3.3, Sec. 4.1).
@@ -71,7 +73,7 @@ def _load():
         lib.orc_nnodes.restype = I64
         lib.orc_nnodes.argtypes = [P]
         lib.orc_copy.restype = None
-        lib.orc_copy.argtypes = [P] * 12 + [I64]
+        lib.orc_copy.argtypes = [P] * 12 + [I64, P]
         lib.orc_free.restype = None
         lib.orc_free.argtypes = [P]
         _lib = lib
@@ -109,9 +111,9 @@ def clip_all(verts_i, tets, centers_i, radii_i, subset=None, nthreads=None, k=0)
         out = dict(p_t=np.empty(np_, np.int32), p_i=np.empty(np_, np.int32), p_vol=np.empty(np_),
                    p_mom=np.empty((np_, 3)), n_kind=np.empty(nn, np.int32), n_key=np.empty((nn, 4), np.int32),
                    n_t=np.empty(nn, np.int32), n_own=np.empty(nn, np.int32), n_link=np.empty(nn, np.int32),
-                   n_frac=np.empty(nn), adj=np.empty((len(T), 4), np.int32))
+                   n_frac=np.empty(nn), adj=np.empty((len(T), 4), np.int32), n_len=np.empty(nn))
         lib.orc_copy(h, *[_ptr(out[k]) for k in ("p_t", "p_i", "p_vol", "p_mom", "n_kind", "n_key", "n_t",
-                                                 "n_own", "n_link", "n_frac", "adj")], len(T))
+                                                 "n_own", "n_link", "n_frac", "adj")], len(T), _ptr(out["n_len"]))
     finally:
         lib.orc_free(h)
     out["nthreads"] = nth
@@ -128,12 +130,13 @@ def aggregate(raw, nt):
         tt = raw["n_t"][sel].astype(np.int64)
         if len(sel) == 0:
             res[kind] = dict(keys=np.zeros((0, kind), np.int64), chi=np.zeros(0, np.int64),
-                             chi_frac=np.zeros(0), beta0=np.zeros(0, np.int64))
+                             chi_frac=np.zeros(0), beta0=np.zeros(0, np.int64), length=np.zeros(0))
             continue
         ukeys, kid = np.unique(keys, axis=0, return_inverse=True)
         kid = kid.ravel()
         chi = np.bincount(kid, weights=raw["n_own"][sel], minlength=len(ukeys)).round().astype(np.int64)
         chi_frac = np.bincount(kid, weights=raw["n_frac"][sel], minlength=len(ukeys))
+        length = np.bincount(kid, weights=raw["n_len"][sel], minlength=len(ukeys))   # edges: segment lengths
         # components: node (kid, t) linked to (kid, adj[t][f]) for each link bit f
         comp = kid * nt + tt
         order = np.argsort(comp, kind="stable")
@@ -156,7 +159,7 @@ def aggregate(raw, nt):
         _, lab = connected_components(g, directed=False)
         pairs = np.unique(np.stack([kid, lab], axis=1), axis=0)
         beta0 = np.bincount(pairs[:, 0], minlength=len(ukeys)).astype(np.int64)
-        res[kind] = dict(keys=ukeys, chi=chi, chi_frac=chi_frac, beta0=beta0)
+        res[kind] = dict(keys=ukeys, chi=chi, chi_frac=chi_frac, beta0=beta0, length=length)
     return res
 
 

@@ -206,7 +206,7 @@ typedef struct {
     /* element nodes */
     int64_t nn, cap_n;
     int32_t *n_kind, *n_key, *n_t, *n_own, *n_link;
-    double *n_frac;
+    double *n_frac, *n_len;
     int status;
     int64_t ndeg;
     /* threading */
@@ -229,9 +229,11 @@ static int grow_n(out_t *o) {
     int64_t c = o->cap_n ? o->cap_n * 2 : 4096;
     void *a = realloc(o->n_kind, c * 4), *b = realloc(o->n_key, c * 16), *d = realloc(o->n_t, c * 4);
     void *e = realloc(o->n_own, c * 4), *f = realloc(o->n_link, c * 4), *g = realloc(o->n_frac, c * 8);
+    void *hl = realloc(o->n_len, c * 8);
+    if (hl) o->n_len = hl;
     if (a) o->n_kind = a; if (b) o->n_key = b; if (d) o->n_t = d;
     if (e) o->n_own = e; if (f) o->n_link = f; if (g) o->n_frac = g;
-    if (!a || !b || !d || !e || !f || !g) return 0;
+    if (!a || !b || !d || !e || !f || !g || !hl) return 0;
     o->cap_n = c;
     return 1;
 }
@@ -559,6 +561,23 @@ static void process_tet(out_t *o, int64_t t, sortkey_t *order, vtx_t *V, vtx_t *
             o->n_own[n] = chi_own;
             o->n_frac[n] = chi_frac;
             o->n_link[n] = link;
+            /* an edge element (two radical planes): its segment's length,
+             * between the two piece vertices on both planes (grid units) */
+            double seg = 0;
+            if (nj == 2) {
+                int ends[2], ne_ = 0;
+                for (int v = 0; v < nvx && ne_ < 2; v++)
+                    if (has(V[v].pl, Jl[z][0]) && has(V[v].pl, Jl[z][1])) ends[ne_++] = v;
+                if (ne_ == 2) {
+                    double d2 = 0;
+                    for (int k = 0; k < 3; k++) {
+                        double d = V[ends[0]].x[k] - V[ends[1]].x[k];
+                        d2 += d * d;
+                    }
+                    seg = sqrt(d2);
+                }
+            }
+            o->n_len[n] = seg;
         }
     }
 }
@@ -913,7 +932,7 @@ typedef struct {
     int32_t *p_t, *p_i;
     double *p_vol, *p_mom;
     int32_t *n_kind, *n_key, *n_t, *n_own, *n_link;
-    double *n_frac;
+    double *n_frac, *n_len;
     int32_t *adj;
 } orc_result;
 
@@ -974,6 +993,7 @@ static orc_result *run_common(int64_t nv, const int64_t *X, int64_t nt, const in
     res->p_vol = malloc(8 * (np + 1)); res->p_mom = malloc(24 * (np + 1));
     res->n_kind = malloc(4 * (nn + 1)); res->n_key = malloc(16 * (nn + 1)); res->n_t = malloc(4 * (nn + 1));
     res->n_own = malloc(4 * (nn + 1)); res->n_link = malloc(4 * (nn + 1)); res->n_frac = malloc(8 * (nn + 1));
+    res->n_len = malloc(8 * (nn + 1));
     int64_t pp = 0, qq = 0;
     for (int k = 0; k < nth; k++) {
         out_t *o = &outs[k];
@@ -982,9 +1002,11 @@ static orc_result *run_common(int64_t nv, const int64_t *X, int64_t nt, const in
         memcpy(res->n_kind + qq, o->n_kind, 4 * o->nn); memcpy(res->n_key + qq * 4, o->n_key, 16 * o->nn);
         memcpy(res->n_t + qq, o->n_t, 4 * o->nn); memcpy(res->n_own + qq, o->n_own, 4 * o->nn);
         memcpy(res->n_link + qq, o->n_link, 4 * o->nn); memcpy(res->n_frac + qq, o->n_frac, 8 * o->nn);
+        memcpy(res->n_len + qq, o->n_len, 8 * o->nn);
         pp += o->np; qq += o->nn;
         free(o->p_t); free(o->p_i); free(o->p_vol); free(o->p_mom);
         free(o->n_kind); free(o->n_key); free(o->n_t); free(o->n_own); free(o->n_link); free(o->n_frac);
+        free(o->n_len);
     }
     res->adj = m.adj;
     free(outs); free(th); free(W); free(m.own); free(m.nshare);
@@ -1013,7 +1035,8 @@ int64_t orc_nnodes(const orc_result *r) { return r->nn; }
 
 void orc_copy(const orc_result *r, int32_t *p_t, int32_t *p_i, double *p_vol, double *p_mom, int32_t *n_kind,
               int32_t *n_key, int32_t *n_t, int32_t *n_own, int32_t *n_link, double *n_frac, int32_t *adj,
-              int64_t nt) {
+              int64_t nt, double *n_len) {
+    if (n_len) memcpy(n_len, r->n_len, 8 * r->nn);
     memcpy(p_t, r->p_t, 4 * r->np); memcpy(p_i, r->p_i, 4 * r->np);
     memcpy(p_vol, r->p_vol, 8 * r->np); memcpy(p_mom, r->p_mom, 24 * r->np);
     memcpy(n_kind, r->n_kind, 4 * r->nn); memcpy(n_key, r->n_key, 16 * r->nn);
@@ -1026,6 +1049,7 @@ void orc_free(orc_result *r) {
     if (!r) return;
     free(r->p_t); free(r->p_i); free(r->p_vol); free(r->p_mom);
     free(r->n_kind); free(r->n_key); free(r->n_t); free(r->n_own); free(r->n_link); free(r->n_frac);
+    free(r->n_len);
     free(r->adj);
     free(r);
 }

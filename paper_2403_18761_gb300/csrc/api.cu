@@ -141,10 +141,23 @@ struct rpd_ctx {
     // partial update: tets whose candidates changed (NULL after a full build)
     uint8_t* changed = nullptr;
     unsigned long long* d_nchanged = nullptr;
+    // boundary faces (4 t + f) the repair loop has grown spheres from; pins
+    // skip them (carried over by partial updates)
+    uint8_t* used_faces = nullptr;
+    // per-RPE-key summed segment lengths (fixed point), computed on first query
+    long long* edge_len = nullptr;
     // boundary triangles of the mesh for sphere shrinking (built on first use)
     double* btri = nullptr;
     int32_t* btri_face = nullptr;
     long long nbtri = -1;
+    // mesh bounding box (world units), computed on first use
+    bool have_bbox = false;
+    double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};
+    // learned radius proposer used by the repair loops (not owned) and the
+    // sphere-shrinking work they did: pins, iterations, rejected proposals
+    rpd_mlp* proposer = nullptr;
+    double proposer_margin = 1.25;
+    long long shrink_pins = 0, shrink_iters = 0, shrink_restarts = 0;
     rpd_stats stats{};
     bool timed = false;   // stats' stage times filled in
     int device = 0;
@@ -456,6 +469,11 @@ rpd_status update(rpd_ctx* c, rpd_ctx* old, const double* d_centers, const doubl
     cudaMemcpyAsync(c->W, old->W, sizeof(long long) * ns0, cudaMemcpyDeviceToDevice, s);
     launch_snap(nullptr, 0, d_centers, d_radii, n_new, c->opt.grid_bits, nullptr, c->Ci + 3 * ns0, c->W + ns0, c->st,
                 s);
+    if (old->used_faces) {
+        c->used_faces = c->alloc<uint8_t>(4 * nt);
+        NEED(c->used_faces);
+        cudaMemcpyAsync(c->used_faces, old->used_faces, 4 * nt, cudaMemcpyDeviceToDevice, s);
+    }
     record(c, 1);
     record(c, 2);   // no mesh combinatorics to wait for
     TRY(cuda_check(c, "update launch"));
@@ -619,6 +637,10 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
             a.rval[k] = c->alloc<int16_t>(cap[k]);
             a.rlink[k] = c->alloc<uint8_t>(cap[k]);
             NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
+            if (k == 1) {
+                a.elen = c->alloc<long long>(cap[k]);
+                NEED(a.elen);
+            }
             fcap[k + 1] = cap[k];
             TRY(finalize_alloc(c, k + 2, d_nseg + k + 1, cap[k], &ftmp[k + 1]));
         }
@@ -845,8 +867,8 @@ rpd_status rpd_pins(rpd_ctx* ctx, rpd_kind kind, int32_t* d_keys, double* d_pins
     if (cap < nfail) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of failing elements");
     const int32_t* parent = (const int32_t*)ctx->ftmp[kind - 1];
     const long long nmax = kind == 1 ? ctx->npairs : ctx->fcap[kind - 1];
-    launch_pins(ctx->clip, kind, o.keys, o.beta, o.chi, o.flag, nk, nfail, parent, nmax, ctx->clip.uf_limit, tmp,
-                d_keys, d_pins, d_normals, d_faces, s);
+    launch_pins(ctx->clip, kind, o.keys, o.beta, o.chi, o.flag, nk, nfail, parent, nmax, ctx->clip.uf_limit,
+                ctx->used_faces, tmp, d_keys, d_pins, d_normals, d_faces, s);
     return cuda_check(ctx, "pin launch");
 }
 
@@ -892,9 +914,210 @@ rpd_status rpd_shrink(rpd_ctx* ctx, const double* d_pins, const double* d_normal
     TRY(ensure_boundary(ctx, &tri, &face_of));
     // a first radius above twice any diameter the grid allows
     const double r0 = ldexp(1.0, 23 - ctx->opt.grid_bits);
-    launch_shrink(tri, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, d_centers, d_radii, d_iters,
-                  ctx->stream);
+    launch_shrink(tri, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, nullptr, d_centers, d_radii, d_iters,
+                  nullptr, ctx->stream);
     return cuda_check(ctx, "shrink launch");
+}
+
+rpd_status rpd_shrink_warm(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const int32_t* d_faces,
+                           int64_t n, const double* d_r_start, double* d_centers, double* d_radii, int32_t* d_iters,
+                           int32_t* d_restarted) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n < 0) return fail(ctx, RPD_E_INVALID, "n must be >= 0");
+    if (n == 0) return RPD_OK;
+    if (!d_pins || !d_normals || !d_faces || !d_r_start || !d_centers || !d_radii || !d_iters)
+        return fail(ctx, RPD_E_INVALID, "null pointer");
+    if (n >= (1ll << 31)) return fail(ctx, RPD_E_INVALID, "n must be < 2^31");
+    double* tri = nullptr;
+    int32_t* face_of = nullptr;
+    TRY(ensure_boundary(ctx, &tri, &face_of));
+    const double r0 = ldexp(1.0, 23 - ctx->opt.grid_bits);
+    launch_shrink(tri, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, d_r_start, d_centers, d_radii, d_iters,
+                  d_restarted, ctx->stream);
+    return cuda_check(ctx, "shrink launch");
+}
+
+// Mesh bounding box from the grid vertices, on first use.
+static rpd_status ensure_bbox(rpd_ctx* c) {
+    if (c->have_bbox) return RPD_OK;
+    int* b = c->alloc<int>(6);
+    if (!b) return fail(c, RPD_E_OOM, "device allocation failed");
+    launch_bbox(c->Xi, c->nv, b, c->stream);
+    int h[6];
+    cudaMemcpyAsync(h, b, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, RPD_E_CUDA, "CUDA error while measuring the mesh");
+    }
+    const double unit = ldexp(1.0, -c->opt.grid_bits);
+    for (int a = 0; a < 3; a++) {
+        c->bb_lo[a] = h[a] * unit;
+        c->bb_hi[a] = h[3 + a] * unit;
+    }
+    c->have_bbox = true;
+    return RPD_OK;
+}
+
+static void bbox_frame(const rpd_ctx* c, double* bc, double* bh, double* diag) {
+    double d2 = 0, half = 0;
+    for (int a = 0; a < 3; a++) {
+        const double e = c->bb_hi[a] - c->bb_lo[a];
+        bc[a] = 0.5 * (c->bb_hi[a] + c->bb_lo[a]);
+        half = std::max(half, 0.5 * e);
+        d2 += e * e;
+    }
+    *bh = half > 0 ? half : 1.0;
+    *diag = d2 > 0 ? sqrt(d2) : 1.0;
+}
+
+rpd_status rpd_pin_features(rpd_ctx* ctx, const double* d_pins, const double* d_normals, const double* d_radii,
+                            int64_t n, float* d_x, float* d_t) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n < 0) return fail(ctx, RPD_E_INVALID, "n must be >= 0");
+    if (n == 0) return RPD_OK;
+    if (!d_pins || !d_normals || !d_x || (d_radii && !d_t)) return fail(ctx, RPD_E_INVALID, "null pointer");
+    TRY(ensure_bbox(ctx));
+    double bc[3], bh, diag;
+    bbox_frame(ctx, bc, &bh, &diag);
+    launch_pin_features(d_pins, d_normals, d_radii, n, bc, bh, diag, d_x, d_t, ctx->stream);
+    return cuda_check(ctx, "feature launch");
+}
+
+rpd_status rpd_propose(rpd_ctx* ctx, rpd_mlp* mlp, const double* d_pins, const double* d_normals, int64_t n,
+                       double margin, double* d_r_start) {
+    if (!ctx) return RPD_E_INVALID;
+    if (!mlp || n < 0 || !(margin >= 1.0)) return fail(ctx, RPD_E_INVALID, "a network, n >= 0 and margin >= 1");
+    if (n == 0) return RPD_OK;
+    if (!d_pins || !d_normals || !d_r_start) return fail(ctx, RPD_E_INVALID, "null pointer");
+    float* x = ctx->alloc<float>(n * RPD_PIN_FEATURES);
+    float* y = ctx->alloc<float>(n);
+    if (!x || !y) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    TRY(rpd_pin_features(ctx, d_pins, d_normals, nullptr, n, x, nullptr));
+    // the network runs on its own stream: let the features land first
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error in the feature kernel");
+    }
+    const rpd_status s = rpd_mlp_forward(mlp, x, n, y);
+    if (s != RPD_OK) return fail(ctx, s, "proposer network failed");
+    double bc[3], bh, diag;
+    bbox_frame(ctx, bc, &bh, &diag);
+    launch_radius_start(y, n, diag, margin, d_r_start, ctx->stream);
+    return cuda_check(ctx, "proposal launch");
+}
+
+rpd_status rpd_set_proposer(rpd_ctx* ctx, rpd_mlp* mlp, double margin) {
+    if (!ctx) return RPD_E_INVALID;
+    if (!(margin >= 1.0)) return fail(ctx, RPD_E_INVALID, "margin must be >= 1");
+    ctx->proposer = mlp;
+    ctx->proposer_margin = margin;
+    return RPD_OK;
+}
+
+rpd_status rpd_shrink_counters(rpd_ctx* ctx, int64_t* pins, int64_t* iters, int64_t* restarts) {
+    if (!ctx) return RPD_E_INVALID;
+    if (pins) *pins = ctx->shrink_pins;
+    if (iters) *iters = ctx->shrink_iters;
+    if (restarts) *restarts = ctx->shrink_restarts;
+    return RPD_OK;
+}
+
+// Per-key RPE lengths, summed from the records on first use (the volume pass
+// that measures the segments runs beside the finalisation, so the sums are
+// taken once the build has joined its streams).
+static rpd_status ensure_edge_lengths(rpd_ctx* c) {
+    if (c->edge_len) return RPD_OK;
+    long long* len = c->alloc<long long>(c->nkeys[2] + 1);
+    if (!len) return fail(c, RPD_E_OOM, "device allocation failed");
+    launch_edge_length_sum(c->clip, c->fcap[2], c->fout[2].keys, c->nkeys[2], len, c->stream);
+    TRY(cuda_check(c, "edge length launch"));
+    c->edge_len = len;
+    return RPD_OK;
+}
+
+rpd_status rpd_edge_lengths(rpd_ctx* ctx, int32_t* d_keys, double* d_len, int64_t cap, int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    TRY(check_kind(ctx, 3));
+    const long long m = ctx->nkeys[2];
+    if (n) *n = m;
+    if (!d_keys && !d_len) return RPD_OK;
+    if (cap < m) return fail(ctx, RPD_E_INVALID, "cap is smaller than the number of elements");
+    if (m == 0) return RPD_OK;
+    const FinalOut& o = ctx->fout[2];
+    if (d_keys) launch_copy_rows(o.keys, d_keys, 3 * m, nullptr, nullptr, 0, 4, ctx->stream);
+    if (d_len) {
+        TRY(ensure_edge_lengths(ctx));
+        launch_fixed_to_world(ctx->edge_len, d_len, m, ldexp(1.0, -24 - ctx->opt.grid_bits), ctx->stream);
+    }
+    return cuda_check(ctx, "edge length launch");
+}
+
+rpd_status rpd_medial(rpd_ctx* ctx, double sigma, rpd_medial_info* info, int32_t* h_edges, int64_t cap_e,
+                      int32_t* h_faces, int64_t cap_f) {
+    if (!ctx || !info) return RPD_E_INVALID;
+    if (!(sigma >= 0)) return fail(ctx, RPD_E_INVALID, "sigma must be >= 0");
+    cudaStream_t s = ctx->stream;
+    const long long nv = ctx->nkeys[0], ne = ctx->nkeys[1], nf = ctx->nkeys[2];
+    const long long nt4 = ctx->kind_ok[3] ? ctx->nkeys[3] : 0;
+    std::vector<int32_t> v(nv), e(2 * ne), f(3 * nf), t(4 * nt4);
+    std::vector<long long> len(nf), w(ctx->ns);
+    if (nv) cudaMemcpyAsync(v.data(), ctx->fout[0].keys, 4 * nv, cudaMemcpyDeviceToHost, s);
+    if (ne) cudaMemcpyAsync(e.data(), ctx->fout[1].keys, 8 * ne, cudaMemcpyDeviceToHost, s);
+    if (nf) {
+        TRY(ensure_edge_lengths(ctx));
+        cudaMemcpyAsync(f.data(), ctx->fout[2].keys, 12 * nf, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(len.data(), ctx->edge_len, 8 * nf, cudaMemcpyDeviceToHost, s);
+    }
+    if (nt4) cudaMemcpyAsync(t.data(), ctx->fout[3].keys, 16 * nt4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(w.data(), ctx->W, sizeof(long long) * ctx->ns, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error while reading the element tables");
+    }
+    // importance alpha = |RPE| / mean of the three diameters (both in grid units)
+    std::vector<double> alpha(nf);
+    for (long long q = 0; q < nf; q++) {
+        double r = 0;
+        for (int z = 0; z < 3; z++) r += sqrt((double)w[f[3 * q + z]]);
+        const double mean_diam = 2.0 * r / 3.0;
+        const double l = ldexp((double)len[q], -24);
+        alpha[q] = mean_diam > 0 ? l / mean_diam : INFINITY;
+    }
+    std::vector<uint8_t> ea, fa, ta;
+    medial_thin(e, f, alpha, t, sigma, ea, fa, ta);
+    long long ne2 = 0, nf2 = 0, nt2 = 0;
+    for (uint8_t x : ea) ne2 += x;
+    for (uint8_t x : fa) nf2 += x;
+    for (uint8_t x : ta) nt2 += x;
+    info->vertices = nv;
+    info->edges = ne;
+    info->faces = nf;
+    info->tets = nt4;
+    info->edges_thin = ne2;
+    info->faces_thin = nf2;
+    info->tets_thin = nt2;
+    info->chi = nv - ne + nf - nt4;
+    info->chi_thin = nv - ne2 + nf2 - nt2;
+    if (h_edges) {
+        if (cap_e < ne2) return fail(ctx, RPD_E_INVALID, "cap_e is smaller than the thinned edge count");
+        long long o = 0;
+        for (long long q = 0; q < ne; q++)
+            if (ea[q]) {
+                h_edges[2 * o] = e[2 * q];
+                h_edges[2 * o + 1] = e[2 * q + 1];
+                o++;
+            }
+    }
+    if (h_faces) {
+        if (cap_f < nf2) return fail(ctx, RPD_E_INVALID, "cap_f is smaller than the thinned triangle count");
+        long long o = 0;
+        for (long long q = 0; q < nf; q++)
+            if (fa[q]) {
+                for (int z = 0; z < 3; z++) h_faces[3 * o + z] = f[3 * q + z];
+                o++;
+            }
+    }
+    return RPD_OK;
 }
 
 rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t cap, int64_t* n) {
@@ -906,130 +1129,319 @@ rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t
     return cuda_check(ctx, "sphere output launch");
 }
 
-rpd_status rpd_repair(rpd_ctx* ctx, int32_t max_rounds, int64_t* rounds, int64_t* inserted, int64_t* failing) {
-    if (!ctx) return RPD_E_INVALID;
-    if (max_rounds < 0) return fail(ctx, RPD_E_INVALID, "max_rounds must be >= 0");
-    long long nround = 0, nins = 0, nfail_total = 0;
+// Grow spheres from pins (host arrays: points, inward normals, boundary face
+// ids): one per boundary triangle not -1, shrunk on the device, rounded to
+// the grid, repeats of existing or of each other dropped, then inserted with a
+// partial update.  *inserted = the number inserted (0: nothing new).
+static rpd_status grow_from_pins(rpd_ctx* ctx, const std::vector<double>& hp, const std::vector<double>& hn,
+                                 const std::vector<int32_t>& hf, long long* inserted) {
+    *inserted = 0;
     const double unit = ldexp(1.0, -ctx->opt.grid_bits), scale = ldexp(1.0, ctx->opt.grid_bits);
-    for (;;) {
-        // pins of every non-contractible cell, face and edge
-        std::vector<double> hp, hn;
-        std::vector<int32_t> hf;
-        nfail_total = 0;
-        for (int kind = 1; kind <= 3; kind++) {
-            if (!ctx->kind_ok[kind - 1]) continue;
-            int64_t m = 0;
-            TRY(rpd_pins(ctx, (rpd_kind)kind, nullptr, nullptr, nullptr, nullptr, 0, &m));
-            nfail_total += m;
-            if (m == 0) continue;
-            int32_t* dk = ctx->alloc<int32_t>(m * kind);
-            double* dp = ctx->alloc<double>(3 * m);
-            double* dn = ctx->alloc<double>(3 * m);
-            int32_t* df = ctx->alloc<int32_t>(m);
-            if (!dk || !dp || !dn || !df) return fail(ctx, RPD_E_OOM, "device allocation failed");
-            TRY(rpd_pins(ctx, (rpd_kind)kind, dk, dp, dn, df, m, &m));
-            const size_t b0 = hf.size();
-            hp.resize(3 * (b0 + m));
-            hn.resize(3 * (b0 + m));
-            hf.resize(b0 + m);
-            cudaMemcpyAsync(hp.data() + 3 * b0, dp, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
-            cudaMemcpyAsync(hn.data() + 3 * b0, dn, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
-            cudaMemcpyAsync(hf.data() + b0, df, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    // one pin per boundary triangle
+    std::vector<int> keep;
+    {
+        std::vector<int32_t> seen;
+        for (size_t q = 0; q < hf.size(); q++) {
+            if (hf[q] < 0) continue;
+            if (std::find(seen.begin(), seen.end(), hf[q]) != seen.end()) continue;
+            seen.push_back(hf[q]);
+            keep.push_back((int)q);
         }
+    }
+    if (keep.empty()) return RPD_OK;   // no boundary point to grow from
+    const long long m = (long long)keep.size();
+    std::vector<double> kp(3 * m), kn(3 * m);
+    std::vector<int32_t> kf(m);
+    for (long long q = 0; q < m; q++) {
+        for (int z = 0; z < 3; z++) {
+            kp[3 * q + z] = hp[3 * keep[q] + z];
+            kn[3 * q + z] = hn[3 * keep[q] + z];
+        }
+        kf[q] = hf[keep[q]];
+    }
+    double* dp = ctx->alloc<double>(3 * m);
+    double* dn = ctx->alloc<double>(3 * m);
+    int32_t* df = ctx->alloc<int32_t>(m);
+    double* dc = ctx->alloc<double>(3 * m);
+    double* dr = ctx->alloc<double>(m);
+    int32_t* di = ctx->alloc<int32_t>(m);
+    if (!dp || !dn || !df || !dc || !dr || !di) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(dp, kp.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(dn, kn.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(df, kf.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->stream);
+    int32_t* drs = ctx->alloc<int32_t>(m);
+    if (!drs) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    if (ctx->proposer) {
+        // the network proposes where the shrinking starts; the shrinking
+        // still decides the sphere
+        double* rs = ctx->alloc<double>(m);
+        if (!rs) return fail(ctx, RPD_E_OOM, "device allocation failed");
+        TRY(rpd_propose(ctx, ctx->proposer, dp, dn, m, ctx->proposer_margin, rs));
+        TRY(rpd_shrink_warm(ctx, dp, dn, df, m, rs, dc, dr, di, drs));
+    } else {
+        TRY(rpd_shrink(ctx, dp, dn, df, m, dc, dr, di));
+        cudaMemsetAsync(drs, 0, sizeof(int32_t) * m, ctx->stream);
+    }
+    if (!ctx->used_faces) {
+        ctx->used_faces = ctx->alloc<uint8_t>(4 * ctx->nt);
+        if (!ctx->used_faces) return fail(ctx, RPD_E_OOM, "device allocation failed");
+        cudaMemsetAsync(ctx->used_faces, 0, 4 * ctx->nt, ctx->stream);
+    }
+    launch_mark_faces(df, m, ctx->used_faces, 4 * ctx->nt, ctx->stream);
+    std::vector<double> hc(3 * m), hr(m);
+    std::vector<int32_t> hit(m), hrs(m);
+    std::vector<int32_t> ci(3 * ctx->ns);
+    std::vector<long long> cw(ctx->ns);
+    cudaMemcpyAsync(hc.data(), dc, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(hr.data(), dr, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(hit.data(), di, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(hrs.data(), drs, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(ci.data(), ctx->Ci, sizeof(int32_t) * 3 * ctx->ns, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(cw.data(), ctx->W, sizeof(long long) * ctx->ns, cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error while reading shrunk spheres");
+    }
+    for (long long q = 0; q < m; q++) {
+        ctx->shrink_pins++;
+        ctx->shrink_iters += hit[q];
+        ctx->shrink_restarts += hrs[q];
+    }
+    // new spheres on the grid, without repeats of each other or of the
+    // existing spheres (a repeat would have a radical plane with no normal)
+    std::vector<unsigned long long> have;   // hashed snapped centres + weights seen
+    auto pack = [](long long x, long long y, long long z, long long w) {
+        unsigned long long h = 1469598103934665603ull;
+        for (unsigned long long v : {(unsigned long long)x, (unsigned long long)y, (unsigned long long)z,
+                                     (unsigned long long)w})
+            h = (h ^ v) * 1099511628211ull;
+        return h;
+    };
+    for (long long q = 0; q < ctx->ns; q++) have.push_back(pack(ci[3 * q], ci[3 * q + 1], ci[3 * q + 2], cw[q]));
+    std::vector<double> nc, nr;
+    for (long long q = 0; q < m; q++) {
+        const double r = hr[q];
+        if (!(r > 0) || !std::isfinite(hc[3 * q]) || !std::isfinite(hc[3 * q + 1]) || !std::isfinite(hc[3 * q + 2]))
+            continue;
+        long long g[3];
+        bool ok = true;
+        // a shrunk sphere lands on symmetric positions of flat or lattice
+        // surfaces, where radical planes can run through mesh faces; a
+        // deterministic -1/0/+1 grid-unit move per axis, keyed on the pin's
+        // face, keeps the inserted spheres in general position
+        unsigned long long hsh = (unsigned long long)kf[q] * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        for (int z = 0; z < 3; z++) {
+            hsh ^= hsh >> 29;
+            hsh *= 0xBF58476D1CE4E5B9ull;
+            hsh ^= hsh >> 32;
+            const double v = rint(hc[3 * q + z] * scale) + (double)((long long)(hsh % 3ull) - 1);
+            if (!(fabs(v) <= (double)RPD_COORD_MAX)) ok = false;
+            g[z] = (long long)v;
+        }
+        const long long rg = (long long)rint(r * scale);
+        if (!ok || rg <= 0) continue;
+        const unsigned long long key = pack(g[0], g[1], g[2], rg * rg);
+        if (std::find(have.begin(), have.end(), key) != have.end()) continue;
+        have.push_back(key);
+        for (int z = 0; z < 3; z++) nc.push_back((double)g[z] * unit);
+        nr.push_back((double)rg * unit);
+    }
+    if (nr.empty()) return RPD_OK;
+    const long long k = (long long)nr.size();
+    double* ic = ctx->alloc<double>(3 * k);
+    double* ir = ctx->alloc<double>(k);
+    if (!ic || !ir) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    cudaMemcpyAsync(ic, nc.data(), sizeof(double) * 3 * k, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(ir, nr.data(), sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream);
+    TRY(rpd_insert(ctx, ic, ir, k));
+    *inserted = k;
+    return RPD_OK;
+}
+
+rpd_status rpd_surface_samples(rpd_ctx* ctx, double* d_points, double* d_normals, int32_t* d_faces, int64_t cap,
+                               int64_t* n) {
+    if (!ctx) return RPD_E_INVALID;
+    double* tri = nullptr;
+    int32_t* face_of = nullptr;
+    TRY(ensure_boundary(ctx, &tri, &face_of));
+    if (n) *n = ctx->nbtri;
+    if (!d_points && !d_normals && !d_faces) return RPD_OK;
+    if (!d_points || !d_normals || !d_faces || cap < ctx->nbtri)
+        return fail(ctx, RPD_E_INVALID, "all three outputs and cap >= n are needed");
+    launch_surface_samples(tri, face_of, ctx->nbtri, d_points, d_normals, d_faces, ctx->stream);
+    return cuda_check(ctx, "surface sample launch");
+}
+
+rpd_status rpd_envelope_distance(rpd_ctx* ctx, const double* d_samples, int64_t n, float* d_dist, int32_t* d_prim) {
+    if (!ctx) return RPD_E_INVALID;
+    if (n < 0) return fail(ctx, RPD_E_INVALID, "n must be >= 0");
+    if (n == 0) return RPD_OK;
+    if (!d_samples || !d_dist || !d_prim) return fail(ctx, RPD_E_INVALID, "null pointer");
+    const long long n1 = ctx->nkeys[0], n2 = ctx->nkeys[1], n3 = ctx->nkeys[2];
+    if (n1 + n2 + n3 >= (1ll << 31)) return fail(ctx, RPD_E_OVERFLOW, "too many medial primitives");
+    // coordinates relative to mesh vertex 0 keep the FP32 arithmetic local
+    int32_t x0[3];
+    cudaMemcpyAsync(x0, ctx->Xi, sizeof(x0), cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error while reading the mesh origin");
+    }
+    const double unit = ldexp(1.0, -ctx->opt.grid_bits);
+    const double o[3] = {x0[0] * unit, x0[1] * unit, x0[2] * unit};
+    void* tmp = ctx->alloc<char>(envelope_tmp_bytes(n1 + n2 + n3));
+    if (!tmp) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    launch_envelope(ctx->fout[0].keys, n1, ctx->fout[1].keys, n2, ctx->fout[2].keys, n3, ctx->Ci, ctx->W, unit, o,
+                    d_samples, n, d_dist, d_prim, tmp, &ctx->st->err, ctx->stream);
+    return cuda_check(ctx, "envelope launch");
+}
+
+// Pins of every non-contractible cell, face and edge, on the host.
+static rpd_status topology_pins(rpd_ctx* ctx, std::vector<double>& hp, std::vector<double>& hn,
+                                std::vector<int32_t>& hf, long long* nfail) {
+    long long nfail_total = 0;
+    for (int kind = 1; kind <= 3; kind++) {
+        if (!ctx->kind_ok[kind - 1]) continue;
+        int64_t m = 0;
+        TRY(rpd_pins(ctx, (rpd_kind)kind, nullptr, nullptr, nullptr, nullptr, 0, &m));
+        nfail_total += m;
+        if (m == 0) continue;
+        int32_t* dk = ctx->alloc<int32_t>(m * kind);
+        double* dp = ctx->alloc<double>(3 * m);
+        double* dn = ctx->alloc<double>(3 * m);
+        int32_t* df = ctx->alloc<int32_t>(m);
+        if (!dk || !dp || !dn || !df) return fail(ctx, RPD_E_OOM, "device allocation failed");
+        TRY(rpd_pins(ctx, (rpd_kind)kind, dk, dp, dn, df, m, &m));
+        const size_t b0 = hf.size();
+        hp.resize(3 * (b0 + m));
+        hn.resize(3 * (b0 + m));
+        hf.resize(b0 + m);
+        cudaMemcpyAsync(hp.data() + 3 * b0, dp, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(hn.data() + 3 * b0, dn, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(hf.data() + b0, df, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, ctx->stream);
+        // the host vectors grow for the next kind: let these copies land first
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, RPD_E_CUDA, "CUDA error while reading pins");
         }
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error while reading pins");
+    }
+    *nfail = nfail_total;
+    return RPD_OK;
+}
+
+rpd_status rpd_repair(rpd_ctx* ctx, int32_t max_rounds, int64_t* rounds, int64_t* inserted, int64_t* failing) {
+    if (!ctx) return RPD_E_INVALID;
+    if (max_rounds < 0) return fail(ctx, RPD_E_INVALID, "max_rounds must be >= 0");
+    long long nround = 0, nins = 0, nfail_total = 0;
+    for (;;) {
+        std::vector<double> hp, hn;
+        std::vector<int32_t> hf;
+        TRY(topology_pins(ctx, hp, hn, hf, &nfail_total));
         if (nfail_total == 0 || nround >= max_rounds) break;
-        // one pin per boundary triangle
-        std::vector<int> keep;
-        {
-            std::vector<int32_t> seen;
-            for (size_t q = 0; q < hf.size(); q++) {
-                if (hf[q] < 0) continue;
-                if (std::find(seen.begin(), seen.end(), hf[q]) != seen.end()) continue;
-                seen.push_back(hf[q]);
-                keep.push_back((int)q);
-            }
-        }
-        if (keep.empty()) break;   // failing elements without a boundary point: nothing to grow from
-        const long long m = (long long)keep.size();
-        std::vector<double> kp(3 * m), kn(3 * m);
-        std::vector<int32_t> kf(m);
-        for (long long q = 0; q < m; q++) {
-            for (int z = 0; z < 3; z++) {
-                kp[3 * q + z] = hp[3 * keep[q] + z];
-                kn[3 * q + z] = hn[3 * keep[q] + z];
-            }
-            kf[q] = hf[keep[q]];
-        }
-        double* dp = ctx->alloc<double>(3 * m);
-        double* dn = ctx->alloc<double>(3 * m);
-        int32_t* df = ctx->alloc<int32_t>(m);
-        double* dc = ctx->alloc<double>(3 * m);
-        double* dr = ctx->alloc<double>(m);
-        int32_t* di = ctx->alloc<int32_t>(m);
-        if (!dp || !dn || !df || !dc || !dr || !di) return fail(ctx, RPD_E_OOM, "device allocation failed");
-        cudaMemcpyAsync(dp, kp.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, ctx->stream);
-        cudaMemcpyAsync(dn, kn.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, ctx->stream);
-        cudaMemcpyAsync(df, kf.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->stream);
-        TRY(rpd_shrink(ctx, dp, dn, df, m, dc, dr, di));
-        std::vector<double> hc(3 * m), hr(m);
-        std::vector<int32_t> ci(3 * ctx->ns);
-        std::vector<long long> cw(ctx->ns);
-        cudaMemcpyAsync(hc.data(), dc, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream);
-        cudaMemcpyAsync(hr.data(), dr, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream);
-        cudaMemcpyAsync(ci.data(), ctx->Ci, sizeof(int32_t) * 3 * ctx->ns, cudaMemcpyDeviceToHost, ctx->stream);
-        cudaMemcpyAsync(cw.data(), ctx->W, sizeof(long long) * ctx->ns, cudaMemcpyDeviceToHost, ctx->stream);
-        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, RPD_E_CUDA, "CUDA error while reading shrunk spheres");
-        }
-        // new spheres on the grid, without repeats of each other or of the
-        // existing spheres (a repeat would have a radical plane with no normal)
-        std::vector<unsigned long long> have;   // hashed snapped centres + weights seen
-        auto pack = [](long long x, long long y, long long z, long long w) {
-            unsigned long long h = 1469598103934665603ull;
-            for (unsigned long long v : {(unsigned long long)x, (unsigned long long)y, (unsigned long long)z,
-                                         (unsigned long long)w})
-                h = (h ^ v) * 1099511628211ull;
-            return h;
-        };
-        for (long long q = 0; q < ctx->ns; q++) have.push_back(pack(ci[3 * q], ci[3 * q + 1], ci[3 * q + 2], cw[q]));
-        std::vector<double> nc, nr;
-        for (long long q = 0; q < m; q++) {
-            const double r = hr[q];
-            if (!(r > 0) || !std::isfinite(hc[3 * q]) || !std::isfinite(hc[3 * q + 1]) || !std::isfinite(hc[3 * q + 2]))
-                continue;
-            long long g[3];
-            bool ok = true;
-            for (int z = 0; z < 3; z++) {
-                const double v = rint(hc[3 * q + z] * scale);
-                if (!(fabs(v) <= (double)RPD_COORD_MAX)) ok = false;
-                g[z] = (long long)v;
-            }
-            const long long rg = (long long)rint(r * scale);
-            if (!ok || rg <= 0) continue;
-            const unsigned long long key = pack(g[0], g[1], g[2], rg * rg);
-            if (std::find(have.begin(), have.end(), key) != have.end()) continue;
-            have.push_back(key);
-            for (int z = 0; z < 3; z++) nc.push_back((double)g[z] * unit);
-            nr.push_back((double)rg * unit);
-        }
-        if (nr.empty()) break;
-        const long long k = (long long)nr.size();
-        double* ic = ctx->alloc<double>(3 * k);
-        double* ir = ctx->alloc<double>(k);
-        if (!ic || !ir) return fail(ctx, RPD_E_OOM, "device allocation failed");
-        cudaMemcpyAsync(ic, nc.data(), sizeof(double) * 3 * k, cudaMemcpyHostToDevice, ctx->stream);
-        cudaMemcpyAsync(ir, nr.data(), sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream);
-        TRY(rpd_insert(ctx, ic, ir, k));
+        long long k = 0;
+        TRY(grow_from_pins(ctx, hp, hn, hf, &k));
+        if (k == 0) break;
         nins += k;
         nround++;
     }
     if (rounds) *rounds = nround;
     if (inserted) *inserted = nins;
     if (failing) *failing = nfail_total;
+    return RPD_OK;
+}
+
+rpd_status rpd_repair_geometry(rpd_ctx* ctx, double delta, int32_t max_rounds, rpd_repair_report* rep) {
+    if (!ctx || !rep) return RPD_E_INVALID;
+    if (max_rounds < 0 || !(delta > 0)) return fail(ctx, RPD_E_INVALID, "max_rounds >= 0 and delta > 0 are needed");
+    *rep = rpd_repair_report{};
+    for (;;) {
+        std::vector<double> hp, hn;
+        std::vector<int32_t> hf;
+        long long nfail = 0;
+        TRY(topology_pins(ctx, hp, hn, hf, &nfail));
+        rep->failing = nfail;
+        // surface samples and their distance to the medial mesh's envelope
+        int64_t nb = 0;
+        TRY(rpd_surface_samples(ctx, nullptr, nullptr, nullptr, 0, &nb));
+        double* sp = ctx->alloc<double>(3 * nb + 3);
+        double* sn = ctx->alloc<double>(3 * nb + 3);
+        int32_t* sf = ctx->alloc<int32_t>(nb + 1);
+        float* sd = ctx->alloc<float>(nb + 1);
+        int32_t* sa = ctx->alloc<int32_t>(nb + 1);
+        if (!sp || !sn || !sf || !sd || !sa) return fail(ctx, RPD_E_OOM, "device allocation failed");
+        TRY(rpd_surface_samples(ctx, sp, sn, sf, nb, &nb));
+        TRY(rpd_envelope_distance(ctx, sp, nb, sd, sa));
+        std::vector<double> gp(3 * nb), gn(3 * nb);
+        std::vector<int32_t> gf(nb);
+        std::vector<float> gd(nb);
+        std::vector<uint8_t> used(ctx->used_faces ? 4 * ctx->nt : 0);
+        cudaMemcpyAsync(gp.data(), sp, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(gn.data(), sn, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(gf.data(), sf, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(gd.data(), sd, sizeof(float) * nb, cudaMemcpyDeviceToHost, ctx->stream);
+        if (!used.empty()) cudaMemcpyAsync(used.data(), ctx->used_faces, used.size(), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, RPD_E_CUDA, "CUDA error while reading envelope distances");
+        }
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (long long q = 0; q < nb; q++)
+            for (int z = 0; z < 3; z++) {
+                lo[z] = std::min(lo[z], gp[3 * q + z]);
+                hi[z] = std::max(hi[z], gp[3 * q + z]);
+            }
+        const double diag = nb ? sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                      (hi[2] - lo[2]) * (hi[2] - lo[2]))
+                               : 0.0;
+        std::vector<double> fp, fn;
+        std::vector<int32_t> ff;
+        long long nfar = 0;
+        double mx = -INFINITY;
+        std::vector<long long> far;
+        for (long long q = 0; q < nb; q++) {
+            const double ratio = diag > 0 ? (double)gd[q] / diag : 0.0;
+            mx = std::max(mx, ratio);
+            if (!(ratio > delta)) continue;
+            nfar++;
+            if (!used.empty() && used[gf[q]]) continue;
+            far.push_back(q);
+        }
+        // farthest samples first; a sample within three of its distances of
+        // one already taken this round waits for the next round (the sphere
+        // grown there usually covers it, and clustered insertions of near
+        // copies of one sphere only fragment the diagram)
+        std::sort(far.begin(), far.end(), [&](long long a, long long b) {
+            return gd[a] > gd[b] || (gd[a] == gd[b] && a < b);
+        });
+        for (long long q : far) {
+            const double rho = 3.0 * (double)gd[q];
+            bool near = false;
+            for (size_t z = 0; z < ff.size() && !near; z++) {
+                const double dx = gp[3 * q] - fp[3 * z], dy = gp[3 * q + 1] - fp[3 * z + 1],
+                             dz = gp[3 * q + 2] - fp[3 * z + 2];
+                near = dx * dx + dy * dy + dz * dz < rho * rho;
+            }
+            if (near) continue;
+            for (int z = 0; z < 3; z++) {
+                fp.push_back(gp[3 * q + z]);
+                fn.push_back(gn[3 * q + z]);
+            }
+            ff.push_back(gf[q]);
+        }
+        rep->far_samples = nfar;
+        rep->max_ratio = nb ? mx : 0.0;
+        if ((nfail == 0 && nfar == 0) || rep->rounds >= max_rounds) break;
+        // topology first (Sec. 4.1), then the geometry (Sec. 4.3)
+        long long k = 0;
+        if (nfail > 0) TRY(grow_from_pins(ctx, hp, hn, hf, &k));
+        if (k == 0 && nfar > 0) TRY(grow_from_pins(ctx, fp, fn, ff, &k));
+        if (k == 0) break;
+        rep->inserted += k;
+        rep->rounds++;
+    }
     return RPD_OK;
 }
 

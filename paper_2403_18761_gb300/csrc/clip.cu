@@ -1076,6 +1076,47 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     pass(h2hi, 64);
     pass(h3lo, 0);
     pass(h3hi, 64);
+    // Length of every restricted-power-edge segment this piece emitted (its
+    // records, in the order emit_records wrote them from e_off[p]): the end
+    // points' chart coordinates P (the apex's is 0) give the world vector
+    // sum_c (X_c - X0) dP_c in grid units; stored as fixed point x 2^24.
+    if (A.elen && A.e_cnt[p]) {
+        long long we = A.e_off[p];
+        auto chart = [&](int v, double* out) {
+            for (int k = 0; k < 3; k++) {
+                if (v == apex) {
+                    out[k] = 0.0;
+                } else {
+                    T x;
+                    V.get(v, k, x);
+                    if constexpr (sizeof(Real) == 4) out[k] = df_to_double(x);
+                    else out[k] = x;
+                }
+            }
+        };
+        for (int v = 0; v < nslot; v++) {
+            const uint32_t tw = V.w(v, 0);
+            if (is_dead(tw)) continue;
+            const uint32_t nw = V.w(v, 1);
+            for (int e = 0; e < 3; e++) {
+                const int x = tb(tw, e), y = tb(tw, (e + 1) % 3);
+                if (!(x < y && x >= 4)) continue;
+                if (L.cand[x - 4] <= L.i || L.cand[y - 4] <= L.i) continue;
+                double pa[3], pb[3];
+                chart(v, pa);
+                chart(tb(nw, e), pb);
+                double dx = 0, dy = 0, dz = 0;
+                for (int c = 1; c <= 3; c++) {
+                    const double d = pa[c - 1] - pb[c - 1];
+                    dx += d * (double)(L.X[c].x - L.X[0].x);
+                    dy += d * (double)(L.X[c].y - L.X[0].y);
+                    dz += d * (double)(L.X[c].z - L.X[0].z);
+                }
+                if (we < A.rcap[1]) A.elen[we] = llrint(sqrt(dx * dx + dy * dy + dz * dz) * 0x1p24);
+                we++;
+            }
+        }
+    }
     fm &= ~((1ull << tb(ta, 0)) | (1ull << tb(ta, 1)) | (1ull << tb(ta, 2)));   // faces through the apex
     VolAcc<Real> acc;
     while (fm) {

@@ -84,6 +84,8 @@ struct ClipArgs {
     uint8_t* rlink[3];            // bits 0-3 links across shared tet faces,
                                   // bits 4-7 tet faces the element touches
     long long rcap[3];
+    long long* elen;              // per RPE record: length of its segment in
+                                  // grid units x 2^24 (fixed point), or NULL
     unsigned long long* rcount;   // [3] device counters
     int key_bits;                 // bits per sphere index in packed keys
     int force_slow;               // 0; 1 = skip the first-stage filter; 2 = exact only
@@ -147,15 +149,50 @@ void launch_pins_count(const uint8_t* flag, long long nkeys, void* tmp, cudaStre
 const int64_t* pins_fpos(const void* tmp, long long nkeys);
 void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t* beta, const int32_t* chi,
                  const uint8_t* flag, long long nkeys, long long nfail, const int32_t* parent, long long nmax,
-                 int uf_limit, void* tmp, int32_t* out_keys, double* pins, double* normals, int32_t* faces,
-                 cudaStream_t s);
+                 int uf_limit, const uint8_t* used, void* tmp, int32_t* out_keys, double* pins, double* normals,
+                 int32_t* faces, cudaStream_t s);
+// Centroids, inward unit normals and face ids of the nb boundary triangles.
+void launch_surface_samples(const double* tri, const int32_t* face_of, long long nb, double* pts, double* nrm,
+                            int32_t* faces, cudaStream_t s);
+// used[faces[i]] = 1 for the n face ids given (those outside [0, n4) skipped).
+void launch_mark_faces(const int32_t* faces, long long n, uint8_t* used, long long n4, cudaStream_t s);
+// Per-key sums of the RPE records' fixed-point segment lengths (a.elen) into
+// len[nkeys] (zeroed here), the records' keys found in the sorted kind-3 rows.
+void launch_edge_length_sum(const ClipArgs& a, long long nmax, const int32_t* keys, long long nkeys, long long* len,
+                            cudaStream_t s);
+// out[i] = (double)in[i] * scale (fixed-point lengths to world units).
+void launch_fixed_to_world(const long long* in, double* out, long long n, double scale, cudaStream_t s);
+// ----------------------------------------------------------- envelope.cu
+// Signed distance (FP32) of samples to the medial mesh's spheres (k1 rows),
+// cones (k2 rows) and slabs (k3 rows), coordinates taken relative to o3;
+// prim_id receives the nearest primitive (row in spheres, cones, slabs order)
+// or -1.  tmp holds envelope_tmp_bytes(n1 + n2 + n3).
+size_t envelope_tmp_bytes(long long np);
+void launch_envelope(const int32_t* k1, long long n1, const int32_t* k2, long long n2, const int32_t* k3, long long n3,
+                     const int32_t* Ci, const long long* W, double unit, const double* o3, const double* samples,
+                     long long nsamp, float* dist, int32_t* prim_id, void* tmp, int* d_err, cudaStream_t s);
+// ------------------------------------------------------------- medial.cu
+// Thinning of the medial mesh (host): alive flags of the edges, triangles
+// and tetrahedra (sorted key rows) after removing simple pairs.
+#include <vector>
+int medial_thin(const std::vector<int32_t>& edges, const std::vector<int32_t>& faces,
+                const std::vector<double>& alpha, const std::vector<int32_t>& tets, double sigma,
+                std::vector<uint8_t>& edge_alive, std::vector<uint8_t>& face_alive, std::vector<uint8_t>& tet_alive);
 // The context's spheres after grid rounding, in world units.
 void launch_sphere_out(const int32_t* Ci, const long long* W, long long ns, double unit, double* c, double* r,
                        cudaStream_t s);
-// Sphere shrinking from n pins against the boundary triangles.
+// Sphere shrinking from n pins against the boundary triangles; r_start
+// (NULL or per pin, 0 = plain) proposes the first radius, restarted (NULL or
+// per pin) flags proposals that were rejected.
 void launch_shrink(const double* tri, long long ntri, const int32_t* face_of, const double* pins,
-                   const double* normals, const int32_t* faces, long long n, double r0, double* centres,
-                   double* radii, int32_t* iters, cudaStream_t s);
+                   const double* normals, const int32_t* faces, long long n, double r0, const double* r_start,
+                   double* centres, double* radii, int32_t* iters, int32_t* restarted, cudaStream_t s);
+// Learned proposer glue: pin features (and log2(r / diag) targets), the
+// decoded first radius, and the grid vertices' bounding box (int[6]).
+void launch_pin_features(const double* pins, const double* normals, const double* radii, long long n,
+                         const double* bc, double bh, double diag, float* x, float* t, cudaStream_t s);
+void launch_radius_start(const float* y, long long n, double diag, double margin, double* rs, cudaStream_t s);
+void launch_bbox(const int32_t* X, long long nv, int* b, cudaStream_t s);
 
 // ---------------------------------------------------------------- topo.cu
 // Iteration bound for ClipArgs::uf_limit (a test hook may lower it).
@@ -167,11 +204,11 @@ int uf_iteration_limit();
 // to int32 rows, contractibility flags.  Outputs hold up to n (kind 1: ns)
 // rows; *count (device) receives the number of keys.
 struct FinalOut {
-    int32_t* keys;    // [count, kind]
-    int32_t* chi;
-    int32_t* beta;
-    uint8_t* flag;
-    long long* count;
+    int32_t* keys = nullptr;    // [count, kind]
+    int32_t* chi = nullptr;
+    int32_t* beta = nullptr;
+    uint8_t* flag = nullptr;
+    long long* count = nullptr;
 };
 // Scratch for up to ncap pieces (kind 1) or records (kinds 2..4); it must be
 // cleared by launch_finalize_clear before launch_finalize (n <= ncap) runs.

@@ -20,6 +20,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "internal.cuh"
 #include "prim.cuh"
 
@@ -102,6 +105,7 @@ struct PinArgs {
     unsigned long long* far2;     // per failing element: largest squared distance
     unsigned long long* best;     // per failing element: (tet << 2) | face
     int uf_limit;
+    const uint8_t* used;          // [4 nt] boundary faces already grown from, or NULL
 };
 
 // Node n of the kind: its tet, its element's key, its link byte; false for
@@ -143,11 +147,13 @@ __device__ __forceinline__ int uf_root(const int32_t* parent, int x, int limit) 
     return -1;
 }
 
-// Tet faces without a neighbour that the element's piece in tet t touches.
-__device__ __forceinline__ unsigned boundary_faces(const ClipArgs& a, long long t, unsigned link) {
+// Tet faces without a neighbour that the element's piece in tet t touches,
+// leaving out the faces already grown from (used[4t+f] != 0, if given).
+__device__ __forceinline__ unsigned boundary_faces(const ClipArgs& a, long long t, unsigned link,
+                                                   const uint8_t* used) {
     unsigned b = 0;
     for (int f = 0; f < 4; f++)
-        if (((link >> (4 + f)) & 1) && a.adj[4 * t + f] < 0) b |= 1u << f;
+        if (((link >> (4 + f)) & 1) && a.adj[4 * t + f] < 0 && !(used && used[4 * t + f])) b |= 1u << f;
     return b;
 }
 
@@ -172,7 +178,7 @@ __global__ void k_pin_anchor(PinArgs P) {
     atomicMin(&P.anchor[f], ((unsigned long long)t << 32) | (unsigned long long)n);
     // chi != 1 with one component: the boundary triangle furthest from the
     // element's (first) sphere
-    const unsigned bf = boundary_faces(P.a, t, link);
+    const unsigned bf = boundary_faces(P.a, t, link, P.used);
     if (!bf) return;
     const long long e = find_row(P.keys, P.nkeys, P.kind, key);
     if (P.beta[e] > 1) return;
@@ -193,7 +199,7 @@ __global__ void k_pin_pick(PinArgs P) {
     unsigned link;
     const long long f = fail_of(P, n, t, key, link);
     if (f < 0) return;
-    const unsigned bf = boundary_faces(P.a, t, link);
+    const unsigned bf = boundary_faces(P.a, t, link, P.used);
     if (!bf) return;
     const long long e = find_row(P.keys, P.nkeys, P.kind, key);
     if (P.beta[e] > 1) {
@@ -325,12 +331,14 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
                                                            const double* __restrict__ pins,
                                                            const double* __restrict__ normals,
                                                            const int32_t* __restrict__ faces, double r0,
+                                                           const double* __restrict__ r_start,
                                                            double* __restrict__ centres, double* __restrict__ radii,
-                                                           int32_t* __restrict__ iters) {
+                                                           int32_t* __restrict__ iters,
+                                                           int32_t* __restrict__ restarted) {
     __shared__ double sd[SHRINK_THREADS / 32];
     __shared__ long long si[SHRINK_THREADS / 32];
     __shared__ double sr;
-    __shared__ int sdone;
+    __shared__ int sdone, swarm;
     const long long j = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int own = faces[j];
@@ -339,14 +347,21 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
             for (int k = 0; k < 3; k++) centres[3 * j + k] = nan("");
             radii[j] = nan("");
             iters[j] = 0;
+            if (restarted) restarted[j] = 0;
         }
         return;
     }
     const double p[3] = {pins[3 * j], pins[3 * j + 1], pins[3 * j + 2]};
     const double n[3] = {normals[3 * j], normals[3 * j + 1], normals[3 * j + 2]};
     if (tid == 0) {
-        sr = r0;
+        // a proposed first radius (0 < r < r0) replaces r0; the first ball
+        // must then contain a surface point, otherwise it may lie below the
+        // fixed point and the shrinking starts over from r0
+        const double rs = r_start ? r_start[j] : 0.0;
+        swarm = rs > 0.0 && rs < r0;
+        sr = swarm ? rs : r0;
         sdone = 0;
+        if (restarted) restarted[j] = 0;
     }
     __syncthreads();
     int it = 0;
@@ -386,9 +401,14 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
                     d = sd[z];
                     k = si[z];
                 }
-            // empty ball (within rounding): done
+            // empty ball (within rounding): done, unless it is a proposed one
             if (k < 0 || sqrt(d) >= r * (1.0 - 1e-12)) {
-                sdone = 1;
+                if (swarm) {
+                    sr = r0;
+                    if (restarted) restarted[j] = 1;
+                } else {
+                    sdone = 1;
+                }
             } else {
                 double q[3];
                 nearest_on_triangle(tri + 9 * k, c, q);
@@ -398,6 +418,7 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
                 if (!(dn > 0) || !(rn < r)) sdone = 1;   // no progress possible
                 else sr = rn;
             }
+            swarm = 0;
         }
         __syncthreads();
         if (sdone) break;
@@ -418,7 +439,78 @@ __global__ void k_sphere_out(const int32_t* __restrict__ Ci, const long long* __
     r[i] = sqrt((double)W[i]) * unit;   // W = (integer radius)^2 < 2^46: the root is exact
 }
 
+__global__ void k_fixed_to_world(const long long* __restrict__ in, double* __restrict__ out, long long n, double scale) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i] * scale;
+}
+
+// Records of restricted power edges: add each segment's fixed-point length to
+// its key's row (64-bit integer sums: the result does not depend on order).
+__global__ void k_edge_len_sum(ClipArgs a, long long nmax, const int32_t* __restrict__ keys, long long nkeys,
+                               unsigned long long* __restrict__ len) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long cnt = (long long)a.rcount[1];
+    if (r >= (cnt < nmax ? cnt : nmax)) return;
+    const uint64_t k = a.rkey[1][r];
+    const uint64_t m = (1ull << a.key_bits) - 1;
+    int key[3];
+    for (int z = 0; z < 3; z++) key[z] = (int)((k >> ((2 - z) * a.key_bits)) & m);
+    const long long e = find_row(keys, nkeys, 3, key);
+    if (e >= 0) atomicAdd(&len[e], (unsigned long long)a.elen[r]);
+}
+
+// Surface samples: centroid of each boundary triangle and its unit normal
+// into the shape ((B - A) x (C - A) points into the tet, see k_bnd_fill).
+__global__ void k_surface_samples(const double* __restrict__ tri, const int32_t* __restrict__ face_of, long long nb,
+                                  double* __restrict__ pts, double* __restrict__ nrm, int32_t* __restrict__ faces) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const double* T = tri + 9 * k;
+    const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+    const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+    const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    const double inv = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);
+    for (int z = 0; z < 3; z++) pts[3 * k + z] = (T[z] + T[3 + z] + T[6 + z]) / 3.0;
+    nrm[3 * k] = nx * inv;
+    nrm[3 * k + 1] = ny * inv;
+    nrm[3 * k + 2] = nz * inv;
+    faces[k] = face_of[k];
+}
+
+__global__ void k_mark_faces(const int32_t* __restrict__ faces, long long n, uint8_t* __restrict__ used,
+                             long long n4) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && faces[i] >= 0 && faces[i] < n4) used[faces[i]] = 1;
+}
+
 }  // namespace
+
+void launch_edge_length_sum(const ClipArgs& a, long long nmax, const int32_t* keys, long long nkeys, long long* len,
+                            cudaStream_t s) {
+    cudaMemsetAsync(len, 0, sizeof(long long) * (nkeys > 0 ? nkeys : 1), s);
+    if (nmax <= 0 || nkeys <= 0 || !a.elen) return;
+    k_edge_len_sum<<<nblk(nmax, 256), 256, 0, s>>>(a, nmax, keys, nkeys, (unsigned long long*)len);
+    note_launch();
+}
+
+void launch_surface_samples(const double* tri, const int32_t* face_of, long long nb, double* pts, double* nrm,
+                            int32_t* faces, cudaStream_t s) {
+    if (nb <= 0) return;
+    k_surface_samples<<<nblk(nb, 256), 256, 0, s>>>(tri, face_of, nb, pts, nrm, faces);
+    note_launch();
+}
+
+void launch_mark_faces(const int32_t* faces, long long n, uint8_t* used, long long n4, cudaStream_t s) {
+    if (n <= 0) return;
+    k_mark_faces<<<nblk(n, 256), 256, 0, s>>>(faces, n, used, n4);
+    note_launch();
+}
+
+void launch_fixed_to_world(const long long* in, double* out, long long n, double scale, cudaStream_t s) {
+    if (n <= 0) return;
+    k_fixed_to_world<<<nblk(n, 256), 256, 0, s>>>(in, out, n, scale);
+    note_launch();
+}
 
 void launch_sphere_out(const int32_t* Ci, const long long* W, long long ns, double unit, double* c, double* r,
                        cudaStream_t s) {
@@ -474,8 +566,8 @@ const int64_t* pins_fpos(const void* tmp, long long nkeys) {
 
 void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t* beta, const int32_t* chi,
                  const uint8_t* flag, long long nkeys, long long nfail, const int32_t* parent, long long nmax,
-                 int uf_limit, void* tmp, int32_t* out_keys, double* pins, double* normals, int32_t* faces,
-                 cudaStream_t s) {
+                 int uf_limit, const uint8_t* used, void* tmp, int32_t* out_keys, double* pins, double* normals,
+                 int32_t* faces, cudaStream_t s) {
     const long long n = nkeys + 1;
     PinArgs P;
     P.a = a;
@@ -492,6 +584,7 @@ void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t
     P.far2 = (unsigned long long*)((char*)tmp + ((8 * n + 255) & ~255ll));
     P.best = (unsigned long long*)((char*)tmp + 2 * ((8 * n + 255) & ~255ll));
     P.uf_limit = uf_limit;
+    P.used = used;
     if (nfail <= 0) return;
     cudaMemsetAsync(P.anchor, 0xff, 8 * nfail, s);
     cudaMemsetAsync(P.far2, 0, 8 * nfail, s);
@@ -507,10 +600,90 @@ void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t
 }
 
 void launch_shrink(const double* tri, long long ntri, const int32_t* face_of, const double* pins,
-                   const double* normals, const int32_t* faces, long long n, double r0, double* centres,
-                   double* radii, int32_t* iters, cudaStream_t s) {
+                   const double* normals, const int32_t* faces, long long n, double r0, const double* r_start,
+                   double* centres, double* radii, int32_t* iters, int32_t* restarted, cudaStream_t s) {
     if (n <= 0) return;
-    k_shrink<<<(unsigned)n, SHRINK_THREADS, 0, s>>>(tri, ntri, face_of, pins, normals, faces, r0, centres, radii,
-                                                     iters);
+    k_shrink<<<(unsigned)n, SHRINK_THREADS, 0, s>>>(tri, ntri, face_of, pins, normals, faces, r0, r_start, centres,
+                                                     radii, iters, restarted);
+    note_launch();
+}
+
+// ----------------------------------------------------- proposer features
+// Features of a pin for the learned radius proposer: its position mapped to
+// [-1, 1]^3 by the mesh's bounding box (centre bc, half of the longest side
+// bh), its unit inward normal, and sin / cos of pi 2^o u for octaves o = 0..3
+// of each mapped coordinate u.  With radii, also the regression target
+// log2(r / diag), diag the box's diagonal.
+__global__ void k_pin_features(const double* __restrict__ pins, const double* __restrict__ normals,
+                               const double* __restrict__ radii, long long n, double bcx, double bcy, double bcz,
+                               double bh, double diag, float* __restrict__ x, float* __restrict__ t) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float* f = x + j * RPD_PIN_FEATURES;
+    const double bc[3] = {bcx, bcy, bcz};
+    float u[3];
+    for (int a = 0; a < 3; a++) {
+        u[a] = (float)((pins[3 * j + a] - bc[a]) / bh);
+        f[a] = u[a];
+        f[3 + a] = (float)normals[3 * j + a];
+    }
+    for (int o = 0; o < 4; o++)
+        for (int a = 0; a < 3; a++) {
+            float sv, cv;
+            sincospif(u[a] * (float)(1 << o), &sv, &cv);
+            f[6 + 6 * o + 2 * a] = sv;
+            f[6 + 6 * o + 2 * a + 1] = cv;
+        }
+    if (radii && t) t[j] = (float)log2(radii[j] / diag);
+}
+
+// Proposed first radius of the shrinking from the network's output y:
+// margin * diag * 2^y (0 for a non-finite y: the plain start).
+__global__ void k_radius_start(const float* __restrict__ y, long long n, double diag, double margin,
+                               double* __restrict__ rs) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double v = (double)y[j];
+    rs[j] = isfinite(v) ? margin * diag * exp2(fmin(fmax(v, -60.0), 4.0)) : 0.0;
+}
+
+// Bounding box of the grid vertices: lo in b[0..2], hi in b[3..5] (b starts
+// at INT_MAX / INT_MIN).
+__global__ void k_bbox(const int32_t* __restrict__ X, long long nv, int* __restrict__ b) {
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; a++) {
+            lo[a] = min(lo[a], X[3 * i + a]);
+            hi[a] = max(hi[a], X[3 * i + a]);
+        }
+    for (int a = 0; a < 3; a++) {
+        for (int off = 16; off; off >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&b[a], lo[a]);
+            atomicMax(&b[3 + a], hi[a]);
+        }
+    }
+}
+
+void launch_pin_features(const double* pins, const double* normals, const double* radii, long long n,
+                         const double* bc, double bh, double diag, float* x, float* t, cudaStream_t s) {
+    if (n <= 0) return;
+    k_pin_features<<<nblk(n, 256), 256, 0, s>>>(pins, normals, radii, n, bc[0], bc[1], bc[2], bh, diag, x, t);
+    note_launch();
+}
+
+void launch_radius_start(const float* y, long long n, double diag, double margin, double* rs, cudaStream_t s) {
+    if (n <= 0) return;
+    k_radius_start<<<nblk(n, 256), 256, 0, s>>>(y, n, diag, margin, rs);
+    note_launch();
+}
+
+void launch_bbox(const int32_t* X, long long nv, int* b, cudaStream_t s) {
+    const int init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    cudaMemcpyAsync(b, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    k_bbox<<<(unsigned)std::max<long long>(1, std::min<long long>(nblk(nv, 256), 152 * 4)), 256, 0, s>>>(X, nv, b);
     note_launch();
 }

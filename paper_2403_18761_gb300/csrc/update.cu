@@ -98,6 +98,7 @@ __global__ void k_keep_records(ClipArgs o, ClipArgs a, long long npairs, const u
             a.rtet[which][d] = o.rtet[which][r];
             a.rval[which][d] = o.rval[which][r];
             a.rlink[which][d] = o.rlink[which][r];
+            if (which == 1 && a.elen) a.elen[d] = o.elen ? o.elen[r] : 0;
         }
     }
 }
@@ -149,6 +150,9 @@ size_t keep_tmp_bytes(long long npairs, long long n_old_rpv) {
 
 void launch_keep(const ClipArgs& o, long long n_old_rpv, const ClipArgs& a, long long npairs,
                  const uint8_t* changed, int ob, int nb, void* tmp, cudaStream_t s) {
+    // with more than 16 bits per sphere index the old context wrote no vertex
+    // records (only counted them): there is nothing to carry over
+    if (4 * ob > 64) n_old_rpv = 0;
     char* p = (char*)tmp;
     const long long n = npairs + 1, m = n_old_rpv + 1;
     int32_t* kf = (int32_t*)p; p += al(sizeof(int32_t) * n);

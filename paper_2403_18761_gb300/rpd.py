@@ -55,6 +55,22 @@ class rpd_stats(ctypes.Structure):
         return out
 
 
+class rpd_medial_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("vertices", "edges", "faces", "tets", "edges_thin", "faces_thin",
+                                               "tets_thin", "chi", "chi_thin")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class rpd_repair_report(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("inserted", ctypes.c_int64), ("failing", ctypes.c_int64),
+                ("far_samples", ctypes.c_int64), ("max_ratio", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -103,6 +119,41 @@ def load(path: str = LIB_PATH):
     lib.rpd_repair.restype = ctypes.c_int
     lib.rpd_spheres.argtypes = [P, P, P, I64, ctypes.POINTER(I64)]
     lib.rpd_spheres.restype = ctypes.c_int
+    lib.rpd_edge_lengths.argtypes = [P, P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_edge_lengths.restype = ctypes.c_int
+    lib.rpd_medial.argtypes = [P, ctypes.c_double, ctypes.POINTER(rpd_medial_info), P, I64, P, I64]
+    lib.rpd_medial.restype = ctypes.c_int
+    lib.rpd_surface_samples.argtypes = [P, P, P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_surface_samples.restype = ctypes.c_int
+    lib.rpd_envelope_distance.argtypes = [P, P, I64, P, P]
+    lib.rpd_envelope_distance.restype = ctypes.c_int
+    lib.rpd_repair_geometry.argtypes = [P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(rpd_repair_report)]
+    lib.rpd_repair_geometry.restype = ctypes.c_int
+    lib.rpd_shrink_warm.argtypes = [P, P, P, P, I64, P, P, P, P, P]
+    lib.rpd_shrink_warm.restype = ctypes.c_int
+    lib.rpd_pin_features.argtypes = [P, P, P, P, I64, P, P]
+    lib.rpd_pin_features.restype = ctypes.c_int
+    lib.rpd_propose.argtypes = [P, P, P, P, I64, ctypes.c_double, P]
+    lib.rpd_propose.restype = ctypes.c_int
+    lib.rpd_set_proposer.argtypes = [P, P, ctypes.c_double]
+    lib.rpd_set_proposer.restype = ctypes.c_int
+    lib.rpd_shrink_counters.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.rpd_shrink_counters.restype = ctypes.c_int
+    lib.rpd_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, P, ctypes.POINTER(P)]
+    lib.rpd_mlp_create.restype = ctypes.c_int
+    lib.rpd_mlp_params.argtypes = [P, P, I64, ctypes.POINTER(I64)]
+    lib.rpd_mlp_params.restype = ctypes.c_int
+    lib.rpd_mlp_set_params.argtypes = [P, P, I64]
+    lib.rpd_mlp_set_params.restype = ctypes.c_int
+    lib.rpd_mlp_forward.argtypes = [P, P, I64, P]
+    lib.rpd_mlp_forward.restype = ctypes.c_int
+    lib.rpd_mlp_grad.argtypes = [P, P, P, I64, P, ctypes.POINTER(ctypes.c_float)]
+    lib.rpd_mlp_grad.restype = ctypes.c_int
+    lib.rpd_mlp_train.argtypes = [P, P, P, I64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                  ctypes.POINTER(ctypes.c_float)]
+    lib.rpd_mlp_train.restype = ctypes.c_int
+    lib.rpd_mlp_destroy.argtypes = [P]
+    lib.rpd_mlp_destroy.restype = None
     _lib = lib
     return lib
 
@@ -348,6 +399,60 @@ class Ctx:
             self.stream.synchronize()
         return c, r, it
 
+    def rpd_shrink_warm(self, pins, normals, faces, r_start):
+        """Shrinking from proposed first radii (0 = plain start): (centres,
+        radii, iterations, restarted int32[n]) on the device."""
+        with torch.cuda.stream(self.stream):
+            P = _dev_f64(pins, self.device).reshape(-1, 3).contiguous()
+            N = _dev_f64(normals, self.device).reshape(-1, 3).contiguous()
+            F = _dev_i32(faces, self.device).reshape(-1).contiguous()
+            R0 = _dev_f64(r_start, self.device).reshape(-1).contiguous()
+            m = P.shape[0]
+            c = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+            r = torch.empty(m, dtype=torch.float64, device=self.device)
+            it = torch.empty(m, dtype=torch.int32, device=self.device)
+            rs = torch.empty(m, dtype=torch.int32, device=self.device)
+            self._check(load().rpd_shrink_warm(self.handle, _ptr(P), _ptr(N), _ptr(F), m, _ptr(R0), _ptr(c), _ptr(r),
+                                               _ptr(it), _ptr(rs)))
+            self.stream.synchronize()
+        return c, r, it, rs
+
+    def rpd_pin_features(self, pins, normals, radii=None):
+        """Proposer features f32[n, RPD_PIN_FEATURES] and, with radii, the
+        targets log2(r / box diagonal) f32[n], on the device."""
+        with torch.cuda.stream(self.stream):
+            P = _dev_f64(pins, self.device).reshape(-1, 3).contiguous()
+            N = _dev_f64(normals, self.device).reshape(-1, 3).contiguous()
+            R = _dev_f64(radii, self.device).reshape(-1).contiguous() if radii is not None else None
+            m = P.shape[0]
+            x = torch.empty((m, RPD_PIN_FEATURES), dtype=torch.float32, device=self.device)
+            t = torch.empty(m, dtype=torch.float32, device=self.device) if R is not None else None
+            self._check(load().rpd_pin_features(self.handle, _ptr(P), _ptr(N), _ptr(R), m, _ptr(x), _ptr(t)))
+            self.stream.synchronize()
+        return (x, t) if R is not None else x
+
+    def rpd_propose(self, mlp, pins, normals, margin=1.25):
+        """First radii f64[n] proposed by the network for the pins."""
+        with torch.cuda.stream(self.stream):
+            P = _dev_f64(pins, self.device).reshape(-1, 3).contiguous()
+            N = _dev_f64(normals, self.device).reshape(-1, 3).contiguous()
+            r = torch.empty(P.shape[0], dtype=torch.float64, device=self.device)
+            self._check(load().rpd_propose(self.handle, mlp.handle, _ptr(P), _ptr(N), P.shape[0], float(margin),
+                                           _ptr(r)))
+            self.stream.synchronize()
+        return r
+
+    def rpd_set_proposer(self, mlp, margin=1.25):
+        """Use the network (None: the plain start) in the repair loops."""
+        self._proposer = mlp
+        self._check(load().rpd_set_proposer(self.handle, mlp.handle if mlp is not None else None, float(margin)))
+
+    def rpd_shrink_counters(self):
+        """(pins shrunk, iterations, proposals rejected) by the repair loops."""
+        a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(load().rpd_shrink_counters(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
     def rpd_repair(self, max_rounds=64):
         """Run the topology repair loop: (rounds, spheres inserted, failing
         elements left)."""
@@ -369,6 +474,60 @@ class Ctx:
         r = torch.empty(n.value, dtype=torch.float64, device=self.device)
         self._check(lib.rpd_spheres(self.handle, _ptr(c), _ptr(r), n.value, ctypes.byref(n)))
         return c, r
+
+    def rpd_edge_lengths(self):
+        """(keys int32[n, 3], length f64[n]) of every restricted power edge."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        self._check(lib.rpd_edge_lengths(self.handle, None, None, 0, ctypes.byref(n)))
+        k = torch.empty((n.value, 3), dtype=torch.int32, device=self.device)
+        l = torch.empty(n.value, dtype=torch.float64, device=self.device)
+        self._check(lib.rpd_edge_lengths(self.handle, _ptr(k), _ptr(l), n.value, ctypes.byref(n)))
+        return k, l
+
+    def rpd_medial(self, sigma):
+        """Thinned dual medial mesh: (info dict, edges int32[m, 2], faces
+        int32[m, 3]) on the host."""
+        lib = load()
+        info = rpd_medial_info()
+        self._check(lib.rpd_medial(self.handle, float(sigma), ctypes.byref(info), None, 0, None, 0))
+        e = np.empty((info.edges_thin, 2), dtype=np.int32)
+        f = np.empty((info.faces_thin, 3), dtype=np.int32)
+        self._check(lib.rpd_medial(self.handle, float(sigma), ctypes.byref(info), e.ctypes.data, len(e),
+                                   f.ctypes.data, len(f)))
+        return info.as_dict(), e, f
+
+    def rpd_surface_samples(self):
+        """Boundary-triangle centroids f64[n, 3], inward unit normals f64[n, 3]
+        and face ids int32[n] (4 tet + face) on the device."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        self._check(lib.rpd_surface_samples(self.handle, None, None, None, 0, ctypes.byref(n)))
+        p = torch.empty((n.value, 3), dtype=torch.float64, device=self.device)
+        q = torch.empty((n.value, 3), dtype=torch.float64, device=self.device)
+        f = torch.empty(n.value, dtype=torch.int32, device=self.device)
+        self._check(lib.rpd_surface_samples(self.handle, _ptr(p), _ptr(q), _ptr(f), n.value, ctypes.byref(n)))
+        return p, q, f
+
+    def rpd_envelope_distance(self, samples):
+        """Signed distance f32[n] of points to the medial mesh's envelope and
+        the nearest primitive int32[n] (RPC rows, then RPF, then RPE)."""
+        with torch.cuda.stream(self.stream):
+            S = _dev_f64(samples, self.device).reshape(-1, 3).contiguous()
+            d = torch.empty(S.shape[0], dtype=torch.float32, device=self.device)
+            a = torch.empty(S.shape[0], dtype=torch.int32, device=self.device)
+            self._check(load().rpd_envelope_distance(self.handle, _ptr(S), S.shape[0], _ptr(d), _ptr(a)))
+            self.stream.synchronize()
+        return d, a
+
+    def rpd_repair_geometry(self, delta, max_rounds=64):
+        """Repair loop with geometric preservation: the report as a dict."""
+        rep = rpd_repair_report()
+        self._check(load().rpd_repair_geometry(self.handle, float(delta), int(max_rounds), ctypes.byref(rep)))
+        self._tabs = None
+        self._buf = None
+        self._nkeys = None
+        return rep.as_dict()
 
     def rpd_stats_get(self):
         st = rpd_stats()
@@ -435,3 +594,77 @@ def collect(ctx):
     out.update(tet=t.cpu().numpy(), sphere=s.cpu().numpy(), vol=v.cpu().numpy(), moment=m.cpu().numpy())
     out["stats"] = ctx.rpd_stats_get()
     return out
+
+
+RPD_PIN_FEATURES = 30
+MLP_NPARAM = 37377
+
+
+class Mlp:
+    """Owns one rpd_mlp: the learned radius proposer (3 x 128 ReLU layers on
+    the tensor cores, BF16 operands, FP32 master weights, Adam)."""
+
+    def __init__(self, n_in=RPD_PIN_FEATURES, seed=0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("librpd needs a CUDA device; there is no CPU fallback")
+        sh, self.stream = _stream_handle(stream)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.n_in = int(n_in)
+        h = ctypes.c_void_p()
+        st = load().rpd_mlp_create(self.n_in, int(seed), sh, ctypes.byref(h))
+        if st != RPD_OK:
+            raise RpdError(st, "rpd_mlp_create failed")
+        self.handle = h
+
+    def _check(self, st, what):
+        if st != RPD_OK:
+            raise RpdError(st, what + " failed")
+
+    def _x(self, x):
+        x = torch.as_tensor(x, dtype=torch.float32).to(self.device).reshape(-1, self.n_in).contiguous()
+        return x
+
+    def params(self):
+        p = torch.empty(MLP_NPARAM, dtype=torch.float32, device=self.device)
+        self._check(load().rpd_mlp_params(self.handle, _ptr(p), MLP_NPARAM, None), "rpd_mlp_params")
+        return p
+
+    def set_params(self, p):
+        p = torch.as_tensor(p, dtype=torch.float32).to(self.device).reshape(-1).contiguous()
+        self._check(load().rpd_mlp_set_params(self.handle, _ptr(p), p.numel()), "rpd_mlp_set_params")
+
+    def forward(self, x):
+        x = self._x(x)
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=self.device)
+        self._check(load().rpd_mlp_forward(self.handle, _ptr(x), x.shape[0], _ptr(y)), "rpd_mlp_forward")
+        return y
+
+    def grad(self, x, t):
+        """(gradient f32[37377] of mean((y - t)^2), loss)."""
+        x = self._x(x)
+        t = torch.as_tensor(t, dtype=torch.float32).to(self.device).reshape(-1).contiguous()
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=self.device)
+        loss = ctypes.c_float(0)
+        self._check(load().rpd_mlp_grad(self.handle, _ptr(x), _ptr(t), x.shape[0], _ptr(g), ctypes.byref(loss)),
+                    "rpd_mlp_grad")
+        return g, loss.value
+
+    def train(self, x, t, steps, batch=1024, lr=1e-3):
+        """Adam steps on consecutive batches of the rows; the last loss."""
+        x = self._x(x)
+        t = torch.as_tensor(t, dtype=torch.float32).to(self.device).reshape(-1).contiguous()
+        loss = ctypes.c_float(0)
+        self._check(load().rpd_mlp_train(self.handle, _ptr(x), _ptr(t), x.shape[0], int(steps), int(batch),
+                                         float(lr), ctypes.byref(loss)), "rpd_mlp_train")
+        return loss.value
+
+    def destroy(self):
+        if self.handle:
+            load().rpd_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

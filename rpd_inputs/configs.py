@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .mesh import lattice_mesh, validate, snap, MAX_COORD, orient_int, KUHN, compact
+from .mesh import lattice_mesh, slab_mesh, validate, snap, MAX_COORD, orient_int, KUHN, compact
 from .shapes import (torus_sdf, torus_core_spheres, block_sdf, block_medial_spheres,
                      BLOCK_HALF, EllipsoidBlob, slab_holes, slab_sdf, slab_medial_spheres)
 
@@ -112,14 +112,21 @@ def blob_c3(seed: int = BASE_SEED + 2, target_tets: int = 2_000_000, ns: int = 2
     return _finish("blob_c3", q, tets, c, r, g, 32, "fp32")
 
 
-def genus_slab(genus: int, seed: int = BASE_SEED + 4, h: float = 0.075, ns: int = 256, hole_r: float = 0.2):
+def genus_slab(genus: int, seed: int = BASE_SEED + 4, h: float = 0.075, ns: int = 256, hole_r: float = 0.2,
+               project: bool = True):
     """A 4x2x1 slab with `genus` z-through holes (genus 0-5; chi = 1 - genus),
     ~100k tets at h = 0.075, and `ns` near-medial starting spheres: the
     topology-repair workload (many shapes of genus 0-5 from 256 spheres)."""
     rng = np.random.default_rng(seed + 97 * genus)
     g = 19
     holes = slab_holes(genus)
-    q, tets = lattice_mesh(slab_sdf(holes, hole_r), -BLOCK_HALF - 0.01, BLOCK_HALF + 0.01, h, g, rng)
+    if project:
+        # flat box faces and hole walls on their cylinders, as a
+        # surface-fitting tetrahedralisation places them
+        q, tets = slab_mesh(BLOCK_HALF, holes, hole_r, h, g, rng)
+    else:
+        # a jittered lattice staircase (a rough, non-fitted boundary)
+        q, tets = lattice_mesh(slab_sdf(holes, hole_r), -BLOCK_HALF - 0.01, BLOCK_HALF + 0.01, h, g, rng)
     c, r = slab_medial_spheres(ns, rng, holes, hole_r)
     w = _finish(f"genus{genus}_slab", q, tets, c, r, g, 32, "fp32", expect_chi=1 - genus)
     w.info["genus"] = genus

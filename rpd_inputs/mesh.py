@@ -222,8 +222,54 @@ def validate(q: np.ndarray, tets: np.ndarray) -> dict:
     return info
 
 
+def project_boundary(q, tets, sdf, grid_bits: int, min_ratio: float = 0.02, rounds: int = 12):
+    """Move the boundary vertices of a carved lattice mesh onto the surface
+    {sdf = 0}: one Newton step x - sdf(x) grad(sdf)(x) (exact for planes and
+    cylinders), on the integer grid.  A vertex whose move would leave one of
+    its tets with less than `min_ratio` of its volume (or inverted) has the
+    move halved, round after round; whatever is still too flat keeps its
+    original position.  Topology is unchanged.  Returns new coordinates."""
+    scale = 1.0 / float(1 << grid_bits)
+    faces = np.sort(np.concatenate([tets[:, list(f)] for f in FACE_LOCAL], axis=0), axis=1)
+    uf, cnt = np.unique(faces, axis=0, return_counts=True)
+    bv = np.unique(uf[cnt == 1].ravel())
+    x = q[bv].astype(np.float64) * scale
+    f = sdf(x)
+    eps = 1e-6 * max(1.0, float(np.abs(x).max()))
+    grad = np.stack([(sdf(x + eps * e) - sdf(x - eps * e)) / (2 * eps) for e in np.eye(3)], axis=1)
+    grad /= np.maximum(np.linalg.norm(grad, axis=1, keepdims=True), 1e-12)
+    disp = -f[:, None] * grad
+    on_b = np.zeros(len(q), dtype=bool)
+    on_b[bv] = True
+    tb = tets[on_b[tets].any(axis=1)]
+    pos = np.full(len(q), -1, dtype=np.int64)
+    pos[bv] = np.arange(len(bv))
+
+    def volumes(qq):
+        p0 = qq[tb[:, 0]].astype(np.float64)
+        return np.einsum("ij,ij->i", qq[tb[:, 1]] - p0, np.cross(qq[tb[:, 2]] - p0, qq[tb[:, 3]] - p0))
+
+    v0 = volumes(q)
+    fac = np.ones(len(bv))
+    qn = q
+    for it in range(rounds + 64):
+        qn = q.copy()
+        qn[bv] = snap(x + fac[:, None] * disp, grid_bits)
+        bad = ~(volumes(qn) > min_ratio * v0)
+        if not bad.any():
+            break
+        vb = np.unique(tb[bad].ravel())
+        vb = vb[on_b[vb]]
+        # halve the moves of the vertices of too-flat tets; after `rounds`
+        # halvings they stay where the carving put them
+        fac[pos[vb]] = fac[pos[vb]] * 0.5 if it < rounds else 0.0
+    if np.any(orient_int(qn, tets) <= 0):   # exact check; fall back to the carved mesh
+        return q
+    return qn
+
+
 def lattice_mesh(sdf, lo, hi, h: float, grid_bits: int, rng: np.random.Generator,
-                 jitter: float = 0.1, inside_by_vertices: bool = False):
+                 jitter: float = 0.1, inside_by_vertices: bool = False, project: bool = False):
     """Jittered Freudenthal lattice restricted to {sdf < 0}, cleaned to a manifold.
 
     Returns (integer vertex coordinates int64[nv,3], tets int64[nt,4]) with every
@@ -265,4 +311,93 @@ def lattice_mesh(sdf, lo, hi, h: float, grid_bits: int, rng: np.random.Generator
     tets[neg] = tets[neg][:, [0, 1, 3, 2]]
     tets = make_manifold(tets, len(q))
     q, tets = compact(q, tets)
+    if project:
+        q = project_boundary(q, tets, sdf, grid_bits)
     return q, tets
+
+
+def slab_mesh(half, holes, hole_r: float, h: float, grid_bits: int, rng: np.random.Generator,
+              jitter: float = 0.1, min_ratio: float = 0.02, rounds: int = 12):
+    """Tet mesh of the box [-half, half] with z-through cylindrical holes of
+    radius hole_r centred at (x, 0) for x in `holes`, with an exactly planar
+    box boundary, as a surface-fitting tetrahedralisation gives.
+
+    The lattice spacing is the largest h' <= h that divides every side; whole
+    lattice cubes (six Kuhn tets each) are kept when their centre lies outside
+    every hole.  Vertices move by up to `jitter` h' along each axis except the
+    axes of the box planes they lie on, so the box faces stay flat.  The
+    corners of removed cubes (the hole walls) are then moved radially in x-y
+    onto the nearest cylinder, z kept; a move that would leave a tet with less
+    than `min_ratio` of its volume is halved, round after round, and after
+    `rounds` halvings dropped.  Returns integer coordinates and tets."""
+    half = np.asarray(half, dtype=np.float64)
+    m = int(np.ceil(1.0 / h - 1e-9))
+    while np.any(np.abs(2 * half * m - np.round(2 * half * m)) > 1e-9):
+        m += 1
+    hh = 1.0 / m
+    n = np.round(2 * half * m).astype(np.int64)
+    nx, ny, nz = (int(v) for v in n)
+    gi, gj, gk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing='ij')
+    idx = np.stack([gi.ravel(), gj.ravel(), gk.ravel()], axis=1)
+    on_plane = (idx == 0) | (idx == n[None, :])
+    jit = rng.uniform(-jitter * hh, jitter * hh, size=idx.shape)
+    jit[on_plane] = 0.0
+    p = -half + hh * idx + jit
+    vid = lambda i, j, k: (i * (ny + 1) + j) * (nz + 1) + k
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing='ij')
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    cen = -half + hh * (np.stack([ci, cj, ck], axis=1) + 0.5)
+    keep = np.ones(len(ci), dtype=bool)
+    for cx in holes:
+        keep &= np.hypot(cen[:, 0] - cx, cen[:, 1]) >= hole_r
+    corners = np.stack([vid(ci + (c & 1), cj + ((c >> 1) & 1), ck + ((c >> 2) & 1)) for c in range(8)], axis=1)
+    wall = np.zeros(len(p), dtype=bool)
+    wall[np.unique(corners[~keep].ravel())] = True
+    tets = corners[keep][:, KUHN].reshape(-1, 4)
+    q = snap(p, grid_bits)
+    if np.abs(q).max() > MAX_COORD:
+        raise ValueError("coordinates exceed the integer grid bound; lower grid_bits")
+    o = orient_int(q, tets)
+    if np.any(o == 0):
+        raise ValueError("flat tetrahedron after jitter")
+    neg = o < 0
+    tets[neg] = tets[neg][:, [0, 1, 3, 2]]
+    tets = make_manifold(tets, len(q))
+    used = np.zeros(len(q), dtype=bool)
+    used[tets.ravel()] = True
+    wv = np.where(wall & used)[0]
+    if len(holes) and len(wv):
+        hc = np.asarray(holes, dtype=np.float64)
+        x = p[wv]
+        k = np.argmin(np.abs(np.hypot(x[:, None, 0] - hc[None, :], x[:, None, 1]) - hole_r), axis=1)
+        dx, dy = x[:, 0] - hc[k], x[:, 1]
+        rad = np.maximum(np.hypot(dx, dy), 1e-12)
+        disp = np.zeros_like(x)
+        disp[:, 0] = dx * (hole_r / rad - 1.0)
+        disp[:, 1] = dy * (hole_r / rad - 1.0)
+        disp[on_plane[wv]] = 0.0   # a wall vertex on an x or y box plane keeps that coordinate
+        on_w = np.zeros(len(q), dtype=bool)
+        on_w[wv] = True
+        tb = tets[on_w[tets].any(axis=1)]
+        pos = np.full(len(q), -1, dtype=np.int64)
+        pos[wv] = np.arange(len(wv))
+
+        def volumes(qq):
+            p0 = qq[tb[:, 0]].astype(np.float64)
+            return np.einsum("ij,ij->i", qq[tb[:, 1]] - p0, np.cross(qq[tb[:, 2]] - p0, qq[tb[:, 3]] - p0))
+
+        v0 = volumes(q)
+        fac = np.ones(len(wv))
+        qn = q
+        for it in range(rounds + 64):
+            qn = q.copy()
+            qn[wv] = snap(x + fac[:, None] * disp, grid_bits)
+            bad = ~(volumes(qn) > min_ratio * v0)
+            if not bad.any():
+                break
+            vb = np.unique(tb[bad].ravel())
+            vb = vb[on_w[vb]]
+            fac[pos[vb]] = fac[pos[vb]] * 0.5 if it < rounds else 0.0
+        if not np.any(orient_int(qn, tets) <= 0):
+            q = qn
+    return compact(q, tets)
