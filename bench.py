@@ -143,7 +143,10 @@ def clip_roofline(stage, k, workload, precision, peaks, hbm_gbs, stage64=None):
         f64 = PLANNED_FLOP_PER_PIECE[kk] * float(np.mean([s["n_pieces"] for s in stage64]))
         fr["fp64_mode_fp64"] = f64 / (ms64 * 1e-3) / 1e12 / p64
         fr["fp64_mode_fp64_executed"] = float(np.mean([counted_flop(s) for s in stage64])) / (ms64 * 1e-3) / 1e12 / p64
-    named = {k: v for k, v in fr.items() if k in ("fp32", "fp64", "hbm", "fp64_mode_fp64")}
+    # the resource closest to its peak, judged on executed work: the planned
+    # count assumes every candidate clips every piece and overstates the
+    # FP64 mode, where the filter's early exits do not apply
+    named = {k: v for k, v in fr.items() if k in (precision + "_executed", "hbm", "fp64_mode_fp64_executed")}
     out["binding"] = max(named, key=named.get)
     return out
 

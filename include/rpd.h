@@ -274,8 +274,10 @@ rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t
  * contractible and fewer than max_rounds rounds have run, take the pins of all
  * failing elements (rpd_pins), one per boundary triangle, grow a sphere from
  * each (rpd_shrink), round it to the grid, drop repeats of existing spheres,
- * and insert them with a partial update (rpd_insert).  The loop also stops
- * when no failing element has a pin or no new sphere remains.
+ * and insert them with a partial update (rpd_insert).  A pin's boundary
+ * triangle is marked used once a sphere has been grown from it, whether or not
+ * the sphere was new, and pins skip used triangles; the loop also stops when
+ * no failing element has an unused triangle to pin.
  *   rounds, inserted, failing: host pointers (may be NULL) receiving the rounds
  *   run, the spheres inserted and the failing elements left (0 = every RPC,
  *   RPF and RPE contractible).

@@ -837,6 +837,17 @@ rpd_status rpd_insert(rpd_ctx* ctx, const double* d_centers, const double* d_rad
         rpd_destroy(c);
         return st;
     }
+    // settings and counters that outlive a diagram (the mesh is unchanged)
+    c->proposer = ctx->proposer;
+    c->proposer_margin = ctx->proposer_margin;
+    c->shrink_pins = ctx->shrink_pins;
+    c->shrink_iters = ctx->shrink_iters;
+    c->shrink_restarts = ctx->shrink_restarts;
+    c->have_bbox = ctx->have_bbox;
+    for (int a = 0; a < 3; a++) {
+        c->bb_lo[a] = ctx->bb_lo[a];
+        c->bb_hi[a] = ctx->bb_hi[a];
+    }
     // the context takes the new diagram; the old one's memory goes with c
     std::swap(*ctx, *c);
     rpd_destroy(c);
@@ -1134,8 +1145,9 @@ rpd_status rpd_spheres(rpd_ctx* ctx, double* d_centers, double* d_radii, int64_t
 // the grid, repeats of existing or of each other dropped, then inserted with a
 // partial update.  *inserted = the number inserted (0: nothing new).
 static rpd_status grow_from_pins(rpd_ctx* ctx, const std::vector<double>& hp, const std::vector<double>& hn,
-                                 const std::vector<int32_t>& hf, long long* inserted) {
+                                 const std::vector<int32_t>& hf, long long* inserted, long long* tried = nullptr) {
     *inserted = 0;
+    if (tried) *tried = 0;
     const double unit = ldexp(1.0, -ctx->opt.grid_bits), scale = ldexp(1.0, ctx->opt.grid_bits);
     // one pin per boundary triangle
     std::vector<int> keep;
@@ -1150,6 +1162,7 @@ static rpd_status grow_from_pins(rpd_ctx* ctx, const std::vector<double>& hp, co
     }
     if (keep.empty()) return RPD_OK;   // no boundary point to grow from
     const long long m = (long long)keep.size();
+    if (tried) *tried = m;
     std::vector<double> kp(3 * m), kn(3 * m);
     std::vector<int32_t> kf(m);
     for (long long q = 0; q < m; q++) {
@@ -1341,9 +1354,12 @@ rpd_status rpd_repair(rpd_ctx* ctx, int32_t max_rounds, int64_t* rounds, int64_t
         std::vector<int32_t> hf;
         TRY(topology_pins(ctx, hp, hn, hf, &nfail_total));
         if (nfail_total == 0 || nround >= max_rounds) break;
-        long long k = 0;
-        TRY(grow_from_pins(ctx, hp, hn, hf, &k));
-        if (k == 0) break;
+        long long k = 0, tried = 0;
+        TRY(grow_from_pins(ctx, hp, hn, hf, &k, &tried));
+        // a round whose spheres all repeat existing ones still marks its
+        // faces used, so the next round pins other faces; stop only when no
+        // unused face is left to pin
+        if (tried == 0) break;
         nins += k;
         nround++;
     }
