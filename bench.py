@@ -287,6 +287,97 @@ def volume_error(w, pieces, sub, o):
             "relative_to": "tet volume (moment: tet volume x diameter)"}
 
 
+def batch_leg(nshapes, steps, warmup, stream, flush, dev, seed=20240323):
+    """Batching (many shapes of uneven size): the same seeded shapes built
+    one rpd_build per shape in a loop, and as one rpd_build_batch, each step
+    with the 12 table queries per build; the batch's k chosen by the
+    library's autotuner first.  Device time by CUDA events on the stream."""
+    import torch
+    from paper_2403_18761_gb300 import rpd_build
+    from paper_2403_18761_gb300.rpd import load, rpd_options, PRECISION, _ptr
+    import ctypes
+    import rpd_inputs
+    ws = rpd_inputs.batch_shapes(nshapes, seed=seed)
+    g = ws[0].grid_bits
+    dshapes = [tuple(torch.as_tensor(a, dtype=dt, device=dev) for a, dt in
+                     zip((w.verts, w.tets, w.centers, w.radii), (torch.float64, torch.int32, torch.float64,
+                                                                 torch.float64))) for w in ws]
+
+    def queries(ctx):
+        for kind in (1, 2, 3, 4):
+            ctx.rpd_euler(kind), ctx.rpd_components(kind), ctx.rpd_contractible(kind)
+
+    def timed(fn):
+        out = []
+        with torch.cuda.stream(stream):
+            for it in range(warmup + steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pieces = fn()
+                e1.record(stream)
+                e1.synchronize()
+                if it >= warmup:
+                    out.append(e0.elapsed_time(e1))
+        return float(np.mean(out)), pieces
+
+    # the autotuner on the batch (k only: the clip tiles follow the candidate counts)
+    lib = load()
+    hv = np.cumsum([0] + [len(w.verts) for w in ws]).astype(np.int64)
+    ht = np.cumsum([0] + [len(w.tets) for w in ws]).astype(np.int64)
+    hs = np.cumsum([0] + [len(w.radii) for w in ws]).astype(np.int64)
+    V = torch.as_tensor(np.concatenate([w.verts for w in ws]), dtype=torch.float64, device=dev)
+    T = torch.as_tensor(np.concatenate([w.tets + o for w, o in zip(ws, hv[:-1])]), dtype=torch.int32, device=dev)
+    C = torch.as_tensor(np.concatenate([w.centers for w in ws]), dtype=torch.float64, device=dev)
+    R = torch.as_tensor(np.concatenate([w.radii for w in ws]), dtype=torch.float64, device=dev)
+    base = rpd_options()
+    lib.rpd_default_options(ctypes.byref(base))
+    base.precision, base.grid_bits = PRECISION["fp32"], g
+    ks = np.asarray([8, 16, 24, 32], dtype=np.int32)
+    best, tms = rpd_options(), ctypes.c_float(0)
+    st = lib.rpd_autotune_batch(_ptr(V), _ptr(T), _ptr(C), _ptr(R), len(ws), hv.ctypes.data, ht.ctypes.data,
+                                hs.ctypes.data, ctypes.byref(base), ks.ctypes.data, len(ks), 2,
+                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(best), ctypes.byref(tms))
+    k = int(best.k) if st == 0 else 32
+
+    def loop():
+        n = 0
+        for (v, t, c, r) in dshapes:
+            ctx = rpd_build(v, t, c, r, precision="fp32", k=k, grid_bits=g, stream=stream)
+            queries(ctx)
+            n += ctx.rpd_stats_get()["n_pieces"]
+            ctx.rpd_destroy()
+        return n
+
+    def batched():
+        from paper_2403_18761_gb300.rpd import Ctx
+        out = ctypes.c_void_p()
+        opt = rpd_options()
+        lib.rpd_default_options(ctypes.byref(opt))
+        opt.precision, opt.grid_bits, opt.k = PRECISION["fp32"], g, k
+        s = lib.rpd_build_batch(_ptr(V), _ptr(T), _ptr(C), _ptr(R), len(ws), hv.ctypes.data, ht.ctypes.data,
+                                hs.ctypes.data, ctypes.byref(opt), ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.byref(out))
+        if s != 0:
+            raise RuntimeError(f"rpd_build_batch failed ({s})")
+        ctx = Ctx(out, stream, dev, (V, T, C, R))
+        queries(ctx)
+        n = ctx.rpd_stats_get()["n_pieces"]
+        ctx.rpd_destroy()
+        return n
+
+    ms_loop, p_loop = timed(loop)
+    ms_batch, p_batch = timed(batched)
+    return {"shapes": len(ws), "tets": int(ht[-1]), "spheres": int(hs[-1]),
+            "workload": f"{len(ws)} seeded tori / genus 0-5 slabs / ellipsoid unions, log-uniform 1k-100k tets, "
+                        f"32-4k spheres (at most one per 4 tets)",
+            "k_autotuned": k, "autotune_ms_best": float(tms.value), "pieces_per_step": int(p_batch),
+            "pieces_equal": bool(p_loop == p_batch),
+            "per_shape_loop": {"ms_per_step": ms_loop, "value": p_loop / (ms_loop * 1e-3), "unit": UNIT},
+            "batched": {"ms_per_step": ms_batch, "value": p_batch / (ms_batch * 1e-3), "unit": UNIT},
+            "batched_over_loop": ms_loop / ms_batch}
+
+
 def run_reference(args, w):
     """The reference arm: the CPU oracle (brute force, FP64 + exact predicates)
     as it stands on the host cores, each step a seeded tet sample."""
@@ -333,6 +424,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision (profiling)")
+    ap.add_argument("--batch-shapes", type=int, default=64,
+                    help="shapes of the batching leg (0 skips it; the full batching workload has 256)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -488,6 +581,8 @@ def main():
     stage64 = ostage if precision == "fp32" else stage
     line["roofline"] = clip_roofline(stage, kk, args.config, precision, peaks, peaks["hbm_gbs"],
                                      stage64=stage64 if stage64 else None)
+    if args.batch_shapes > 0:
+        line["batch"] = batch_leg(args.batch_shapes, args.steps, args.warmup, stream, flush, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, legs, (sub, o) = cpu_baselines(w, args.config)
         line["cpu_baseline"] = cb

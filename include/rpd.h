@@ -124,6 +124,54 @@ rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, i
                      const rpd_options* opt, void* cuda_stream, rpd_ctx** out);
 
 /*
+ * Batched build (not in the paper, which builds one shape at a time): nshapes
+ * independent problems in one context.  Their arrays are concatenated, shape
+ * s owning vertices [h_vert_off[s], h_vert_off[s+1]), tets [h_tet_off[s],
+ * ...) and spheres [h_sphere_off[s], ...) (HOST i64[nshapes + 1] prefix
+ * offsets from 0); tets hold GLOBAL vertex indices, each inside its own shape
+ * (RPD_E_INVALID otherwise).  Every stage runs once over the union: the
+ * neighbour search walks one sphere grid per shape, so a tet sees only its
+ * own shape's spheres, and the pairs of all shapes are binned together by
+ * candidate count, so shapes of uneven size share the launches.  Results use
+ * global tet and sphere ids; shape s's rows of every table are contiguous
+ * (rpd_batch_offsets) and equal those of rpd_build on shape s alone with its
+ * ids shifted by its offsets.
+ * Limits: fewer than 2^21 spheres in all (RPV keys, as for rpd_build, need
+ * fewer than 2^16), at most 5600 per shape (one grid of 2 n_s + 64 cells in
+ * shared memory), shapes of >= 4 vertices, 1 tet and 1 sphere; no
+ * rpd_insert (and so no repair loop) on a batch context.
+ * Synchronises like rpd_build.
+ */
+rpd_status rpd_build_batch(const double* d_verts, const int32_t* d_tets, const double* d_centers,
+                           const double* d_radii, int32_t nshapes, const int64_t* h_vert_off,
+                           const int64_t* h_tet_off, const int64_t* h_sphere_off, const rpd_options* opt,
+                           void* cuda_stream, rpd_ctx** out);
+/* Per-shape row ranges of a batch's tables: h_off (HOST i64[nshapes + 1])
+ * receives the first row of each shape and the total, for kind 1..4 (the
+ * rows of rpd_euler / rpd_components / rpd_contractible) or 0 (the pieces
+ * of rpd_pieces).  Synchronises the stream. */
+rpd_status rpd_batch_offsets(rpd_ctx* ctx, int32_t kind, int64_t* h_off);
+
+/*
+ * Autotuner (not in the paper): builds the problem (or batch) with each
+ * neighbour count k in ks[0..nk) (nk <= 32), reps timed builds after one
+ * warm-up per k (reps <= 64), CUDA events on the stream, and returns in
+ * *best the base options (NULL = defaults) with the k of the fastest median
+ * build, and that median in *ms_best (may be NULL).  The diagram does not
+ * depend on k (the candidate sets are exact), only the time does.  The clip's
+ * tiles follow each tet's candidate count and need no tuning.  Errors of a
+ * build are returned as they are.
+ */
+rpd_status rpd_autotune(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt, const double* d_centers,
+                        const double* d_radii, int64_t ns, const rpd_options* base, const int32_t* ks, int32_t nk,
+                        int32_t reps, void* cuda_stream, rpd_options* best, float* ms_best);
+rpd_status rpd_autotune_batch(const double* d_verts, const int32_t* d_tets, const double* d_centers,
+                              const double* d_radii, int32_t nshapes, const int64_t* h_vert_off,
+                              const int64_t* h_tet_off, const int64_t* h_sphere_off, const rpd_options* base,
+                              const int32_t* ks, int32_t nk, int32_t reps, void* cuda_stream, rpd_options* best,
+                              float* ms_best);
+
+/*
  * Fractional Euler characteristic chi of every element of one kind
  * (Sec. 4.1.2: chi = sum of the per-tet contributions, Eq. 7).
  * Two-phase: with d_keys == NULL only *n is set.  Otherwise cap >= *n is

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librpd.so")
-SOURCES = ["api.cu", "prep.cu", "knn.cu", "clip.cu", "topo.cu", "prim.cu", "static_api.cu", "peaks.cu", "update.cu", "repair.cu", "medial.cu", "envelope.cu", "mlp.cu"]
+SOURCES = ["api.cu", "prep.cu", "knn.cu", "clip.cu", "topo.cu", "prim.cu", "static_api.cu", "peaks.cu", "update.cu", "repair.cu", "medial.cu", "envelope.cu", "mlp.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--extended-lambda",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

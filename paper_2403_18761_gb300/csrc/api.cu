@@ -150,6 +150,12 @@ struct rpd_ctx {
     double* btri = nullptr;
     int32_t* btri_face = nullptr;
     long long nbtri = -1;
+    // batches (rpd_build_batch): shape offsets of vertices, tets and spheres
+    // (device copies and the host's), and the largest per-shape grid
+    int nshapes = 1;
+    long long *d_voff = nullptr, *d_toff = nullptr, *d_soff = nullptr;
+    std::vector<long long> h_voff, h_toff, h_soff;
+    long long max_shape_ncap = 0;
     // mesh bounding box (world units), computed on first use
     bool have_bbox = false;
     double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};
@@ -438,6 +444,19 @@ rpd_status build(rpd_ctx* c, const double* d_verts, const int32_t* d_tets, const
     size_t tmp_bytes = prep_tmp_bytes(nt, nv);
     void* tmp = c->alloc<char>(tmp_bytes);
     NEED(tmp);
+    if (c->nshapes > 1) {
+        // batch: shape offsets on the device, every tet inside its own shape (checked before the mesh
+        // combinatorics start, so a cross-shape tet reports RPD_E_INVALID first)
+        const int S = c->nshapes;
+        c->d_voff = c->alloc<long long>(S + 1);
+        c->d_toff = c->alloc<long long>(S + 1);
+        c->d_soff = c->alloc<long long>(S + 1);
+        NEED(c->d_voff && c->d_toff && c->d_soff);
+        cudaMemcpyAsync(c->d_voff, c->h_voff.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(c->d_toff, c->h_toff.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(c->d_soff, c->h_soff.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, s);
+        launch_batch_check(c->tets, c->d_toff, c->d_voff, S, nt, c->st, s);
+    }
     record(c, 1);
     cudaStreamWaitEvent(bs->s[0], c->ev[1], 0);
     launch_prep_mesh(c->tets, nt, nv, c->Xi, c->adj, c->own, tmp, c->st, bs->s[0]);
@@ -487,8 +506,11 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
     const long long nv = c->nv, nt = c->nt, ns = c->ns;
     BinStreams* bs = bin_streams();
     // ---- A1
-    long long ncap = 2 * ns + 64;
-    c->gp = c->alloc<GridParams>(1);
+    // one grid (2 ns + 64 cells), or one per shape of a batch (2 n_s + 64
+    // cells and an end offset each, laid end to end)
+    const bool batch = c->nshapes > 1;
+    long long ncap = batch ? 2 * ns + 65ll * c->nshapes : 2 * ns + 64;
+    c->gp = c->alloc<GridParams>(c->nshapes);
     c->cell_start = c->alloc<int64_t>(ncap + 1);
     c->cell_ids = c->alloc<int32_t>(ns);
     c->cell_wmax = c->alloc<long long>(2 * ncap);
@@ -500,10 +522,14 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
     long long* cell_w = c->alloc<long long>(ns);
     void* ktmp = c->alloc<char>(knn_tmp_bytes(nv));
     NEED(cell_sph && cell_w && ktmp);
-    launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
-                       gtmp, s);
+    if (batch)
+        launch_sphere_grid_batch(c->Ci, c->W, c->d_soff, c->nshapes, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph,
+                                 cell_w, c->cell_wmax, c->max_shape_ncap, s);
+    else
+        launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
+                           gtmp, s);
     launch_knn(c->Xi, nv, ns, c->gp, c->cell_start, cell_sph, cell_w, c->cell_wmax, ncap, c->K, c->knn, c->dplus, ktmp,
-               &c->st->err, (c->opt.debug_checks & 4) != 0, s);
+               &c->st->err, (c->opt.debug_checks & 4) != 0, s, c->d_voff, c->nshapes);
     TRY(cuda_check(c, "knn launch"));
     record(c, 3);
     // ---- A2
@@ -519,7 +545,8 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
     NEED(c->cand_cnt && c->cand && c->cand_ord && c->fb_list && c->fb_count && c->pair_off && stmp && c->bin_count &&
          c->bin_fill);
     launch_candidates(c->tets, nt, nv, c->Xi, c->Ci, c->W, c->knn, c->dplus, c->K, c->gp, c->cell_start,
-                      c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->cand_ord, c->fb_list, c->fb_count, c->st, s);
+                      c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->cand_ord, c->fb_list, c->fb_count, c->st, s,
+                      c->d_voff, c->nshapes);
     scan_excl(c->cand_cnt, c->pair_off, nt, stmp, s);
     if (old) {   // partial update: clip only the tets whose candidates changed
         c->changed = c->alloc<uint8_t>(nt);
@@ -817,8 +844,178 @@ rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, i
     return RPD_OK;
 }
 
+rpd_status rpd_build_batch(const double* d_verts, const int32_t* d_tets, const double* d_centers,
+                           const double* d_radii, int32_t nshapes, const int64_t* h_vert_off,
+                           const int64_t* h_tet_off, const int64_t* h_sphere_off, const rpd_options* opt,
+                           void* cuda_stream, rpd_ctx** out) {
+    if (!out) return RPD_E_INVALID;
+    *out = nullptr;
+    auto reject = [](const char* m) {
+        g_build_error = m;
+        return RPD_E_INVALID;
+    };
+    if (nshapes < 1 || nshapes > (1 << 20)) return reject("nshapes must be in [1, 2^20]");
+    if (!h_vert_off || !h_tet_off || !h_sphere_off) return reject("null offset array");
+    if (h_vert_off[0] != 0 || h_tet_off[0] != 0 || h_sphere_off[0] != 0) return reject("offsets must start at 0");
+    long long max_ncap = 0;
+    for (int s = 0; s < nshapes; s++) {
+        const long long nv_s = h_vert_off[s + 1] - h_vert_off[s], nt_s = h_tet_off[s + 1] - h_tet_off[s],
+                        ns_s = h_sphere_off[s + 1] - h_sphere_off[s];
+        if (nv_s < 4 || nt_s < 1 || ns_s < 1) return reject("every shape needs >= 4 vertices, a tet and a sphere");
+        max_ncap = std::max(max_ncap, 2 * ns_s + 64);
+    }
+    if (max_ncap > batch_grid_cap()) return reject("a shape of a batch has more spheres than its grid takes");
+    const long long nv = h_vert_off[nshapes], nt = h_tet_off[nshapes], ns = h_sphere_off[nshapes];
+    if (ns >= (1ll << 21)) return reject("a batch holds fewer than 2^21 spheres");
+    rpd_options o;
+    rpd_default_options(&o);
+    if (opt) o = *opt;
+    if (o.debug_checks & 4) return reject("the tiled neighbour search does not take batches");
+    if (nshapes == 1) return rpd_build(d_verts, nv, d_tets, nt, d_centers, d_radii, ns, &o, cuda_stream, out);
+    if (nv >= (1ll << 21)) return reject("nv must be < 2^21");
+    if (nt >= (1ll << 31) / RPD_MAXC) return reject("nt must be < 2^26");
+    if (!d_verts || !d_tets || !d_centers || !d_radii) return reject("null input pointer");
+    if (o.k < 1 || o.k > RPD_MAXK) return reject("k must be in [1, 32]");
+    if (o.grid_bits < 0 || o.grid_bits > 40) return reject("grid_bits must be in [0, 40]");
+    if (o.precision != RPD_FP64 && o.precision != RPD_FP32_FILTERED) return reject("unknown precision");
+    rpd_ctx* c = new rpd_ctx();
+    c->stream = (cudaStream_t)cuda_stream;
+    c->opt = o;
+    c->nv = nv;
+    c->nt = nt;
+    c->ns = ns;
+    c->K = o.k;
+    c->key_bits = bits_for(ns);
+    c->nshapes = nshapes;
+    c->h_voff.assign(h_vert_off, h_vert_off + nshapes + 1);
+    c->h_toff.assign(h_tet_off, h_tet_off + nshapes + 1);
+    c->h_soff.assign(h_sphere_off, h_sphere_off + nshapes + 1);
+    c->max_shape_ncap = max_ncap;
+    rpd_status st = build(c, d_verts, d_tets, d_centers, d_radii);
+    if (st != RPD_OK) {
+        g_build_error = c->last_error.empty() ? "build failed" : c->last_error;
+        rpd_destroy(c);
+        return st;
+    }
+    g_build_error.clear();
+    *out = c;
+    return RPD_OK;
+}
+
+}  // extern "C"
+
+// Time `build` (which makes and returns a context) for each k of ks, reps
+// times after one warm-up, with CUDA events on the stream; keep the fastest
+// median.  Every k gives the same diagram (the candidate sets are exact), so
+// only the time decides.
+template <typename Build>
+static rpd_status autotune(const rpd_options* base, const int32_t* ks, int32_t nk, int32_t reps, void* cuda_stream,
+                           Build build, rpd_options* best, float* ms_best) {
+    if (!ks || nk < 1 || nk > 32 || reps < 1 || reps > 64 || !best) return RPD_E_INVALID;
+    rpd_options o;
+    rpd_default_options(&o);
+    if (base) o = *base;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return RPD_E_CUDA;
+    }
+    float best_ms = INFINITY;
+    int best_k = -1;
+    rpd_status err = RPD_OK;
+    for (int q = 0; q < nk && err == RPD_OK; q++) {
+        o.k = ks[q];
+        std::vector<float> t;
+        for (int r = 0; r <= reps && err == RPD_OK; r++) {
+            rpd_ctx* c = nullptr;
+            cudaEventRecord(e0, s);
+            err = build(&o, &c);
+            cudaEventRecord(e1, s);
+            float ms = 0;
+            if (err == RPD_OK &&
+                (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)) {
+                cudaGetLastError();
+                err = RPD_E_CUDA;
+            }
+            if (c) rpd_destroy(c);
+            if (r > 0) t.push_back(ms);   // the first build of each k warms up
+        }
+        if (err != RPD_OK) break;
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            best_k = ks[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != RPD_OK) return err;
+    o.k = best_k;
+    *best = o;
+    if (ms_best) *ms_best = best_ms;
+    return RPD_OK;
+}
+
+extern "C" {
+
+rpd_status rpd_autotune(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt, const double* d_centers,
+                        const double* d_radii, int64_t ns, const rpd_options* base, const int32_t* ks, int32_t nk,
+                        int32_t reps, void* cuda_stream, rpd_options* best, float* ms_best) {
+    return autotune(base, ks, nk, reps, cuda_stream,
+                    [&](const rpd_options* o, rpd_ctx** c) {
+                        return rpd_build(d_verts, nv, d_tets, nt, d_centers, d_radii, ns, o, cuda_stream, c);
+                    },
+                    best, ms_best);
+}
+
+rpd_status rpd_autotune_batch(const double* d_verts, const int32_t* d_tets, const double* d_centers,
+                              const double* d_radii, int32_t nshapes, const int64_t* h_vert_off,
+                              const int64_t* h_tet_off, const int64_t* h_sphere_off, const rpd_options* base,
+                              const int32_t* ks, int32_t nk, int32_t reps, void* cuda_stream, rpd_options* best,
+                              float* ms_best) {
+    return autotune(base, ks, nk, reps, cuda_stream,
+                    [&](const rpd_options* o, rpd_ctx** c) {
+                        return rpd_build_batch(d_verts, d_tets, d_centers, d_radii, nshapes, h_vert_off, h_tet_off,
+                                               h_sphere_off, o, cuda_stream, c);
+                    },
+                    best, ms_best);
+}
+
+rpd_status rpd_batch_offsets(rpd_ctx* ctx, int32_t kind, int64_t* h_off) {
+    if (!ctx) return RPD_E_INVALID;
+    if (!h_off) return fail(ctx, RPD_E_INVALID, "null output");
+    const int S = ctx->nshapes;
+    if (S == 1) {
+        h_off[0] = 0;
+        if (kind == 0) h_off[1] = ctx->npieces;
+        else {
+            TRY(check_kind(ctx, (rpd_kind)kind));
+            h_off[1] = ctx->nkeys[kind - 1];
+        }
+        return RPD_OK;
+    }
+    long long* d = ctx->alloc<long long>(S + 1);
+    if (!d) return fail(ctx, RPD_E_OOM, "device allocation failed");
+    if (kind == 0) {
+        launch_batch_cut_pieces(ctx->pair_off, ctx->piece_off, ctx->d_toff, S, d, ctx->stream);
+    } else {
+        TRY(check_kind(ctx, (rpd_kind)kind));
+        launch_batch_cut(ctx->fout[kind - 1].keys, ctx->nkeys[kind - 1], kind, ctx->d_soff, S, d, ctx->stream);
+    }
+    cudaMemcpyAsync(h_off, d, sizeof(long long) * (S + 1), cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RPD_E_CUDA, "CUDA error while cutting the tables by shape");
+    }
+    return RPD_OK;
+}
+
 rpd_status rpd_insert(rpd_ctx* ctx, const double* d_centers, const double* d_radii, int64_t n_new) {
     if (!ctx) return RPD_E_INVALID;
+    if (ctx->nshapes > 1) return fail(ctx, RPD_E_INVALID, "a batch context takes no insertions");
     if (n_new < 0 || ctx->ns + n_new >= (1ll << 21))
         return fail(ctx, RPD_E_INVALID, "n_new must be >= 0 and ns + n_new < 2^21");
     if (n_new == 0) return RPD_OK;

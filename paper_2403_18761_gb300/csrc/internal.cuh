@@ -13,6 +13,8 @@ struct GridParams {
     int3 dim;          // cells per axis
     int ncell;
     long long wmax;    // largest power weight r^2
+    long long cbase;   // offset of this grid's cells in the cell arrays (batches: one grid per shape)
+    long long sbase;   // id of the grid's first sphere (its slots hold ids relative to it)
 };
 
 // ---------------------------------------------------------------- prep.cu
@@ -42,14 +44,27 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
 size_t knn_tmp_bytes(long long nv);
 void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
                 const int4* cell_sph, const long long* cell_w, const long long* cell_wmax, long long ncap, int K,
-                int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s);
+                int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s,
+                const long long* voff = nullptr, int nshapes = 1);
+// Batches: one grid per shape, all built by one launch (a block per shape).
+// Shape s owns spheres [soff[s], soff[s + 1]) (device array) and cells
+// [2 soff[s] + 65 s, 2 soff[s + 1] + 65 (s + 1)) of cell_start (its
+// 2 n_s + 64 cells and one end offset) and of both halves of cell_wmax
+// (cell maxima, then row maxima at + ncap_total).  Every shape needs
+// 2 n_s + 64 <= batch_grid_cap() cells.
+long long batch_grid_cap();
+void launch_sphere_grid_batch(const int32_t* Ci, const long long* W, const long long* soff, int nshapes,
+                              long long ncap_total, GridParams* gp, int64_t* cell_start, int32_t* cell_ids,
+                              int4* cell_sph, long long* cell_w, long long* cell_wmax, long long max_shape_ncap,
+                              cudaStream_t s);
 // Candidate spheres of every tet (superset of the spheres whose cell meets
 // the tet with positive volume), sorted by index, at most RPD_MAXC.
 void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, const int32_t* Ci,
                        const long long* W, const int32_t* knn, const long long* dplus, int K,
                        const GridParams* gp, const int64_t* cell_start, const int32_t* cell_ids,
                        const long long* cell_wmax, int32_t* cand_cnt, int32_t* cand, uint8_t* cand_ord,
-                       int32_t* fb_list, int32_t* fb_count, DevState* st, cudaStream_t s);
+                       int32_t* fb_list, int32_t* fb_count, DevState* st, cudaStream_t s,
+                       const long long* voff = nullptr, int nshapes = 1);
 
 // ---------------------------------------------------------------- clip.cu
 struct ClipArgs {
@@ -181,6 +196,18 @@ int medial_thin(const std::vector<int32_t>& edges, const std::vector<int32_t>& f
 // The context's spheres after grid rounding, in world units.
 void launch_sphere_out(const int32_t* Ci, const long long* W, long long ns, double unit, double* c, double* r,
                        cudaStream_t s);
+// --------------------------------------------------------------- batch.cu
+// Device offsets voff/toff (nshapes + 1 entries).  A tet with a corner of
+// another shape raises RPD_E_INVALID on the status word.
+void launch_batch_check(const int32_t* tets, const long long* toff, const long long* voff, int nshapes,
+                        long long nt, DevState* st, cudaStream_t s);
+// out[0..nshapes]: first row of each shape in a table sorted by its leading
+// column (row stride `stride` int32), by the leading-column bounds `bound`.
+void launch_batch_cut(const int32_t* lead, long long rows, int stride, const long long* bound, int nshapes,
+                      long long* out, cudaStream_t s);
+void launch_batch_cut_pieces(const int64_t* pair_off, const int64_t* piece_off, const long long* toff, int nshapes,
+                             long long* out, cudaStream_t s);
+
 // Sphere shrinking from n pins against the boundary triangles; r_start
 // (NULL or per pin, 0 = plain) proposes the first radius, restarted (NULL or
 // per pin) flags proposals that were rejected.

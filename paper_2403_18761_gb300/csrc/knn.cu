@@ -83,7 +83,22 @@ __device__ GridParams grid_params(const int* mn, const int* mx, long long wm, lo
     g.dim = make_int3((int)d[0], (int)d[1], (int)d[2]);
     g.ncell = (int)(d[0] * d[1] * d[2]);
     g.wmax = wm;
+    g.cbase = 0;
+    g.sbase = 0;
     return g;
+}
+
+// Shape of vertex v in a batch: the s with voff[s] <= v < voff[s + 1]
+// (0 without a batch).
+__device__ __forceinline__ int shape_of(const long long* __restrict__ voff, int nshapes, long long v) {
+    if (!voff || nshapes <= 1) return 0;
+    int lo = 0, hi = nshapes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (voff[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Bounding box of the sphere centres and the largest weight, reduced over
@@ -206,6 +221,67 @@ __global__ void __launch_bounds__(1024) k_grid_small(const int32_t* __restrict__
         ids[pos] = (int32_t)i;
         sph[pos] = make_int4(ci.x, ci.y, ci.z, (int)i);
         sw[pos] = W[i];
+    }
+}
+
+// One grid per shape of a batch, a block per shape: as k_grid_small on the
+// shape's spheres, with cell offsets relative to the shape's cell base and
+// sorted slots at the shape's sphere offset.
+__global__ void __launch_bounds__(1024) k_grid_batch(const int32_t* __restrict__ Ci, const long long* __restrict__ W,
+                                                     const long long* __restrict__ soff, long long ncap_total,
+                                                     GridParams* gp, int64_t* __restrict__ start_all,
+                                                     int32_t* __restrict__ ids, int4* __restrict__ sph,
+                                                     long long* __restrict__ sw, long long* __restrict__ cwmax_all) {
+    extern __shared__ int scount[];
+    __shared__ GridParams sg;
+    const int sh = blockIdx.x;
+    const long long s0 = soff[sh], ns = soff[sh + 1] - s0;
+    const long long ncap = 2 * ns + 64, cbase = 2 * s0 + 65ll * sh;
+    int64_t* start = start_all + cbase;
+    long long* cwmax = cwmax_all + cbase;
+    long long* rwmax = cwmax_all + ncap_total + cbase;
+    block_grid_params(Ci + 3 * s0, W + s0, ns, ncap, &sg);
+    for (long long q = threadIdx.x; q < ncap; q += blockDim.x) {
+        scount[q] = 0;
+        cwmax[q] = 0;
+        rwmax[q] = 0;
+    }
+    __syncthreads();
+    GridParams g = sg;
+    g.cbase = cbase;
+    g.sbase = s0;
+    if (threadIdx.x == 0) gp[sh] = g;
+    for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int3 c = cell_of(ld_int3(Ci, s0 + i), g);
+        const int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
+        atomicAdd(&scount[q], 1);
+        atomicMax((unsigned long long*)&cwmax[q], (unsigned long long)W[s0 + i]);
+        atomicMax((unsigned long long*)&rwmax[c.z * g.dim.y + c.y], (unsigned long long)W[s0 + i]);
+    }
+    __syncthreads();
+    const int per = (int)((ncap + blockDim.x - 1) / blockDim.x);
+    const int lo = min((long long)threadIdx.x * per, ncap), hi = min((long long)lo + per, ncap);
+    int sum = 0;
+    for (int q = lo; q < hi; q++) sum += scount[q];
+    int total;
+    int run = block_excl_scan(sum, &total);
+    for (int q = lo; q < hi; q++) {
+        const int n = scount[q];
+        start[q] = s0 + run;
+        scount[q] = run;
+        run += n;
+    }
+    if (threadIdx.x == 0) start[ncap] = s0 + total;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        const long long gi = s0 + i;
+        const int3 ci = ld_int3(Ci, gi);
+        const int3 c = cell_of(ci, g);
+        const int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
+        const long long pos = s0 + atomicAdd(&scount[q], 1);
+        ids[pos] = (int32_t)gi;
+        sph[pos] = make_int4(ci.x, ci.y, ci.z, (int)i);   // shape-local id: 17 bits of the kNN key suffice
+        sw[pos] = W[gi];
     }
 }
 
@@ -554,10 +630,11 @@ __device__ __forceinline__ long long knn_key_dist(unsigned long long e) { return
 
 __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
                                                   long long nv, const GridParams* __restrict__ gp,
-                                                  const int64_t* __restrict__ start, const int4* __restrict__ sph,
+                                                  const int64_t* __restrict__ start_all, const int4* __restrict__ sph,
                                                   const long long* __restrict__ sw,
-                                                  const long long* __restrict__ rwmax, int K,
-                                                  int32_t* __restrict__ knn, long long* __restrict__ dplus) {
+                                                  const long long* __restrict__ rwmax_all, int K,
+                                                  int32_t* __restrict__ knn, long long* __restrict__ dplus,
+                                                  const long long* __restrict__ voff, int nshapes) {
     typedef unsigned long long U;
     const unsigned FULL = 0xffffffffu;
     const U EMPTY = ~0ull;
@@ -565,7 +642,9 @@ __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nv) return;   // warp-uniform
     const long long v = vorder ? (long long)vorder[w] : w;
-    const GridParams g = *gp;
+    const GridParams g = gp[shape_of(voff, nshapes, v)];   // the vertex's own shape's grid
+    const int64_t* __restrict__ start = start_all + g.cbase;
+    const long long* __restrict__ rwmax = rwmax_all + g.cbase;
     const int3 x = ld_int3(Xi, v);
     const int3 c = cell_of(x, g);
     U L = EMPTY;               // lane j: the j-th smallest key so far
@@ -696,7 +775,7 @@ __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi
     if (lb2 != LLONG_MAX) dp = min(dp, lb2 - g.wmax);   // whatever was not explored
 #pragma unroll
     for (int o = 16; o; o >>= 1) dp = min(dp, __shfl_xor_sync(FULL, dp, o));
-    if (lane < K) knn[v * K + lane] = L == EMPTY ? -1 : (int)(L & 0x1ffffu);
+    if (lane < K) knn[v * K + lane] = L == EMPTY ? -1 : (int)(L & 0x1ffffu) + (int)g.sbase;
     if (lane == 0) dplus[v] = dp;
 }
 
@@ -922,9 +1001,10 @@ constexpr int FB_THREADS = 256;
 __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
     const int32_t* __restrict__ T, long long nv, const int32_t* __restrict__ Xi, const int32_t* __restrict__ Ci,
     const long long* __restrict__ W, const int32_t* __restrict__ knn, int K, const GridParams* __restrict__ gp,
-    const int64_t* __restrict__ start, const int32_t* __restrict__ ids, const long long* __restrict__ cwmax,
+    const int64_t* __restrict__ start_all, const int32_t* __restrict__ ids, const long long* __restrict__ cwmax_all,
     const int32_t* __restrict__ fb_list, const int32_t* __restrict__ fb_count, int32_t* __restrict__ cand_cnt,
-    int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st) {
+    int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st, const long long* __restrict__ voff,
+    int nshapes) {
     const unsigned FULL = 0xffffffffu;
     __shared__ int sid[FB_GATHER];
     __shared__ long long sD[FB_GATHER][4];
@@ -932,8 +1012,6 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
     __shared__ int sn;
     const int tid = threadIdx.x, lane = tid & 31;
     const long long nfb = *fb_count;
-    const GridParams g = *gp;
-    const int ncell = g.dim.x * g.dim.y * g.dim.z, nxy = g.dim.x * g.dim.y;
     for (long long q = blockIdx.x; q < nfb; q += gridDim.x) {
         const long long t = fb_list[q];   // uniform over the block
         int v[4];
@@ -942,6 +1020,11 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
             if (tid == 0) cand_cnt[t] = 0;
             continue;
         }
+        // the grid of the tet's shape (its first corner's)
+        const GridParams g = gp[shape_of(voff, nshapes, v[0])];
+        const int64_t* __restrict__ start = start_all + g.cbase;
+        const long long* __restrict__ cwmax = cwmax_all + g.cbase;
+        const int ncell = g.dim.x * g.dim.y * g.dim.z, nxy = g.dim.x * g.dim.y;
         int o[4];
         for (int a = 0; a < 4; a++) o[a] = knn[(long long)v[a] * K];
         long long M[4][4];
@@ -1090,9 +1173,22 @@ size_t knn_tmp_bytes(long long nv) {
     return 2 * al(sizeof(uint64_t) * nv) + 2 * al(sizeof(uint32_t) * nv) + radix_tmp_bytes(nv);
 }
 
+long long batch_grid_cap() { return GRID_SMALL_CAP; }
+
+void launch_sphere_grid_batch(const int32_t* Ci, const long long* W, const long long* soff, int nshapes,
+                              long long ncap_total, GridParams* gp, int64_t* cell_start, int32_t* cell_ids,
+                              int4* cell_sph, long long* cell_w, long long* cell_wmax, long long max_shape_ncap,
+                              cudaStream_t s) {
+    if (nshapes <= 0) return;
+    k_grid_batch<<<(unsigned)nshapes, 1024, sizeof(int) * max_shape_ncap, s>>>(Ci, W, soff, ncap_total, gp, cell_start,
+                                                                                cell_ids, cell_sph, cell_w, cell_wmax);
+    note_launch();
+}
+
 void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
                 const int4* cell_sph, const long long* cell_w, const long long* cell_wmax, long long ncap, int K,
-                int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s) {
+                int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s,
+                const long long* voff, int nshapes) {
     if (nv == 0) return;
     char* p = (char*)tmp;
     uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
@@ -1101,10 +1197,10 @@ void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams*
     uint32_t* v1 = (uint32_t*)p; p += al(sizeof(uint32_t) * nv);
     int bits = 1;
     while ((1ll << bits) < ncap) bits++;
-    if (ns <= (1 << 17) && !two_word) {
+    if ((ns <= (1 << 17) || nshapes > 1) && !two_word) {   // batches: shape-local ids in the key
         // one vertex per warp in input order: the sphere grid stays in cache
         k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nullptr, nv, gp, cell_start, cell_sph, cell_w,
-                                                       cell_wmax + ncap, K, knn, dplus);
+                                                       cell_wmax + ncap, K, knn, dplus, voff, nshapes);
     } else {
         k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
         note_launch();
@@ -1119,7 +1215,7 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
                        const long long* W, const int32_t* knn, const long long* dplus, int K, const GridParams* gp,
                        const int64_t* cell_start, const int32_t* cell_ids, const long long* cell_wmax,
                        int32_t* cand_cnt, int32_t* cand, uint8_t* cand_ord, int32_t* fb_list, int32_t* fb_count,
-                       DevState* st, cudaStream_t s) {
+                       DevState* st, cudaStream_t s, const long long* voff, int nshapes) {
     if (nt == 0) return;
     cudaMemsetAsync(fb_count, 0, sizeof(int32_t), s);
     k_candidates_warp<<<nblk(32 * nt, 256), 256, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand,
@@ -1127,6 +1223,7 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
                                                fb_list, fb_count, st);
     note_launch();
     k_candidates_fallback<<<152 * 4, FB_THREADS, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids,
-                                                         cell_wmax, fb_list, fb_count, cand_cnt, cand, cand_ord, st);
+                                                         cell_wmax, fb_list, fb_count, cand_cnt, cand, cand_ord, st,
+                                                         voff, nshapes);
     note_launch();
 }

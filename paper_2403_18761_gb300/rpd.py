@@ -129,6 +129,14 @@ def load(path: str = LIB_PATH):
     lib.rpd_envelope_distance.restype = ctypes.c_int
     lib.rpd_repair_geometry.argtypes = [P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(rpd_repair_report)]
     lib.rpd_repair_geometry.restype = ctypes.c_int
+    lib.rpd_build_batch.argtypes = [P, P, P, P, ctypes.c_int32, P, P, P, ctypes.POINTER(rpd_options), P,
+                                    ctypes.POINTER(P)]
+    lib.rpd_build_batch.restype = ctypes.c_int
+    lib.rpd_autotune.argtypes = [P, I64, P, I64, P, P, I64, ctypes.POINTER(rpd_options), P, ctypes.c_int32,
+                                 ctypes.c_int32, P, ctypes.POINTER(rpd_options), ctypes.POINTER(ctypes.c_float)]
+    lib.rpd_autotune.restype = ctypes.c_int
+    lib.rpd_batch_offsets.argtypes = [P, ctypes.c_int32, P]
+    lib.rpd_batch_offsets.restype = ctypes.c_int
     lib.rpd_shrink_warm.argtypes = [P, P, P, P, I64, P, P, P, P, P]
     lib.rpd_shrink_warm.restype = ctypes.c_int
     lib.rpd_pin_features.argtypes = [P, P, P, P, I64, P, P]
@@ -399,6 +407,14 @@ class Ctx:
             self.stream.synchronize()
         return c, r, it
 
+    def shape_offsets(self, kind):
+        """First row of each shape of a batch in the tables of `kind`
+        (1..4; 0 for the pieces), and the total: int64[nshapes + 1]."""
+        nshapes = len(self.batch["sphere_off"]) - 1 if getattr(self, "batch", None) else 1
+        out = np.zeros(nshapes + 1, dtype=np.int64)
+        self._check(load().rpd_batch_offsets(self.handle, int(kind), out.ctypes.data))
+        return out
+
     def rpd_shrink_warm(self, pins, normals, faces, r_start):
         """Shrinking from proposed first radii (0 = plain start): (centres,
         radii, iterations, restarted int32[n]) on the device."""
@@ -573,6 +589,69 @@ def rpd_build(verts, tets, centers, radii, precision="fp32", k=16, grid_bits=20,
     if st != RPD_OK:
         raise RpdError(st, lib.rpd_build_error().decode())
     return Ctx(out, stream, dev, (V, T, C, R))
+
+
+def rpd_build_batch(shapes, precision="fp32", k=16, grid_bits=20, stream=None, debug=0):
+    """rpd_build_batch on a list of (verts, tets, centers, radii) with
+    shape-local tet indices: the arrays are concatenated and the tets
+    offset (argument marshalling); returns a Ctx whose `shape_offsets(kind)`
+    gives each shape's rows."""
+    lib = load()
+    if not torch.cuda.is_available():
+        raise RuntimeError("librpd needs a CUDA device; there is no CPU fallback")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vs, ts, cs, rs = [], [], [], []
+    voff, toff, soff = [0], [0], [0]
+    for (v, t, c, r) in shapes:
+        v = np.asarray(v, dtype=np.float64).reshape(-1, 3)
+        t = np.asarray(t, dtype=np.int64).reshape(-1, 4) + voff[-1]
+        c = np.asarray(c, dtype=np.float64).reshape(-1, 3)
+        r = np.asarray(r, dtype=np.float64).reshape(-1)
+        vs.append(v), ts.append(t), cs.append(c), rs.append(r)
+        voff.append(voff[-1] + len(v)), toff.append(toff[-1] + len(t)), soff.append(soff[-1] + len(r))
+    V = _dev_f64(np.concatenate(vs), dev)
+    T = _dev_i32(np.concatenate(ts).astype(np.int32), dev)
+    C = _dev_f64(np.concatenate(cs), dev)
+    R = _dev_f64(np.concatenate(rs), dev)
+    hv, ht, hs = (np.asarray(o, dtype=np.int64) for o in (voff, toff, soff))
+    opt = rpd_options()
+    lib.rpd_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    opt.k = int(k)
+    opt.grid_bits = int(grid_bits)
+    opt.debug_checks = int(debug)
+    sh, stream = _stream_handle(stream)
+    out = ctypes.c_void_p()
+    st = lib.rpd_build_batch(_ptr(V), _ptr(T), _ptr(C), _ptr(R), len(shapes), hv.ctypes.data, ht.ctypes.data,
+                             hs.ctypes.data, ctypes.byref(opt), sh, ctypes.byref(out))
+    if st != RPD_OK:
+        raise RpdError(st, lib.rpd_build_error().decode())
+    ctx = Ctx(out, stream, dev, (V, T, C, R))
+    ctx.batch = dict(vert_off=hv, tet_off=ht, sphere_off=hs)
+    return ctx
+
+
+def rpd_autotune(verts, tets, centers, radii, ks=(8, 16, 24, 32), reps=3, precision="fp32", grid_bits=20,
+                 stream=None):
+    """The library's autotuner: (fastest k, its median build time in ms)."""
+    lib = load()
+    if not torch.cuda.is_available():
+        raise RuntimeError("librpd needs a CUDA device; there is no CPU fallback")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    V, T, C, R = _dev_f64(verts, dev), _dev_i32(tets, dev), _dev_f64(centers, dev), _dev_f64(radii, dev)
+    base = rpd_options()
+    lib.rpd_default_options(ctypes.byref(base))
+    base.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    base.grid_bits = int(grid_bits)
+    kk = np.asarray(ks, dtype=np.int32)
+    best = rpd_options()
+    ms = ctypes.c_float(0)
+    sh, _ = _stream_handle(stream)
+    st = lib.rpd_autotune(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(C), _ptr(R), R.shape[0], ctypes.byref(base),
+                          kk.ctypes.data, len(kk), int(reps), sh, ctypes.byref(best), ctypes.byref(ms))
+    if st != RPD_OK:
+        raise RpdError(st, lib.rpd_build_error().decode())
+    return int(best.k), float(ms.value)
 
 
 def build_workload(w, precision=None, k=None, stream=None, debug=0):
