@@ -71,7 +71,9 @@ typedef struct {
                              filter to the FP64 stage, value 2 straight to the
                              exact 256-bit stage; bit 4 makes the neighbour
                              search keep distance and id apart (the form used
-                             above 2^17 spheres).  Results must not change.     */
+                             above 2^17 spheres); bit 8 keeps the heaviest
+                             spheres in the neighbour grid instead of scanning
+                             them first.  Results must not change.              */
 } rpd_options;
 
 typedef struct {

@@ -522,14 +522,30 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
     long long* cell_w = c->alloc<long long>(ns);
     void* ktmp = c->alloc<char>(knn_tmp_bytes(nv));
     NEED(cell_sph && cell_w && ktmp);
+    // the heaviest spheres stay out of the grid and every vertex scans them
+    // first (warp-form neighbour search of one shape only)
+    const bool two_word = (c->opt.debug_checks & 4) != 0;
+    const bool heavy = !batch && !two_word && ns <= (1 << 17) && !(c->opt.debug_checks & 8) && heavy_count(ns) > 0;
+    long long* wcut = nullptr;
+    int4* hsph = nullptr;
+    long long* hw = nullptr;
+    int* nheavy = nullptr;
+    if (heavy) {
+        wcut = c->alloc<long long>(1);
+        hsph = c->alloc<int4>(heavy_count(ns));
+        hw = c->alloc<long long>(heavy_count(ns));
+        nheavy = c->alloc<int>(1);
+        NEED(wcut && hsph && hw && nheavy);
+        launch_heavy_select(c->Ci, c->W, ns, wcut, hsph, hw, nheavy, s);
+    }
     if (batch)
         launch_sphere_grid_batch(c->Ci, c->W, c->d_soff, c->nshapes, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph,
                                  cell_w, c->cell_wmax, c->max_shape_ncap, s);
     else
         launch_sphere_grid(c->Ci, c->W, ns, ncap, c->gp, c->cell_start, c->cell_ids, cell_sph, cell_w, c->cell_wmax,
-                           gtmp, s);
+                           gtmp, s, wcut);
     launch_knn(c->Xi, nv, ns, c->gp, c->cell_start, cell_sph, cell_w, c->cell_wmax, ncap, c->K, c->knn, c->dplus, ktmp,
-               &c->st->err, (c->opt.debug_checks & 4) != 0, s, c->d_voff, c->nshapes);
+               &c->st->err, two_word, s, c->d_voff, c->nshapes, hsph, hw, nheavy);
     TRY(cuda_check(c, "knn launch"));
     record(c, 3);
     // ---- A2
@@ -546,7 +562,7 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
          c->bin_fill);
     launch_candidates(c->tets, nt, nv, c->Xi, c->Ci, c->W, c->knn, c->dplus, c->K, c->gp, c->cell_start,
                       c->cell_ids, c->cell_wmax, c->cand_cnt, c->cand, c->cand_ord, c->fb_list, c->fb_count, c->st, s,
-                      c->d_voff, c->nshapes);
+                      c->d_voff, c->nshapes, hsph, hw, nheavy);
     scan_excl(c->cand_cnt, c->pair_off, nt, stmp, s);
     if (old) {   // partial update: clip only the tets whose candidates changed
         c->changed = c->alloc<uint8_t>(nt);

@@ -827,10 +827,12 @@ struct RowCache {
 #pragma unroll
         for (int c = 0; c < 4; c++) F[c] = get(slot, c);
     }
+    // rows of the candidate slots in `mask` (bit s2: plane 4 + s2), the only
+    // planes the piece's vertices lie on
     __device__ __forceinline__ void fill(const Lane& L, const int32_t* __restrict__ Ci,
-                                         const long long* __restrict__ W) const {
-        for (int s2 = 0; s2 < L.n; s2++) {
-            if (s2 == L.si) continue;
+                                         const long long* __restrict__ W, unsigned mask) const {
+        for (; mask; mask &= mask - 1) {
+            const int s2 = __ffs(mask) - 1;
             long long F[4];
             row_i64(L, Ci, W, s2, F);
 #pragma unroll
@@ -1032,13 +1034,19 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
         L.X[k] = ld_int3(A.Xi, A.tets[4 * L.t + k]);
         L.di[k] = pd_exact(L.X[k], ci, wi);
     }
-    RC.fill(L, A.Ci, A.W);
     int apex = -1;
+    unsigned pmask = 0;   // candidate slots whose radical planes the piece's vertices lie on
     for (int v = 0; v < nslot; v++) {
-        V.w(v, 0) = A.qtrip[(2LL * v) * A.qcap + q];
+        const uint32_t tw = A.qtrip[(2LL * v) * A.qcap + q];
+        V.w(v, 0) = tw;
         V.w(v, 1) = A.qtrip[(2LL * v + 1) * A.qcap + q];
-        if (apex < 0 && !is_dead(V.w(v, 0))) apex = v;
+        if (is_dead(tw)) continue;
+        if (apex < 0) apex = v;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            if (tb(tw, k) >= 4) pmask |= 1u << (tb(tw, k) - 4);
     }
+    RC.fill(L, A.Ci, A.W, pmask);
     // chart coordinates relative to the apex vertex
     T O[3];
     const uint32_t ta = V.w(apex, 0);

@@ -37,7 +37,14 @@ size_t grid_tmp_bytes(long long ns, long long ncap);
 // of each row of cells along x (index z * dim.y + y).
 void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
                         int64_t* cell_start, int32_t* cell_ids, int4* cell_sph, long long* cell_w,
-                        long long* cell_wmax, void* tmp, cudaStream_t s);
+                        long long* cell_wmax, void* tmp, cudaStream_t s, const long long* wcut = nullptr);
+// Heavy spheres (the up to min(128, ns / 128) largest weights): *wcut = the
+// largest weight left in the grid (spheres above it are heavy), hsph/hw
+// their (centre, id) and weights in id order, *nheavy their count.  Pass
+// wcut to launch_sphere_grid and the rest to launch_knn / launch_candidates.
+int heavy_count(long long ns);
+void launch_heavy_select(const int32_t* Ci, const long long* W, long long ns, long long* wcut, int4* hsph,
+                         long long* hw, int* nheavy, cudaStream_t s);
 // k nearest spheres in power distance of every mesh vertex, with D+ = a lower
 // bound of the power distance of every sphere left out of the list.
 // tmp must hold knn_tmp_bytes(nv); ncap bounds the number of grid cells.
@@ -45,7 +52,8 @@ size_t knn_tmp_bytes(long long nv);
 void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
                 const int4* cell_sph, const long long* cell_w, const long long* cell_wmax, long long ncap, int K,
                 int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s,
-                const long long* voff = nullptr, int nshapes = 1);
+                const long long* voff = nullptr, int nshapes = 1, const int4* hsph = nullptr,
+                const long long* hw = nullptr, const int* nheavy = nullptr);
 // Batches: one grid per shape, all built by one launch (a block per shape).
 // Shape s owns spheres [soff[s], soff[s + 1]) (device array) and cells
 // [2 soff[s] + 65 s, 2 soff[s + 1] + 65 (s + 1)) of cell_start (its
@@ -64,7 +72,8 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
                        const GridParams* gp, const int64_t* cell_start, const int32_t* cell_ids,
                        const long long* cell_wmax, int32_t* cand_cnt, int32_t* cand, uint8_t* cand_ord,
                        int32_t* fb_list, int32_t* fb_count, DevState* st, cudaStream_t s,
-                       const long long* voff = nullptr, int nshapes = 1);
+                       const long long* voff = nullptr, int nshapes = 1, const int4* hsph = nullptr,
+                       const long long* hw = nullptr, const int* nheavy = nullptr);
 
 // ---------------------------------------------------------------- clip.cu
 struct ClipArgs {

@@ -104,12 +104,13 @@ __device__ __forceinline__ int shape_of(const long long* __restrict__ voff, int 
 // Bounding box of the sphere centres and the largest weight, reduced over
 // the block; thread 0 returns the grid parameters in *out (shared memory).
 __device__ void block_grid_params(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns,
-                                  long long ncap, GridParams* out) {
+                                  long long ncap, GridParams* out, long long cut = LLONG_MAX) {
     __shared__ int smin[3][32], smax[3][32];
     __shared__ long long swm[32];
     int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
     long long wm = 0;
     for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        if (W[i] > cut) continue;   // a heavy sphere: kept out of the grid
         for (int a = 0; a < 3; a++) {
             int v = Ci[3 * i + a];
             mn[a] = min(mn[a], v);
@@ -139,9 +140,9 @@ __device__ void block_grid_params(const int32_t* __restrict__ Ci, const long lon
 }
 
 __global__ void k_bbox(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns, long long ncap,
-                       GridParams* gp) {
+                       GridParams* gp, const long long* __restrict__ wcut) {
     __shared__ GridParams sg;
-    block_grid_params(Ci, W, ns, ncap, &sg);
+    block_grid_params(Ci, W, ns, ncap, &sg, wcut ? *wcut : LLONG_MAX);
     if (threadIdx.x == 0) *gp = sg;
 }
 
@@ -149,6 +150,7 @@ __global__ void k_bbox(const int32_t* __restrict__ Ci, const long long* __restri
 // grid parameters, per-cell counts in shared memory, their exclusive scan
 // (cell_start) and the fill, with no launches in between.
 constexpr int GRID_SMALL_CAP = 11264;   // counts within 44 KB of shared memory
+constexpr int HEAVY_MAX = 128;          // heavy spheres kept out of the grid at most
 
 __device__ __forceinline__ int block_excl_scan(int v, int* total) {
     __shared__ int wsum[32];
@@ -179,10 +181,12 @@ __global__ void __launch_bounds__(1024) k_grid_small(const int32_t* __restrict__
                                                      long long ns, long long ncap, GridParams* gp,
                                                      int64_t* __restrict__ start, int32_t* __restrict__ ids,
                                                      int4* __restrict__ sph, long long* __restrict__ sw,
-                                                     long long* __restrict__ cwmax, long long* __restrict__ rwmax) {
+                                                     long long* __restrict__ cwmax, long long* __restrict__ rwmax,
+                                                     const long long* __restrict__ wcut) {
     extern __shared__ int scount[];
     __shared__ GridParams sg;
-    block_grid_params(Ci, W, ns, ncap, &sg);
+    const long long cut = wcut ? *wcut : LLONG_MAX;
+    block_grid_params(Ci, W, ns, ncap, &sg, cut);
     for (long long q = threadIdx.x; q < ncap; q += blockDim.x) {
         scount[q] = 0;
         cwmax[q] = 0;
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(1024) k_grid_small(const int32_t* __restrict__
     const GridParams g = sg;
     if (threadIdx.x == 0) *gp = g;
     for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        if (W[i] > cut) continue;
         const int3 c = cell_of(ld_int3(Ci, i), g);
         const int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
         atomicAdd(&scount[q], 1);
@@ -214,6 +219,7 @@ __global__ void __launch_bounds__(1024) k_grid_small(const int32_t* __restrict__
     if (threadIdx.x == 0) start[ncap] = total;
     __syncthreads();
     for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+        if (W[i] > cut) continue;
         const int3 ci = ld_int3(Ci, i);
         const int3 c = cell_of(ci, g);
         const int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
@@ -221,6 +227,66 @@ __global__ void __launch_bounds__(1024) k_grid_small(const int32_t* __restrict__
         ids[pos] = (int32_t)i;
         sph[pos] = make_int4(ci.x, ci.y, ci.z, (int)i);
         sw[pos] = W[i];
+    }
+}
+
+// Heavy spheres: the up to H largest power weights.  The neighbour walk stops
+// once the next shell's distance minus the largest weight of the grid exceeds
+// the K-th distance, so a few heavy spheres would keep every vertex walking;
+// they are kept out of the grid and every vertex evaluates them first.  One
+// block: the (H + 1)-th largest weight t by an 8-bit radix select from the
+// top byte down (weights are >= 0), then the spheres with W > t (at most H)
+// in id order by a chunked block scan.
+__global__ void __launch_bounds__(1024) k_heavy_select(const int32_t* __restrict__ Ci,
+                                                       const long long* __restrict__ W, long long ns, int H,
+                                                       long long* __restrict__ wcut, int4* __restrict__ hsph,
+                                                       long long* __restrict__ hw, int* __restrict__ nheavy) {
+    __shared__ int hist[256];
+    __shared__ unsigned long long sprefix;
+    __shared__ long long sneed;
+    if (threadIdx.x == 0) {
+        sprefix = 0;
+        sneed = H + 1;
+    }
+    for (int pos = 7; pos >= 0; pos--) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const unsigned long long prefix = sprefix;
+        const unsigned long long hmask = pos == 7 ? 0ull : (~0ull << (8 * (pos + 1)));
+        for (long long i = threadIdx.x; i < ns; i += blockDim.x) {
+            const unsigned long long v = (unsigned long long)W[i];
+            if ((v & hmask) == prefix) atomicAdd(&hist[(v >> (8 * pos)) & 0xff], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long need = sneed, cum = 0;
+            int b = 255;
+            for (; b > 0; b--) {
+                if (cum + hist[b] >= need) break;
+                cum += hist[b];
+            }
+            sneed = need - cum;
+            sprefix = prefix | ((unsigned long long)b << (8 * pos));
+        }
+        __syncthreads();
+    }
+    const long long t = (long long)sprefix;
+    int base = 0;
+    for (long long c0 = 0; c0 < ns; c0 += blockDim.x) {
+        const long long i = c0 + threadIdx.x;
+        const int f = i < ns && W[i] > t;
+        int total;
+        const int at = base + block_excl_scan(f, &total);
+        if (f && at < H) {
+            hsph[at] = make_int4(Ci[3 * i], Ci[3 * i + 1], Ci[3 * i + 2], (int)i);
+            hw[at] = W[i];
+        }
+        base += total;
+        __syncthreads();   // block_excl_scan's shared words are reused
+    }
+    if (threadIdx.x == 0) {
+        *wcut = t;
+        *nheavy = min(base, H);
     }
 }
 
@@ -287,9 +353,10 @@ __global__ void __launch_bounds__(1024) k_grid_batch(const int32_t* __restrict__
 
 __global__ void k_cell_count(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns,
                              const GridParams* __restrict__ gp, int32_t* __restrict__ count,
-                             long long* __restrict__ cwmax, long long* __restrict__ rwmax) {
+                             long long* __restrict__ cwmax, long long* __restrict__ rwmax,
+                             const long long* __restrict__ wcut) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
+    if (i >= ns || (wcut && W[i] > *wcut)) return;
     GridParams g = *gp;
     int3 c = cell_of(ld_int3(Ci, i), g);
     int q = (c.z * g.dim.y + c.y) * g.dim.x + c.x;
@@ -302,9 +369,9 @@ __global__ void k_cell_count(const int32_t* __restrict__ Ci, const long long* __
 __global__ void k_cell_fill(const int32_t* __restrict__ Ci, const long long* __restrict__ W, long long ns,
                             const GridParams* __restrict__ gp, const int64_t* __restrict__ start,
                             int32_t* __restrict__ fill, int32_t* __restrict__ ids, int4* __restrict__ sph,
-                            long long* __restrict__ sw) {
+                            long long* __restrict__ sw, const long long* __restrict__ wcut) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
+    if (i >= ns || (wcut && W[i] > *wcut)) return;
     GridParams g = *gp;
     int3 c = ld_int3(Ci, i);
     int3 cc = cell_of(c, g);
@@ -628,13 +695,73 @@ __device__ __forceinline__ unsigned long long knn_key(long long d, int id) {
 }
 __device__ __forceinline__ long long knn_key_dist(unsigned long long e) { return (long long)(e >> 17) - (1ll << 46); }
 
+// One chunk of 32 keys (one per lane, EMPTY for none) into the warp's sorted
+// list of the K smallest keys L (lane j holds the j-th): keys below the K-th
+// enter one by one (ballot + shuffle) when few, else by a bitonic sort of the
+// chunk merged with the list; every key rejected or pushed out lowers dp.
+__device__ __forceinline__ void knn_insert(unsigned long long key, unsigned long long& L, long long& dp, int K,
+                                           int lane) {
+    typedef unsigned long long U;
+    const unsigned FULL = 0xffffffffu;
+    const U EMPTY = ~0ull;
+    const U tau = __shfl_sync(FULL, L, K - 1);
+    const bool pass = key < tau;
+    if (!pass && key != EMPTY) dp = min(dp, knn_key_dist(key));
+    unsigned bal = __ballot_sync(FULL, pass);
+    if (__popc(bal) <= 6) {
+        while (bal) {   // one by one
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const U k = __shfl_sync(FULL, key, src);
+            const int pos = __popc(__ballot_sync(FULL, L < k));
+            if (pos >= K) {   // an earlier insertion raised the bar
+                dp = min(dp, knn_key_dist(k));
+                continue;
+            }
+            const U ev = __shfl_sync(FULL, L, K - 1);
+            if (ev != EMPTY) dp = min(dp, knn_key_dist(ev));
+            const U up = __shfl_up_sync(FULL, L, 1);
+            if (lane > pos) L = up;
+            if (lane == pos) L = k;
+            if (lane >= K) L = EMPTY;
+        }
+    } else {   // bitonic sort of the entering keys, then merge
+        U s = pass ? key : EMPTY;
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                const U o = __shfl_xor_sync(FULL, s, jj);
+                const bool lower = (lane & jj) == 0, up = (lane & kk) == 0;
+                s = (lower == up) ? min(s, o) : max(s, o);
+            }
+        }
+        const U rv = __shfl_sync(FULL, s, 31 - lane);
+        U lo = min(L, rv);
+        const U hi = max(L, rv);
+        if (hi != EMPTY) dp = min(dp, knn_key_dist(hi));
+#pragma unroll
+        for (int jj = 16; jj > 0; jj >>= 1) {
+            const U o = __shfl_xor_sync(FULL, lo, jj);
+            lo = (lane & jj) ? max(lo, o) : min(lo, o);
+        }
+        L = lo;
+        if (lane >= K) {
+            if (L != EMPTY) dp = min(dp, knn_key_dist(L));
+            L = EMPTY;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
                                                   long long nv, const GridParams* __restrict__ gp,
                                                   const int64_t* __restrict__ start_all, const int4* __restrict__ sph,
                                                   const long long* __restrict__ sw,
                                                   const long long* __restrict__ rwmax_all, int K,
                                                   int32_t* __restrict__ knn, long long* __restrict__ dplus,
-                                                  const long long* __restrict__ voff, int nshapes) {
+                                                  const long long* __restrict__ voff, int nshapes,
+                                                  const int4* __restrict__ hsph, const long long* __restrict__ hw,
+                                                  const int* __restrict__ nheavy) {
     typedef unsigned long long U;
     const unsigned FULL = 0xffffffffu;
     const U EMPTY = ~0ull;
@@ -651,6 +778,16 @@ __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi
     long long dp = LLONG_MAX;  // smallest distance known to be outside the list
     int3 plo = make_int3(1, 1, 1), phi = make_int3(0, 0, 0);   // processed box (empty)
     long long lb2 = LLONG_MAX;
+    // the heavy spheres, kept out of the grid, first
+    const int nh = nheavy ? *nheavy : 0;
+    for (int hb = 0; hb < nh; hb += 32) {
+        U key = EMPTY;
+        if (hb + lane < nh) {
+            const int4 cs = hsph[hb + lane];
+            key = knn_key(pd_exact(x, make_int3(cs.x, cs.y, cs.z), hw[hb + lane]), cs.w);
+        }
+        knn_insert(key, L, dp, K, lane);
+    }
     for (int r = 0; r < (1 << 22); r++) {
         const int3 blo = make_int3(max(c.x - r, 0), max(c.y - r, 0), max(c.z - r, 0));
         const int3 bhi = make_int3(min(c.x + r, g.dim.x - 1), min(c.y + r, g.dim.y - 1), min(c.z + r, g.dim.z - 1));
@@ -717,53 +854,7 @@ __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi
                     const int4 cs = sph[e];
                     key = knn_key(pd_exact(x, make_int3(cs.x, cs.y, cs.z), sw[e]), cs.w);
                 }
-                const U tau = __shfl_sync(FULL, L, K - 1);
-                const bool pass = key < tau;
-                if (!pass && key != EMPTY) dp = min(dp, knn_key_dist(key));
-                unsigned bal = __ballot_sync(FULL, pass);
-                if (__popc(bal) <= 6) {
-                    while (bal) {   // one by one
-                        const int src = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                        const U k = __shfl_sync(FULL, key, src);
-                        const int pos = __popc(__ballot_sync(FULL, L < k));
-                        if (pos >= K) {   // an earlier insertion raised the bar
-                            dp = min(dp, knn_key_dist(k));
-                            continue;
-                        }
-                        const U ev = __shfl_sync(FULL, L, K - 1);
-                        if (ev != EMPTY) dp = min(dp, knn_key_dist(ev));
-                        const U up = __shfl_up_sync(FULL, L, 1);
-                        if (lane > pos) L = up;
-                        if (lane == pos) L = k;
-                        if (lane >= K) L = EMPTY;
-                    }
-                } else {   // bitonic sort of the entering keys, then merge
-                    U s = pass ? key : EMPTY;
-#pragma unroll
-                    for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-                        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                            const U o = __shfl_xor_sync(FULL, s, jj);
-                            const bool lower = (lane & jj) == 0, up = (lane & kk) == 0;
-                            s = (lower == up) ? min(s, o) : max(s, o);
-                        }
-                    }
-                    const U rv = __shfl_sync(FULL, s, 31 - lane);
-                    U lo = min(L, rv);
-                    const U hi = max(L, rv);
-                    if (hi != EMPTY) dp = min(dp, knn_key_dist(hi));
-#pragma unroll
-                    for (int jj = 16; jj > 0; jj >>= 1) {
-                        const U o = __shfl_xor_sync(FULL, lo, jj);
-                        lo = (lane & jj) ? max(lo, o) : min(lo, o);
-                    }
-                    L = lo;
-                    if (lane >= K) {
-                        if (L != EMPTY) dp = min(dp, knn_key_dist(L));
-                        L = EMPTY;
-                    }
-                }
+                knn_insert(key, L, dp, K, lane);
             }
         }
         plo = blo;
@@ -1004,7 +1095,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
     const int64_t* __restrict__ start_all, const int32_t* __restrict__ ids, const long long* __restrict__ cwmax_all,
     const int32_t* __restrict__ fb_list, const int32_t* __restrict__ fb_count, int32_t* __restrict__ cand_cnt,
     int32_t* __restrict__ cand, uint8_t* __restrict__ cand_ord, DevState* st, const long long* __restrict__ voff,
-    int nshapes) {
+    int nshapes, const int4* __restrict__ hsph, const long long* __restrict__ hw, const int* __restrict__ nheavy) {
     const unsigned FULL = 0xffffffffu;
     __shared__ int sid[FB_GATHER];
     __shared__ long long sD[FB_GATHER][4];
@@ -1012,6 +1103,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
     __shared__ int sn;
     const int tid = threadIdx.x, lane = tid & 31;
     const long long nfb = *fb_count;
+    const int nh = nheavy ? *nheavy : 0;
     for (long long q = blockIdx.x; q < nfb; q += gridDim.x) {
         const long long t = fb_list[q];   // uniform over the block
         int v[4];
@@ -1062,6 +1154,15 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
                 const int pos = atomicAdd(&sn, 1);
                 if (pos < FB_GATHER) sid[pos] = sph;
             }
+        }
+        // and the heavy spheres, which the grid leaves out
+        for (int h = tid; h < nh; h += FB_THREADS) {
+            const int4 cs = hsph[h];
+            bool in = false;
+            for (int a = 0; a < 4; a++) in |= pd_exact(X[a], make_int3(cs.x, cs.y, cs.z), hw[h]) <= thr[a];
+            if (!in) continue;
+            const int pos = atomicAdd(&sn, 1);
+            if (pos < FB_GATHER) sid[pos] = cs.w;
         }
         __syncthreads();
         const int n = sn;
@@ -1144,12 +1245,28 @@ size_t grid_tmp_bytes(long long ns, long long ncap) {
     return al(sizeof(int32_t) * (ncap + 1)) * 2 + al(scan_tmp_bytes(ncap));
 }
 
+int heavy_count(long long ns) { return (int)std::min<long long>(HEAVY_MAX, ns / 128); }
+
+void launch_heavy_select(const int32_t* Ci, const long long* W, long long ns, long long* wcut, int4* hsph,
+                         long long* hw, int* nheavy, cudaStream_t s) {
+    const int H = heavy_count(ns);
+    if (H < 1) {
+        const long long big = LLONG_MAX;
+        const int zero = 0;
+        cudaMemcpyAsync(wcut, &big, sizeof(big), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(nheavy, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+        return;
+    }
+    k_heavy_select<<<1, 1024, 0, s>>>(Ci, W, ns, H, wcut, hsph, hw, nheavy);
+    note_launch();
+}
+
 void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, long long ncap, GridParams* gp,
                         int64_t* cell_start, int32_t* cell_ids, int4* cell_sph, long long* cell_w,
-                        long long* cell_wmax, void* tmp, cudaStream_t s) {
+                        long long* cell_wmax, void* tmp, cudaStream_t s, const long long* wcut) {
     if (ncap <= GRID_SMALL_CAP) {
         k_grid_small<<<1, 1024, sizeof(int) * ncap, s>>>(Ci, W, ns, ncap, gp, cell_start, cell_ids, cell_sph, cell_w,
-                                                         cell_wmax, cell_wmax + ncap);
+                                                         cell_wmax, cell_wmax + ncap, wcut);
         note_launch();
         return;
     }
@@ -1157,15 +1274,15 @@ void launch_sphere_grid(const int32_t* Ci, const long long* W, long long ns, lon
     int32_t* count = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
     int32_t* fill = (int32_t*)p; p += al(sizeof(int32_t) * (ncap + 1));
     void* stmp = p;
-    k_bbox<<<1, 1024, 0, s>>>(Ci, W, ns, ncap, gp);
+    k_bbox<<<1, 1024, 0, s>>>(Ci, W, ns, ncap, gp, wcut);
     note_launch();
     cudaMemsetAsync(count, 0, sizeof(int32_t) * ncap, s);
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncap, s);
     cudaMemsetAsync(cell_wmax, 0, sizeof(long long) * 2 * ncap, s);
-    k_cell_count<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, count, cell_wmax, cell_wmax + ncap);
+    k_cell_count<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, count, cell_wmax, cell_wmax + ncap, wcut);
     note_launch();
     scan_excl(count, cell_start, ncap, stmp, s);
-    k_cell_fill<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, cell_start, fill, cell_ids, cell_sph, cell_w);
+    k_cell_fill<<<nblk(ns, 256), 256, 0, s>>>(Ci, W, ns, gp, cell_start, fill, cell_ids, cell_sph, cell_w, wcut);
     note_launch();
 }
 
@@ -1188,7 +1305,7 @@ void launch_sphere_grid_batch(const int32_t* Ci, const long long* W, const long 
 void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams* gp, const int64_t* cell_start,
                 const int4* cell_sph, const long long* cell_w, const long long* cell_wmax, long long ncap, int K,
                 int32_t* knn, long long* dplus, void* tmp, int* d_err, bool two_word, cudaStream_t s,
-                const long long* voff, int nshapes) {
+                const long long* voff, int nshapes, const int4* hsph, const long long* hw, const int* nheavy) {
     if (nv == 0) return;
     char* p = (char*)tmp;
     uint64_t* k0 = (uint64_t*)p; p += al(sizeof(uint64_t) * nv);
@@ -1200,7 +1317,8 @@ void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams*
     if ((ns <= (1 << 17) || nshapes > 1) && !two_word) {   // batches: shape-local ids in the key
         // one vertex per warp in input order: the sphere grid stays in cache
         k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nullptr, nv, gp, cell_start, cell_sph, cell_w,
-                                                       cell_wmax + ncap, K, knn, dplus, voff, nshapes);
+                                                       cell_wmax + ncap, K, knn, dplus, voff, nshapes, hsph, hw,
+                                                       nheavy);
     } else {
         k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
         note_launch();
@@ -1215,7 +1333,8 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
                        const long long* W, const int32_t* knn, const long long* dplus, int K, const GridParams* gp,
                        const int64_t* cell_start, const int32_t* cell_ids, const long long* cell_wmax,
                        int32_t* cand_cnt, int32_t* cand, uint8_t* cand_ord, int32_t* fb_list, int32_t* fb_count,
-                       DevState* st, cudaStream_t s, const long long* voff, int nshapes) {
+                       DevState* st, cudaStream_t s, const long long* voff, int nshapes, const int4* hsph,
+                       const long long* hw, const int* nheavy) {
     if (nt == 0) return;
     cudaMemsetAsync(fb_count, 0, sizeof(int32_t), s);
     k_candidates_warp<<<nblk(32 * nt, 256), 256, 0, s>>>(d_tets, nt, nv, Xi, Ci, W, knn, dplus, K, cand_cnt, cand,
@@ -1224,6 +1343,6 @@ void launch_candidates(const int32_t* d_tets, long long nt, long long nv, const 
     note_launch();
     k_candidates_fallback<<<152 * 4, FB_THREADS, 0, s>>>(d_tets, nv, Xi, Ci, W, knn, K, gp, cell_start, cell_ids,
                                                          cell_wmax, fb_list, fb_count, cand_cnt, cand, cand_ord, st,
-                                                         voff, nshapes);
+                                                         voff, nshapes, hsph, hw, nheavy);
     note_launch();
 }
