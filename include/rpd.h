@@ -484,9 +484,8 @@ int64_t rpd_launch_count(void);
  *           NULL only sets *n
  *   n       host pointer, receives the number of elements
  * The first call on a device looks up the array's device address and caches
- * it for the rest of the process: make that first call before any stream
- * capture, and do not use the entry point again on a device after
- * cudaDeviceReset there.  Every call reuses the same array (it is cleared as
+ * it for the rest of the process: do not use the entry point again on a
+ * device after cudaDeviceReset there.  Every call reuses the same array (it is cleared as
  * needed), so calls that overlap on the GPU race: serialise them.
  * Synchronises the stream three times (sizes of the later stages are read on
  * the host).  Errors are reported by status only (RPD_E_INVALID for bad

@@ -1009,6 +1009,73 @@ struct VStore {
     }
 };
 
+// Volume and first moment of a piece cut by one radical plane only (every
+// vertex on tet faces and the plane of one sphere s): the part F . beta <= 0
+// of the tet in barycentric coordinates beta, F the exact row of s.  With K
+// the corners where F < 0 and s_ax = F_a / (F_a - F_x) the position of the
+// cut along edge a -> x:
+//   |K| = 1, K = {a}: the tet (a, p_ab, p_ac, p_ad), fraction s_ab s_ac s_ad;
+//   |K| = 3: the tet minus that tet at the fourth corner;
+//   |K| = 2, K = {a, b}: the wedge between the triangles (a, p_ac, p_ad) and
+//     (b, p_bc, p_bd), split into the tets (a, p_ac, p_ad, b),
+//     (p_ac, p_ad, b, p_bc) and (p_ad, b, p_bc, p_bd) of fractions
+//     s_ac s_ad, s_ad s_bc (1 - s_ac) and s_bc s_bd (1 - s_ad), all positive.
+// frac = volume / vol(t); M = first moment / vol(t) in barycentric
+// coordinates (the fraction-weighted vertex means of the tets).
+__device__ __forceinline__ void one_plane_piece(const long long F[4], double& frac, double M[4]) {
+    int neg = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) neg += F[c] < 0;
+    frac = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) M[c] = 0.0;
+    auto cut = [&](int a, int x) { return (double)F[a] / ((double)F[a] - (double)F[x]); };
+    if (neg == 1 || neg == 3) {
+        // the corner a on the minority side and the tet it cuts off
+        int a = 0;
+        for (int c = 0; c < 4; c++)
+            if ((F[c] < 0) == (neg == 1)) a = c;
+        double fs = 1.0, cen[4] = {0, 0, 0, 0}, rest = 0.0;
+        for (int x = 0; x < 4; x++) {
+            if (x == a) continue;
+            const double s = cut(a, x);
+            fs *= s;
+            cen[x] = 0.25 * s;
+            rest += 1.0 - s;
+        }
+        cen[a] = 0.25 * (1.0 + rest);
+        if (neg == 1) {
+            frac = fs;
+            for (int c = 0; c < 4; c++) M[c] = fs * cen[c];
+        } else {
+            frac = 1.0 - fs;
+            for (int c = 0; c < 4; c++) M[c] = 0.25 - fs * cen[c];
+        }
+        return;
+    }
+    int k0 = -1, k1 = -1, o0 = -1, o1 = -1;
+    for (int c = 0; c < 4; c++) {
+        if (F[c] < 0) (k0 < 0 ? k0 : k1) = c;
+        else (o0 < 0 ? o0 : o1) = c;
+    }
+    const int a = k0, b = k1, c = o0, d = o1;
+    const double sac = cut(a, c), sad = cut(a, d), sbc = cut(b, c), sbd = cut(b, d);
+    // vertices in barycentric coordinates
+    double ea[4] = {0, 0, 0, 0}, eb[4] = {0, 0, 0, 0}, pac[4] = {0, 0, 0, 0}, pad[4] = {0, 0, 0, 0},
+           pbc[4] = {0, 0, 0, 0}, pbd[4] = {0, 0, 0, 0};
+    ea[a] = 1.0;
+    eb[b] = 1.0;
+    pac[a] = 1.0 - sac, pac[c] = sac;
+    pad[a] = 1.0 - sad, pad[d] = sad;
+    pbc[b] = 1.0 - sbc, pbc[c] = sbc;
+    pbd[b] = 1.0 - sbd, pbd[d] = sbd;
+    const double f1 = sac * sad, f2 = sad * sbc * (1.0 - sac), f3 = sbc * sbd * (1.0 - sad);
+    frac = f1 + f2 + f3;
+    for (int q = 0; q < 4; q++)
+        M[q] = 0.25 * (f1 * (ea[q] + pac[q] + pad[q] + eb[q]) + f2 * (pac[q] + pad[q] + eb[q] + pbc[q]) +
+                       f3 * (pad[q] + eb[q] + pbc[q] + pbd[q]));
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) {
     typedef typename std::conditional<sizeof(Real) == 4, df, double>::type T;
@@ -1045,6 +1112,24 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
 #pragma unroll
         for (int k = 0; k < 3; k++)
             if (tb(tw, k) >= 4) pmask |= 1u << (tb(tw, k) - 4);
+    }
+    if (__popc(pmask) == 1) {   // cut by one radical plane: closed form
+        long long F[4];
+        row_i64(L, A.Ci, A.W, __ffs(pmask) - 1, F);
+        double frac, M[4];
+        one_plane_piece(F, frac, M);
+        const double vt = tet_volume6(L.X) / 6.0;
+        const double u3 = A.unit * A.unit * A.unit;
+        A.p_vol[p] = vt * frac * u3;
+        const int xs[4][3] = {{L.X[0].x, L.X[0].y, L.X[0].z}, {L.X[1].x, L.X[1].y, L.X[1].z},
+                              {L.X[2].x, L.X[2].y, L.X[2].z}, {L.X[3].x, L.X[3].y, L.X[3].z}};
+        for (int k = 0; k < 3; k++) {   // relative to corner 0: sum_c M_c = frac
+            const double x0 = (double)xs[0][k];
+            double m = frac * x0;
+            for (int cc = 1; cc <= 3; cc++) m += M[cc] * ((double)xs[cc][k] - x0);
+            A.p_mom[3 * p + k] = vt * m * u3 * A.unit;
+        }
+        return;
     }
     RC.fill(L, A.Ci, A.W, pmask);
     // chart coordinates relative to the apex vertex

@@ -14,8 +14,7 @@
 //
 // In host code `g_scratch` only names the symbol; its device address is
 // looked up with cudaGetSymbolAddress once per device (the first call on a
-// device, which should therefore come before any stream capture) and cached
-// for the life of the process: after cudaDeviceReset on that device the
+// device) and cached for the life of the process: after cudaDeviceReset on that device the
 // cached address is stale, so the entry point must not be used again in that
 // process.  The call synchronises its stream three times (the sizes of the
 // later stages are read on the host).  All calls
