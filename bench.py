@@ -338,7 +338,10 @@ def batch_leg(nshapes, steps, warmup, stream, flush, dev, seed=20240323):
     st = lib.rpd_autotune_batch(_ptr(V), _ptr(T), _ptr(C), _ptr(R), len(ws), hv.ctypes.data, ht.ctypes.data,
                                 hs.ctypes.data, ctypes.byref(base), ks.ctypes.data, len(ks), 2,
                                 ctypes.c_void_p(stream.cuda_stream), ctypes.byref(best), ctypes.byref(tms))
-    k = int(best.k) if st == 0 else 32
+    if st != 0:
+        return {"shapes": len(ws), "error": f"rpd_autotune_batch returned {st}: "
+                                            f"{lib.rpd_build_error().decode()}"}
+    k = int(best.k)
 
     def loop():
         n = 0
@@ -370,12 +373,76 @@ def batch_leg(nshapes, steps, warmup, stream, flush, dev, seed=20240323):
     ms_batch, p_batch = timed(batched)
     return {"shapes": len(ws), "tets": int(ht[-1]), "spheres": int(hs[-1]),
             "workload": f"{len(ws)} seeded tori / genus 0-5 slabs / ellipsoid unions, log-uniform 1k-100k tets, "
-                        f"32-4k spheres (at most one per 4 tets)",
+                        f"32-4k spheres (at most one per 8 tets)",
             "k_autotuned": k, "autotune_ms_best": float(tms.value), "pieces_per_step": int(p_batch),
             "pieces_equal": bool(p_loop == p_batch),
             "per_shape_loop": {"ms_per_step": ms_loop, "value": p_loop / (ms_loop * 1e-3), "unit": UNIT},
             "batched": {"ms_per_step": ms_batch, "value": p_batch / (ms_batch * 1e-3), "unit": UNIT},
             "batched_over_loop": ms_loop / ms_batch}
+
+
+def repair_leg(nshapes, stream, dev, seed=20240330):
+    """The topology-repair workload: seeded genus 0-5 slabs (~125k tets, 256
+    near-medial starting spheres) repaired by rpd_repair, plain and with the
+    learned radius proposer (trained first by the library's own kernels on
+    the (pin features -> shrunk radius) pairs of ten other slabs); wall time
+    per shape on the host clock (the loop synchronises every round)."""
+    import torch
+    from paper_2403_18761_gb300 import build_workload, Mlp
+    import rpd_inputs
+    train = [rpd_inputs.genus_slab(g, seed=seed + 1 + s, h=0.075, ns=64) for g in (0, 1, 2, 4, 5) for s in (0, 1)]
+    xs, ts = [], []
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for w in train:
+            ctx = build_workload(w, stream=stream)
+            P, N, F = ctx.rpd_surface_samples()
+            _, r, _ = ctx.rpd_shrink(P, N, F)
+            x, t = ctx.rpd_pin_features(P, N, r)
+            keep = torch.isfinite(t)
+            xs.append(x[keep])
+            ts.append(t[keep])
+            ctx.rpd_destroy()
+        x, t = torch.cat(xs), torch.cat(ts)
+        perm = torch.randperm(x.shape[0], generator=torch.Generator().manual_seed(0)).to(dev)
+        x, t = x[perm].contiguous(), t[perm].contiguous()
+        net = Mlp(seed=7, stream=stream)
+        _, l0 = net.grad(x, t)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.train(x, t, steps=3000, batch=1024, lr=1e-3)
+        e1.record(stream)
+        e1.synchronize()
+        _, l1 = net.grad(x, t)
+    train_ms = e0.elapsed_time(e1)
+    shapes = []
+    for g in range(nshapes):
+        w = rpd_inputs.genus_slab(g % 6, seed=seed + 100 + g, h=0.075, ns=256)
+        row = {"genus": g % 6, "tets": int(w.nt)}
+        for mode in ("plain", "learned"):
+            with torch.cuda.stream(stream):
+                ctx = build_workload(w, stream=stream)
+                if mode == "learned":
+                    ctx.rpd_set_proposer(net, 1.25)
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                rounds, inserted, failing = ctx.rpd_repair(96)
+                b = time.perf_counter()
+                pins, iters, rej = ctx.rpd_shrink_counters()
+                ctx.rpd_destroy()
+            row[mode] = {"ms": (b - a) * 1e3, "rounds": rounds, "inserted": inserted, "failing": failing,
+                         "shrink_pins": pins, "shrink_iters": iters, "rejected": rej}
+        shapes.append(row)
+    tot = {m: {"ms": sum(r[m]["ms"] for r in shapes), "shrink_iters": sum(r[m]["shrink_iters"] for r in shapes),
+               "failing": sum(r[m]["failing"] for r in shapes), "inserted": sum(r[m]["inserted"] for r in shapes)}
+           for m in ("plain", "learned")}
+    return {"workload": f"{nshapes} genus 0-5 slabs 4x2x1 (~125k tets each), 256 near-medial starting spheres",
+            "training": {"pairs": int(x.shape[0]), "steps": 3000, "batch": 1024, "loss_before": l0,
+                         "loss_after": l1, "train_ms": train_ms,
+                         "setup_s": time.perf_counter() - t0},
+            "shapes": shapes, "total": tot,
+            "same_result": all(r["plain"]["inserted"] == r["learned"]["inserted"] and
+                               r["plain"]["failing"] == r["learned"]["failing"] for r in shapes)}
 
 
 def run_reference(args, w):
@@ -424,6 +491,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision (profiling)")
+    ap.add_argument("--repair-shapes", type=int, default=6,
+                    help="genus 0-5 slabs of the repair leg (0 skips it; the full repair workload has 64)")
     ap.add_argument("--batch-shapes", type=int, default=64,
                     help="shapes of the batching leg (0 skips it; the full batching workload has 256)")
     args = ap.parse_args()
@@ -582,7 +651,15 @@ def main():
     line["roofline"] = clip_roofline(stage, kk, args.config, precision, peaks, peaks["hbm_gbs"],
                                      stage64=stage64 if stage64 else None)
     if args.batch_shapes > 0:
-        line["batch"] = batch_leg(args.batch_shapes, args.steps, args.warmup, stream, flush, dev)
+        try:
+            line["batch"] = batch_leg(args.batch_shapes, args.steps, args.warmup, stream, flush, dev)
+        except Exception as e:   # reported in the line; the headline stands on its own
+            line["batch"] = {"shapes": args.batch_shapes, "error": f"{type(e).__name__}: {e}"}
+    if args.repair_shapes > 0:
+        try:
+            line["repair"] = repair_leg(args.repair_shapes, stream, dev)
+        except Exception as e:
+            line["repair"] = {"shapes": args.repair_shapes, "error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, legs, (sub, o) = cpu_baselines(w, args.config)
         line["cpu_baseline"] = cb

@@ -72,8 +72,9 @@ typedef struct {
                              exact 256-bit stage; bit 4 makes the neighbour
                              search keep distance and id apart (the form used
                              above 2^17 spheres); bit 8 keeps the heaviest
-                             spheres in the neighbour grid instead of scanning
-                             them first.  Results must not change.              */
+                             spheres out of the neighbour grid and scans them
+                             first (a tuning choice, off by default: slower on
+                             the organic blob).  Results must not change.       */
 } rpd_options;
 
 typedef struct {

@@ -522,10 +522,10 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
     long long* cell_w = c->alloc<long long>(ns);
     void* ktmp = c->alloc<char>(knn_tmp_bytes(nv));
     NEED(cell_sph && cell_w && ktmp);
-    // the heaviest spheres stay out of the grid and every vertex scans them
-    // first (warp-form neighbour search of one shape only)
+    // with debug bit 8 the heaviest spheres stay out of the grid and every
+    // vertex scans them first (warp-form neighbour search of one shape only)
     const bool two_word = (c->opt.debug_checks & 4) != 0;
-    const bool heavy = !batch && !two_word && ns <= (1 << 17) && !(c->opt.debug_checks & 8) && heavy_count(ns) > 0;
+    const bool heavy = !batch && !two_word && ns <= (1 << 17) && (c->opt.debug_checks & 8) && heavy_count(ns) > 0;
     long long* wcut = nullptr;
     int4* hsph = nullptr;
     long long* hw = nullptr;

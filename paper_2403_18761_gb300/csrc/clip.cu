@@ -1020,60 +1020,104 @@ struct VStore {
 //     (b, p_bc, p_bd), split into the tets (a, p_ac, p_ad, b),
 //     (p_ac, p_ad, b, p_bc) and (p_ad, b, p_bc, p_bd) of fractions
 //     s_ac s_ad, s_ad s_bc (1 - s_ac) and s_bc s_bd (1 - s_ad), all positive.
-// frac = volume / vol(t); M = first moment / vol(t) in barycentric
-// coordinates (the fraction-weighted vertex means of the tets).
-__device__ __forceinline__ void one_plane_piece(const long long F[4], double& frac, double M[4]) {
-    int neg = 0;
-#pragma unroll
-    for (int c = 0; c < 4; c++) neg += F[c] < 0;
-    frac = 0.0;
-#pragma unroll
-    for (int c = 0; c < 4; c++) M[c] = 0.0;
-    auto cut = [&](int a, int x) { return (double)F[a] / ((double)F[a] - (double)F[x]); };
+// The barycentric first moment is the fraction-weighted vertex mean of those
+// tets.  T is double-float in the FP32-filtered mode (FP32 pipes; native
+// FP64 runs at 1/64 of the rate) and double in the FP64 mode.
+template <typename T>
+struct Arith;
+template <>
+struct Arith<df> {
+    static __device__ __forceinline__ df add(df a, df b) { return df_add(a, b); }
+    static __device__ __forceinline__ df sub(df a, df b) { return df_sub(a, b); }
+    static __device__ __forceinline__ df mul(df a, df b) { return df_mul(a, b); }
+    static __device__ __forceinline__ df div(df a, df b) { return df_div_fast(a, b); }
+    static __device__ __forceinline__ df from_i64(long long v) { return df_from_i64(v); }
+    static __device__ __forceinline__ df num(float v) { return df_make(v); }
+    static __device__ __forceinline__ double dbl(df v) { return df_to_double(v); }
+};
+template <>
+struct Arith<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double from_i64(long long v) { return (double)v; }
+    static __device__ __forceinline__ double num(float v) { return (double)v; }
+    static __device__ __forceinline__ double dbl(double v) { return v; }
+};
+
+// frac = volume / vol(t); mom[k] = (first moment / vol(t))_k - frac X0_k, in
+// grid units: sum over corners l of M_l (X_l - X0)_k.
+template <typename T>
+__device__ __forceinline__ void one_plane_piece(const long long F[4], const int3* X, double& frac, double mom[3]) {
+    typedef Arith<T> A;
+    const int neg = (F[0] < 0) + (F[1] < 0) + (F[2] < 0) + (F[3] < 0);
+    auto cut = [&](int a, int x) {
+        const long long fa = get4(F, a), fx = get4(F, x);
+        return A::div(A::from_i64(fa), A::from_i64(fa - fx));   // |fa - fx| < 2^48: exact operands
+    };
+    // corners of the tet relative to corner 0, as exact FP32 values (< 2^22)
+    auto dX = [&](int l, int k) {
+        const int3 p = l == 0 ? X[0] : (l == 1 ? X[1] : (l == 2 ? X[2] : X[3]));
+        const int v = k == 0 ? p.x - X[0].x : (k == 1 ? p.y - X[0].y : p.z - X[0].z);
+        return A::num((float)v);
+    };
+    T m[3] = {A::num(0.f), A::num(0.f), A::num(0.f)};
+    auto acc = [&](T M, int l) {   // mom += M (X_l - X0)
+        if (l == 0) return;
+        for (int k = 0; k < 3; k++) m[k] = A::add(m[k], A::mul(M, dX(l, k)));
+    };
+    T fr;
     if (neg == 1 || neg == 3) {
         // the corner a on the minority side and the tet it cuts off
-        int a = 0;
-        for (int c = 0; c < 4; c++)
-            if ((F[c] < 0) == (neg == 1)) a = c;
-        double fs = 1.0, cen[4] = {0, 0, 0, 0}, rest = 0.0;
-        for (int x = 0; x < 4; x++) {
-            if (x == a) continue;
-            const double s = cut(a, x);
-            fs *= s;
-            cen[x] = 0.25 * s;
-            rest += 1.0 - s;
+        const bool want = neg == 1;
+        const int a = ((F[0] < 0) == want) ? 0 : (((F[1] < 0) == want) ? 1 : (((F[2] < 0) == want) ? 2 : 3));
+        const int x1 = (a + 1) & 3, x2 = (a + 2) & 3, x3 = (a + 3) & 3;
+        const T s1 = cut(a, x1), s2 = cut(a, x2), s3 = cut(a, x3);
+        const T fs = A::mul(A::mul(s1, s2), s3);
+        const T q = A::mul(fs, A::num(0.25f));
+        const T ca = A::mul(q, A::sub(A::num(4.f), A::add(A::add(s1, s2), s3)));   // fs * centroid_a
+        if (want) {
+            fr = fs;
+            acc(ca, a);
+            acc(A::mul(q, s1), x1);
+            acc(A::mul(q, s2), x2);
+            acc(A::mul(q, s3), x3);
+        } else {   // the whole tet's moment (1/4 each) minus the corner tet's
+            fr = A::sub(A::num(1.f), fs);
+            const T qt = A::num(0.25f);
+            acc(A::sub(qt, ca), a);
+            acc(A::sub(qt, A::mul(q, s1)), x1);
+            acc(A::sub(qt, A::mul(q, s2)), x2);
+            acc(A::sub(qt, A::mul(q, s3)), x3);
         }
-        cen[a] = 0.25 * (1.0 + rest);
-        if (neg == 1) {
-            frac = fs;
-            for (int c = 0; c < 4; c++) M[c] = fs * cen[c];
-        } else {
-            frac = 1.0 - fs;
-            for (int c = 0; c < 4; c++) M[c] = 0.25 - fs * cen[c];
+    } else {
+        int a = -1, b = -1, c = -1, d = -1;
+        for (int l = 0; l < 4; l++) {
+            if (F[l] < 0) (a < 0 ? a : b) = l;
+            else (c < 0 ? c : d) = l;
         }
-        return;
+        const T sac = cut(a, c), sad = cut(a, d), sbc = cut(b, c), sbd = cut(b, d);
+        const T one = A::num(1.f);
+        const T f1 = A::mul(sac, sad), f2 = A::mul(A::mul(sad, sbc), A::sub(one, sac)),
+                f3 = A::mul(A::mul(sbc, sbd), A::sub(one, sad));
+        fr = A::add(A::add(f1, f2), f3);
+        const T q = A::num(0.25f);
+        // vertex sums of the three tets, corner by corner
+        const T Ma = A::mul(q, A::add(A::add(A::mul(f1, A::sub(A::num(3.f), A::add(sac, sad))),
+                                             A::mul(f2, A::sub(A::num(2.f), A::add(sac, sad)))),
+                                      A::mul(f3, A::sub(one, sad))));
+        const T Mb = A::mul(q, A::add(A::add(f1, A::mul(f2, A::sub(A::num(2.f), sbc))),
+                                      A::mul(f3, A::sub(A::num(3.f), A::add(sbc, sbd)))));
+        const T Mc = A::mul(q, A::add(A::add(A::mul(f1, sac), A::mul(f2, A::add(sac, sbc))), A::mul(f3, sbc)));
+        const T Md = A::mul(q, A::add(A::mul(A::add(f1, f2), sad), A::mul(f3, A::add(sad, sbd))));
+        acc(Ma, a);
+        acc(Mb, b);
+        acc(Mc, c);
+        acc(Md, d);
     }
-    int k0 = -1, k1 = -1, o0 = -1, o1 = -1;
-    for (int c = 0; c < 4; c++) {
-        if (F[c] < 0) (k0 < 0 ? k0 : k1) = c;
-        else (o0 < 0 ? o0 : o1) = c;
-    }
-    const int a = k0, b = k1, c = o0, d = o1;
-    const double sac = cut(a, c), sad = cut(a, d), sbc = cut(b, c), sbd = cut(b, d);
-    // vertices in barycentric coordinates
-    double ea[4] = {0, 0, 0, 0}, eb[4] = {0, 0, 0, 0}, pac[4] = {0, 0, 0, 0}, pad[4] = {0, 0, 0, 0},
-           pbc[4] = {0, 0, 0, 0}, pbd[4] = {0, 0, 0, 0};
-    ea[a] = 1.0;
-    eb[b] = 1.0;
-    pac[a] = 1.0 - sac, pac[c] = sac;
-    pad[a] = 1.0 - sad, pad[d] = sad;
-    pbc[b] = 1.0 - sbc, pbc[c] = sbc;
-    pbd[b] = 1.0 - sbd, pbd[d] = sbd;
-    const double f1 = sac * sad, f2 = sad * sbc * (1.0 - sac), f3 = sbc * sbd * (1.0 - sad);
-    frac = f1 + f2 + f3;
-    for (int q = 0; q < 4; q++)
-        M[q] = 0.25 * (f1 * (ea[q] + pac[q] + pad[q] + eb[q]) + f2 * (pac[q] + pad[q] + eb[q] + pbc[q]) +
-                       f3 * (pad[q] + eb[q] + pbc[q] + pbd[q]));
+    frac = A::dbl(fr);
+    for (int k = 0; k < 3; k++) mom[k] = A::dbl(m[k]);
 }
 
 template <typename Real>
@@ -1116,19 +1160,13 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     if (__popc(pmask) == 1) {   // cut by one radical plane: closed form
         long long F[4];
         row_i64(L, A.Ci, A.W, __ffs(pmask) - 1, F);
-        double frac, M[4];
-        one_plane_piece(F, frac, M);
+        double frac, mom[3];
+        one_plane_piece<T>(F, L.X, frac, mom);
         const double vt = tet_volume6(L.X) / 6.0;
         const double u3 = A.unit * A.unit * A.unit;
         A.p_vol[p] = vt * frac * u3;
-        const int xs[4][3] = {{L.X[0].x, L.X[0].y, L.X[0].z}, {L.X[1].x, L.X[1].y, L.X[1].z},
-                              {L.X[2].x, L.X[2].y, L.X[2].z}, {L.X[3].x, L.X[3].y, L.X[3].z}};
-        for (int k = 0; k < 3; k++) {   // relative to corner 0: sum_c M_c = frac
-            const double x0 = (double)xs[0][k];
-            double m = frac * x0;
-            for (int cc = 1; cc <= 3; cc++) m += M[cc] * ((double)xs[cc][k] - x0);
-            A.p_mom[3 * p + k] = vt * m * u3 * A.unit;
-        }
+        const double x0[3] = {(double)L.X[0].x, (double)L.X[0].y, (double)L.X[0].z};
+        for (int k = 0; k < 3; k++) A.p_mom[3 * p + k] = vt * (frac * x0[k] + mom[k]) * u3 * A.unit;
         return;
     }
     RC.fill(L, A.Ci, A.W, pmask);

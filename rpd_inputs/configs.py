@@ -201,24 +201,28 @@ def batch_shapes(n: int = 32, seed: int = BASE_SEED + 5, tmin: int = 1000, tmax:
                  smax: int = 4000, g: int = 19):
     """The batching workload: n seeded shapes cycling through solid tori,
     genus 0-5 slabs and ellipsoid unions, with log-uniform tet counts in
-    [tmin, tmax] and sphere counts in [smin, smax] (at most one sphere per 4
-    tets), all on one grid of 2^-g.  Returns a list of Workloads."""
+    [tmin, tmax] and sphere counts in [smin, smax] (at most one sphere per 8
+    tets, and for tori at most 4 per tet length along the core circle), all
+    on one grid of 2^-g.  Returns a list of Workloads."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
         nt = float(np.exp(rng.uniform(np.log(tmin), np.log(tmax))))
-        ns = int(min(np.exp(rng.uniform(np.log(smin), np.log(smax))), max(smin, nt / 4)))
+        ns = int(min(np.exp(rng.uniform(np.log(smin), np.log(smax))), max(smin, nt / 8)))
         kind = i % 3
         if kind == 0:
             R, r = 1.0, rng.uniform(0.3, 0.45)
             h = (6.0 * 2 * np.pi ** 2 * R * r * r / nt) ** (1.0 / 3.0)
+            # core-circle spheres at most ~4 per tet length along the core,
+            # so a tet meets at most a few dozen cells
+            ns = min(ns, max(smin, int(4 * 2 * np.pi * R / h)))
             q, tets = lattice_mesh(torus_sdf(R, r), [-R - r - 0.05] * 2 + [-r - 0.05], [R + r + 0.05] * 2 + [r + 0.05],
                                    h, g, rng)
             c, rad = torus_core_spheres(ns, rng, R=R, rmin=0.75 * r, rmax=r)
             w = _finish(f"batch{i}_torus", q, tets, c, rad, g, 16, "fp32", expect_chi=0)
         elif kind == 1:
-            genus = (i // 3) % 6
             m = max(2, int(round((nt / 48.0) ** (1.0 / 3.0))))
+            genus = (i // 3) % 6 if m >= 8 else 0   # holes need a few cubes across
             holes = slab_holes(genus)
             q, tets = slab_mesh(BLOCK_HALF, holes, 0.2, 1.0 / m, g, rng)
             c, rad = slab_medial_spheres(ns, rng, holes, 0.2)
