@@ -75,6 +75,9 @@ typedef struct {
                              spheres out of the neighbour grid and scans them
                              first (a tuning choice, off by default: slower on
                              the organic blob).  Results must not change.       */
+    int32_t edge_lengths; /* 1: the volume pass also measures every restricted
+                             power edge segment (rpd_edge_lengths and rpd_medial
+                             need it, and partial updates keep it); 0: skipped  */
 } rpd_options;
 
 typedef struct {
@@ -103,7 +106,8 @@ typedef struct {
 
 typedef struct rpd_ctx rpd_ctx;   /* opaque; owns all device workspace and results */
 
-/* Fill *opt with defaults: FP32_FILTERED, k = 16, grid_bits = 20, no debug. */
+/* Fill *opt with defaults: FP32_FILTERED, k = 16, grid_bits = 20, no debug,
+ * no edge lengths. */
 void rpd_default_options(rpd_options* opt);
 
 /*
@@ -286,7 +290,9 @@ rpd_status rpd_pin_features(rpd_ctx* ctx, const double* d_pins, const double* d_
  * segments), with its key; the dual triangle's importance in the thinning
  * (Sec. 5.3).  d_keys i32[n*3], d_len f64[n] (world units); two-phase like
  * rpd_euler.  Lengths are summed per key in 64-bit fixed point (2^-24 grid
- * units), so they do not depend on the order of the segments. */
+ * units), so they do not depend on the order of the segments.  The context
+ * must be built with rpd_options.edge_lengths = 1 (RPD_E_INVALID otherwise);
+ * so must rpd_medial's. */
 rpd_status rpd_edge_lengths(rpd_ctx* ctx, int32_t* d_keys, double* d_len, int64_t cap, int64_t* n);
 
 typedef struct {

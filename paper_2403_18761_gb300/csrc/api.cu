@@ -680,7 +680,7 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
             a.rval[k] = c->alloc<int16_t>(cap[k]);
             a.rlink[k] = c->alloc<uint8_t>(cap[k]);
             NEED(a.rkey[k] && a.rtet[k] && a.rval[k] && a.rlink[k]);
-            if (k == 1) {
+            if (k == 1 && c->opt.edge_lengths) {
                 a.elen = c->alloc<long long>(cap[k]);
                 NEED(a.elen);
             }
@@ -821,6 +821,7 @@ void rpd_default_options(rpd_options* opt) {
     opt->k = 16;
     opt->grid_bits = 20;
     opt->debug_checks = 0;
+    opt->edge_lengths = 0;
 }
 
 rpd_status rpd_build(const double* d_verts, int64_t nv, const int32_t* d_tets, int64_t nt, const double* d_centers,
@@ -1251,6 +1252,8 @@ rpd_status rpd_shrink_counters(rpd_ctx* ctx, int64_t* pins, int64_t* iters, int6
 // taken once the build has joined its streams).
 static rpd_status ensure_edge_lengths(rpd_ctx* c) {
     if (c->edge_len) return RPD_OK;
+    if (!c->clip.elen)
+        return fail(c, RPD_E_INVALID, "edge lengths need a context built with rpd_options.edge_lengths = 1");
     long long* len = c->alloc<long long>(c->nkeys[2] + 1);
     if (!len) return fail(c, RPD_E_OOM, "device allocation failed");
     launch_edge_length_sum(c->clip, c->fcap[2], c->fout[2].keys, c->nkeys[2], len, c->stream);

@@ -1157,7 +1157,7 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
         for (int k = 0; k < 3; k++)
             if (tb(tw, k) >= 4) pmask |= 1u << (tb(tw, k) - 4);
     }
-    if (__popc(pmask) == 1) {   // cut by one radical plane: closed form
+    if (L.n == 2) {   // two candidates (a whole bin): one radical plane, closed form
         long long F[4];
         row_i64(L, A.Ci, A.W, __ffs(pmask) - 1, F);
         double frac, mom[3];
@@ -1212,18 +1212,18 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     // points' chart coordinates P (the apex's is 0) give the world vector
     // sum_c (X_c - X0) dP_c in grid units; stored as fixed point x 2^24.
     if (A.elen && A.e_cnt[p]) {
+        // in the chart type: double-float on the FP32 pipes in the
+        // FP32-filtered mode (native FP64 runs at 1/64 of the rate there)
         long long we = A.e_off[p];
-        auto chart = [&](int v, double* out) {
-            for (int k = 0; k < 3; k++) {
-                if (v == apex) {
-                    out[k] = 0.0;
-                } else {
-                    T x;
-                    V.get(v, k, x);
-                    if constexpr (sizeof(Real) == 4) out[k] = df_to_double(x);
-                    else out[k] = x;
-                }
+        auto chart = [&](int v, int k) {
+            T x;
+            if (v == apex) {
+                if constexpr (sizeof(Real) == 4) x = df_make(0.0f);
+                else x = 0.0;
+            } else {
+                V.get(v, k, x);
             }
+            return x;
         };
         for (int v = 0; v < nslot; v++) {
             const uint32_t tw = V.w(v, 0);
@@ -1233,17 +1233,31 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
                 const int x = tb(tw, e), y = tb(tw, (e + 1) % 3);
                 if (!(x < y && x >= 4)) continue;
                 if (L.cand[x - 4] <= L.i || L.cand[y - 4] <= L.i) continue;
-                double pa[3], pb[3];
-                chart(v, pa);
-                chart(tb(nw, e), pb);
-                double dx = 0, dy = 0, dz = 0;
-                for (int c = 1; c <= 3; c++) {
-                    const double d = pa[c - 1] - pb[c - 1];
-                    dx += d * (double)(L.X[c].x - L.X[0].x);
-                    dy += d * (double)(L.X[c].y - L.X[0].y);
-                    dz += d * (double)(L.X[c].z - L.X[0].z);
+                const int u = tb(nw, e);
+                double len;
+                if constexpr (sizeof(Real) == 4) {
+                    df w3[3] = {df_make(0.f), df_make(0.f), df_make(0.f)};
+                    for (int c = 1; c <= 3; c++) {
+                        const df d = df_sub(chart(v, c - 1), chart(u, c - 1));
+                        const float ex = (float)(L.X[c].x - L.X[0].x), ey = (float)(L.X[c].y - L.X[0].y),
+                                    ez = (float)(L.X[c].z - L.X[0].z);   // exact: < 2^22
+                        w3[0] = df_add(w3[0], df_mul(d, df_make(ex)));
+                        w3[1] = df_add(w3[1], df_mul(d, df_make(ey)));
+                        w3[2] = df_add(w3[2], df_mul(d, df_make(ez)));
+                    }
+                    const df l2 = df_add(df_add(df_mul(w3[0], w3[0]), df_mul(w3[1], w3[1])), df_mul(w3[2], w3[2]));
+                    len = df_to_double(df_sqrt(l2));
+                } else {
+                    double dx = 0, dy = 0, dz = 0;
+                    for (int c = 1; c <= 3; c++) {
+                        const double d = chart(v, c - 1) - chart(u, c - 1);
+                        dx += d * (double)(L.X[c].x - L.X[0].x);
+                        dy += d * (double)(L.X[c].y - L.X[0].y);
+                        dz += d * (double)(L.X[c].z - L.X[0].z);
+                    }
+                    len = sqrt(dx * dx + dy * dy + dz * dz);
                 }
-                if (we < A.rcap[1]) A.elen[we] = llrint(sqrt(dx * dx + dy * dy + dz * dz) * 0x1p24);
+                if (we < A.rcap[1]) A.elen[we] = llrint(len * 0x1p24);
                 we++;
             }
         }

@@ -63,6 +63,17 @@ __device__ __forceinline__ df df_div_fast(df a, df b) {
 
 __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
 
+// sqrt(x) for x >= 0 (0 otherwise): the FP32 root s and one Newton step on
+// the exact residual x - s^2 (two-product by FMA), relative error about 2^-44.
+__device__ __forceinline__ df df_sqrt(df x) {
+    if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+    const float s = __fsqrt_rn(x.hi);
+    const float p = __fmul_rn(s, s);
+    const float pe = __fmaf_rn(s, s, -p);   // s * s = p + pe exactly
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
+    return fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
+
 // Exact conversion of |v| < 2^48 (two exactly representable parts).
 __device__ __forceinline__ df df_from_i64(long long v) {
     long long h = v >> 24;                 // arithmetic shift: v = h * 2^24 + l, 0 <= l < 2^24

@@ -753,7 +753,8 @@ __device__ __forceinline__ void knn_insert(unsigned long long key, unsigned long
     }
 }
 
-__global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
+template <bool HEAVY>
+__global__ void __launch_bounds__(256, 4) k_knn_warp(const int32_t* __restrict__ Xi, const uint32_t* __restrict__ vorder,
                                                   long long nv, const GridParams* __restrict__ gp,
                                                   const int64_t* __restrict__ start_all, const int4* __restrict__ sph,
                                                   const long long* __restrict__ sw,
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(256) k_knn_warp(const int32_t* __restrict__ Xi
     int3 plo = make_int3(1, 1, 1), phi = make_int3(0, 0, 0);   // processed box (empty)
     long long lb2 = LLONG_MAX;
     // the heavy spheres, kept out of the grid, first
-    const int nh = nheavy ? *nheavy : 0;
+    const int nh = HEAVY ? *nheavy : 0;
     for (int hb = 0; hb < nh; hb += 32) {
         U key = EMPTY;
         if (hb + lane < nh) {
@@ -1316,9 +1317,14 @@ void launch_knn(const int32_t* Xi, long long nv, long long ns, const GridParams*
     while ((1ll << bits) < ncap) bits++;
     if ((ns <= (1 << 17) || nshapes > 1) && !two_word) {   // batches: shape-local ids in the key
         // one vertex per warp in input order: the sphere grid stays in cache
-        k_knn_warp<<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nullptr, nv, gp, cell_start, cell_sph, cell_w,
-                                                       cell_wmax + ncap, K, knn, dplus, voff, nshapes, hsph, hw,
-                                                       nheavy);
+        if (nheavy)
+            k_knn_warp<true><<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nullptr, nv, gp, cell_start, cell_sph, cell_w,
+                                                                 cell_wmax + ncap, K, knn, dplus, voff, nshapes, hsph,
+                                                                 hw, nheavy);
+        else
+            k_knn_warp<false><<<nblk(32 * nv, 256), 256, 0, s>>>(Xi, nullptr, nv, gp, cell_start, cell_sph, cell_w,
+                                                                  cell_wmax + ncap, K, knn, dplus, voff, nshapes,
+                                                                  nullptr, nullptr, nullptr);
     } else {
         k_vertex_cells<<<nblk(nv, 256), 256, 0, s>>>(Xi, nv, gp, k0, v0);
         note_launch();

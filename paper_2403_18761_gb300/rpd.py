@@ -35,7 +35,7 @@ class RpdError(RuntimeError):
 
 class rpd_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("k", ctypes.c_int32), ("grid_bits", ctypes.c_int32),
-                ("debug_checks", ctypes.c_int32)]
+                ("debug_checks", ctypes.c_int32), ("edge_lengths", ctypes.c_int32)]
 
 
 class rpd_stats(ctypes.Structure):
@@ -563,7 +563,7 @@ class Ctx:
 
 
 def rpd_build(verts, tets, centers, radii, precision="fp32", k=16, grid_bits=20, stream=None,
-              device="cuda", debug=0) -> Ctx:
+              device="cuda", debug=0, edge_lengths=False) -> Ctx:
     """Build the restricted power diagram.  Inputs may be host arrays or device
     tensors; host inputs are copied to the device first."""
     if not torch.cuda.is_available():
@@ -582,6 +582,7 @@ def rpd_build(verts, tets, centers, radii, precision="fp32", k=16, grid_bits=20,
     opt.k = int(k)
     opt.grid_bits = int(grid_bits)
     opt.debug_checks = int(debug)
+    opt.edge_lengths = int(bool(edge_lengths))
     sh, stream = _stream_handle(stream)
     out = ctypes.c_void_p()
     st = lib.rpd_build(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(C), _ptr(R), R.shape[0],
@@ -654,10 +655,10 @@ def rpd_autotune(verts, tets, centers, radii, ks=(8, 16, 24, 32), reps=3, precis
     return int(best.k), float(ms.value)
 
 
-def build_workload(w, precision=None, k=None, stream=None, debug=0):
+def build_workload(w, precision=None, k=None, stream=None, debug=0, edge_lengths=False):
     """rpd_build on a seeded workload (see rpd_inputs)."""
     return rpd_build(w.verts, w.tets, w.centers, w.radii, precision=precision or w.precision,
-                     k=k or w.k, grid_bits=w.grid_bits, stream=stream, debug=debug)
+                     k=k or w.k, grid_bits=w.grid_bits, stream=stream, debug=debug, edge_lengths=edge_lengths)
 
 
 def collect(ctx):

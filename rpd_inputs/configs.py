@@ -197,12 +197,40 @@ def tiny_set(count: int = 24, base_seed: int = BASE_SEED + 100):
     return out
 
 
+def _thin_spheres(c, r, dmin):
+    """Greedy Poisson-disk thinning in input order: keep a sphere only when
+    no kept centre lies within dmin (a hash grid of cell dmin)."""
+    keep, cells = [], {}
+    for i, p in enumerate(c):
+        key = tuple(np.floor(p / dmin).astype(np.int64))
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for j in cells.get((key[0] + dx, key[1] + dy, key[2] + dz), ()):
+                        if np.sum((c[j] - p) ** 2) < dmin * dmin:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            keep.append(i)
+            cells.setdefault(key, []).append(i)
+    keep = np.asarray(keep, dtype=np.int64)
+    return c[keep], r[keep]
+
+
 def batch_shapes(n: int = 32, seed: int = BASE_SEED + 5, tmin: int = 1000, tmax: int = 100_000, smin: int = 32,
                  smax: int = 4000, g: int = 19):
     """The batching workload: n seeded shapes cycling through solid tori,
     genus 0-5 slabs and ellipsoid unions, with log-uniform tet counts in
     [tmin, tmax] and sphere counts in [smin, smax] (at most one sphere per 8
-    tets, and for tori at most 4 per tet length along the core circle), all
+    tets, for tori at most 4 per tet length along the core circle, and no two
+    centres closer than 3/4 of the lattice spacing), all
     on one grid of 2^-g.  Returns a list of Workloads."""
     rng = np.random.default_rng(seed)
     out = []
@@ -219,6 +247,7 @@ def batch_shapes(n: int = 32, seed: int = BASE_SEED + 5, tmin: int = 1000, tmax:
             q, tets = lattice_mesh(torus_sdf(R, r), [-R - r - 0.05] * 2 + [-r - 0.05], [R + r + 0.05] * 2 + [r + 0.05],
                                    h, g, rng)
             c, rad = torus_core_spheres(ns, rng, R=R, rmin=0.75 * r, rmax=r)
+            c, rad = _thin_spheres(c, rad, 0.75 * h)
             w = _finish(f"batch{i}_torus", q, tets, c, rad, g, 16, "fp32", expect_chi=0)
         elif kind == 1:
             m = max(2, int(round((nt / 48.0) ** (1.0 / 3.0))))
@@ -226,6 +255,7 @@ def batch_shapes(n: int = 32, seed: int = BASE_SEED + 5, tmin: int = 1000, tmax:
             holes = slab_holes(genus)
             q, tets = slab_mesh(BLOCK_HALF, holes, 0.2, 1.0 / m, g, rng)
             c, rad = slab_medial_spheres(ns, rng, holes, 0.2)
+            c, rad = _thin_spheres(c, rad, 0.75 / m)
             w = _finish(f"batch{i}_slab{genus}", q, tets, c, rad, g, 32, "fp32", expect_chi=1 - genus)
         else:
             blob = EllipsoidBlob(int(rng.integers(6, 24)), rng)
@@ -234,6 +264,7 @@ def batch_shapes(n: int = 32, seed: int = BASE_SEED + 5, tmin: int = 1000, tmax:
             h = (6.0 * vol / nt) ** (1.0 / 3.0)
             q, tets = lattice_mesh(blob.sdf, blob.lo - h, blob.hi + h, h, g, rng, inside_by_vertices=True)
             c, rad = blob.medial_spheres(ns, rng)
+            c, rad = _thin_spheres(c, rad, 0.75 * h)
             w = _finish(f"batch{i}_blob", q, tets, c, rad, g, 32, "fp32")
         out.append(w)
     return out

@@ -21,7 +21,7 @@ def test_option_defaults_without_gpu():
     lib = pkg.load()
     o = rpd.rpd_options()
     lib.rpd_default_options(ctypes.byref(o))
-    assert (o.precision, o.k, o.grid_bits, o.debug_checks) == (rpd.RPD_FP32_FILTERED, 16, 20, 0)
+    assert (o.precision, o.k, o.grid_bits, o.debug_checks, o.edge_lengths) == (rpd.RPD_FP32_FILTERED, 16, 20, 0, 0)
 
 
 def test_build_rejects_bad_sizes_before_touching_the_device():

@@ -32,7 +32,7 @@ def _setup():
 @pytest.mark.parametrize("case", ["torus", "block"])
 def test_edge_lengths_match_oracle(case, precision):
     w = torus_c1() if case == "torus" else block_c2(h=0.15, ns=300)
-    ctx = build_workload(w, precision=precision)
+    ctx = build_workload(w, precision=precision, edge_lengths=True)
     keys, length = (x.cpu().numpy() for x in ctx.rpd_edge_lengths())
     o = oracle.run(w)["kinds"][3]
     assert np.array_equal(keys, o["keys"].astype(np.int32))
@@ -55,7 +55,7 @@ def _tables(ctx, w):
 @pytest.mark.parametrize("sigma", [0.1, 0.3, 10.0])
 def test_thinning_matches_cpu_restatement(sigma):
     w = block_c2(h=0.15, ns=300)
-    ctx = build_workload(w)
+    ctx = build_workload(w, edge_lengths=True)
     g, edges, faces, tets, alpha = _tables(ctx, w)
     info, e, f = ctx.rpd_medial(sigma)
     assert info["vertices"] == len(g["kinds"][1]["keys"]) and info["tets"] == len(tets)
@@ -72,9 +72,20 @@ def test_nerve_theorem_after_repair():
     thinning removes every tetrahedron without changing it."""
     w = torus_c1()
     sub = Workload(w.name, w.verts, w.tets, w.centers[::16], w.radii[::16], w.grid_bits, w.k, w.precision, w.info)
-    ctx = build_workload(sub)
+    ctx = build_workload(sub, edge_lengths=True)
     _, _, failing = ctx.rpd_repair(64)
     assert failing == 0
     info, e, f = ctx.rpd_medial(0.3)
     assert info["chi"] == w.info["chi"] == 0
     assert info["chi_thin"] == 0 and info["tets_thin"] == 0
+
+
+def test_edge_lengths_need_the_build_option():
+    from paper_2403_18761_gb300 import RpdError
+    from paper_2403_18761_gb300.rpd import RPD_E_INVALID
+    ctx = build_workload(torus_c1())
+    with pytest.raises(RpdError) as e:
+        ctx.rpd_edge_lengths()
+    assert e.value.status == RPD_E_INVALID
+    with pytest.raises(RpdError):
+        ctx.rpd_medial(0.3)
