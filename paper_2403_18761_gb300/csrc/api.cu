@@ -358,10 +358,14 @@ rpd_status run_clip(rpd_ctx* c, bool zero_rcount, bool zero_qcount) {
             launch_clip(a, b, c->opt.precision, c->bins + off[b], c->bin_count + b, n, sb);
             launch_records(a, b, n, sb);
             cudaEventRecord(c->evc[1 + b], sb);
+            // the bin's volume pass follows its records on the same stream,
+            // beside the other bins' clips (latency-bound, so the SMs have
+            // room), and joins at the end of the build
+            launch_volume(a, b, c->opt.precision, n, sb);
         }
+        cudaEventRecord(c->evc[1 + RPD_NBINS + b], sb);
         // the records (what the finalisation reads) are complete once the
-        // record kernel is; the bin's volume pass is launched with the
-        // finalisation and joins at the end of the build
+        // record kernel is
         cudaStreamWaitEvent(s, c->evc[1 + b], 0);
     }
     return cuda_check(c, "clip launch");
@@ -715,23 +719,6 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
                 cudaMemsetAsync(d_nseg + kind - 1, 0, sizeof(long long), sk);
             }
             cudaEventRecord(c->ev[6 + kind - 1], sk);
-        }
-        // the volume passes start with the finalisation (high-priority
-        // streams first), so they do not compete with the clip kernels
-        for (int b = RPD_NBINS - 1; b >= 0; b--) {
-            if (c->hbin[b] == 0) continue;
-            cudaStream_t sb = bs->s[b];
-            if (b > 0) {
-                cudaStreamWaitEvent(sb, c->ev[5], 0);
-                ClipArgs va = c->clip;
-                va.qpair = c->qpair[b];
-                va.qnv = c->qnv[b];
-                va.qtrip = c->qtrip[b];
-                va.qcap = c->hbin[b];
-                va.qcount = c->qcount + b;
-                launch_volume(va, b, c->opt.precision, c->hbin[b], sb);
-            }
-            cudaEventRecord(c->evc[1 + RPD_NBINS + b], sb);
         }
         scan_excl(a.pflag, c->piece_off, npairs, ptmp, s);
         TRY(cuda_check(c, "finalize launch"));
