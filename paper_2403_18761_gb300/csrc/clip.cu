@@ -816,29 +816,22 @@ __global__ void __launch_bounds__(128) k_records(ClipArgs A) {
 // face's first vertex; faces are walked through the dual adjacency.
 //   vol(P) = vol(t) |sum d|,  d = det(P_R, P_v, P_v')
 //   int_P x = vol(P) X0 + vol(t) sum_c (X_c - X0) (beta_a,c |sum d| + sign * sum d (P_R+P_v+P_v')_c / 4)
-// Exact rows F_s[c] = pd(X_c, i) - pd(X_c, s) of every candidate plane of a
-// piece, built once per piece (all loads issued together) and read by the
-// vertex coordinates.  Shared memory, [slot][corner][lane].
+// Exact rows F_s[c] = pd(X_c, i) - pd(X_c, s) of a candidate plane, computed
+// where a vertex coordinate needs them (the sphere's centre and weight come
+// from the L1/L2-resident sphere arrays).  Keeping them in shared memory
+// instead cost 1 KB per warp per candidate and halved the occupancy of the
+// middle bins.
 struct RowCache {
-    long long* base;
-    int lane;
-    __device__ __forceinline__ long long get(int slot, int c) const { return base[(slot * 4 + c) * 32 + lane]; }
-    __device__ __forceinline__ void row(int slot, long long F[4]) const {
-#pragma unroll
-        for (int c = 0; c < 4; c++) F[c] = get(slot, c);
+    const Lane& L;
+    const int32_t* __restrict__ Ci;
+    const long long* __restrict__ W;
+    __device__ __forceinline__ long long get(int slot, int c) const {
+        const int s = L.cand[slot];
+        const int3 x = c == 0 ? L.X[0] : (c == 1 ? L.X[1] : (c == 2 ? L.X[2] : L.X[3]));
+        const long long d = c == 0 ? L.di[0] : (c == 1 ? L.di[1] : (c == 2 ? L.di[2] : L.di[3]));
+        return d - pd_exact(x, ld_int3(Ci, s), W[s]);
     }
-    // rows of the candidate slots in `mask` (bit s2: plane 4 + s2), the only
-    // planes the piece's vertices lie on
-    __device__ __forceinline__ void fill(const Lane& L, const int32_t* __restrict__ Ci,
-                                         const long long* __restrict__ W, unsigned mask) const {
-        for (; mask; mask &= mask - 1) {
-            const int s2 = __ffs(mask) - 1;
-            long long F[4];
-            row_i64(L, Ci, W, s2, F);
-#pragma unroll
-            for (int c = 0; c < 4; c++) base[(s2 * 4 + c) * 32 + lane] = F[c];
-        }
-    }
+    __device__ __forceinline__ void row(int slot, long long F[4]) const { row_i64(L, Ci, W, slot, F); }
 };
 
 template <typename Real>
@@ -1127,7 +1120,8 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const VStore<T> V{smem + (size_t)warp * vmax * 8 * 32, lane};
-    const RowCache RC{(long long*)(smem + (size_t)nwarps * vmax * 8 * 32) + (size_t)warp * rmax * 4 * 32, lane};
+    (void)rmax;
+    (void)nwarps;
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)*A.qcount;
     if (q >= n || q >= A.qcap) return;
@@ -1169,7 +1163,7 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
         for (int k = 0; k < 3; k++) A.p_mom[3 * p + k] = vt * (frac * x0[k] + mom[k]) * u3 * A.unit;
         return;
     }
-    RC.fill(L, A.Ci, A.W, pmask);
+    const RowCache RC{L, A.Ci, A.W};
     // chart coordinates relative to the apex vertex
     T O[3];
     const uint32_t ta = V.w(apex, 0);
@@ -1450,7 +1444,7 @@ void launch_clip_t(const ClipArgs& a, const int32_t* pairs, const int32_t* d_n, 
 template <typename Real>
 void launch_volume_t(const ClipArgs& a, int vmax, int rmax, int warps, long long nmax, cudaStream_t s) {
     if (nmax <= 0) return;
-    const size_t smem = (size_t)warps * vmax * 8 * 32 * sizeof(uint32_t) + (size_t)warps * rmax * 4 * 32 * 8;
+    const size_t smem = (size_t)warps * vmax * 8 * 32 * sizeof(uint32_t);
     static SmemLimit lim;
     raise_smem_limit((const void*)k_volume<Real>, smem, lim);
     k_volume<Real><<<nblk(nmax, 32 * warps), 32 * warps, smem, s>>>(a, vmax, rmax);
