@@ -43,23 +43,51 @@ __global__ void k_snap_radii(const double* __restrict__ r, long long n, double s
 
 // Mesh combinatorics by hashing: every tet inserts its 4 faces (sorted vertex
 // triples) and 6 edges (sorted pairs) into open-addressing tables keyed by the
-// packed vertex ids; per face the table counts the tets and keeps the lowest
-// and highest (tet, face) index, per edge the lowest (tet, edge) index, per
-// vertex the lowest tet.  A second pass looks every entry up again: face
-// adjacency, ownership by the lowest-numbered tet, and > 2 tets per face as a
-// non-manifold error.  The results do not depend on the insertion order.
+// packed vertex ids; per face the table keeps the (tet, face) indices of the
+// (at most two) tets that hold it, per edge the lowest (tet, edge) index, per
+// vertex the lowest tet.  A third tet on a face is a non-manifold error.  A
+// second pass looks every entry up again: face adjacency and ownership by the
+// lowest-numbered tet.  The results do not depend on the insertion order.
+// A slot is 16 bytes, key and payload together, so an insertion or a lookup
+// touches one 32-byte sector of the table (the probing and the atomics on the
+// payload land on the same line).
 struct MeshTables {
-    uint64_t* fk;   // face keys
-    uint32_t* fc;   // tets per face
-    uint32_t* fmin;
-    uint32_t* fmax;
-    uint64_t* ek;   // edge keys
-    uint32_t* emin;
+    uint64_t* ft;   // face slots: [key, (first index, second index)]
+    uint64_t* et;   // edge slots: [key, (lowest index, unused)]
     uint32_t* vmin;   // lowest tet per vertex
     unsigned long long fmask, emask;
     int fshift, eshift;
     int vb;
 };
+
+constexpr uint32_t NONE32 = 0xffffffffu;
+
+// Slot of `key` in a table of 16-byte slots (the key first), inserted if
+// absent; -1 when the table is full.
+__device__ __forceinline__ long long slot_insert(uint64_t* t, unsigned long long mask, int shift, uint64_t key) {
+    unsigned long long h = hslot(key, shift);
+    for (unsigned long long it = 0; it <= mask; it++) {
+        const uint64_t k = t[2 * h];
+        if (k == key) return (long long)h;
+        if (k == HEMPTY) {
+            const uint64_t old = atomicCAS((unsigned long long*)&t[2 * h], HEMPTY, key);
+            if (old == HEMPTY || old == key) return (long long)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ long long slot_find(const uint64_t* t, unsigned long long mask, int shift, uint64_t key) {
+    unsigned long long h = hslot(key, shift);
+    for (unsigned long long it = 0; it <= mask; it++) {
+        const uint64_t k = t[2 * h];
+        if (k == key) return (long long)h;
+        if (k == HEMPTY) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
 
 __device__ __forceinline__ void sort3(unsigned long long& a, unsigned long long& b, unsigned long long& c) {
     unsigned long long t;
@@ -127,24 +155,24 @@ __global__ void k_mesh_insert(const int32_t* __restrict__ T, long long nt, long 
     for (int a = 0; a < 4; a++) atomicMin(&M.vmin[v[a]], (uint32_t)t);
 #pragma unroll
     for (int f = 0; f < 4; f++) {
-        const long long h = table_insert(M.fk, M.fmask, M.fshift, face_key(v, f, M.vb));
+        const long long h = slot_insert(M.ft, M.fmask, M.fshift, face_key(v, f, M.vb));
         if (h < 0) {
             dev_fail(st, RPD_E_OVERFLOW, CNT_CAPACITY);
             continue;
         }
         const uint32_t i = (uint32_t)(4 * t + f);
-        atomicAdd(&M.fc[h], 1u);
-        atomicMin(&M.fmin[h], i);
-        atomicMax(&M.fmax[h], i);
+        uint32_t* ab = reinterpret_cast<uint32_t*>(&M.ft[2 * h + 1]);
+        if (atomicCAS(&ab[0], NONE32, i) != NONE32 && atomicCAS(&ab[1], NONE32, i) != NONE32)
+            dev_fail(st, RPD_E_NONMANIFOLD, CNT_NONMANIFOLD);   // a third tet on the face
     }
 #pragma unroll
     for (int e = 0; e < 6; e++) {
-        const long long h = table_insert(M.ek, M.emask, M.eshift, edge_key(v, e, M.vb));
+        const long long h = slot_insert(M.et, M.emask, M.eshift, edge_key(v, e, M.vb));
         if (h < 0) {
             dev_fail(st, RPD_E_OVERFLOW, CNT_CAPACITY);
             continue;
         }
-        atomicMin(&M.emin[h], (uint32_t)(6 * t + e));
+        atomicMin(reinterpret_cast<uint32_t*>(&M.et[2 * h + 1]), (uint32_t)(6 * t + e));
     }
 }
 
@@ -169,22 +197,20 @@ __global__ void k_mesh_finish(const int32_t* __restrict__ T, long long nt, long 
     for (int f = 0; f < 4; f++) {
         const uint32_t i = (uint32_t)(4 * t + f);
         int32_t nb = -1;
-        const long long h = table_find(M.fk, M.fmask, M.fshift, face_key(v, f, M.vb));
+        const long long h = slot_find(M.ft, M.fmask, M.fshift, face_key(v, f, M.vb));
         if (h >= 0) {
-            const uint32_t c = M.fc[h], mn = M.fmin[h];
-            if (c > 2) {
-                dev_fail(st, RPD_E_NONMANIFOLD, CNT_NONMANIFOLD);
-            } else {
-                if (mn == i) bits |= 1u << (10 + f);
-                if (c == 2) nb = (int32_t)((mn == i ? M.fmax[h] : mn) >> 2);
-            }
+            const uint64_t w = M.ft[2 * h + 1];
+            const uint32_t a = (uint32_t)w, b = (uint32_t)(w >> 32);
+            const uint32_t mn = min(a, b), mx = max(a, b);   // NONE32 sorts last
+            if (mn == i) bits |= 1u << (10 + f);
+            if (mx != NONE32) nb = (int32_t)((mn == i ? mx : mn) >> 2);
         }
         adj[4 * t + f] = nb;
     }
 #pragma unroll
     for (int e = 0; e < 6; e++) {
-        const long long h = table_find(M.ek, M.emask, M.eshift, edge_key(v, e, M.vb));
-        if (h >= 0 && M.emin[h] == (uint32_t)(6 * t + e)) bits |= 1u << (4 + e);
+        const long long h = slot_find(M.et, M.emask, M.eshift, edge_key(v, e, M.vb));
+        if (h >= 0 && (uint32_t)M.et[2 * h + 1] == (uint32_t)(6 * t + e)) bits |= 1u << (4 + e);
     }
     own[t] = bits;
 }
@@ -218,8 +244,7 @@ static int log2_cap(long long n) {
 
 size_t prep_tmp_bytes(long long nt, long long nv) {
     const long long cf = 1ll << log2_cap(6 * nt), ce = 1ll << log2_cap(8 * nt);
-    return al(sizeof(uint64_t) * (cf + ce)) + al(sizeof(uint32_t) * (cf + ce + nv)) +
-           al(sizeof(uint32_t) * 2 * cf);
+    return al(2 * sizeof(uint64_t) * (cf + ce)) + al(sizeof(uint32_t) * nv);
 }
 
 void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const int32_t* Xi, int32_t* adj,
@@ -230,15 +255,10 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
     const long long cf = 1ll << bf, ce = 1ll << be;
     char* p = (char*)tmp;
     MeshTables M;
-    M.fk = (uint64_t*)p;
-    M.ek = M.fk + cf;
-    p += al(sizeof(uint64_t) * (cf + ce));
-    M.fmin = (uint32_t*)p;
-    M.emin = M.fmin + cf;
-    M.vmin = M.emin + ce;
-    p += al(sizeof(uint32_t) * (cf + ce + nv));
-    M.fc = (uint32_t*)p;
-    M.fmax = M.fc + cf;
+    M.ft = (uint64_t*)p;
+    M.et = M.ft + 2 * cf;
+    p += al(2 * sizeof(uint64_t) * (cf + ce));
+    M.vmin = (uint32_t*)p;
     M.fmask = (unsigned long long)(cf - 1);
     M.emask = (unsigned long long)(ce - 1);
     M.fshift = 64 - bf;
@@ -246,9 +266,9 @@ void launch_prep_mesh(const int32_t* d_tets, long long nt, long long nv, const i
     int vb = 1;
     while ((1ll << vb) < nv) vb++;
     M.vb = vb;
-    cudaMemsetAsync(M.fk, 0xff, sizeof(uint64_t) * (cf + ce), s);
-    cudaMemsetAsync(M.fmin, 0xff, sizeof(uint32_t) * (cf + ce + nv), s);
-    cudaMemsetAsync(M.fc, 0, sizeof(uint32_t) * 2 * cf, s);
+    // every key empty, every payload NONE32
+    cudaMemsetAsync(M.ft, 0xff, 2 * sizeof(uint64_t) * (cf + ce), s);
+    cudaMemsetAsync(M.vmin, 0xff, sizeof(uint32_t) * nv, s);
     k_mesh_insert<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, Xi, M, st);
     note_launch();
     k_mesh_finish<<<nblk(nt, T), T, 0, s>>>(d_tets, nt, nv, M, adj, own, st);

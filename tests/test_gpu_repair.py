@@ -198,3 +198,25 @@ def test_repair_genus_slab(genus):
     assert failing == 0, (genus, rounds, inserted, failing)
     c, r = (x.cpu().numpy() for x in ctx.rpd_spheres())
     _oracle_all_contractible(w, c, r, collect(ctx))
+
+
+@pytest.mark.parametrize("genus", [0, 1, 2, 3, 4, 5])
+def test_repair_genus_slab_full_size(genus):
+    """The repair workload at its full size (~125k tets, 256 near-medial
+    starting spheres): every element contractible at the end, judged by the
+    C oracle's same-algorithm tier (kNN candidates, exact predicates; equal
+    to its brute force by the CPU tests) on the final sphere set."""
+    w = genus_slab(genus, seed=20240330 + 100 + genus, h=0.075, ns=256)
+    ctx = build_workload(w)
+    rounds, inserted, failing = ctx.rpd_repair(96)
+    assert failing == 0, (genus, rounds, inserted, failing)
+    c, r = (x.cpu().numpy() for x in ctx.rpd_spheres())
+    fin = Workload(w.name, w.verts, w.tets, c, r, w.grid_bits, w.k, w.precision, w.info)
+    o = oracle.run(fin, k=32)
+    g = collect(ctx)
+    for kind in (1, 2, 3):
+        d = o["kinds"][kind]
+        assert np.all(d["flag"]), (kind, int((~d["flag"]).sum()))
+        assert np.array_equal(g["kinds"][kind]["keys"], d["keys"].astype(np.int32)), kind
+        assert np.array_equal(g["kinds"][kind]["chi"], d["chi"].astype(np.int32)), kind
+        assert np.array_equal(g["kinds"][kind]["beta0"], d["beta0"].astype(np.int32)), kind
