@@ -311,6 +311,14 @@ __device__ __forceinline__ unsigned fbits(int p) { return p < 4 ? (1u << p) : 0u
 __device__ __forceinline__ unsigned tfbits(uint32_t tw) { return fbits(tb(tw, 0)) | fbits(tb(tw, 1)) | fbits(tb(tw, 2)); }
 __device__ __forceinline__ int pos_of(uint32_t tw, int p) { return tb(tw, 0) == p ? 0 : (tb(tw, 1) == p ? 1 : (tb(tw, 2) == p ? 2 : -1)); }
 
+__device__ __forceinline__ __int128 tet_det6(const int3* X) {
+    long long ax = X[1].x - X[0].x, ay = X[1].y - X[0].y, az = X[1].z - X[0].z;
+    long long bx = X[2].x - X[0].x, by = X[2].y - X[0].y, bz = X[2].z - X[0].z;
+    long long cx = X[3].x - X[0].x, cy = X[3].y - X[0].y, cz = X[3].z - X[0].z;
+    return (__int128)ax * ((__int128)by * cz - (__int128)bz * cy) - (__int128)ay * ((__int128)bx * cz - (__int128)bz * cx) +
+           (__int128)az * ((__int128)bx * cy - (__int128)by * cx);
+}
+
 __device__ __forceinline__ double tet_volume6(const int3* X) {
     long long ax = X[1].x - X[0].x, ay = X[1].y - X[0].y, az = X[1].z - X[0].z;
     long long bx = X[2].x - X[0].x, by = X[2].y - X[0].y, bz = X[2].z - X[0].z;
@@ -1282,6 +1290,26 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
             prev = cur;
             cur = next(cur);
         }
+    }
+    if constexpr (sizeof(Real) == 4) {
+        // the tail in double-float too (FP32 pipes), one conversion per output
+        const bool neg = acc.s0.hi < 0.0f;
+        const df frac = neg ? df_neg(acc.s0) : acc.s0;
+        const df Sc[3] = {neg ? df_neg(acc.s1) : acc.s1, neg ? df_neg(acc.s2) : acc.s2, neg ? df_neg(acc.s3) : acc.s3};
+        const df vt6 = df_from_i128(tet_det6(L.X));   // 6 vol(t), grid units
+        const double u3 = A.unit * A.unit * A.unit;
+        A.p_vol[p] = df_to_double(df_mul(vt6, frac)) * (u3 / 6.0);
+        const int xs[4][3] = {{L.X[0].x, L.X[0].y, L.X[0].z}, {L.X[1].x, L.X[1].y, L.X[1].z},
+                              {L.X[2].x, L.X[2].y, L.X[2].z}, {L.X[3].x, L.X[3].y, L.X[3].z}};
+        df wc[3];
+        for (int cc = 0; cc < 3; cc++) wc[cc] = df_add(df_mul(O[cc], frac), df_scale(Sc[cc], 0.25f));
+        for (int k = 0; k < 3; k++) {
+            const int x0 = xs[0][k];
+            df m = df_mul(frac, df_from_i64(x0));
+            for (int cc = 1; cc <= 3; cc++) m = df_add(m, df_mul(wc[cc - 1], df_make((float)(xs[cc][k] - x0))));
+            A.p_mom[3 * p + k] = df_to_double(df_mul(vt6, m)) * (u3 * A.unit / 6.0);
+        }
+        return;
     }
     double S[4];
     acc.result(S);
