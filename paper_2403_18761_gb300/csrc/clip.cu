@@ -1047,10 +1047,10 @@ struct Arith<double> {
     static __device__ __forceinline__ double dbl(double v) { return v; }
 };
 
-// frac = volume / vol(t); mom[k] = (first moment / vol(t))_k - frac X0_k, in
-// grid units: sum over corners l of M_l (X_l - X0)_k.
+// fr = volume / vol(t); m[k] = (first moment / vol(t))_k - fr X0_k, in grid
+// units: sum over corners l of M_l (X_l - X0)_k.
 template <typename T>
-__device__ __forceinline__ void one_plane_piece(const long long F[4], const int3* X, double& frac, double mom[3]) {
+__device__ __forceinline__ void one_plane_piece(const long long F[4], const int3* X, T& fr, T m[3]) {
     typedef Arith<T> A;
     const int neg = (F[0] < 0) + (F[1] < 0) + (F[2] < 0) + (F[3] < 0);
     auto cut = [&](int a, int x) {
@@ -1063,12 +1063,11 @@ __device__ __forceinline__ void one_plane_piece(const long long F[4], const int3
         const int v = k == 0 ? p.x - X[0].x : (k == 1 ? p.y - X[0].y : p.z - X[0].z);
         return A::num((float)v);
     };
-    T m[3] = {A::num(0.f), A::num(0.f), A::num(0.f)};
+    for (int k = 0; k < 3; k++) m[k] = A::num(0.f);
     auto acc = [&](T M, int l) {   // mom += M (X_l - X0)
         if (l == 0) return;
         for (int k = 0; k < 3; k++) m[k] = A::add(m[k], A::mul(M, dX(l, k)));
     };
-    T fr;
     if (neg == 1 || neg == 3) {
         // the corner a on the minority side and the tet it cuts off
         const bool want = neg == 1;
@@ -1117,8 +1116,6 @@ __device__ __forceinline__ void one_plane_piece(const long long F[4], const int3
         acc(Mc, c);
         acc(Md, d);
     }
-    frac = A::dbl(fr);
-    for (int k = 0; k < 3; k++) mom[k] = A::dbl(m[k]);
 }
 
 template <typename Real>
@@ -1162,13 +1159,21 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     if (L.n == 2) {   // two candidates (a whole bin): one radical plane, closed form
         long long F[4];
         row_i64(L, A.Ci, A.W, __ffs(pmask) - 1, F);
-        double frac, mom[3];
-        one_plane_piece<T>(F, L.X, frac, mom);
-        const double vt = tet_volume6(L.X) / 6.0;
+        T fr, mom[3];
+        one_plane_piece<T>(F, L.X, fr, mom);
         const double u3 = A.unit * A.unit * A.unit;
-        A.p_vol[p] = vt * frac * u3;
-        const double x0[3] = {(double)L.X[0].x, (double)L.X[0].y, (double)L.X[0].z};
-        for (int k = 0; k < 3; k++) A.p_mom[3 * p + k] = vt * (frac * x0[k] + mom[k]) * u3 * A.unit;
+        const int x0[3] = {L.X[0].x, L.X[0].y, L.X[0].z};
+        if constexpr (sizeof(Real) == 4) {   // double-float to the end, one conversion per output
+            const df vt6 = df_from_i128(tet_det6(L.X));
+            A.p_vol[p] = df_to_double(df_mul(vt6, fr)) * (u3 / 6.0);
+            for (int k = 0; k < 3; k++)
+                A.p_mom[3 * p + k] =
+                    df_to_double(df_mul(vt6, df_add(df_mul(fr, df_from_i64(x0[k])), mom[k]))) * (u3 * A.unit / 6.0);
+        } else {
+            const double vt = tet_volume6(L.X) / 6.0;
+            A.p_vol[p] = vt * fr * u3;
+            for (int k = 0; k < 3; k++) A.p_mom[3 * p + k] = vt * (fr * (double)x0[k] + mom[k]) * u3 * A.unit;
+        }
         return;
     }
     const RowCache RC{L, A.Ci, A.W};
