@@ -445,6 +445,56 @@ def repair_leg(nshapes, stream, dev, seed=20240330):
                                r["plain"]["failing"] == r["learned"]["failing"] for r in shapes)}
 
 
+def medial_envelope_leg(w, precision, kk, stream, dev, steps=3):
+    """The dual medial mesh and its thinning (Sec. 3.2, 5.3) and the
+    geometric check (Sec. 4.3) on the headline workload: a build that also
+    measures the RPE lengths, rpd_medial (sigma 0.1, organic shapes), and the
+    envelope distance of every boundary-triangle centroid to the spheres,
+    cones and slabs.  Device times by CUDA events on the stream; the thinning
+    is a host process (its wall time)."""
+    import torch
+    from paper_2403_18761_gb300 import rpd_build
+    V = torch.as_tensor(w.verts, dtype=torch.float64, device=dev)
+    T = torch.as_tensor(w.tets, dtype=torch.int32, device=dev)
+    C = torch.as_tensor(w.centers, dtype=torch.float64, device=dev)
+    R = torch.as_tensor(w.radii, dtype=torch.float64, device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        ms_len, ms_env, s_thin = [], [], []
+        for it in range(steps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx = rpd_build(V, T, C, R, precision=precision, k=kk, grid_bits=w.grid_bits, stream=stream,
+                            edge_lengths=True)
+            e1.record(stream)
+            e1.synchronize()
+            a = time.perf_counter()
+            info, _, _ = ctx.rpd_medial(0.1)
+            b = time.perf_counter()
+            P, N, F = ctx.rpd_surface_samples()
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            d, prim = ctx.rpd_envelope_distance(P)
+            f1.record(stream)
+            f1.synchronize()
+            if it > 0:
+                ms_len.append(e0.elapsed_time(e1))
+                ms_env.append(f0.elapsed_time(f1))
+                s_thin.append(b - a)
+            nsamp = int(P.shape[0])
+            diag = float(torch.linalg.norm(P.max(dim=0).values - P.min(dim=0).values))
+            dd = d.double() / diag
+            ctx.rpd_destroy()
+    nprim = info["vertices"] + info["edges"] + info["faces"]
+    out["medial"] = {"build_with_edge_lengths_ms": float(np.mean(ms_len)), "thinning_s": float(np.mean(s_thin)),
+                     "sigma": 0.1, "info": info}
+    out["envelope"] = {"samples": nsamp, "primitives": int(nprim), "ms": float(np.mean(ms_env)),
+                       "samples_per_s": nsamp / (float(np.mean(ms_env)) * 1e-3),
+                       "max_distance_over_diagonal": float(dd.max()), "mean_distance_over_diagonal": float(dd.mean())}
+    return out
+
+
 def run_reference(args, w):
     """The reference arm: the CPU oracle (brute force, FP64 + exact predicates)
     as it stands on the host cores, each step a seeded tet sample."""
@@ -491,6 +541,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision (profiling)")
+    ap.add_argument("--no-medial", action="store_true", help="skip the medial-mesh and envelope leg")
     ap.add_argument("--repair-shapes", type=int, default=6,
                     help="genus 0-5 slabs of the repair leg (0 skips it; the full repair workload has 64)")
     ap.add_argument("--batch-shapes", type=int, default=64,
@@ -655,6 +706,11 @@ def main():
             line["batch"] = batch_leg(args.batch_shapes, args.steps, args.warmup, stream, flush, dev)
         except Exception as e:   # reported in the line; the headline stands on its own
             line["batch"] = {"shapes": args.batch_shapes, "error": f"{type(e).__name__}: {e}"}
+    if not args.no_medial:
+        try:
+            line.update(medial_envelope_leg(w, precision, kk, stream, dev))
+        except Exception as e:
+            line["medial"] = {"error": f"{type(e).__name__}: {e}"}
     if args.repair_shapes > 0:
         try:
             line["repair"] = repair_leg(args.repair_shapes, stream, dev)
