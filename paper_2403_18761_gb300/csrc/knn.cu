@@ -894,7 +894,7 @@ __device__ __forceinline__ bool load_tet(const int32_t* __restrict__ T, long lon
 }
 
 // One warp per tet: the gathered spheres live one per lane.
-__global__ void __launch_bounds__(256) k_candidates_warp(
+__global__ void __launch_bounds__(256, 5) k_candidates_warp(
     const int32_t* __restrict__ T, long long nt, long long nv, const int32_t* __restrict__ Xi,
     const int32_t* __restrict__ Ci, const long long* __restrict__ W, const int32_t* __restrict__ knn,
     const long long* __restrict__ dplus, int K, int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand,
