@@ -1117,7 +1117,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
         const GridParams g = gp[shape_of(voff, nshapes, v[0])];
         const int64_t* __restrict__ start = start_all + g.cbase;
         const long long* __restrict__ cwmax = cwmax_all + g.cbase;
-        const int ncell = g.dim.x * g.dim.y * g.dim.z, nxy = g.dim.x * g.dim.y;
+
         int o[4];
         for (int a = 0; a < 4; a++) o[a] = knn[(long long)v[a] * K];
         long long M[4][4];
@@ -1137,10 +1137,29 @@ __global__ void __launch_bounds__(FB_THREADS) k_candidates_fallback(
         for (int a = 0; a < 4; a++) thr[a] = M[a][bstar];
         if (tid == 0) sn = 0;
         __syncthreads();
-        // every grid cell once: opened when some corner a may have a sphere
-        // of it within thr_a (|X_a - cell|^2 - max r^2 of the cell <= thr_a)
-        for (int ci = tid; ci < ncell; ci += FB_THREADS) {
-            const int qz = ci / nxy, rxy = ci - qz * nxy, qy = rxy / g.dim.x, qx = rxy - qy * g.dim.x;
+        // A sphere with pd(X_a) <= thr_a has its centre within
+        // sqrt(thr_a + wmax) of X_a, so only the cells of the box around the
+        // four corners' balls can hold one; each of those cells is opened
+        // when some corner a may have a sphere of it within thr_a
+        // (|X_a - cell|^2 - max r^2 of the cell <= thr_a).
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        for (int a = 0; a < 4; a++) {
+            const long long r2 = thr[a] + g.wmax;
+            const long long rad = r2 > 0 ? (long long)sqrt((double)r2) + 2 : 1;
+            const long long xa[3] = {X[a].x, X[a].y, X[a].z};
+            const int org[3] = {g.org.x, g.org.y, g.org.z}, dim[3] = {g.dim.x, g.dim.y, g.dim.z};
+            for (int k = 0; k < 3; k++) {
+                const long long c0 = (xa[k] - rad - org[k]) / g.cell - 1, c1 = (xa[k] + rad - org[k]) / g.cell + 1;
+                lo[k] = min(lo[k], (int)max(0LL, min(c0, (long long)dim[k] - 1)));
+                hi[k] = max(hi[k], (int)max(0LL, min(c1, (long long)dim[k] - 1)));
+            }
+        }
+        const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, bxy = bx * by;
+        const int nbox = bxy * (hi[2] - lo[2] + 1);
+        for (int bi = tid; bi < nbox; bi += FB_THREADS) {
+            const int bz = bi / bxy, rxy = bi - bz * bxy, byy = rxy / bx, bxx = rxy - byy * bx;
+            const int qx = lo[0] + bxx, qy = lo[1] + byy, qz = lo[2] + bz;
+            const int ci = (qz * g.dim.y + qy) * g.dim.x + qx;
             const long long cw = cwmax[ci];
             bool open = false;
             for (int a = 0; a < 4; a++) open |= box_dist2(X[a], g, qx, qy, qz) - cw <= thr[a];
