@@ -415,6 +415,12 @@ def repair_leg(nshapes, stream, dev, seed=20240330):
         e1.synchronize()
         _, l1 = net.grad(x, t)
     train_ms = e0.elapsed_time(e1)
+    # tensor-core work of training: per row, the three hidden layers'
+    # forward GEMMs (32x128, 128x128, 128x128), their weight gradients (the
+    # same flops) and the input gradients of layers 2 and 1
+    gemm_flop = 3000 * 1024 * 2.0 * (2 * (32 * 128 + 2 * 128 * 128) + 2 * 128 * 128)
+    bf16_peak = measured_peaks().get("bf16_tflops")
+    mlp_tf = gemm_flop / (train_ms * 1e-3) / 1e12
     shapes = []
     for g in range(nshapes):
         w = rpd_inputs.genus_slab(g % 6, seed=seed + 100 + g, h=0.075, ns=256)
@@ -439,6 +445,11 @@ def repair_leg(nshapes, stream, dev, seed=20240330):
     return {"workload": f"{nshapes} genus 0-5 slabs 4x2x1 (~125k tets each), 256 near-medial starting spheres",
             "training": {"pairs": int(x.shape[0]), "steps": 3000, "batch": 1024, "loss_before": l0,
                          "loss_after": l1, "train_ms": train_ms,
+                         "roofline": {"bound": "tensor", "achieved": mlp_tf, "unit": "TFLOP/s",
+                                      "peak": bf16_peak, "frac": (mlp_tf / bf16_peak) if bf16_peak else None,
+                                      "flop": gemm_flop,
+                                      "note": "tcgen05 BF16 GEMMs of 128-row tiles, 15 launches per step; "
+                                              "launch-bound at this batch"},
                          "setup_s": time.perf_counter() - t0},
             "shapes": shapes, "total": tot,
             "same_result": all(r["plain"]["inserted"] == r["learned"]["inserted"] and
