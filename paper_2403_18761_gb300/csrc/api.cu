@@ -1504,7 +1504,7 @@ rpd_status rpd_envelope_distance(rpd_ctx* ctx, const double* d_samples, int64_t 
     }
     const double unit = ldexp(1.0, -ctx->opt.grid_bits);
     const double o[3] = {x0[0] * unit, x0[1] * unit, x0[2] * unit};
-    void* tmp = ctx->alloc<char>(envelope_tmp_bytes(n1 + n2 + n3));
+    void* tmp = ctx->alloc<char>(envelope_tmp_bytes(n1 + n2 + n3, n));
     if (!tmp) return fail(ctx, RPD_E_OOM, "device allocation failed");
     launch_envelope(ctx->fout[0].keys, n1, ctx->fout[1].keys, n2, ctx->fout[2].keys, n3, ctx->Ci, ctx->W, unit, o,
                     d_samples, n, d_dist, d_prim, tmp, &ctx->st->err, ctx->stream);

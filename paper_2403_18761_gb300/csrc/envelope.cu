@@ -163,6 +163,32 @@ __global__ void k_env_prims(const int32_t* __restrict__ k1, long long n1, const 
     idx[i] = (uint32_t)i;
 }
 
+// Morton code of a sample (world coordinates), in the primitives' code space.
+__device__ __forceinline__ unsigned long long spread21(unsigned long long v) {
+    v &= 0x1fffffull;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+}
+
+__global__ void k_env_sample_keys(const double* __restrict__ samples, long long ns, double scale, int3 gmin, int shift,
+                                  uint64_t* __restrict__ morton, uint32_t* __restrict__ idx) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    unsigned long long u[3];
+    const int gm[3] = {gmin.x, gmin.y, gmin.z};
+    for (int a = 0; a < 3; a++) {
+        double g = rint(samples[3 * i + a] * scale);
+        g = fmin(fmax(g, (double)gm[a]), (double)(-gm[a] - 1));   // inside the code's range
+        u[a] = (unsigned long long)(((long long)g - gm[a]) >> shift);
+    }
+    morton[i] = spread21(u[0]) | (spread21(u[1]) << 1) | (spread21(u[2]) << 2);
+    idx[i] = (uint32_t)i;
+}
+
 __global__ void k_env_gather(const Prim* __restrict__ in, const uint32_t* __restrict__ order, long long n,
                              Prim* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,21 +233,45 @@ __global__ void k_env_tiles(const Prim* __restrict__ p, long long n, float4* __r
     }
 }
 
+// One thread per sample, the samples taken in Morton order (sorder) so that a
+// block's samples are close together; the block starts at the tile of
+// primitives whose Morton codes follow its first sample's and alternates
+// outwards (t0, t0 + 1, t0 - 1, ...), so the best distances shrink early and
+// far tiles fail the ball test.
 __global__ void __launch_bounds__(ENV_THREADS) k_env_dist(const double* __restrict__ samples, long long ns, double3 o,
                                                           const Prim* __restrict__ prims, long long np,
-                                                          const float4* __restrict__ tiles, float* __restrict__ dist,
+                                                          const float4* __restrict__ tiles,
+                                                          const uint64_t* __restrict__ pkeys,
+                                                          const uint64_t* __restrict__ skeys,
+                                                          const uint32_t* __restrict__ sorder, float* __restrict__ dist,
                                                           int32_t* __restrict__ arg) {
     __shared__ Prim tile[ENV_TILE];
     __shared__ int skip;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < ns;
+    __shared__ long long t0s;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < ns;
+    const long long i = live ? (long long)sorder[q] : 0;
     const float3 p = live ? make_float3((float)(samples[3 * i] - o.x), (float)(samples[3 * i + 1] - o.y),
                                         (float)(samples[3 * i + 2] - o.z))
                           : make_float3(0, 0, 0);
     float best = INFINITY;
     int bi = -1;
     const long long ntile = (np + ENV_TILE - 1) / ENV_TILE;
-    for (long long t = 0; t < ntile; t++) {
+    if (threadIdx.x == 0) {   // first primitive whose code is >= the block's first sample's
+        const uint64_t key = skeys[(long long)blockIdx.x * blockDim.x];
+        long long lo = 0, hi = np;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (pkeys[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        t0s = lo < np ? lo / ENV_TILE : ntile - 1;
+    }
+    __syncthreads();
+    const long long t0 = t0s;
+    for (long long j = 0; j < 2 * ntile; j++) {
+        const long long t = (j & 1) ? t0 + (j + 1) / 2 : t0 - j / 2;   // t0, t0 + 1, t0 - 1, t0 + 2, ...
+        if (t < 0 || t >= ntile) continue;   // uniform over the block
         // the block skips a tile whose bounding ball is farther from every
         // live sample than that sample's best distance
         const float4 tb = tiles[t];
@@ -259,11 +309,12 @@ __global__ void k_env_unsort(int32_t* __restrict__ arg, long long n, const uint3
 
 }  // namespace
 
-size_t envelope_tmp_bytes(long long np) {
+size_t envelope_tmp_bytes(long long np, long long nsamp) {
     const size_t a = ((size_t)np * sizeof(Prim) + 255) & ~(size_t)255;
     const size_t t = (((size_t)(np + ENV_TILE - 1) / ENV_TILE + 1) * sizeof(float4) + 255) & ~(size_t)255;
     const size_t k = ((size_t)(np + 1) * 8 + 255) & ~(size_t)255, v = ((size_t)(np + 1) * 4 + 255) & ~(size_t)255;
-    return 2 * a + t + 2 * k + 2 * v + radix_tmp_bytes(np);
+    const size_t ks = ((size_t)(nsamp + 1) * 8 + 255) & ~(size_t)255, vs = ((size_t)(nsamp + 1) * 4 + 255) & ~(size_t)255;
+    return 2 * a + t + 2 * k + 2 * v + 2 * ks + 2 * vs + radix_tmp_bytes(np > nsamp ? np : nsamp);
 }
 
 // Primitive table sorted by the Morton code of the primitive's mean centre,
@@ -292,6 +343,15 @@ void launch_envelope(const int32_t* k1, long long n1, const int32_t* k2, long lo
     p += v;
     uint32_t* i1 = (uint32_t*)p;
     p += v;
+    const size_t ks = ((size_t)(nsamp + 1) * 8 + 255) & ~(size_t)255, vs = ((size_t)(nsamp + 1) * 4 + 255) & ~(size_t)255;
+    uint64_t* sk0 = (uint64_t*)p;
+    p += ks;
+    uint64_t* sk1 = (uint64_t*)p;
+    p += ks;
+    uint32_t* so0 = (uint32_t*)p;
+    p += vs;
+    uint32_t* so1 = (uint32_t*)p;
+    p += vs;
     const double3 o = make_double3(o3[0], o3[1], o3[2]);
     // grid coordinates are in (-2^21, 2^21): shifted by 2^21 and halved they fit 21 bits
     const int g0 = -(1 << 21);
@@ -304,7 +364,11 @@ void launch_envelope(const int32_t* k1, long long n1, const int32_t* k2, long lo
     const long long ntile = (np + ENV_TILE - 1) / ENV_TILE;
     k_env_tiles<<<(unsigned)ntile, 128, 0, s>>>(sorted, np, tiles);
     note_launch();
-    k_env_dist<<<nblk(nsamp, ENV_THREADS), ENV_THREADS, 0, s>>>(samples, nsamp, o, sorted, np, tiles, dist, prim_id);
+    k_env_sample_keys<<<nblk(nsamp, 256), 256, 0, s>>>(samples, nsamp, 1.0 / unit, make_int3(g0, g0, g0), 1, sk0, so0);
+    note_launch();
+    radix_sort_pairs(sk0, so0, sk1, so1, nsamp, 63, p, d_err, s);
+    k_env_dist<<<nblk(nsamp, ENV_THREADS), ENV_THREADS, 0, s>>>(samples, nsamp, o, sorted, np, tiles, m1, sk1, so1, dist,
+                                                                  prim_id);
     note_launch();
     k_env_unsort<<<nblk(nsamp, 256), 256, 0, s>>>(prim_id, nsamp, i1);   // sorted positions -> table rows
     note_launch();

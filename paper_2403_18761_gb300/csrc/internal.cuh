@@ -190,8 +190,8 @@ void launch_fixed_to_world(const long long* in, double* out, long long n, double
 // Signed distance (FP32) of samples to the medial mesh's spheres (k1 rows),
 // cones (k2 rows) and slabs (k3 rows), coordinates taken relative to o3;
 // prim_id receives the nearest primitive (row in spheres, cones, slabs order)
-// or -1.  tmp holds envelope_tmp_bytes(n1 + n2 + n3).
-size_t envelope_tmp_bytes(long long np);
+// or -1.  tmp holds envelope_tmp_bytes(n1 + n2 + n3, nsamp).
+size_t envelope_tmp_bytes(long long np, long long nsamp);
 void launch_envelope(const int32_t* k1, long long n1, const int32_t* k2, long long n2, const int32_t* k3, long long n3,
                      const int32_t* Ci, const long long* W, double unit, const double* o3, const double* samples,
                      long long nsamp, float* dist, int32_t* prim_id, void* tmp, int* d_err, cudaStream_t s);
