@@ -26,10 +26,11 @@
 //    centres; it counts when l lies inside the triangle and rho > 0, and the
 //    distance is then v.(s - c_1) - r_1.
 //
-// FP32 arithmetic on coordinates relative to the mesh's bounding-box centre
-// (the distances only decide a threshold); one thread per sample, the
-// primitives staged through shared memory in tiles, tiles skipped when their
-// bounding ball is already farther than the sample's best distance.
+// FP32 arithmetic on coordinates relative to mesh vertex 0 (the distances
+// only decide a threshold); one thread per sample, the samples in Morton
+// order, the Morton-sorted primitives staged through shared memory in tiles,
+// scanned outwards from the block's position and skipped when their bounding
+// ball is already farther than every sample's best distance.
 #include <cuda_runtime.h>
 #include <math.h>
 
