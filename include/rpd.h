@@ -420,9 +420,12 @@ rpd_status rpd_mlp_forward(rpd_mlp* mlp, const float* d_x, int64_t n, float* d_y
 /* Gradient (d_grad f32[37377], may be NULL) of the mean squared error
  * mean((y - t)^2) over the n rows, and the loss on the host; no update. */
 rpd_status rpd_mlp_grad(rpd_mlp* mlp, const float* d_x, const float* d_t, int64_t n, float* d_grad, float* h_loss);
-/* `steps` Adam steps with learning rate lr on consecutive slices of `batch`
- * rows (wrapping around; shuffle the rows beforehand); *h_loss = the last
- * step's loss. */
+/* `steps` Adam steps with learning rate lr on consecutive batches of `batch`
+ * rows (row r of a batch is row (start + r) mod n, each batch starting where
+ * the last ended; shuffle the rows beforehand); *h_loss = the last step's
+ * loss.  The batch rows are chosen on the device, so one step's launches are
+ * captured once as a CUDA graph on the network's private stream and replayed
+ * `steps` times. */
 rpd_status rpd_mlp_train(rpd_mlp* mlp, const float* d_x, const float* d_t, int64_t n, int32_t steps, int32_t batch,
                          float lr, float* h_loss);
 void rpd_mlp_destroy(rpd_mlp* mlp);

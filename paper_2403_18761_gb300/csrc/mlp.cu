@@ -314,6 +314,24 @@ __global__ void k_to_bf16(const float* __restrict__ x, long long n, int n_in, lo
     X[i] = __float2bfloat16(r < n && c < n_in ? x[r * n_in + c] : 0.0f);
 }
 
+// Training batch: row r of the batch is row (cur[0] + r) mod n_total of the
+// data (cur on the device, so every step is the same launch sequence).
+__global__ void k_to_bf16_batch(const float* __restrict__ x, long long n_total, int n_in, long long b, long long cap,
+                                const long long* __restrict__ cur, __nv_bfloat16* __restrict__ X) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap * NIN) return;
+    const long long r = i / NIN;
+    const int c = (int)(i % NIN);
+    const long long src = (cur[0] + r) % n_total;
+    X[i] = __float2bfloat16(r < b && c < n_in ? x[src * n_in + c] : 0.0f);
+}
+
+// After a step: the next batch starts b rows later; one more Adam step.
+__global__ void k_cursor_advance(long long* cur, long long b, long long n_total) {
+    cur[0] = (cur[0] + b) % n_total;
+    cur[1] += 1;
+}
+
 __global__ void k_cast_weights(const float* __restrict__ p, __nv_bfloat16* __restrict__ W0,
                                __nv_bfloat16* __restrict__ W1, __nv_bfloat16* __restrict__ W2) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,7 +347,8 @@ __global__ void k_cast_weights(const float* __restrict__ p, __nv_bfloat16* __res
 // dZ2 = bf16(dy w3 (H2 > 0)), and the head's weight and bias gradients.
 __global__ void k_head(const __nv_bfloat16* __restrict__ H2, long long n, const float* __restrict__ p,
                        float* __restrict__ y, const float* __restrict__ t, __nv_bfloat16* __restrict__ dZ2,
-                       float* __restrict__ g, float* __restrict__ loss) {
+                       float* __restrict__ g, float* __restrict__ loss, const long long* __restrict__ cur,
+                       long long n_total) {
     __shared__ float sw[HID + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = threadIdx.x; k <= HID; k += blockDim.x) sw[k] = 0.0f;
@@ -348,7 +367,7 @@ __global__ void k_head(const __nv_bfloat16* __restrict__ H2, long long n, const 
         const float yr = s + b3;
         if (lane == 0 && y) y[r] = yr;
         if (!t) continue;
-        const float e = yr - t[r];
+        const float e = yr - t[cur ? (cur[0] + r) % n_total : r];
         const float dy = 2.0f * e / (float)n;
         if (lane == 0) {
             lsum += e * e;
@@ -374,11 +393,14 @@ __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dZ, long long n, f
     atomicAdd(&g[off + c], s);
 }
 
-// Adam step on the FP32 master parameters.
+// Adam step on the FP32 master parameters; step number cur[1] + 1 (bias
+// corrections 1 - b^step).
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       long long n, float lr, float b1, float b2, float eps, const long long* __restrict__ cur) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const float step = (float)(cur[1] + 1);
+    const float c1 = 1.0f - powf(b1, step), c2 = 1.0f - powf(b2, step);
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi, vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
@@ -406,6 +428,9 @@ struct rpd_mlp {
     int* err = nullptr;
     float* loss = nullptr;
     long long step = 0;
+    long long* cur = nullptr;          // device: [next batch row, Adam steps taken]
+    cudaStream_t tstream = nullptr;    // private stream the training steps are captured on
+    cudaEvent_t tev[2] = {nullptr, nullptr};
     long long cap = 0;    // rows of the activation buffers (multiple of 128)
     __nv_bfloat16 *X = nullptr, *H0 = nullptr, *H1 = nullptr, *H2 = nullptr, *D2 = nullptr, *D1 = nullptr,
                   *D0 = nullptr;
@@ -451,12 +476,17 @@ rpd_status launch_check(rpd_mlp* q) {
     return e ? (rpd_status)e : RPD_OK;
 }
 
-// Forward through the three hidden layers (tensor cores) and the head.
-void forward(rpd_mlp* q, const float* x, long long n, float* y, const float* t) {
+// Forward through the three hidden layers (tensor cores) and the head.  With
+// n_total > 0 the n rows are the training batch that starts at the device
+// cursor's row of the n_total data rows (x and t are the whole data).
+void forward(rpd_mlp* q, const float* x, long long n, float* y, const float* t, long long n_total = 0) {
     cudaStream_t s = q->stream;
     const unsigned tiles = (unsigned)((n + TM - 1) / TM);
     const size_t sm = tile_smem();
-    k_to_bf16<<<nblk(q->cap * NIN, 256), 256, 0, s>>>(x, n, q->n_in, q->cap, q->X);
+    if (n_total > 0)
+        k_to_bf16_batch<<<nblk(q->cap * NIN, 256), 256, 0, s>>>(x, n_total, q->n_in, n, q->cap, q->cur, q->X);
+    else
+        k_to_bf16<<<nblk(q->cap * NIN, 256), 256, 0, s>>>(x, n, q->n_in, q->cap, q->X);
     note_launch();
     k_mlp_fwd<<<tiles, MLP_THREADS, sm, s>>>(q->X, n, NIN, q->W0(), q->p + OB0, HID, q->H0, q->err);
     k_mlp_fwd<<<tiles, MLP_THREADS, sm, s>>>(q->H0, n, HID, q->W1(), q->p + OB1, HID, q->H1, q->err);
@@ -466,7 +496,8 @@ void forward(rpd_mlp* q, const float* x, long long n, float* y, const float* t) 
         cudaMemsetAsync(q->g, 0, sizeof(float) * NPARAM, s);
         cudaMemsetAsync(q->loss, 0, sizeof(float), s);
     }
-    k_head<<<152 * 4, 256, 0, s>>>(q->H2, n, q->p, y, t, q->D2, q->g, q->loss);
+    k_head<<<152 * 4, 256, 0, s>>>(q->H2, n, q->p, y, t, q->D2, q->g, q->loss, n_total > 0 ? q->cur : nullptr,
+                                   n_total);
     note_launch();
 }
 
@@ -512,7 +543,11 @@ rpd_status rpd_mlp_create(int32_t n_in, uint64_t seed, void* cuda_stream, rpd_ml
          cudaMalloc(&q->m, sizeof(float) * NPARAM) == cudaSuccess &&
          cudaMalloc(&q->v, sizeof(float) * NPARAM) == cudaSuccess &&
          cudaMalloc(&q->Wb, sizeof(__nv_bfloat16) * (HID * NIN + 2 * HID * HID)) == cudaSuccess &&
-         cudaMalloc(&q->err, sizeof(int)) == cudaSuccess && cudaMalloc(&q->loss, sizeof(float)) == cudaSuccess;
+         cudaMalloc(&q->err, sizeof(int)) == cudaSuccess && cudaMalloc(&q->loss, sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&q->cur, 2 * sizeof(long long)) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&q->tstream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&q->tev[0], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&q->tev[1], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         rpd_mlp_destroy(q);
@@ -586,17 +621,47 @@ rpd_status rpd_mlp_train(rpd_mlp* q, const float* d_x, const float* d_t, int64_t
     if (!q || n < 1 || !d_x || !d_t || steps < 0 || batch < 1 || !(lr > 0)) return RPD_E_INVALID;
     const long long b = std::min<long long>(batch, n);
     TRY_M(ensure_acts(q, b));
-    for (int it = 0; it < steps; it++) {
-        // consecutive slices of the (caller-shuffled) data, wrapping around
-        const long long off = ((long long)it * b) % n;
-        const long long m = std::min<long long>(b, n - off);
-        forward(q, d_x + off * q->n_in, m, nullptr, d_t + off);
-        backward(q, m);
-        q->step++;
-        const float c1 = 1.0f - powf(0.9f, (float)q->step), c2 = 1.0f - powf(0.999f, (float)q->step);
-        k_adam<<<nblk(NPARAM, 256), 256, 0, q->stream>>>(q->p, q->g, q->m, q->v, NPARAM, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
-        note_launch();
-        cast_weights(q);
+    if (steps > 0) {
+        // consecutive batches of the (caller-shuffled) data, wrapping around:
+        // batch rows chosen on the device from the cursor, so one step's
+        // launches are captured once as a CUDA graph and replayed
+        const long long c0[2] = {0, q->step};
+        cudaMemcpyAsync(q->cur, c0, sizeof(c0), cudaMemcpyHostToDevice, q->stream);
+        cudaEventRecord(q->tev[0], q->stream);
+        cudaStreamWaitEvent(q->tstream, q->tev[0], 0);
+        cudaStream_t user = q->stream;
+        q->stream = q->tstream;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const long long l0 = rpd_launch_count();
+        bool ok = cudaStreamBeginCapture(q->tstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            forward(q, d_x, b, nullptr, d_t, n);
+            backward(q, b);
+            k_adam<<<nblk(NPARAM, 256), 256, 0, q->tstream>>>(q->p, q->g, q->m, q->v, NPARAM, lr, 0.9f, 0.999f, 1e-8f,
+                                                               q->cur);
+            note_launch();
+            cast_weights(q);
+            k_cursor_advance<<<1, 1, 0, q->tstream>>>(q->cur, b, n);
+            note_launch();
+            ok = cudaStreamEndCapture(q->tstream, &graph) == cudaSuccess && graph;
+        }
+        const long long per_step = rpd_launch_count() - l0;
+        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        for (int it = 0; ok && it < steps; it++) ok = cudaGraphLaunch(exec, q->tstream) == cudaSuccess;
+        if (ok)   // the captured launches ran `steps` times, not once
+            for (long long k = 0; k < per_step * (steps - 1); k++) note_launch();
+        cudaEventRecord(q->tev[1], q->tstream);
+        q->stream = user;
+        cudaStreamWaitEvent(q->stream, q->tev[1], 0);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            cudaStreamSynchronize(q->tstream);
+            return RPD_E_CUDA;
+        }
+        q->step += steps;
     }
     if (h_loss) cudaMemcpyAsync(h_loss, q->loss, sizeof(float), cudaMemcpyDeviceToHost, q->stream);
     return launch_check(q);
@@ -606,8 +671,13 @@ void rpd_mlp_destroy(rpd_mlp* q) {
     if (!q) return;
     if (q->stream) cudaStreamSynchronize(q->stream);
     free_acts(q);
-    for (void* b : {(void*)q->p, (void*)q->g, (void*)q->m, (void*)q->v, (void*)q->Wb, (void*)q->err, (void*)q->loss})
+    if (q->tstream) cudaStreamSynchronize(q->tstream);
+    for (void* b : {(void*)q->p, (void*)q->g, (void*)q->m, (void*)q->v, (void*)q->Wb, (void*)q->err, (void*)q->loss,
+                    (void*)q->cur})
         if (b) cudaFree(b);
+    for (cudaEvent_t e : q->tev)
+        if (e) cudaEventDestroy(e);
+    if (q->tstream) cudaStreamDestroy(q->tstream);
     cudaGetLastError();
     delete q;
 }
