@@ -665,6 +665,23 @@ rpd_status build_rest(rpd_ctx* c, rpd_ctx* old) {
     long long fcap[4] = {npairs, 0, 0, 0};
     TRY(finalize_alloc(c, 1, d_nseg, npairs, &ftmp[0]));
     long long cap[3] = {3 * npairs + 1024, 2 * npairs + 1024, npairs / 2 + 1024};
+    if (!old) {
+        // A face, edge or vertex of the diagram meets a tet in one convex
+        // piece, so a tet with n candidates emits at most C(n,2) RPF, C(n,3)
+        // RPE and C(n,4) RPV records: per pair of a bin whose tets have at
+        // most nb candidates, (nb-1)/2, (nb-1)(nb-2)/6 and (nb-1)(nb-2)(nb-3)/24.
+        // The smaller of that and the default sizes the record and table
+        // buffers (the records of a partial update also hold kept ones).
+        static const int nbmax[RPD_NBINS] = {1, 2, 3, 4, 6, 8, 16, 32};
+        double bound[3] = {0, 0, 0};
+        for (int b = 0; b < RPD_NBINS; b++) {
+            const double n = nbmax[b], p = (double)c->hbin[b];
+            bound[0] += p * (n - 1) / 2;
+            bound[1] += p * (n - 1) * (n - 2) / 6;
+            bound[2] += p * (n - 1) * (n - 2) * (n - 3) / 24;
+        }
+        for (int k = 0; k < 3; k++) cap[k] = std::min(cap[k], (long long)ceil(bound[k]) + 1024);
+    }
     if (const char* e = getenv("RPD_RECORD_CAP")) {   // test hook: small first capacities force a rebuild
         const long long v = atoll(e);
         if (v > 0)
