@@ -240,7 +240,8 @@ def batch_shapes(n: int = 32, seed: int = BASE_SEED + 5, tmin: int = 1000, tmax:
         kind = i % 3
         if kind == 0:
             R, r = 1.0, rng.uniform(0.3, 0.45)
-            h = (6.0 * 2 * np.pi ** 2 * R * r * r / nt) ** (1.0 / 3.0)
+            # at least 2.5 lattice cells across the tube, or the hole is lost
+            h = min((6.0 * 2 * np.pi ** 2 * R * r * r / nt) ** (1.0 / 3.0), r / 2.5)
             # core-circle spheres at most ~4 per tet length along the core,
             # so a tet meets at most a few dozen cells
             ns = min(ns, max(smin, int(4 * 2 * np.pi * R / h)))
