@@ -493,10 +493,10 @@ int64_t rpd_launch_count(void);
  *   d_keys  i32[n*kind], d_chi i32[n]: caller-owned outputs, cap >= n; both
  *           NULL only sets *n
  *   n       host pointer, receives the number of elements
- * The first call on a device looks up the array's device address and caches
- * it for the rest of the process: do not use the entry point again on a
- * device after cudaDeviceReset there.  Every call reuses the same array (it is cleared as
- * needed), so calls that overlap on the GPU race: serialise them.
+ * Every call looks up the array's device address on the current device
+ * (host-side, no device work), so a context re-created after
+ * cudaDeviceReset is served too.  Every call reuses the same array (it is
+ * cleared as needed), so calls that overlap on the GPU race: serialise them.
  * Synchronises the stream three times (sizes of the later stages are read on
  * the host).  Errors are reported by status only (RPD_E_INVALID for bad
  * arguments or cap < n; RPD_E_OVERFLOW when the problem needs more than the

@@ -13,18 +13,16 @@
 // fit are rejected with RPD_E_OVERFLOW before the stage that would need more.
 //
 // In host code `g_scratch` only names the symbol; its device address is
-// looked up with cudaGetSymbolAddress once per device (the first call on a
-// device) and cached for the life of the process: after cudaDeviceReset on that device the
-// cached address is stale, so the entry point must not be used again in that
-// process.  The call synchronises its stream three times (the sizes of the
-// later stages are read on the host).  All calls
+// looked up with cudaGetSymbolAddress at every call (a host-side lookup with
+// no device work), so a module reloaded after cudaDeviceReset is seen.  The
+// call synchronises its stream three times (the sizes of the later stages are
+// read on the host).  All calls
 // share the array and it keeps the previous call's contents, so every buffer
 // that must start at zero is cleared here, and calls that overlap on the GPU
 // (other streams or host threads) race with each other.
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include <mutex>
 
 #include "internal.cuh"
 #include "prim.cuh"
@@ -36,24 +34,12 @@ static __device__ __align__(256) unsigned char g_scratch[RPD_STATIC_SCRATCH_BYTE
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device (set-up once).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
