@@ -17,6 +17,7 @@
 // neighbour); a pin is the centroid of such a triangle, its normal points
 // into the tet.  Which component a piece belongs to is read from the
 // union-find parents the finalisation left for that element kind.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -323,27 +324,42 @@ __device__ __forceinline__ void nearest_on_triangle(const double* T, const doubl
 
 constexpr int SHRINK_THREADS = 256;
 constexpr int SHRINK_ITERS = 100;
+constexpr int SHRINK_CLUSTER = 8;   // CTAs per pin (a portable cluster size)
 
-// One block per pin: sphere shrinking against all boundary triangles except
-// the pin's own.  Output centre and radius (NaN for a pin row without a face).
-__global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restrict__ tri, long long ntri,
-                                                           const int32_t* __restrict__ face_of,
-                                                           const double* __restrict__ pins,
-                                                           const double* __restrict__ normals,
-                                                           const int32_t* __restrict__ faces, double r0,
-                                                           const double* __restrict__ r_start,
-                                                           double* __restrict__ centres, double* __restrict__ radii,
-                                                           int32_t* __restrict__ iters,
-                                                           int32_t* __restrict__ restarted) {
+// (distance, triangle) pairs ordered by distance, then by the lower index; a
+// pair with no triangle (-1) loses every tie.
+__device__ __forceinline__ bool closer(double d, long long k, double bd, long long bk) {
+    return d < bd || (d == bd && k >= 0 && (bk < 0 || k < bk));
+}
+
+// Sphere shrinking against all boundary triangles except the pin's own, one
+// thread-block cluster of SHRINK_CLUSTER CTAs per pin.  Each CTA scans one
+// contiguous part of the triangles for the one nearest to the current centre;
+// the parts' results meet through distributed shared memory after a cluster
+// barrier, and every CTA takes the same (distance, lowest index) minimum over
+// them in rank order, so all CTAs follow the same radii and leave the loop
+// together.  The minimum does not depend on how the triangles are split, so
+// the result equals that of a single block scanning them all.  Output centre
+// and radius (NaN for a pin row without a face).
+__global__ void __cluster_dims__(SHRINK_CLUSTER, 1, 1) __launch_bounds__(SHRINK_THREADS)
+    k_shrink(const double* __restrict__ tri, long long ntri, const int32_t* __restrict__ face_of,
+             const double* __restrict__ pins, const double* __restrict__ normals, const int32_t* __restrict__ faces,
+             double r0, const double* __restrict__ r_start, double* __restrict__ centres, double* __restrict__ radii,
+             int32_t* __restrict__ iters, int32_t* __restrict__ restarted) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     __shared__ double sd[SHRINK_THREADS / 32];
     __shared__ long long si[SHRINK_THREADS / 32];
+    __shared__ double part_d[2];        // this CTA's nearest triangle, by iteration parity
+    __shared__ long long part_k[2];
     __shared__ double sr;
     __shared__ int sdone, swarm;
-    const long long j = blockIdx.x;
+    const unsigned rank = cluster.block_rank();
+    const long long j = blockIdx.x / SHRINK_CLUSTER;   // the cluster's pin (uniform over the cluster)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int own = faces[j];
-    if (own < 0) {
-        if (tid == 0) {
+    if (own < 0) {   // every CTA of the cluster leaves here, before any cluster barrier
+        if (rank == 0 && tid == 0) {
             for (int k = 0; k < 3; k++) centres[3 * j + k] = nan("");
             radii[j] = nan("");
             iters[j] = 0;
@@ -351,8 +367,11 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
         }
         return;
     }
+    const long long per = (ntri + SHRINK_CLUSTER - 1) / SHRINK_CLUSTER;
+    const long long lo = per * rank, hi = lo + per < ntri ? lo + per : ntri;
     const double p[3] = {pins[3 * j], pins[3 * j + 1], pins[3 * j + 2]};
     const double n[3] = {normals[3 * j], normals[3 * j + 1], normals[3 * j + 2]};
+    int rs_flag = 0;
     if (tid == 0) {
         // a proposed first radius (0 < r < r0) replaces r0; the first ball
         // must then contain a surface point, otherwise it may lie below the
@@ -361,7 +380,6 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
         swarm = rs > 0.0 && rs < r0;
         sr = swarm ? rs : r0;
         sdone = 0;
-        if (restarted) restarted[j] = 0;
     }
     __syncthreads();
     int it = 0;
@@ -370,7 +388,7 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
         const double c[3] = {p[0] + r * n[0], p[1] + r * n[1], p[2] + r * n[2]};
         double bd = INFINITY;
         long long bi = -1;
-        for (long long k = tid; k < ntri; k += SHRINK_THREADS) {
+        for (long long k = lo + tid; k < hi; k += SHRINK_THREADS) {
             if (face_of[k] == own) continue;
             double q[3];
             nearest_on_triangle(tri + 9 * k, c, q);
@@ -383,7 +401,7 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
         for (int off = 16; off; off >>= 1) {
             const double od = __shfl_down_sync(0xffffffffu, bd, off);
             const long long oi = __shfl_down_sync(0xffffffffu, bi, off);
-            if (od < bd || (od == bd && oi >= 0 && (bi < 0 || oi < bi))) {
+            if (closer(od, oi, bd, bi)) {
                 bd = od;
                 bi = oi;
             }
@@ -393,19 +411,40 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
             si[w] = bi;
         }
         __syncthreads();
+        const int par = it & 1;
         if (tid == 0) {
             double d = INFINITY;
             long long k = -1;
             for (int z = 0; z < SHRINK_THREADS / 32; z++)
-                if (sd[z] < d || (sd[z] == d && si[z] >= 0 && (k < 0 || si[z] < k))) {
+                if (closer(sd[z], si[z], d, k)) {
                     d = sd[z];
                     k = si[z];
                 }
+            part_d[par] = d;
+            part_k[par] = k;
+        }
+        // the parts of this iteration are visible cluster-wide after the
+        // barrier; a part slot is written again two iterations later, after
+        // the next barrier, which every CTA reaches only once it has read it
+        cluster.sync();
+        if (tid == 0) {
+            double d = INFINITY;
+            long long k = -1;
+            for (unsigned z = 0; z < SHRINK_CLUSTER; z++) {
+                const double* pd = cluster.map_shared_rank(&part_d[par], z);
+                const long long* pk = cluster.map_shared_rank(&part_k[par], z);
+                const double od = *pd;
+                const long long ok = *pk;
+                if (closer(od, ok, d, k)) {
+                    d = od;
+                    k = ok;
+                }
+            }
             // empty ball (within rounding): done, unless it is a proposed one
             if (k < 0 || sqrt(d) >= r * (1.0 - 1e-12)) {
                 if (swarm) {
                     sr = r0;
-                    if (restarted) restarted[j] = 1;
+                    rs_flag = 1;
                 } else {
                     sdone = 1;
                 }
@@ -423,11 +462,14 @@ __global__ void __launch_bounds__(SHRINK_THREADS) k_shrink(const double* __restr
         __syncthreads();
         if (sdone) break;
     }
-    if (tid == 0) {
+    // peers may still be reading this CTA's parts: leave together
+    cluster.sync();
+    if (rank == 0 && tid == 0) {
         const double r = sr;
         for (int k = 0; k < 3; k++) centres[3 * j + k] = p[k] + r * n[k];
         radii[j] = r;
         iters[j] = it + 1;
+        if (restarted) restarted[j] = rs_flag;
     }
 }
 
@@ -602,10 +644,14 @@ void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t
 void launch_shrink(const double* tri, long long ntri, const int32_t* face_of, const double* pins,
                    const double* normals, const int32_t* faces, long long n, double r0, const double* r_start,
                    double* centres, double* radii, int32_t* iters, int32_t* restarted, cudaStream_t s) {
-    if (n <= 0) return;
-    k_shrink<<<(unsigned)n, SHRINK_THREADS, 0, s>>>(tri, ntri, face_of, pins, normals, faces, r0, r_start, centres,
-                                                     radii, iters, restarted);
-    note_launch();
+    // one cluster per pin, in launches of at most 2^24 pins (grid x < 2^31)
+    for (long long b = 0; b < n; b += (1ll << 24)) {
+        const long long m = n - b < (1ll << 24) ? n - b : (1ll << 24);
+        k_shrink<<<(unsigned)(m * SHRINK_CLUSTER), SHRINK_THREADS, 0, s>>>(
+            tri, ntri, face_of, pins + 3 * b, normals + 3 * b, faces + b, r0, r_start ? r_start + b : nullptr,
+            centres + 3 * b, radii + b, iters + b, restarted ? restarted + b : nullptr);
+        note_launch();
+    }
 }
 
 // ----------------------------------------------------- proposer features
