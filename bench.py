@@ -442,22 +442,7 @@ def repair_leg(nshapes, stream, dev, seed=20240330):
             row[mode] = {"ms": (b - a) * 1e3, "rounds": rounds, "inserted": inserted, "failing": failing,
                          "shrink_pins": pins, "shrink_iters": iters, "rejected": rej}
         shapes.append(row)
-    modes = ("plain", "learned")
-    keys = ("ms", "rounds", "inserted", "failing", "shrink_pins", "shrink_iters", "rejected")
-
-    def total(rows):
-        return {m: {k: sum(r[m][k] for r in rows) for k in keys} for m in modes}
-
-    # shapes that both arms brought to all-contractible, and the others
-    done = [r for r in shapes if r["plain"]["failing"] == 0 and r["learned"]["failing"] == 0]
-    stalled = [dict(r, index=i) for i, r in enumerate(shapes)
-               if r["plain"]["failing"] or r["learned"]["failing"]]
-    by_genus = {}
-    for g in sorted({r["genus"] for r in shapes}):
-        rows = [r for r in shapes if r["genus"] == g]
-        by_genus[str(g)] = dict(total(rows), shapes=len(rows),
-                                repaired=sum(1 for r in rows if r["plain"]["failing"] == 0),
-                                needed_repair=sum(1 for r in rows if r["plain"]["rounds"] > 0))
+    summary = repair_summary(shapes)
     return {"workload": f"{nshapes} genus 0-5 slabs 4x2x1 (~125k tets each), 256 near-medial starting spheres",
             "training": {"pairs": int(x.shape[0]), "steps": TRAIN_STEPS, "batch": TRAIN_BATCH, "loss_before": l0,
                          "loss_after": l1, "train_ms": train_ms,
@@ -467,7 +452,29 @@ def repair_leg(nshapes, stream, dev, seed=20240330):
                                       "note": "tcgen05 BF16 GEMMs of 128-row tiles (one CTA each), 15 kernels "
                                               "per step replayed from a CUDA graph; latency-bound at this batch"},
                          "setup_s": time.perf_counter() - t0},
-            "shapes": len(shapes), "repaired": len(done), "by_genus": by_genus,
+            **summary}
+
+
+def repair_summary(shapes):
+    """Per-shape repair rows ({"genus", "tets", "plain": {...}, "learned":
+    {...}}) summed: over the shapes both arms brought to all-contractible,
+    over all, and per genus; the shapes left with failing elements listed."""
+    modes = ("plain", "learned")
+    keys = ("ms", "rounds", "inserted", "failing", "shrink_pins", "shrink_iters", "rejected")
+
+    def total(rows):
+        return {m: {k: sum(r[m][k] for r in rows) for k in keys} for m in modes}
+
+    done = [r for r in shapes if r["plain"]["failing"] == 0 and r["learned"]["failing"] == 0]
+    stalled = [dict(r, index=i) for i, r in enumerate(shapes)
+               if r["plain"]["failing"] or r["learned"]["failing"]]
+    by_genus = {}
+    for g in sorted({r["genus"] for r in shapes}):
+        rows = [r for r in shapes if r["genus"] == g]
+        by_genus[str(g)] = dict(total(rows), shapes=len(rows),
+                                repaired=sum(1 for r in rows if r["plain"]["failing"] == 0),
+                                needed_repair=sum(1 for r in rows if r["plain"]["rounds"] > 0))
+    return {"shapes": len(shapes), "repaired": len(done), "by_genus": by_genus,
             "total_repaired": total(done), "total": total(shapes), "stalled": stalled,
             "same_result": all(r["plain"]["inserted"] == r["learned"]["inserted"] and
                                r["plain"]["failing"] == r["learned"]["failing"] for r in shapes)}

@@ -56,3 +56,29 @@ def test_cpu_samples_cover_every_workload():
     for name in bench.WORKLOADS:
         c = bench.CPU_SAMPLES[name]
         assert c["oracle"] >= 1 and c["oracle_1t"] >= 1 and 0 < c["fair"] <= 1 and c["ref"] >= 1
+
+
+def _row(genus, plain, learned):
+    def arm(ms, rounds, inserted, failing, iters, rej):
+        return {"ms": ms, "rounds": rounds, "inserted": inserted, "failing": failing, "shrink_pins": inserted,
+                "shrink_iters": iters, "rejected": rej}
+    return {"genus": genus, "tets": 1000, "plain": arm(*plain), "learned": arm(*learned)}
+
+
+def test_repair_summary_splits_repaired_and_stalled_shapes():
+    rows = [_row(0, (1.0, 0, 0, 0, 0, 0), (0.5, 0, 0, 0, 0, 0)),
+            _row(1, (4.0, 2, 3, 0, 30, 0), (3.0, 2, 3, 0, 20, 1)),
+            _row(1, (9.0, 5, 7, 4, 70, 0), (8.0, 5, 7, 4, 50, 2)),
+            _row(0, (2.0, 1, 1, 0, 10, 0), (2.5, 1, 1, 0, 6, 0))]
+    s = bench.repair_summary(rows)
+    assert s["shapes"] == 4 and s["repaired"] == 3 and s["same_result"]
+    assert [r["index"] for r in s["stalled"]] == [2]
+    assert s["total_repaired"]["plain"]["ms"] == 7.0 and s["total_repaired"]["learned"]["shrink_iters"] == 26
+    assert s["total"]["plain"]["failing"] == 4 and s["total"]["learned"]["rejected"] == 3
+    g0, g1 = s["by_genus"]["0"], s["by_genus"]["1"]
+    assert (g0["shapes"], g0["repaired"], g0["needed_repair"]) == (2, 2, 1)
+    assert (g1["shapes"], g1["repaired"], g1["needed_repair"]) == (2, 1, 2)
+    assert g1["plain"]["inserted"] == 10
+    # arms that end differently on some shape are flagged
+    rows[1]["learned"]["inserted"] = 4
+    assert not bench.repair_summary(rows)["same_result"]
