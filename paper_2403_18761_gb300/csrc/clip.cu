@@ -1131,7 +1131,6 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
     const long long n = (long long)*A.qcount;
     if (q >= n || q >= A.qcap) return;
     const long long p = A.qpair[q];
-    const int nslot = A.qnv[q];
     Lane L;
     L.t = A.pair_tet[p];
     L.si = (int)(p - A.pair_off[L.t]);
@@ -1144,21 +1143,11 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
         L.X[k] = ld_int3(A.Xi, A.tets[4 * L.t + k]);
         L.di[k] = pd_exact(L.X[k], ci, wi);
     }
-    int apex = -1;
-    unsigned pmask = 0;   // candidate slots whose radical planes the piece's vertices lie on
-    for (int v = 0; v < nslot; v++) {
-        const uint32_t tw = A.qtrip[(2LL * v) * A.qcap + q];
-        V.w(v, 0) = tw;
-        V.w(v, 1) = A.qtrip[(2LL * v + 1) * A.qcap + q];
-        if (is_dead(tw)) continue;
-        if (apex < 0) apex = v;
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            if (tb(tw, k) >= 4) pmask |= 1u << (tb(tw, k) - 4);
-    }
     if (L.n == 2) {   // two candidates (a whole bin): one radical plane, closed form
+        // the only plane that can cut the piece is the other candidate's, so
+        // the queued polytope is not read
         long long F[4];
-        row_i64(L, A.Ci, A.W, __ffs(pmask) - 1, F);
+        row_i64(L, A.Ci, A.W, 1 - L.si, F);
         T fr, mom[3];
         one_plane_piece<T>(F, L.X, fr, mom);
         const double u3 = A.unit * A.unit * A.unit;
@@ -1175,6 +1164,14 @@ __global__ void __launch_bounds__(128) k_volume(ClipArgs A, int vmax, int rmax) 
             for (int k = 0; k < 3; k++) A.p_mom[3 * p + k] = vt * (fr * (double)x0[k] + mom[k]) * u3 * A.unit;
         }
         return;
+    }
+    const int nslot = A.qnv[q];
+    int apex = -1;
+    for (int v = 0; v < nslot; v++) {
+        const uint32_t tw = A.qtrip[(2LL * v) * A.qcap + q];
+        V.w(v, 0) = tw;
+        V.w(v, 1) = A.qtrip[(2LL * v + 1) * A.qcap + q];
+        if (apex < 0 && !is_dead(tw)) apex = v;
     }
     const RowCache RC{L, A.Ci, A.W};
     // chart coordinates relative to the apex vertex
