@@ -149,6 +149,7 @@ struct rpd_ctx {
     // boundary triangles of the mesh for sphere shrinking (built on first use)
     double* btri = nullptr;
     int32_t* btri_face = nullptr;
+    float4* btri_ball = nullptr;   // FP32 bounding balls of the boundary triangles
     long long nbtri = -1;
     // batches (rpd_build_batch): shape offsets of vertices, tets and spheres
     // (device copies and the host's), and the largest per-shape grid
@@ -1118,11 +1119,14 @@ static rpd_status ensure_boundary(rpd_ctx* c, double** tri, int32_t** face_of) {
         }
         double* t = c->alloc<double>(9 * nb + 9);
         int32_t* f = c->alloc<int32_t>(nb + 1);
-        if (!t || !f) return fail(c, RPD_E_OOM, "device allocation failed");
+        float4* b = c->alloc<float4>(nb + 1);
+        if (!t || !f || !b) return fail(c, RPD_E_OOM, "device allocation failed");
         launch_boundary_fill(c->tets, c->adj, c->Xi, c->nt, pos, ldexp(1.0, -c->opt.grid_bits), t, f, s);
+        launch_boundary_spheres(t, nb, b, s);
         TRY(cuda_check(c, "boundary launch"));
         c->btri = t;
         c->btri_face = f;
+        c->btri_ball = b;
         c->nbtri = nb;
     }
     *tri = c->btri;
@@ -1143,8 +1147,8 @@ rpd_status rpd_shrink(rpd_ctx* ctx, const double* d_pins, const double* d_normal
     TRY(ensure_boundary(ctx, &tri, &face_of));
     // a first radius above twice any diameter the grid allows
     const double r0 = ldexp(1.0, 23 - ctx->opt.grid_bits);
-    launch_shrink(tri, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, nullptr, d_centers, d_radii, d_iters,
-                  nullptr, ctx->stream);
+    launch_shrink(tri, ctx->btri_ball, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, nullptr, d_centers,
+                  d_radii, d_iters, nullptr, ctx->stream);
     return cuda_check(ctx, "shrink launch");
 }
 
@@ -1161,8 +1165,8 @@ rpd_status rpd_shrink_warm(rpd_ctx* ctx, const double* d_pins, const double* d_n
     int32_t* face_of = nullptr;
     TRY(ensure_boundary(ctx, &tri, &face_of));
     const double r0 = ldexp(1.0, 23 - ctx->opt.grid_bits);
-    launch_shrink(tri, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, d_r_start, d_centers, d_radii, d_iters,
-                  d_restarted, ctx->stream);
+    launch_shrink(tri, ctx->btri_ball, ctx->nbtri, face_of, d_pins, d_normals, d_faces, n, r0, d_r_start, d_centers,
+                  d_radii, d_iters, d_restarted, ctx->stream);
     return cuda_check(ctx, "shrink launch");
 }
 

@@ -220,7 +220,10 @@ void launch_batch_cut_pieces(const int64_t* pair_off, const int64_t* piece_off, 
 // Sphere shrinking from n pins against the boundary triangles; r_start
 // (NULL or per pin, 0 = plain) proposes the first radius, restarted (NULL or
 // per pin) flags proposals that were rejected.
-void launch_shrink(const double* tri, long long ntri, const int32_t* face_of, const double* pins,
+// FP32 bounding balls (centre, radius) of the boundary triangles, for the
+// shrinking's cull.
+void launch_boundary_spheres(const double* tri, long long n, float4* bs, cudaStream_t s);
+void launch_shrink(const double* tri, const float4* bs, long long ntri, const int32_t* face_of, const double* pins,
                    const double* normals, const int32_t* faces, long long n, double r0, const double* r_start,
                    double* centres, double* radii, int32_t* iters, int32_t* restarted, cudaStream_t s);
 // Learned proposer glue: pin features (and log2(r / diag) targets), the

@@ -265,6 +265,27 @@ __global__ void k_not_flag(const uint8_t* __restrict__ flag, long long n, uint8_
     if (i < n) out[i] = flag[i] ? 0 : 1;
 }
 
+// Bounding ball of each boundary triangle for the shrinking's cull: the
+// centroid rounded to FP32, and a radius, measured in FP64 from that rounded
+// centre to the corners, rounded up to FP32 with a 2^-20 relative margin.
+__global__ void k_bnd_spheres(const double* __restrict__ tri, long long n, float4* __restrict__ bs) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* T = tri + 9 * i;
+    float g[3];
+    for (int k = 0; k < 3; k++) g[k] = (float)((T[k] + T[3 + k] + T[6 + k]) / 3.0);
+    double r = 0.0;
+    for (int v = 0; v < 3; v++) {
+        double d2 = 0.0;
+        for (int k = 0; k < 3; k++) {
+            const double d = T[3 * v + k] - (double)g[k];
+            d2 += d * d;
+        }
+        r = fmax(r, sqrt(d2));
+    }
+    bs[i] = make_float4(g[0], g[1], g[2], __double2float_ru(r * (1.0 + 0x1p-20)));
+}
+
 // ------------------------------------------------------------ shrinking
 // Nearest point q to x on triangle (A, B, C).  With e1 = B - A, e2 = C - A
 // the projection of x onto the triangle's plane is A + s e1 + t e2, where
@@ -339,11 +360,20 @@ __device__ __forceinline__ bool closer(double d, long long k, double bd, long lo
 // barrier, and every CTA takes the same (distance, lowest index) minimum over
 // them in rank order, so all CTAs follow the same radii and leave the loop
 // together.  The minimum does not depend on how the triangles are split, so
-// the result equals that of a single block scanning them all.  Output centre
-// and radius (NaN for a pin row without a face).
+// the result equals that of a single block scanning them all.
+//
+// Cull: a triangle whose bounding ball lies farther from the centre than the
+// current radius r cannot be the nearest one, nor tie with it: the nearest
+// one of a non-empty ball is within r, and an empty ball ends the shrinking
+// whichever triangle is nearest.  The test runs in FP32 on the rounded centre
+// with margins (2^-18 of the distance and 3 x 2^-18 of the centre's largest
+// coordinate) far above the FP32 rounding of the test, so it never culls a
+// triangle within r; only the triangles left are tested in FP64, and the
+// result is that of testing them all.  Output centre and radius (NaN for a
+// pin row without a face).
 __global__ void __cluster_dims__(SHRINK_CLUSTER, 1, 1) __launch_bounds__(SHRINK_THREADS)
-    k_shrink(const double* __restrict__ tri, long long ntri, const int32_t* __restrict__ face_of,
-             const double* __restrict__ pins, const double* __restrict__ normals, const int32_t* __restrict__ faces,
+    k_shrink(const double* __restrict__ tri, const float4* __restrict__ bs, long long ntri,
+             const int32_t* __restrict__ face_of, const double* __restrict__ pins, const double* __restrict__ normals, const int32_t* __restrict__ faces,
              double r0, const double* __restrict__ r_start, double* __restrict__ centres, double* __restrict__ radii,
              int32_t* __restrict__ iters, int32_t* __restrict__ restarted) {
     namespace cg = cooperative_groups;
@@ -386,9 +416,16 @@ __global__ void __cluster_dims__(SHRINK_CLUSTER, 1, 1) __launch_bounds__(SHRINK_
     for (; it < SHRINK_ITERS; it++) {
         const double r = sr;
         const double c[3] = {p[0] + r * n[0], p[1] + r * n[1], p[2] + r * n[2]};
+        const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]};
+        const float cslack = 3.0f * 0x1p-18f * fmaxf(fabsf(cf[0]), fmaxf(fabsf(cf[1]), fabsf(cf[2])));
+        const float uf = __double2float_ru(r * (1.0 + 0x1p-20));
         double bd = INFINITY;
         long long bi = -1;
         for (long long k = lo + tid; k < hi; k += SHRINK_THREADS) {
+            const float4 b = bs[k];
+            const float dx = cf[0] - b.x, dy = cf[1] - b.y, dz = cf[2] - b.z;
+            const float lb = sqrtf(dx * dx + dy * dy + dz * dz) * (1.0f - 0x1p-18f) - b.w - cslack;
+            if (lb > uf) continue;   // the whole triangle lies farther than r
             if (face_of[k] == own) continue;
             double q[3];
             nearest_on_triangle(tri + 9 * k, c, q);
@@ -641,14 +678,20 @@ void launch_pins(const ClipArgs& a, int kind, const int32_t* keys, const int32_t
     note_launch();
 }
 
-void launch_shrink(const double* tri, long long ntri, const int32_t* face_of, const double* pins,
+void launch_boundary_spheres(const double* tri, long long n, float4* bs, cudaStream_t s) {
+    if (n <= 0) return;
+    k_bnd_spheres<<<nblk(n, 256), 256, 0, s>>>(tri, n, bs);
+    note_launch();
+}
+
+void launch_shrink(const double* tri, const float4* bs, long long ntri, const int32_t* face_of, const double* pins,
                    const double* normals, const int32_t* faces, long long n, double r0, const double* r_start,
                    double* centres, double* radii, int32_t* iters, int32_t* restarted, cudaStream_t s) {
     // one cluster per pin, in launches of at most 2^24 pins (grid x < 2^31)
     for (long long b = 0; b < n; b += (1ll << 24)) {
         const long long m = n - b < (1ll << 24) ? n - b : (1ll << 24);
         k_shrink<<<(unsigned)(m * SHRINK_CLUSTER), SHRINK_THREADS, 0, s>>>(
-            tri, ntri, face_of, pins + 3 * b, normals + 3 * b, faces + b, r0, r_start ? r_start + b : nullptr,
+            tri, bs, ntri, face_of, pins + 3 * b, normals + 3 * b, faces + b, r0, r_start ? r_start + b : nullptr,
             centres + 3 * b, radii + b, iters + b, restarted ? restarted + b : nullptr);
         note_launch();
     }
