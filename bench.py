@@ -736,17 +736,18 @@ def main():
     stage64 = ostage if precision == "fp32" else stage
     line["roofline"] = clip_roofline(stage, kk, args.config, precision, peaks, peaks["hbm_gbs"],
                                      stage64=stage64 if stage64 else None)
-    if args.batch_shapes > 0:
+    # the legs below are reported by rank 0 alone, so only rank 0 runs them
+    if args.batch_shapes > 0 and rank == 0:
         try:
             line["batch"] = batch_leg(args.batch_shapes, args.steps, args.warmup, stream, flush, dev)
         except Exception as e:   # reported in the line; the headline stands on its own
             line["batch"] = {"shapes": args.batch_shapes, "error": f"{type(e).__name__}: {e}"}
-    if not args.no_medial:
+    if not args.no_medial and rank == 0:
         try:
             line.update(medial_envelope_leg(w, precision, kk, stream, dev))
         except Exception as e:
             line["medial"] = {"error": f"{type(e).__name__}: {e}"}
-    if args.repair_shapes > 0:
+    if args.repair_shapes > 0 and rank == 0:
         try:
             line["repair"] = repair_leg(args.repair_shapes, stream, dev)
         except Exception as e:
